@@ -1,0 +1,73 @@
+"""Synthetic workloads: sizes, seeds and seeded input draws (no arithmetic of the method).
+
+The paper's experiments (Sec. 5) use synthetic data: a true parameter drawn from
+the prior and observations of its forward response plus Gaussian noise. The
+workloads below fix the shapes of those experiments for this library: level
+hierarchy, KL truncation, observation grid, particle count and Markov steps.
+This module only draws seeded standard-normal inputs and lists coordinates; the
+data vector y itself is produced by solving the forward problem, which is not
+done here.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    inv_h: tuple            # level hierarchy, 1/h per level, coarse to fine
+    inv_h_data: int         # mesh used to synthesise y (finer than every level)
+    K: int                  # KL terms (N_sto)
+    corr_len: float         # correlation length of the exponential covariance
+    obs_per_side: int       # observation grid: points (i/(n+1), j/(n+1)), i, j = 1..n
+    J: int                  # particles
+    n_mcmc: int             # pCN steps per update
+    s_pcn: float = 0.2
+    tau_star: float = 1.0
+    J_tilde: int = 100
+    variance: float = 1.0
+    seed_true: int = 1
+    seed_noise: int = 2
+    seed_sampler: int = 3
+    precision: str = "fp64"   # "fp64" or "mixed"
+    noise_frac: float = 0.01  # sigma = noise_frac * max |p_data|
+
+    @property
+    def n_obs(self):
+        return self.obs_per_side ** 2
+
+
+WORKLOADS = {
+    # single-level SMC, plain FP64, h = 1/16
+    "smc_fp64_h16": Workload("smc_fp64_h16", (16,), 64, 16, 0.3, 7, 1000, 5,
+                             seed_true=1, seed_noise=2, seed_sampler=3, precision="fp64"),
+    # MLS^2MC, 4 levels h = 1/8 .. 1/64, K = 32, J = 4000, mixed precision
+    "mls2mc_mixed_h8_64": Workload("mls2mc_mixed_h8_64", (8, 16, 32, 64), 256, 32, 0.1, 7,
+                                   4000, 5, seed_true=11, seed_noise=12, seed_sampler=13,
+                                   precision="mixed"),
+}
+
+
+def obs_grid(n):
+    """Points (i/(n+1), j/(n+1)) for i, j = 1..n, row-major in j. n = 7 gives (i/8, j/8)."""
+    pts = [((i + 1) / (n + 1), (j + 1) / (n + 1)) for j in range(n) for i in range(n)]
+    return np.array(pts, dtype=np.float64)
+
+
+def standard_normals(shape, seed):
+    """Seeded N(0, 1) draws (numpy PCG64); used for theta_true, noise and test particles."""
+    return np.random.default_rng(seed).standard_normal(shape)
+
+
+def theta_true(w: Workload):
+    return standard_normals((w.K,), w.seed_true)
+
+
+def noise(w: Workload):
+    return standard_normals((w.n_obs,), w.seed_noise)
+
+
+def particles(J, K, seed):
+    """Test/bench particle batch theta ~ N(0, I_K), shape (J, K)."""
+    return standard_normals((J, K), seed)

@@ -1,0 +1,159 @@
+"""Pins of the oracle's SMC pieces: identities, monotonicity, resampling properties,
+prior invariance of pCN, the Philox draw layout, closed-form linear-Gaussian
+posteriors and evidence, and the exact cost identity of the update scheme."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import gaussian, philox, smc
+from oracle.forward import potential
+
+
+def test_kish_identity():
+    w = np.random.default_rng(0).exponential(size=500)
+    assert smc.ess(w) == pytest.approx(w.sum() ** 2 / np.sum(w * w), rel=1e-12)
+    assert smc.cv(np.full(10, 3.0)) == 0.0
+
+
+def test_cv_monotone_in_increment():
+    """d/dDelta log(1 + cv^2) = 2 (E_Delta[a] - E_2Delta[a]) >= 0: cv never decreases along Delta."""
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        a = rng.gamma(2.0, 50.0, size=300)
+        ds = np.linspace(0, 0.2, 200)
+        c = np.array([smc.cv_of_increment(a, d) for d in ds])
+        assert c[0] == 0.0
+        assert np.all(np.diff(c) >= -1e-12)
+
+
+def test_next_increment_hits_target_and_respects_bounds():
+    rng = np.random.default_rng(2)
+    a = rng.gamma(3.0, 40.0, size=1000)
+    d = smc.next_increment(a, 1.0, 1.0, 1e-6)
+    assert smc.cv_of_increment(a, d) == pytest.approx(1.0, abs=1e-10)
+    # remaining step small enough: whole step taken
+    assert smc.next_increment(a * 1e-6, 0.3, 1.0, 1e-6) == 0.3
+    # equal potentials: cv == 0 for every step, whole step taken
+    assert smc.next_increment(np.full(50, 7.0), 0.25, 1.0, 1e-6) == 0.25
+    # target unreachable above eps: the minimum step eps is taken
+    huge = np.concatenate([np.zeros(1), np.full(99, 1e12)])
+    assert smc.next_increment(huge, 1.0, 1.0, 1e-6) == 1e-6
+
+
+def test_log_mean_weight():
+    a = np.random.default_rng(3).uniform(0, 50, 100)
+    for d in (0.0, 0.01, 0.3):
+        assert smc.log_mean_weight(a, d) == pytest.approx(math.log(np.mean(np.exp(-d * a))), rel=1e-12, abs=1e-14)
+    # survives magnitudes where exp underflows without the shift
+    big = a + 1e5
+    assert smc.log_mean_weight(big, 1.0) == pytest.approx(smc.log_mean_weight(a, 1.0) - 1e5, rel=1e-12)
+
+
+def test_systematic_resampling_properties():
+    rng = np.random.default_rng(4)
+    J = 257
+    logw = rng.normal(0, 2, J)
+    W = np.exp(logw - logw.max())
+    W /= W.sum()
+    for U in rng.uniform(0, 1, 50):
+        anc = smc.systematic_resample(logw, U)
+        assert anc.size == J and anc.min() >= 0 and anc.max() < J
+        assert np.all(np.diff(anc) >= 0)
+        cnt = np.bincount(anc, minlength=J)
+        assert np.all(cnt >= np.floor(J * W) - 1e-9) and np.all(cnt <= np.ceil(J * W) + 1e-9)
+    # offspring mean over U equals J * W (the scheme is unbiased)
+    Us = (np.arange(4000) + 0.5) / 4000
+    mean = np.mean([np.bincount(smc.systematic_resample(logw, U), minlength=J) for U in Us], axis=0)
+    assert np.allclose(mean, J * W, atol=2e-3)
+    # equal weights: identity
+    assert np.array_equal(smc.systematic_resample(np.zeros(J), 0.5), np.arange(J))
+
+
+def test_philox_uniform_and_normal_statistics():
+    u = philox.uniforms_open(200000, 7, philox.PURPOSE_PCN_U, 12345)
+    assert u.min() > 0 and u.max() <= 1
+    hist = np.histogram(u, bins=20, range=(0, 1))[0]
+    chi2 = np.sum((hist - 10000) ** 2 / 10000)
+    assert chi2 < 45            # 19 dof, p ~ 0.001
+    z = philox.normals(20000, 10, 3, philox.PURPOSE_PCN_XI, 99)
+    assert abs(z.mean()) < 0.01 and abs(z.var() - 1) < 0.01
+    c = np.corrcoef(z[:, :4].T)
+    assert np.abs(c - np.eye(4)).max() < 0.03
+    # distinct counters give distinct outputs; different seeds differ
+    x = philox.philox4x32_10(np.arange(10000), 0, 0, 0, 1)[0]
+    assert np.unique(x).size == 10000
+    assert not np.array_equal(philox.normals(4, 4, 0, 2, 1), philox.normals(4, 4, 0, 2, 2))
+    # odd K drops the last sine of each particle's final block
+    assert np.array_equal(philox.normals(3, 5, 0, 2, 7), philox.normals(3, 6, 0, 2, 7)[:, :5])
+
+
+def test_pcn_preserves_prior_with_zero_potential():
+    """Phi == 0: every proposal is accepted and N(0, I) is invariant under the pCN map."""
+    K, J = 4, 20000
+    s = smc.Sampler(lambda l, th: np.zeros(th.shape[0]), 1, K, J, n_mcmc=3, seed=5)
+    s.step()
+    assert s.done and s.path[-1]['accept'] == 1.0 and s.path[-1]['delta'] == 1.0
+    m, v = s.moments()
+    assert np.all(np.abs(m) < 4 / math.sqrt(J)) and np.all(np.abs(v - 1) < 0.05)
+
+
+def _linear_problem(K=3, n=5, sigma=0.5, seed=0):
+    rng = np.random.default_rng(seed)
+    A = rng.normal(0, 1, (n, K))
+    y = A @ rng.normal(0, 1, K) + sigma * rng.normal(0, 1, n)
+    return A, y, sigma
+
+
+def test_single_level_smc_linear_gaussian():
+    """Adaptive tempering + pCN reproduces the closed-form posterior and evidence."""
+    A, y, sigma = _linear_problem()
+    m_ex, C_ex = gaussian.posterior(A, y, sigma)
+    lz_ex = gaussian.log_evidence(A, y, sigma)
+    J = 4000
+    ev = lambda l, th: potential(th @ A.T, y, sigma)
+    s = smc.Sampler(ev, 1, 3, J, n_mcmc=10, s_pcn=0.5, seed=11).run()
+    m, v = s.moments()
+    se_m = np.sqrt(np.diag(C_ex) / J) * 3.0          # generous: SMC particles are correlated
+    assert np.all(np.abs(m - m_ex) < 4 * se_m), (m, m_ex)
+    assert np.allclose(v, np.diag(C_ex), rtol=0.15)
+    assert s.log_z == pytest.approx(lz_ex, abs=0.15)
+    assert all(p['kind'] == 'ITU' for p in s.path)
+    assert s.beta == 1.0
+
+
+def test_mls2mc_linear_gaussian_levels_and_cost_identity():
+    """Two-level hierarchy A_l = A + 4^-l B: posterior on the fine level, path rules and the
+    cost identity of Prop. Cost_Proposition (extended by n_mcmc steps and the J~ pre-evaluations)."""
+    A, y, sigma = _linear_problem(K=3, n=6, sigma=0.2, seed=3)
+    B = np.random.default_rng(9).normal(0, 1, A.shape)
+    As = [A + 4.0 ** -(l + 1) * B * 8 for l in range(3)]
+    J, nm, jt = 2000, 6, 100
+    ev = lambda l, th: potential(th @ As[l].T, y, sigma)
+    s = smc.Sampler(ev, 3, 3, J, J_tilde=jt, n_mcmc=nm, s_pcn=0.4, seed=21).run()
+    m_ex, C_ex = gaussian.posterior(As[-1], y, sigma)
+    m, v = s.moments()
+    assert np.all(np.abs(m - m_ex) < 12 * np.sqrt(np.diag(C_ex) / J)), (m, m_ex)
+    assert np.allclose(v, np.diag(C_ex), rtol=0.25)
+    assert s.log_z == pytest.approx(gaussian.log_evidence(As[-1], y, sigma), abs=0.3)
+    # path rules: first update is an ITU; an LU is followed by an ITU unless beta is already 1
+    kinds = [(p['kind'], p['level']) for p in s.path]
+    assert kinds[0] == ('ITU', 0)
+    # cost identity
+    expect = np.zeros(3, dtype=np.int64)
+    expect[0] += J                                     # prior particles on level 1
+    prev_level = 0
+    for i, p in enumerate(s.path):
+        if p['kind'] == 'ITU':
+            expect[p['level']] += nm * J
+            if 'cv_lu' in p:
+                expect[p['level'] + 1] += jt           # discarded cv^LU pre-evaluations
+        else:
+            first_bridge = p['level'] != prev_level
+            if first_bridge:
+                expect[p['level']] += J                # new level on all particles (J~ reused)
+            expect[p['level']] += nm * J
+            expect[p['level'] - 1] += nm * J
+        prev_level = p['level']
+    assert np.array_equal(expect, s.evals), (expect, s.evals)
+    assert s.level == 2 and s.beta == 1.0
