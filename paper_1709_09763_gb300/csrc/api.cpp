@@ -1,0 +1,264 @@
+// C ABI of the library: handle set-up and the likelihood entry points.
+//
+// The handle owns all device memory: per level the KL table Psi (FP64 and FP32
+// copies, Eq. truncKL), the observation interpolation table (3 nodes and P1
+// weights per point) and the data y; plus particle buffers for the sampler.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+#include "internal.h"
+
+using namespace mls2mc;
+
+namespace mls2mc {
+
+int Handle::fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    last_error = buf;
+    return code;
+}
+
+int Handle::cuda_fail(cudaError_t e, const char* what) {
+    return fail(SMC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+template <typename T>
+static cudaError_t upload(T** dst, const T* src, size_t count) {
+    *dst = nullptr;
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)dst, count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+Handle::~Handle() {
+    for (auto& L : levels) {
+        cudaFree(L.psi64);
+        cudaFree(L.psi32);
+        cudaFree(L.obs_idx);
+        cudaFree(L.obs_w);
+        cudaFree(L.linA);
+    }
+    cudaFree(d_y);
+    free_sampler();
+    cudaFree(scratch_theta);
+    cudaFree(scratch_G);
+    cudaFree(scratch_phi);
+    cudaFree(scratch_iters);
+}
+
+int Handle::ensure_scratch(int n) {
+    if (n <= scratch_cap) return SMC_OK;
+    cudaFree(scratch_theta);
+    cudaFree(scratch_G);
+    cudaFree(scratch_phi);
+    cudaFree(scratch_iters);
+    scratch_theta = nullptr;
+    scratch_G = nullptr;
+    scratch_phi = nullptr;
+    scratch_iters = nullptr;
+    scratch_cap = 0;
+    cudaError_t e = cudaMalloc((void**)&scratch_theta, sizeof(double) * (size_t)n * K);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&scratch_G, sizeof(double) * (size_t)n * n_obs);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&scratch_phi, sizeof(double) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&scratch_iters, sizeof(int) * (size_t)n);
+    if (e != cudaSuccess) return fail(SMC_ENOMEM, "scratch allocation for %d particles: %s", n, cudaGetErrorString(e));
+    scratch_cap = n;
+    return SMC_OK;
+}
+
+int Handle::eval_device(int level, int n, const double* theta, double* G, double* Phi, int* iters,
+                        cudaStream_t st) {
+    if (level < 0 || level >= (int)levels.size()) return fail(SMC_EINVAL, "level %d out of range", level);
+    if (n < 0) return fail(SMC_EINVAL, "negative particle count");
+    if (n == 0) return SMC_OK;
+    if (!theta || !Phi) return fail(SMC_EINVAL, "theta and Phi must not be NULL");
+    const Level& L = levels[level];
+    cudaError_t e;
+    if (forward_kind == SMC_FWD_LINEAR) {
+        e = linear_eval_launch(L.linA, n, K, n_obs, theta, d_y, 1.0 / (sigma * sigma), G, Phi, iters, st);
+    } else {
+        FemArgs a{};
+        a.N = L.N;
+        a.precision = precision;
+        a.n = n;
+        a.K = K;
+        a.theta = theta;
+        a.psi = precision == SMC_MIXED ? (const void*)L.psi32 : (const void*)L.psi64;
+        a.obs_idx = L.obs_idx;
+        a.obs_w = L.obs_w;
+        a.n_obs = n_obs;
+        a.y = d_y;
+        a.inv_sigma2 = 1.0 / (sigma * sigma);
+        a.G = G;
+        a.Phi = Phi;
+        a.iters = iters;
+        a.rtol = rtol;
+        a.rtol_in = precision == SMC_MIXED ? 1e-4 : std::max(0.5 * rtol, 1e-14);
+        a.max_outer = precision == SMC_MIXED ? 8 : 3;
+        a.max_inner = max_iter;
+        e = fem_eval_launch(a, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "forward-solve launch");
+    return SMC_OK;
+}
+
+}  // namespace mls2mc
+
+extern "C" {
+
+int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** out) {
+    if (!out) return SMC_EINVAL;
+    *out = nullptr;
+    if (!P || !O) return SMC_EINVAL;
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return SMC_ENOMEM;
+    auto bail = [&](int code) {
+        // keep the handle so the caller can read the reason, unless nothing was built
+        *out = reinterpret_cast<smc_handle*>(h);
+        return code;
+    };
+    if (P->n_levels < 1 || P->n_levels > 8 || !P->inv_h) return bail(h->fail(SMC_EINVAL, "n_levels must be in [1, 8]"));
+    if (P->K < 1 || P->K > 256) return bail(h->fail(SMC_EINVAL, "K must be in [1, 256]"));
+    if (P->n_obs < 1 || P->n_obs > 1024 || !P->obs_xy || !P->y)
+        return bail(h->fail(SMC_EINVAL, "n_obs must be in [1, 1024] with obs_xy and y given"));
+    if (!(P->sigma > 0.0)) return bail(h->fail(SMC_EINVAL, "sigma must be positive"));
+    if (P->forward_kind != SMC_FWD_FEM && P->forward_kind != SMC_FWD_LINEAR)
+        return bail(h->fail(SMC_EINVAL, "unknown forward_kind"));
+    if (P->forward_kind == SMC_FWD_LINEAR && !P->linear_A)
+        return bail(h->fail(SMC_EINVAL, "linear_A required for SMC_FWD_LINEAR"));
+    if (O->precision != SMC_FP64 && O->precision != SMC_MIXED) return bail(h->fail(SMC_EINVAL, "unknown precision"));
+    if (O->J < 0) return bail(h->fail(SMC_EINVAL, "J must be >= 0"));
+    if (P->forward_kind == SMC_FWD_FEM) {
+        if (!(P->corr_len > 0.0) || !(P->variance > 0.0))
+            return bail(h->fail(SMC_EINVAL, "corr_len and variance must be positive"));
+        for (int l = 0; l < P->n_levels; ++l) {
+            if (!fem_level_supported(P->inv_h[l], O->precision))
+                return bail(h->fail(SMC_EINVAL, "level %d: 1/h = %d not supported at this precision", l, P->inv_h[l]));
+            if (l > 0 && P->inv_h[l] <= P->inv_h[l - 1])
+                return bail(h->fail(SMC_EINVAL, "levels must be strictly refining"));
+        }
+        for (int r = 0; r < P->n_obs; ++r)
+            for (int c = 0; c < 2; ++c)
+                if (!(P->obs_xy[2 * r + c] >= 0.0 && P->obs_xy[2 * r + c] <= 1.0))
+                    return bail(h->fail(SMC_EINVAL, "observation %d outside the unit square", r));
+    }
+    h->K = P->K;
+    h->n_obs = P->n_obs;
+    h->sigma = P->sigma;
+    h->forward_kind = P->forward_kind;
+    h->precision = O->precision;
+    h->opts = *O;
+    h->stream = (cudaStream_t)O->stream;
+    h->rtol = O->rtol > 0 ? O->rtol : (O->precision == SMC_MIXED ? 1e-8 : 1e-13);
+    h->max_iter = O->max_iter > 0 ? O->max_iter : 100;
+    h->y_host.assign(P->y, P->y + P->n_obs);
+    cudaError_t e = upload(&h->d_y, P->y, (size_t)P->n_obs);
+    if (e != cudaSuccess) return bail(h->cuda_fail(e, "upload y"));
+    for (int l = 0; l < P->n_levels; ++l) {
+        Level L;
+        if (P->forward_kind == SMC_FWD_FEM) {
+            L.N = P->inv_h[l];
+            std::vector<double> psi, lam;
+            kl_table(L.N, P->corr_len, P->variance, P->K, psi, lam);
+            std::vector<float> psi32(psi.begin(), psi.end());
+            std::vector<int> idx;
+            std::vector<double> wts;
+            obs_table(L.N, P->n_obs, P->obs_xy, idx, wts);
+            e = upload(&L.psi64, psi.data(), psi.size());
+            if (e == cudaSuccess) e = upload(&L.psi32, psi32.data(), psi32.size());
+            if (e == cudaSuccess) e = upload(&L.obs_idx, idx.data(), idx.size());
+            if (e == cudaSuccess) e = upload(&L.obs_w, wts.data(), wts.size());
+            L.lambda = lam;
+            L.psi_host = std::move(psi);
+        } else {
+            L.N = P->inv_h ? P->inv_h[l] : 0;
+            e = upload(&L.linA, P->linear_A + (size_t)l * P->n_obs * P->K, (size_t)P->n_obs * P->K);
+        }
+        h->levels.push_back(L);
+        if (e != cudaSuccess) return bail(h->cuda_fail(e, "upload level tables"));
+    }
+    int rc = h->alloc_sampler();
+    if (rc != SMC_OK) return bail(rc);
+    *out = reinterpret_cast<smc_handle*>(h);
+    return SMC_OK;
+}
+
+void smc_destroy(smc_handle* hh) { delete reinterpret_cast<Handle*>(hh); }
+
+const char* smc_last_error(const smc_handle* hh) {
+    if (!hh) return "null handle";
+    return reinterpret_cast<const Handle*>(hh)->last_error.c_str();
+}
+
+int smc_sizes(const smc_handle* hh, int* K, int* n_obs, int* n_levels, int* J) {
+    if (!hh) return SMC_EINVAL;
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    if (K) *K = h->K;
+    if (n_obs) *n_obs = h->n_obs;
+    if (n_levels) *n_levels = (int)h->levels.size();
+    if (J) *J = h->opts.J;
+    return SMC_OK;
+}
+
+int smc_kl_table(const smc_handle* hh, int level, double* psi, double* lambda) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = const_cast<Handle*>(reinterpret_cast<const Handle*>(hh));
+    if (level < 0 || level >= (int)h->levels.size()) return h->fail(SMC_EINVAL, "level %d out of range", level);
+    const Level& L = h->levels[level];
+    if (h->forward_kind != SMC_FWD_FEM) return h->fail(SMC_EINVAL, "no KL table for a linear forward model");
+    if (psi) std::memcpy(psi, L.psi_host.data(), L.psi_host.size() * sizeof(double));
+    if (lambda) std::memcpy(lambda, L.lambda.data(), L.lambda.size() * sizeof(double));
+    return SMC_OK;
+}
+
+int smc_eval_likelihood_device(smc_handle* hh, int level, int n, const double* theta, double* G, double* Phi,
+                               int* iters, void* stream) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    return h->eval_device(level, n, theta, G, Phi, iters, stream ? (cudaStream_t)stream : h->stream);
+}
+
+int smc_eval_likelihood(smc_handle* hh, int level, int n, const double* theta, double* G, double* Phi) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (n < 0) return h->fail(SMC_EINVAL, "negative particle count");
+    if (n == 0) return SMC_OK;
+    if (!theta || !Phi) return h->fail(SMC_EINVAL, "theta and Phi must not be NULL");
+    int rc = h->ensure_scratch(n);
+    if (rc != SMC_OK) return rc;
+    cudaStream_t st = h->stream;
+    cudaError_t e = cudaMemcpyAsync(h->scratch_theta, theta, sizeof(double) * (size_t)n * h->K,
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return h->cuda_fail(e, "copy theta to device");
+    rc = h->eval_device(level, n, h->scratch_theta, G ? h->scratch_G : nullptr, h->scratch_phi, h->scratch_iters, st);
+    if (rc != SMC_OK) return rc;
+    if (G) {
+        e = cudaMemcpyAsync(G, h->scratch_G, sizeof(double) * (size_t)n * h->n_obs, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return h->cuda_fail(e, "copy G to host");
+    }
+    e = cudaMemcpyAsync(Phi, h->scratch_phi, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return h->cuda_fail(e, "copy Phi to host");
+    std::vector<int> its((size_t)n);
+    e = cudaMemcpyAsync(its.data(), h->scratch_iters, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return h->cuda_fail(e, "forward solve");
+    for (int i = 0; i < n; ++i)
+        if (its[i] < 0) return h->fail(SMC_ENOCONV, "particle %d: solve did not reach rtol", i);
+    return SMC_OK;
+}
+
+}  // extern "C"

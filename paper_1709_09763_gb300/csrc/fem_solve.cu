@@ -1,0 +1,538 @@
+// Batched likelihood evaluation G_l(theta), Phi_l(theta) on one mesh level.
+//
+// Path (Sec. 2.1, Sec. 5): theta -> u = theta . Psi on every triangle (Eq. truncKL)
+// -> kappa = exp(u) -> P1 FEM solve of -div(kappa grad p) = 1, p = 0 on the
+// boundary -> observations p(d_n) -> Phi = 1/2 sum ((y - G)/sigma)^2 (Eq. phi).
+//
+// Design: one thread block owns one particle and keeps its whole problem on chip.
+// For P1 elements on the uniform mesh whose cells are split by the (i,j)-(i+1,j+1)
+// diagonal the stiffness matrix is a 5-point stencil: edge (i,j)-(i+1,j) has
+// weight (kappa_lower(i,j) + kappa_upper(i,j-1))/2, edge (i,j)-(i,j+1) has weight
+// (kappa_lower(i-1,j) + kappa_upper(i,j))/2, diagonal-edge couplings vanish, and
+// the load of f = 1 is h^2 at every interior node. The linear system is solved
+// matrix-free by multigrid-preconditioned CG:
+//  * hierarchy N, N/2, ..., 2 cells per side; the coarse mesh is nested, the
+//    prolongation is P1 interpolation and restriction its transpose, and the
+//    coarse operator is the same stencil built from the mean kappa of the four
+//    fine triangles inside each coarse triangle -- for piecewise-constant kappa
+//    this equals the Galerkin product P^T A P exactly;
+//  * symmetric V(1,1) cycle with red-black Gauss-Seidel (red-black before the
+//    coarse correction, black-red after), exact solve on the single coarsest node;
+//  * SMC_MIXED: the field, stencil, multigrid and CG run in FP32; each pass ends
+//    with an FP64 update of the residual r <- r - A d, computed in edge form
+//    sum_e a_e (d_i - d_j) from the FP32 edge weights (so its diagonal is their
+//    exact sum), and an FP64 accumulation x <- x + d, until the FP64 relative
+//    residual reaches rtol (mixed-precision iterative refinement);
+//    SMC_FP64: the same algorithm in FP64 throughout.
+// Shared memory holds, per level, the edge weights aE, aN, the diagonal D and the
+// vectors e (multigrid correction), res (residual) and rhs (fine level: the CG
+// direction p). The fine-level CG vectors r, d and the FP64 x, r live in
+// registers: every fine node belongs to one thread for the whole solve.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace mls2mc {
+
+namespace {
+
+__host__ __device__ constexpr int padded(int n) { return (n + 3) & ~3; }
+__host__ __device__ constexpr int lvl_size(int NL) { return padded((NL + 1) * (NL + 1)); }
+// element offset of level NL inside the shared arena of a hierarchy with top level N
+__host__ __device__ constexpr int lvl_offset(int N, int NL) { return N == NL ? 0 : 6 * lvl_size(N) + lvl_offset(N / 2, NL); }
+__host__ __device__ constexpr int arena_size(int N) { return N < 2 ? 0 : 6 * lvl_size(N) + arena_size(N / 2); }
+
+template <typename Real>
+struct Lv {
+    Real *aE, *aN, *D, *e, *res, *rhs;
+};
+
+template <typename Real, int N, int NL>
+__device__ __forceinline__ Lv<Real> level_ptrs(Real* arena) {
+    Real* b = arena + lvl_offset(N, NL);
+    constexpr int z = lvl_size(NL);
+    return Lv<Real>{b, b + z, b + 2 * z, b + 3 * z, b + 4 * z, b + 5 * z};
+}
+
+// sum of a_nb * v_nb over the four stencil neighbours of padded node n (row stride S)
+template <typename Real, int S>
+__device__ __forceinline__ Real offsum(const Real* aE, const Real* aN, const Real* v, int n) {
+    return aE[n] * v[n + 1] + aE[n - 1] * v[n - 1] + aN[n] * v[n + S] + aN[n - S] * v[n - S];
+}
+
+// ---- block reductions (every thread gets the same result, summed in a fixed order) ----
+template <int T, typename Acc>
+__device__ __forceinline__ void block_sum(Acc& a, double* buf_raw) {
+    Acc* buf = reinterpret_cast<Acc*>(buf_raw);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+    if ((threadIdx.x & 31) == 0) buf[threadIdx.x >> 5] = a;
+    __syncthreads();
+    Acc s = 0;
+#pragma unroll
+    for (int i = 0; i < T / 32; ++i) s += buf[i];
+    a = s;
+}
+
+// ---- error-free transformations (Knuth TwoSum, Dekker), double-float accumulation ----
+template <typename Real>
+__device__ __forceinline__ void two_sum(Real a, Real b, Real& s, Real& e) {
+    s = a + b;
+    const Real bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (ah, al) += (bh, bl), result renormalised so that |al| <= ulp(ah)/2
+template <typename Real>
+__device__ __forceinline__ void df_add(Real& ah, Real& al, Real bh, Real bl) {
+    Real s, e;
+    two_sum(ah, bh, s, e);
+    e += al + bl;
+    ah = s + e;
+    al = e - (ah - s);
+}
+
+// ---- coarse-level multigrid pieces (rhs in shared memory) --------------------------------
+template <typename Real, int NL, int T>
+__device__ __forceinline__ void smooth_first_red(const Lv<Real>& L) {
+    // starting from e = 0: red nodes get rhs/D, black nodes are zeroed
+    constexpr int M = NL - 1, S = NL + 1;
+    for (int idx = threadIdx.x; idx < M * M; idx += T) {
+        const int j = idx / M + 1, i = idx - (j - 1) * M + 1, n = j * S + i;
+        L.e[n] = (((i + j) & 1) == 0) ? L.rhs[n] / L.D[n] : Real(0);
+    }
+}
+
+template <typename Real, int NL, int T>
+__device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
+    constexpr int M = NL - 1, S = NL + 1;
+    for (int idx = threadIdx.x; idx < M * M; idx += T) {
+        const int j = idx / M + 1, i = idx - (j - 1) * M + 1, n = j * S + i;
+        if (((i + j) & 1) == color) L.e[n] = (L.rhs[n] + offsum<Real, S>(L.aE, L.aN, L.e, n)) / L.D[n];
+    }
+}
+
+template <typename Real, int NL, int T>
+__device__ __forceinline__ void residual(const Lv<Real>& L) {
+    constexpr int M = NL - 1, S = NL + 1;
+    for (int idx = threadIdx.x; idx < M * M; idx += T) {
+        const int j = idx / M + 1, i = idx - (j - 1) * M + 1, n = j * S + i;
+        L.res[n] = L.rhs[n] - (L.D[n] * L.e[n] - offsum<Real, S>(L.aE, L.aN, L.e, n));
+    }
+}
+
+// coarse rhs = P^T fine residual: P1 interpolation weights 1 and 1/2 along the six
+// mesh directions (+-x, +-y, and the (1,1) diagonal)
+template <typename Real, int NC, int T>
+__device__ __forceinline__ void restrict_to(const Real* res_f, Real* rhs_c) {
+    constexpr int MC = NC - 1, SC = NC + 1, SF = 2 * NC + 1;
+    for (int idx = threadIdx.x; idx < MC * MC; idx += T) {
+        const int J = idx / MC + 1, I = idx - (J - 1) * MC + 1;
+        const int f = (2 * J) * SF + 2 * I;
+        rhs_c[J * SC + I] = res_f[f] + Real(0.5) * (res_f[f + 1] + res_f[f - 1] + res_f[f + SF] +
+                                                     res_f[f - SF] + res_f[f + SF + 1] + res_f[f - SF - 1]);
+    }
+}
+
+// P1 interpolation of the coarse correction at fine node (i, j)
+template <typename Real, int NC>
+__device__ __forceinline__ Real prolong_at(const Real* ec, int i, int j) {
+    constexpr int SC = NC + 1;
+    const int I = i >> 1, J = j >> 1;
+    const int c = J * SC + I;
+    if ((i & 1) == 0 && (j & 1) == 0) return ec[c];
+    if ((j & 1) == 0) return Real(0.5) * (ec[c] + ec[c + 1]);
+    if ((i & 1) == 0) return Real(0.5) * (ec[c] + ec[c + SC]);
+    return Real(0.5) * (ec[c] + ec[c + SC + 1]);
+}
+
+template <typename Real, int NL, int T>
+__device__ __forceinline__ void prolong_add(const Lv<Real>& L, const Real* ec) {
+    constexpr int M = NL - 1, S = NL + 1;
+    for (int idx = threadIdx.x; idx < M * M; idx += T) {
+        const int j = idx / M + 1, i = idx - (j - 1) * M + 1;
+        L.e[j * S + i] += prolong_at<Real, NL / 2>(ec, i, j);
+    }
+}
+
+// V(1,1) cycle on a coarse level: reads L.rhs, writes L.e
+template <typename Real, int N, int NL, int T>
+__device__ void vcycle_coarse(Real* arena) {
+    Lv<Real> L = level_ptrs<Real, N, NL>(arena);
+    if constexpr (NL == 2) {
+        if (threadIdx.x == 0) L.e[4] = L.rhs[4] / L.D[4];   // single interior node (1,1), S = 3
+        __syncthreads();
+    } else {
+        Lv<Real> C = level_ptrs<Real, N, NL / 2>(arena);
+        smooth_first_red<Real, NL, T>(L);
+        __syncthreads();
+        smooth_color<Real, NL, T>(L, 1);
+        __syncthreads();
+        residual<Real, NL, T>(L);
+        __syncthreads();
+        restrict_to<Real, NL / 2, T>(L.res, C.rhs);
+        __syncthreads();
+        vcycle_coarse<Real, N, NL / 2, T>(arena);
+        prolong_add<Real, NL, T>(L, C.e);
+        __syncthreads();
+        smooth_color<Real, NL, T>(L, 1);
+        __syncthreads();
+        smooth_color<Real, NL, T>(L, 0);
+        __syncthreads();
+    }
+}
+
+// ---- stencil coefficients from per-triangle kappa ----------------------------------------
+// kappa in element order e = 2*(j*NL+i) + t (t = 0 lower, 1 upper half of cell (i, j))
+template <typename Real, int NL, int T>
+__device__ __forceinline__ void build_coeffs(const Lv<Real>& L, const Real* kap) {
+    constexpr int S = NL + 1;
+    for (int n = threadIdx.x; n < S * S; n += T) {
+        const int j = n / S, i = n - j * S;
+        Real ae = 0, an = 0;
+        if (i < NL) {   // horizontal edge (i,j)-(i+1,j): lower of cell (i,j), upper of cell (i,j-1)
+            if (j < NL) ae += kap[2 * (j * NL + i)];
+            if (j > 0) ae += kap[2 * ((j - 1) * NL + i) + 1];
+        }
+        if (j < NL) {   // vertical edge (i,j)-(i,j+1): lower of cell (i-1,j), upper of cell (i,j)
+            if (i > 0) an += kap[2 * (j * NL + i - 1)];
+            if (i < NL) an += kap[2 * (j * NL + i) + 1];
+        }
+        L.aE[n] = Real(0.5) * ae;
+        L.aN[n] = Real(0.5) * an;
+    }
+}
+
+template <typename Real, int NL, int T>
+__device__ __forceinline__ void build_diag(const Lv<Real>& L) {
+    constexpr int S = NL + 1;
+    for (int n = threadIdx.x; n < S * S; n += T) {
+        const int j = n / S, i = n - j * S;
+        Real d = 0;
+        if (i > 0 && j > 0 && i < NL && j < NL) d = L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S];
+        L.D[n] = (d == Real(0)) ? Real(1) : d;   // boundary entries are never used as divisors
+    }
+}
+
+// mean kappa of the four fine triangles inside each coarse triangle
+template <typename Real, int NC, int T>
+__device__ __forceinline__ void coarsen_kappa(const Real* kf, Real* kc) {
+    constexpr int NF = 2 * NC;
+    for (int c = threadIdx.x; c < NC * NC; c += T) {
+        const int J = c / NC, I = c - J * NC;
+        const int i = 2 * I, j = 2 * J;
+        auto lo = [&](int a, int b) { return kf[2 * (b * NF + a)]; };
+        auto up = [&](int a, int b) { return kf[2 * (b * NF + a) + 1]; };
+        kc[2 * c] = Real(0.25) * (lo(i, j) + lo(i + 1, j) + up(i + 1, j) + lo(i + 1, j + 1));
+        kc[2 * c + 1] = Real(0.25) * (up(i, j) + up(i, j + 1) + lo(i, j + 1) + up(i + 1, j + 1));
+    }
+}
+
+// builds coefficients of level NL from kappa at kin, coarser kappa into the other half
+// of the staging area, then recurses
+template <typename Real, int N, int NL, int T>
+__device__ void setup_levels(Real* arena, Real* stage, bool ping) {
+    Lv<Real> L = level_ptrs<Real, N, NL>(arena);
+    Real* kin = ping ? stage : stage + 2 * N * N;
+    build_coeffs<Real, NL, T>(L, kin);
+    if constexpr (NL > 2) {
+        Real* kout = ping ? stage + 2 * N * N : stage;
+        coarsen_kappa<Real, NL / 2, T>(kin, kout);
+        __syncthreads();
+        build_diag<Real, NL, T>(L);
+        setup_levels<Real, N, NL / 2, T>(arena, stage, !ping);
+    } else {
+        __syncthreads();
+        build_diag<Real, NL, T>(L);
+        __syncthreads();
+    }
+}
+
+template <typename Real, int N>
+struct Fine {
+    static constexpr int M = N - 1, S = N + 1, NI = M * M;
+};
+
+// ---- the kernel ----------------------------------------------------------------------
+template <typename Real, int N, int T>
+__global__ void __launch_bounds__(T, 1)
+fem_eval_kernel(FemArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real* arena = reinterpret_cast<Real*>(smem_raw);
+    __shared__ double red_buf[2][64];
+    __shared__ Real theta_s[256];
+
+    constexpr int M = Fine<Real, N>::M, S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
+    constexpr int NPT = (NI + T - 1) / T;
+    constexpr int E = 2 * N * N;
+    const int tid = threadIdx.x;
+    const int p = blockIdx.x;
+    if (p >= a.n) return;
+
+    Lv<Real> F = level_ptrs<Real, N, N>(arena);
+    Real* stage = F.e;     // e, res, p of the fine level are contiguous: 3*lvl_size(N) >= 2.5 N^2
+
+    // 1) field u = theta . Psi and kappa = exp(u) on every fine triangle
+    for (int k = tid; k < a.K; k += T) theta_s[k] = (Real)a.theta[(size_t)p * a.K + k];
+    __syncthreads();
+    const Real* psi = static_cast<const Real*>(a.psi);
+    for (int e = tid; e < E; e += T) {
+        Real u = 0;
+        for (int k = 0; k < a.K; ++k) u = fma(theta_s[k], psi[(size_t)k * E + e], u);
+        stage[e] = exp(u);
+    }
+    __syncthreads();
+
+    // 2) stencil hierarchy
+    setup_levels<Real, N, N, T>(arena, stage, true);
+    // zero every vector e, res, rhs of every level (their boundary rings must read as zero)
+    {
+        int off = 0;
+#pragma unroll
+        for (int NL = N; NL >= 2; NL >>= 1) {
+            const int z = ((NL + 1) * (NL + 1) + 3) & ~3;
+            for (int q = tid; q < 3 * z; q += T) arena[off + 3 * z + q] = Real(0);
+            off += 6 * z;
+        }
+    }
+    __syncthreads();
+
+    // fine nodes owned by this thread
+    int node[NPT];
+    bool valid[NPT], red[NPT];
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+        const int idx = tid + T * q;
+        valid[q] = idx < NI;
+        const int jj = (valid[q] ? idx : 0) / M + 1, ii = (valid[q] ? idx : 0) - (jj - 1) * M + 1;
+        node[q] = jj * S + ii;
+        red[q] = ((ii + jj) & 1) == 0;
+    }
+
+    // right-hand side h^2 (f = 1), exact in FP32 for N a power of two
+    const Real h2 = Real(1) / (Real(N) * Real(N));
+    // solution x and residual r of the refinement: FP64, or double-float pairs (hi + lo)
+    // of FP32 numbers on the mixed path so that no FP64 instruction runs in the solve
+    Real xh[NPT], xl[NPT], rh[NPT], rl[NPT];
+    Real r[NPT], d[NPT];
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+        xh[q] = xl[q] = rl[q] = Real(0);
+        rh[q] = valid[q] ? h2 : Real(0);
+    }
+    const Real bnorm2 = Real(NI) * h2 * h2;
+    const Real stop_outer = Real(a.rtol * a.rtol) * bnorm2;
+    const Real rtol_in2 = Real(a.rtol_in * a.rtol_in);
+    int parity = 0;
+    int total_it = 0;
+    bool converged = false;
+    Lv<Real> C1 = level_ptrs<Real, N, N / 2>(arena);
+    Real* P = F.rhs;   // fine-level CG direction
+
+    for (int pass = 0; pass < a.max_outer && !converged; ++pass) {
+        // ---- inner multigrid-preconditioned CG on A d = r (working precision) ----
+        Real rr0 = 0;
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+            r[q] = rh[q];
+            d[q] = Real(0);
+            rr0 += r[q] * r[q];
+        }
+        block_sum<T>(rr0, red_buf[parity]);
+        parity ^= 1;
+        if (rr0 == Real(0)) break;
+        const Real stop2 = rtol_in2 * rr0;
+        Real rz = 0;
+        for (int it = 0; it < a.max_inner; ++it) {
+            // z = M^{-1} r: V(1,1) cycle with the fine rhs held in registers
+#pragma unroll
+            for (int q = 0; q < NPT; ++q)
+                if (valid[q]) F.e[node[q]] = red[q] ? r[q] / F.D[node[q]] : Real(0);
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < NPT; ++q)
+                if (valid[q] && !red[q]) {
+                    const int n = node[q];
+                    F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) / F.D[n];
+                }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < NPT; ++q)
+                if (valid[q]) {
+                    const int n = node[q];
+                    F.res[n] = r[q] - (F.D[n] * F.e[n] - offsum<Real, S>(F.aE, F.aN, F.e, n));
+                }
+            __syncthreads();
+            restrict_to<Real, N / 2, T>(F.res, C1.rhs);
+            __syncthreads();
+            vcycle_coarse<Real, N, N / 2, T>(arena);
+#pragma unroll
+            for (int q = 0; q < NPT; ++q)
+                if (valid[q]) {
+                    const int n = node[q];
+                    const int jj = n / S, ii = n - jj * S;
+                    F.e[n] += prolong_at<Real, N / 2>(C1.e, ii, jj);
+                }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < NPT; ++q)
+                if (valid[q] && !red[q]) {
+                    const int n = node[q];
+                    F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) / F.D[n];
+                }
+            __syncthreads();
+            Real rz_new = 0;
+#pragma unroll
+            for (int q = 0; q < NPT; ++q)
+                if (valid[q] && red[q]) {
+                    const int n = node[q];
+                    F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) / F.D[n];
+                }
+#pragma unroll
+            for (int q = 0; q < NPT; ++q)
+                if (valid[q]) rz_new += r[q] * F.e[node[q]];
+            block_sum<T>(rz_new, red_buf[parity]);
+            parity ^= 1;
+            // p = z + beta p
+            const Real beta = (it == 0) ? Real(0) : rz_new / rz;
+            rz = rz_new;
+#pragma unroll
+            for (int q = 0; q < NPT; ++q)
+                if (valid[q]) P[node[q]] = (it == 0) ? F.e[node[q]] : F.e[node[q]] + beta * P[node[q]];
+            __syncthreads();
+            // q = A p, alpha = rz / p.q
+            Real qv[NPT];
+            Real pq = 0;
+#pragma unroll
+            for (int q = 0; q < NPT; ++q) {
+                qv[q] = Real(0);
+                if (valid[q]) {
+                    const int n = node[q];
+                    qv[q] = F.D[n] * P[n] - offsum<Real, S>(F.aE, F.aN, P, n);
+                    pq += P[n] * qv[q];
+                }
+            }
+            block_sum<T>(pq, red_buf[parity]);
+            parity ^= 1;
+            const Real alpha = rz / pq;
+            Real rr = 0;
+#pragma unroll
+            for (int q = 0; q < NPT; ++q)
+                if (valid[q]) {
+                    d[q] = fma(alpha, P[node[q]], d[q]);
+                    r[q] = fma(-alpha, qv[q], r[q]);
+                    rr += r[q] * r[q];
+                }
+            block_sum<T>(rr, red_buf[parity]);
+            parity ^= 1;
+            ++total_it;
+            if (!(rr > stop2)) break;   // also leaves on NaN
+        }
+        // ---- refinement: x += d, r -= A d in extended precision ----
+        // A d in edge form sum_e a_e (d_i - d_j): its diagonal is the exact sum of the four
+        // edge weights, so the refined system is the FEM stencil of the stored edge weights
+        // (the rounded working-precision diagonal would act as a spurious reaction term).
+#pragma unroll
+        for (int q = 0; q < NPT; ++q)
+            if (valid[q]) P[node[q]] = d[q];
+        __syncthreads();
+        Real rr_out = 0;
+#pragma unroll
+        for (int q = 0; q < NPT; ++q)
+            if (valid[q]) {
+                const int n = node[q];
+                const Real di = P[n];
+                const Real w[4] = {F.aE[n], F.aE[n - 1], F.aN[n], F.aN[n - S]};
+                const Real dj[4] = {P[n + 1], P[n - 1], P[n + S], P[n - S]};
+                if constexpr (sizeof(Real) == 8) {
+                    Real Ad = 0;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) Ad = fma(w[t], di - dj[t], Ad);
+                    rh[q] -= Ad;
+                    xh[q] += d[q];
+                } else {
+                    Real ah = 0, al = 0;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        Real sh, sl;
+                        two_sum(di, -dj[t], sh, sl);        // d_i - d_j exactly
+                        const Real ph = __fmul_rn(w[t], sh);   // kept out of FMA contraction
+                        Real pl = fma(w[t], sh, -ph);          // exact product error
+                        pl = fma(w[t], sl, pl);
+                        df_add(ah, al, ph, pl);
+                    }
+                    df_add(rh[q], rl[q], -ah, -al);
+                    df_add(xh[q], xl[q], d[q], Real(0));
+                }
+                rr_out += rh[q] * rh[q];
+            }
+        block_sum<T>(rr_out, red_buf[parity]);
+        parity ^= 1;
+        converged = rr_out <= stop_outer;
+    }
+
+    // ---- observations and misfit (FP64) ----
+    double* xs = reinterpret_cast<double*>(F.e);   // e and res: 2*lvl_size(N) Real >= (N+1)^2 doubles
+    for (int n = tid; n < S * S; n += T) xs[n] = 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NPT; ++q)
+        if (valid[q]) xs[node[q]] = (double)xh[q] + (double)xl[q];
+    __syncthreads();
+    double misfit = 0.0;
+    for (int o = tid; o < a.n_obs; o += T) {
+        const double g = a.obs_w[3 * o] * xs[a.obs_idx[3 * o]] + a.obs_w[3 * o + 1] * xs[a.obs_idx[3 * o + 1]] +
+                         a.obs_w[3 * o + 2] * xs[a.obs_idx[3 * o + 2]];
+        if (a.G) a.G[(size_t)p * a.n_obs + o] = g;
+        const double rdf = a.y[o] - g;
+        misfit += rdf * rdf;
+    }
+    block_sum<T>(misfit, red_buf[parity]);
+    if (tid == 0) {
+        a.Phi[p] = 0.5 * misfit * a.inv_sigma2;
+        if (a.iters) a.iters[p] = converged ? total_it : -(total_it + 1);
+    }
+}
+
+template <typename Real, int N, int T>
+cudaError_t launch_one(const FemArgs& a, cudaStream_t st) {
+    const size_t smem = sizeof(Real) * (size_t)arena_size(N);
+    auto kern = fem_eval_kernel<Real, N, T>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    kern<<<a.n, T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fem_level_supported(int N, int precision) {
+    if (precision == SMC_MIXED) return N == 4 || N == 8 || N == 16 || N == 32 || N == 64;
+    return N == 4 || N == 8 || N == 16 || N == 32;
+}
+
+cudaError_t fem_eval_launch(const FemArgs& a, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    if (a.precision == SMC_MIXED) {
+        switch (a.N) {
+            case 4: return launch_one<float, 4, 32>(a, st);
+            case 8: return launch_one<float, 8, 64>(a, st);
+            case 16: return launch_one<float, 16, 128>(a, st);
+            case 32: return launch_one<float, 32, 256>(a, st);
+            case 64: return launch_one<float, 64, 512>(a, st);
+        }
+    } else {
+        switch (a.N) {
+            case 4: return launch_one<double, 4, 32>(a, st);
+            case 8: return launch_one<double, 8, 64>(a, st);
+            case 16: return launch_one<double, 16, 128>(a, st);
+            case 32: return launch_one<double, 32, 256>(a, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace mls2mc

@@ -1,0 +1,58 @@
+// The opaque smc_handle behind the C ABI (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace mls2mc {
+
+struct Level {
+    int N = 0;                   // 1/h
+    double* psi64 = nullptr;     // [K][2N^2]
+    float* psi32 = nullptr;      // [K][2N^2]
+    int* obs_idx = nullptr;      // [n_obs][3]
+    double* obs_w = nullptr;     // [n_obs][3]
+    double* linA = nullptr;      // linear forward model [n_obs][K]
+    std::vector<double> lambda;  // KL eigenvalues
+    std::vector<double> psi_host;
+};
+
+struct Handle {
+    int K = 0, n_obs = 0, forward_kind = SMC_FWD_FEM, precision = SMC_FP64;
+    double sigma = 1.0, rtol = 1e-13;
+    int max_iter = 100;
+    smc_sampler_opts opts{};
+    cudaStream_t stream = nullptr;
+    std::vector<Level> levels;
+    std::vector<double> y_host;
+    double* d_y = nullptr;
+    std::string last_error;
+
+    // staging buffers of the host-pointer entry points
+    double* scratch_theta = nullptr;
+    double* scratch_G = nullptr;
+    double* scratch_phi = nullptr;
+    int* scratch_iters = nullptr;
+    int scratch_cap = 0;
+
+    // sampler state (smc_kernels.cu / controller.cpp)
+    struct Sampler* smp = nullptr;
+
+    ~Handle();
+    int fail(int code, const char* fmt, ...);
+    int cuda_fail(cudaError_t e, const char* what);
+    int ensure_scratch(int n);
+    int eval_device(int level, int n, const double* theta, double* G, double* Phi, int* iters, cudaStream_t st);
+    int alloc_sampler();
+    void free_sampler();
+};
+
+// G = A theta and Phi for the linear test forward model (smc_kernels.cu)
+cudaError_t linear_eval_launch(const double* A, int n, int K, int n_obs, const double* theta, const double* y,
+                               double inv_sigma2, double* G, double* Phi, int* iters, cudaStream_t st);
+
+}  // namespace mls2mc

@@ -1,0 +1,45 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mls2mc.h"
+
+namespace mls2mc {
+
+// ---- host set-up (kl_host.cpp) ---------------------------------------------------------
+void kl_eig_1d(double corr_len, int n_modes, std::vector<double>& lam, std::vector<double>& omega);
+void kl_table(int N, double corr_len, double variance, int K, std::vector<double>& psi,
+              std::vector<double>& lambda);
+void obs_table(int N, int n_obs, const double* xy, std::vector<int>& idx, std::vector<double>& wts);
+
+// ---- forward solve (fem_solve.cu) -------------------------------------------------------
+struct FemArgs {
+    int N;                  // cells per side of this level (power of two, 4..64)
+    int precision;          // SMC_FP64 or SMC_MIXED
+    int n;                  // particles
+    int K;                  // KL terms
+    const double* theta;    // [n][K] device
+    const void* psi;        // [K][2N^2] device, double (FP64) or float (MIXED)
+    const int* obs_idx;     // [n_obs][3] node indices into the (N+1)^2 grid
+    const double* obs_w;    // [n_obs][3] P1 weights
+    int n_obs;
+    const double* y;        // [n_obs]
+    double inv_sigma2;      // 1 / sigma^2
+    double* G;              // [n][n_obs] or null
+    double* Phi;            // [n]
+    int* iters;             // [n] or null
+    double rtol;            // FP64 relative residual target
+    double rtol_in;         // relative reduction of each inner CG pass
+    int max_outer;          // refinement passes
+    int max_inner;          // inner CG iterations per pass
+};
+// Returns cudaSuccess or the launch error.
+cudaError_t fem_eval_launch(const FemArgs& a, cudaStream_t stream);
+bool fem_level_supported(int N, int precision);
+
+}  // namespace mls2mc

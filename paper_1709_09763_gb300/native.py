@@ -1,0 +1,161 @@
+"""ctypes binding of libmls2mc.so: the C ABI of include/mls2mc.h, argument marshalling only.
+
+Every computation happens inside the library's CUDA kernels. Loading fails loudly
+when the library has not been built; there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmls2mc.so")
+
+SMC_OK = 0
+SMC_EINVAL = -1
+SMC_ENOMEM = -2
+SMC_ECUDA = -3
+SMC_ENOCONV = -4
+SMC_ESINGULAR = -5
+SMC_ETIMEOUT = -6
+SMC_FP64 = 0
+SMC_MIXED = 1
+SMC_FWD_FEM = 0
+SMC_FWD_LINEAR = 1
+
+ERROR_NAMES = {0: "SMC_OK", -1: "SMC_EINVAL", -2: "SMC_ENOMEM", -3: "SMC_ECUDA", -4: "SMC_ENOCONV",
+               -5: "SMC_ESINGULAR", -6: "SMC_ETIMEOUT"}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int), ("inv_h", _ip), ("K", ctypes.c_int),
+                ("corr_len", ctypes.c_double), ("variance", ctypes.c_double),
+                ("n_obs", ctypes.c_int), ("obs_xy", _dp), ("y", _dp), ("sigma", ctypes.c_double),
+                ("forward_kind", ctypes.c_int), ("linear_A", _dp)]
+
+
+class SamplerOpts(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_int), ("J_tilde", ctypes.c_int), ("n_mcmc", ctypes.c_int),
+                ("tau_star", ctypes.c_double), ("tau_lu", ctypes.c_double), ("eps", ctypes.c_double),
+                ("s_pcn", ctypes.c_double), ("precision", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("max_iter", ctypes.c_int), ("rtol", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+
+class StageInfo(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("level", ctypes.c_int), ("beta", ctypes.c_double),
+                ("zeta", ctypes.c_double), ("delta", ctypes.c_double), ("cv", ctypes.c_double),
+                ("cv_lu", ctypes.c_double), ("log_z_inc", ctypes.c_double),
+                ("accept_rate", ctypes.c_double), ("da_stage1_rate", ctypes.c_double),
+                ("evals_per_level", ctypes.c_longlong * 8), ("status", ctypes.c_int)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); every function the header declares
+SIGNATURES = {
+    "smc_init": (ctypes.c_int, [ctypes.POINTER(ProblemDesc), ctypes.POINTER(SamplerOpts),
+                                ctypes.POINTER(ctypes.c_void_p)]),
+    "smc_destroy": (None, [ctypes.c_void_p]),
+    "smc_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "smc_eval_likelihood": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]),
+    "smc_eval_likelihood_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_void_p]),
+    "smc_kl_table": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, _dp]),
+    "smc_sizes": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip, _ip, _ip]),
+}
+
+
+def load():
+    """Load libmls2mc.so (build it first with paper_1709_09763_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_1709_09763_gb300.build` "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+class Handle:
+    """Owns one smc_handle. Arrays passed in are kept alive for the call's duration only."""
+
+    def __init__(self, inv_h, K, obs_xy, y, sigma, corr_len=0.1, variance=1.0, J=0, J_tilde=100,
+                 n_mcmc=5, tau_star=1.0, tau_lu=None, eps=1e-6, s_pcn=0.2, precision=SMC_FP64, seed=0,
+                 max_iter=100, rtol=0.0, stream=None, linear_A=None):
+        lib = load()
+        self._lib = lib
+        self._inv_h = np.ascontiguousarray(inv_h, dtype=np.int32)
+        self._obs = np.ascontiguousarray(obs_xy, dtype=np.float64).reshape(-1, 2)
+        self._y = np.ascontiguousarray(y, dtype=np.float64).ravel()
+        self._A = None if linear_A is None else np.ascontiguousarray(linear_A, dtype=np.float64)
+        d = ProblemDesc(len(self._inv_h), self._inv_h.ctypes.data_as(_ip), int(K), float(corr_len),
+                        float(variance), self._obs.shape[0], _dptr(self._obs), _dptr(self._y), float(sigma),
+                        SMC_FWD_LINEAR if self._A is not None else SMC_FWD_FEM, _dptr(self._A))
+        o = SamplerOpts(int(J), int(J_tilde), int(n_mcmc), float(tau_star),
+                        float(tau_star if tau_lu is None else tau_lu), float(eps), float(s_pcn), int(precision),
+                        int(seed), int(max_iter), float(rtol), stream)
+        h = ctypes.c_void_p()
+        rc = lib.smc_init(ctypes.byref(d), ctypes.byref(o), ctypes.byref(h))
+        self._h = h
+        if rc != SMC_OK:
+            msg = lib.smc_last_error(h).decode() if h.value else "no handle"
+            self.close()
+            raise SmcError(rc, msg)
+        K_, n_obs, nl, J_ = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        lib.smc_sizes(h, ctypes.byref(K_), ctypes.byref(n_obs), ctypes.byref(nl), ctypes.byref(J_))
+        self.K, self.n_obs, self.n_levels, self.J = K_.value, n_obs.value, nl.value, J_.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.smc_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != SMC_OK:
+            raise SmcError(rc, self._lib.smc_last_error(self._h).decode())
+
+    def eval_likelihood(self, level, theta, want_G=True):
+        """Host arrays in and out: returns (G [n, n_obs] or None, Phi [n])."""
+        theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, self.K)
+        n = theta.shape[0]
+        G = np.empty((n, self.n_obs)) if want_G else None
+        Phi = np.empty(n)
+        self._check(self._lib.smc_eval_likelihood(self._h, level, n, _dptr(theta), _dptr(G), _dptr(Phi)))
+        return G, Phi
+
+    def eval_likelihood_device(self, level, n, theta_ptr, G_ptr, Phi_ptr, iters_ptr=None, stream=None):
+        """Device pointers (ints, e.g. torch tensor data_ptr()); queued on stream, no wait."""
+        self._check(self._lib.smc_eval_likelihood_device(self._h, level, n, theta_ptr, G_ptr, Phi_ptr,
+                                                         iters_ptr, stream))
+
+    def kl_table(self, level, N):
+        psi = np.empty((self.K, 2 * N * N))
+        lam = np.empty(self.K)
+        self._check(self._lib.smc_kl_table(self._h, level, _dptr(psi), _dptr(lam)))
+        return psi, lam

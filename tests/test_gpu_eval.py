@@ -1,0 +1,136 @@
+"""GPU parity of the likelihood path G_l(theta), Phi_l(theta) against the FP64 oracle.
+
+Tolerances: per-particle observation vectors to 1e-10 relative (max-norm) on the
+FP64 path, 1e-6 on the mixed path; Phi to the bound those G tolerances imply
+through Phi = 1/2 |y - G|^2 / sigma^2 (the residual y - G cancels digits of G).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import forward as ofwd
+from oracle import kl as okl
+from paper_1709_09763_gb300 import native
+from paper_1709_09763_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _data(name):
+    with open(os.path.join(GOLD, f"data_{name}.json")) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1709_09763_gb300 import build
+    build.build()
+
+
+def _oracle(N, w, theta, obs, y, sigma):
+    lv = ofwd.Level(N, w.corr_len, w.variance, w.K, obs)
+    G = lv.G_batch(theta)
+    return G, ofwd.potential(G, y, sigma)
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b), axis=-1) / np.max(np.abs(b), axis=-1)
+
+
+def _phi_ok(Phi, Phir, Gr, sigma, tol):
+    """Phi tolerance implied by a max-norm relative tolerance `tol` on G:
+    |dPhi| <= |y - G|_2 |dG|_2 / sigma^2 + |dG|_2^2 / (2 sigma^2), |y - G|_2 = sigma sqrt(2 Phi),
+    |dG|_2 <= tol * max|G| * sqrt(n_obs)."""
+    dG = tol * np.max(np.abs(Gr), axis=-1) * np.sqrt(Gr.shape[-1])
+    bound = np.sqrt(2 * Phir) * dG / sigma + 0.5 * (dG / sigma) ** 2
+    return np.all(np.abs(Phi - Phir) <= bound)
+
+
+def test_kl_table_matches_oracle():
+    w = wl.WORKLOADS["mls2mc_mixed_h8_64"]
+    d = _data(w.name)
+    h = native.Handle(w.inv_h, w.K, wl.obs_grid(7), d["y"], d["sigma"], corr_len=w.corr_len,
+                      precision=native.SMC_MIXED)
+    for l, N in enumerate(w.inv_h):
+        psi, lam = h.kl_table(l, N)
+        ref = okl.kl_table(N, w.corr_len, 1.0, w.K)
+        assert np.abs(psi - ref).max() < 1e-12
+        assert np.allclose(lam, [p[0] for p in okl.kl_pairs(w.corr_len, 1.0, w.K)], rtol=1e-13)
+
+
+@pytest.mark.parametrize("N", [4, 8, 16, 32])
+def test_fp64_path_parity(N):
+    w = wl.WORKLOADS["smc_fp64_h16"]
+    d = _data(w.name)
+    obs = wl.obs_grid(7)
+    theta = wl.particles(37, w.K, 100 + N)           # 37: not a multiple of a warp
+    h = native.Handle([N], w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, precision=native.SMC_FP64,
+                      rtol=1e-13)
+    G, Phi = h.eval_likelihood(0, theta)
+    Gr, Phir = _oracle(N, w, theta, obs, np.array(d["y"]), d["sigma"])
+    assert _rel(G, Gr).max() < 1e-10
+    assert _phi_ok(Phi, Phir, Gr, d["sigma"], 1e-10)
+
+
+@pytest.mark.parametrize("N", [4, 8, 16, 32, 64])
+def test_mixed_path_parity(N):
+    w = wl.WORKLOADS["mls2mc_mixed_h8_64"]
+    d = _data(w.name)
+    obs = wl.obs_grid(7)
+    theta = wl.particles(23 if N == 64 else 41, w.K, 200 + N)
+    h = native.Handle([N], w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, precision=native.SMC_MIXED)
+    G, Phi = h.eval_likelihood(0, theta)
+    Gr, Phir = _oracle(N, w, theta, obs, np.array(d["y"]), d["sigma"])
+    assert _rel(G, Gr).max() < 1e-6
+    assert _phi_ok(Phi, Phir, Gr, d["sigma"], 1e-6)
+
+
+def test_interpolated_observations_and_small_K():
+    """12 x 12 points at (i/13, j/13) are not mesh nodes: P1 barycentric interpolation; K = 1."""
+    obs = wl.obs_grid(12)
+    rng = np.random.default_rng(7)
+    for K, prec, tol in ((1, native.SMC_FP64, 1e-10), (5, native.SMC_MIXED, 1e-6)):
+        w = wl.Workload("t", (16,), 64, K, 0.2, 12, 0, 0)
+        y = rng.normal(0, 0.01, 144)
+        theta = wl.particles(9, K, 5)
+        h = native.Handle([16], K, obs, y, 0.01, corr_len=0.2, precision=prec)
+        G, Phi = h.eval_likelihood(0, theta)
+        Gr, Phir = _oracle(16, w, theta, obs, y, 0.01)
+        assert _rel(G, Gr).max() < tol
+
+
+def test_empty_and_single_batches():
+    w = wl.WORKLOADS["smc_fp64_h16"]
+    d = _data(w.name)
+    h = native.Handle([16], w.K, wl.obs_grid(7), d["y"], d["sigma"], corr_len=w.corr_len)
+    G, Phi = h.eval_likelihood(0, np.zeros((0, w.K)))
+    assert G.shape == (0, 49) and Phi.shape == (0,)
+    theta = np.zeros((1, w.K))                        # kappa == 1: the torsion problem
+    G, Phi = h.eval_likelihood(0, theta)
+    Gr, _ = _oracle(16, w, theta, wl.obs_grid(7), np.array(d["y"]), d["sigma"])
+    assert _rel(G, Gr).max() < 1e-10
+
+
+def test_full_size_sampled_parity():
+    """The benchmark's launch: J = 4000 particles on the 1/64 level (mixed); 6 sampled particles vs oracle."""
+    import torch
+    w = wl.WORKLOADS["mls2mc_mixed_h8_64"]
+    d = _data(w.name)
+    h = native.Handle(w.inv_h, w.K, wl.obs_grid(7), d["y"], d["sigma"], corr_len=w.corr_len,
+                      precision=native.SMC_MIXED)
+    theta = wl.particles(w.J, w.K, 4242)
+    th = torch.from_numpy(theta).cuda()
+    G = torch.empty((w.J, 49), dtype=torch.float64, device="cuda")
+    Phi = torch.empty(w.J, dtype=torch.float64, device="cuda")
+    it = torch.empty(w.J, dtype=torch.int32, device="cuda")
+    h.eval_likelihood_device(3, w.J, th.data_ptr(), G.data_ptr(), Phi.data_ptr(), it.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert int(it.min()) > 0
+    idx = np.array([0, 1, 777, 2048, 3998, 3999])
+    Gr, Phir = _oracle(64, w, theta[idx], wl.obs_grid(7), np.array(d["y"]), d["sigma"])
+    assert _rel(G.cpu().numpy()[idx], Gr).max() < 1e-6
+    assert np.all(np.isfinite(Phi.cpu().numpy()))
