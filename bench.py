@@ -1,0 +1,326 @@
+"""Benchmark of the MLS^2MC likelihood hot path on GB300.
+
+Workload: the MLS^2MC configuration of 4 levels h = 1/8, 1/16, 1/32, 1/64, K = 32 KL
+terms (correlation length 0.1), 49 observations on the 7 x 7 grid, J = 4000 particles,
+mixed precision (FP32 multigrid-PCG with extended-precision refinement). One step is
+one pass of the hot path over the particle batch: the likelihood G_l(theta), Phi_l(theta)
+of every particle on every level of the hierarchy (KL field, P1 solve, observation
+gather, Gaussian misfit).
+
+value: likelihood evaluations per second over the whole job (all levels, all ranks),
+inputs resident in device memory, L2 flushed between steps. e2e: the same step through
+the host-pointer C-ABI call (theta copied in from pinned host memory, G and Phi copied
+out every step). Multi-GPU: independent replicas per rank (no data-path collective).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "mls2mc_mixed_h8_64"
+
+
+def algorithmic_flops_per_eval(N, K, iters, passes):
+    """FP32 operations of one likelihood evaluation on level 1/h = N, counted from the algorithm.
+
+    Per fine interior node and CG iteration: V(1,1) fine-level work (red/black smoothing
+    before and after: 2 x (0.5 x 1 + 0.5 x 10), residual 11, restriction 2, prolongation
+    1.5) = 24.5, coarse levels 1/3 of that, CG vector work 22 -> 54.7. Per refinement pass:
+    the residual update in double-float arithmetic, ~100 FP32 operations per node. Set-up:
+    KL synthesis 2*K*E, exp E, coefficients ~10 per node.
+    """
+    n = (N - 1) ** 2
+    E = 2 * N * N
+    per_iter = (24.5 * 4.0 / 3.0 + 22.0) * n
+    return iters * per_iter + passes * 100.0 * n + 2.0 * K * E + E + 10.0 * (N + 1) ** 2
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_data():
+    with open(os.path.join(ROOT, "tests", "golden", f"data_{WORKLOAD}.json")) as f:
+        return json.load(f)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(seconds=12.0, per_step=False):
+    """The FP64 oracle timed on the host: round-robin over the 4 levels, one particle at a time."""
+    from oracle import forward as ofwd
+    from paper_1709_09763_gb300 import workloads as wl
+    w = wl.WORKLOADS[WORKLOAD]
+    d = load_data()
+    obs = wl.obs_grid(w.obs_per_side)
+    levels = [ofwd.Level(N, w.corr_len, w.variance, w.K, obs) for N in w.inv_h]
+    theta = wl.particles(64, w.K, 777)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        for lv in levels:
+            G = lv.G(theta[n % 64])
+            ofwd.potential(G, d["y"], d["sigma"])
+            n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 oracle evaluations ({n // 4} per level, levels 1/8..1/64, "
+                      f"sparse direct solve) in {dt:.1f} s on 1 host core"}
+
+
+def run_reference(args, rank):
+    """The oracle as the reference arm: each step a bounded sample of the workload on host cores."""
+    if rank != 0:
+        return
+    from oracle import forward as ofwd
+    from paper_1709_09763_gb300 import workloads as wl
+    w = wl.WORKLOADS[WORKLOAD]
+    d = load_data()
+    obs = wl.obs_grid(w.obs_per_side)
+    levels = [ofwd.Level(N, w.corr_len, w.variance, w.K, obs) for N in w.inv_h]
+    per_step = 2                       # particles per level per step (bounded sample)
+    theta = wl.particles(per_step * (args.steps + args.warmup), w.K, 99)
+
+    def step(s):
+        for lv in levels:
+            G = lv.G_batch(theta[s * per_step:(s + 1) * per_step])
+            ofwd.potential(G, d["y"], d["sigma"])
+    for s in range(args.warmup):
+        step(s)
+    t0 = time.perf_counter()
+    for s in range(args.warmup, args.warmup + args.steps):
+        step(s)
+    dt = (time.perf_counter() - t0) / args.steps
+    evals = per_step * len(levels)
+    value = evals / dt
+    line = {"impl": "reference", "metric": "likelihood evals/s per mesh level", "value": value,
+            "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "levels_inv_h": list(w.inv_h), "K": w.K, "n_obs": w.n_obs,
+                       "J": w.J, "precision": "fp64 oracle",
+                       "sample": f"{per_step} of the J particles per level per step"},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} particles x {len(levels)} levels per step"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1709_09763_gb300 import build, native
+    from paper_1709_09763_gb300 import workloads as wl
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    build.build()
+    w = wl.WORKLOADS[WORKLOAD]
+    d = load_data()
+    obs = wl.obs_grid(w.obs_per_side)
+    stream = torch.cuda.current_stream(dev)
+    h = native.Handle(w.inv_h, w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, variance=w.variance,
+                      precision=native.SMC_MIXED, stream=stream.cuda_stream)
+    J, L, n_obs = w.J, len(w.inv_h), w.n_obs
+    theta = torch.from_numpy(wl.particles(J, w.K, 1000 + rank)).to(dev)
+    G = torch.empty((L, J, n_obs), dtype=torch.float64, device=dev)
+    Phi = torch.empty((L, J), dtype=torch.float64, device=dev)
+    iters = torch.empty((L, J), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
+    s = stream.cuda_stream
+
+    def step(ev=None):
+        for l in range(L):
+            if ev is not None:
+                ev[l][0].record(stream)
+            h.eval_likelihood_device(l, J, theta.data_ptr(), G[l].data_ptr(), Phi[l].data_ptr(),
+                                     iters[l].data_ptr(), s)
+            if ev is not None:
+                ev[l][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    step_ms, level_ms = [], [[] for _ in range(L)]
+    for _ in range(args.steps):
+        flush.zero_()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(L)]
+        step(ev)
+        torch.cuda.synchronize(dev)
+        for l in range(L):
+            level_ms[l].append(ev[l][0].elapsed_time(ev[l][1]))
+        step_ms.append(ev[0][0].elapsed_time(ev[L - 1][1]))
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = float(np.mean(step_ms))
+    it = iters.cpu().numpy()
+    if (it <= 0).any():
+        raise RuntimeError("a forward solve did not converge inside the timed region")
+
+    # e2e: the host-pointer C-ABI call; pinned host theta in, G and Phi out, every step
+    th_host = torch.empty((J, w.K), dtype=torch.float64, pin_memory=True)
+    th_host.copy_(theta.cpu())
+    G_host = torch.empty((J, n_obs), dtype=torch.float64, pin_memory=True)
+    Phi_host = torch.empty(J, dtype=torch.float64, pin_memory=True)
+    thn, Gn, Pn = th_host.numpy(), G_host.numpy(), Phi_host.numpy()
+    ptr = lambda a: a.ctypes.data_as(native._dp)
+    lib = native.load()
+
+    def e2e_step():
+        for l in range(L):
+            rc = lib.smc_eval_likelihood(h._h, l, J, ptr(thn), ptr(Gn), ptr(Pn))
+            if rc != 0:
+                raise native.SmcError(rc, lib.smc_last_error(h._h).decode())
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e = float(np.mean(e2e_ms))
+
+    t = torch.tensor([ms, e2e] + [float(np.mean(x)) for x in level_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, e2e = float(t[0]), float(t[1])
+    lvl_ms = [float(x) for x in t[2:]]
+    if rank == 0:
+        peaks, src = measured_peaks()
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s, FMA = 2 flops
+        mean_it = float(it[L - 1].mean())
+        passes = 2.0
+        flops = algorithmic_flops_per_eval(w.inv_h[-1], w.K, mean_it, passes) * J
+        achieved = flops / (lvl_ms[-1] * 1e-3) / 1e12
+        total_evals = J * L * world
+        line = {
+            "metric": "likelihood evals/s per mesh level", "value": total_evals / (ms * 1e-3),
+            "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "levels_inv_h": list(w.inv_h), "K": w.K, "n_obs": n_obs, "J": J,
+                       "precision": "mixed", "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "per_level": {str(N): {"evals_per_s": J * world / (lm * 1e-3), "ms": lm,
+                                   "mean_cg_iters": float(it[l].mean())}
+                          for l, (N, lm) in enumerate(zip(w.inv_h, lvl_ms))},
+            "roofline": {"kernel": f"fem_eval_kernel<float,{w.inv_h[-1]},512>", "bound": "alu",
+                         "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": None,
+                         "peak_source": f"FP32 FMA issue rate: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "
+                                        f"(sm_max_mhz {src})"},
+            "e2e": {"value": total_evals / (e2e * 1e-3), "unit": "evals/s",
+                    "h2d_bytes_per_step": L * J * w.K * 8,
+                    "d2h_bytes_per_step": L * J * (n_obs * 8 + 8 + 4)},
+            "gpu_launches": args.steps * L,
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
