@@ -113,6 +113,75 @@ int smc_kl_table(const smc_handle* h, int level, double* psi, double* lambda);
 /* Sizes of a handle: K, n_obs, number of levels, J. Any pointer may be NULL. */
 int smc_sizes(const smc_handle* h, int* K, int* n_obs, int* n_levels, int* J);
 
+/* ---- the sampler (needs opts.J > 0) ------------------------------------------------------- */
+
+/* One record per importance-sampling update: an inverse temperature update (type 0, ITU) or one
+ * bridging step of a level update (type 1, LU) (Sec. 4.1). beta, zeta: the temperatures after the
+ * update (zeta = -1 for an ITU); delta: the chosen increment (Eq. Eq_cv_opt); cv: cv of its
+ * incremental weights (Sec. 3.4); cv_lu: the predictor of Sec. 4.4 when it decided this update
+ * (else -1); log_z_inc: log of the mean incremental weight (the evidence factor, Sec. 5.1.3);
+ * evals_per_level: cumulative forward solves per level after the update. */
+typedef struct {
+    int type;
+    int level;
+    double beta;
+    double zeta;
+    double delta;
+    double cv;
+    double cv_lu;
+    double log_z_inc;
+    double accept_rate;
+    double da_stage1_rate;
+    long long evals_per_level[8];
+    int n_bridge;
+    int status;            /* 1: the sampler had already reached beta = 1 on the finest level */
+} smc_stage_info;
+
+/* One step of the update scheme u of Eq. eq_updatescheme_final (Sec. 4.4): an ITU, or a whole LU
+ * with all its bridging steps. The first call draws the prior particles (Philox, see the
+ * library documentation) and evaluates Phi_1 on them. info (may be NULL) receives the last
+ * update's record; info->status = 1 when there was nothing left to do. */
+int smc_step(smc_handle* h, smc_stage_info* info);
+
+/* Steps until beta = 1 on the finest level, or max_updates steps (<= 0: no cap). */
+int smc_run(smc_handle* h, int max_updates, smc_stage_info* last);
+
+/* Sampler state: current level (0-based), beta, log of the evidence estimate (Sec. 5.1.3),
+ * number of importance-sampling updates so far, forward solves per level [8]. Any pointer may be NULL. */
+int smc_state(const smc_handle* h, int* level, double* beta, double* log_evidence, int* n_updates,
+              long long* evals_per_level);
+
+/* Copy up to max_records update records (oldest first) into out; *count = records available. */
+int smc_path(const smc_handle* h, int max_records, smc_stage_info* out, int* count);
+
+/* Mean and variance (population, 1/J) of each KL coefficient over the current equally weighted
+ * particles, and log Z (Sec. 5.1). mean, var: [K] host arrays, each may be NULL. */
+int smc_posterior_moments(smc_handle* h, double* mean, double* var, double* log_evidence);
+
+/* Copy the current particles theta [J][K] and their potential Phi on the current level [J]. */
+int smc_get_particles(const smc_handle* h, double* theta, double* phi);
+
+/* Replace the particles by theta [J][K] (host), restart the sampler at beta = 0 on level 0 and
+ * evaluate Phi_1 there (instead of drawing from the prior). */
+int smc_set_particles(smc_handle* h, const double* theta);
+
+/* ---- kernel-level entry points of the sampler's device steps -------------------------------- */
+
+/* The adaptive increment of Eq. Eq_cv_opt for incremental log-weights -delta * a_j, j < n <= J:
+ * the argmin over delta in [min(eps, dmax), dmax] of (cv(exp(-delta a)) - tau*)^2 (tau*, eps from
+ * the options). out3 = {delta, log mean_j exp(-delta a_j), cv at delta}. Host arrays. */
+int smc_next_increment(smc_handle* h, int n, const double* a, double dmax, double* out3);
+
+/* Systematic resampling of n <= J particles with unnormalised weights w (> 0) and offset U in
+ * [0, 1): anc[i] = min{ j : c_j > (U + i)/n }, c the cumulative normalised weights (c_{n-1} = 1). */
+int smc_systematic_resample(smc_handle* h, int n, const double* w, double U, int* anc);
+
+/* Philox4x32-10 draws of the library's layout with key opts.seed: out [J][K] standard normals
+ * (counter (k/2, j, event, purpose), Box-Muller), or out [J] uniforms in (0, 1] (counter (0, j, event,
+ * purpose), 1 - 53-bit uniform). */
+int smc_philox_normals(smc_handle* h, int J, int K, unsigned event, unsigned purpose, double* out);
+int smc_philox_uniforms(smc_handle* h, int J, unsigned event, unsigned purpose, double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,15 +1,411 @@
-// Host controller of the MLS^2MC sampler (Sec. 4.4): placeholder until the sampler lands.
+// Host controller of the MLS^2MC sampler (Sec. 4): the update scheme of Eq. eq_updatescheme_final
+// with the cv^LU predictor on the first J~ particles (Sec. 4.4). All per-particle work is queued on
+// the device (likelihood, increment search, resampling, pCN); the host reads back a few scalars
+// per update (the chosen increment, log mean weight, cv, accept count).
+//
+// Order of operations and random draws (Philox counter layout) are the library's convention:
+//   prior particles              event 0, purpose 1 (normals)
+//   resampling offset U          event = importance-sampling update index, purpose 4
+//   pCN step m (global counter)  event = m; normals purpose 2, accept uniform purpose 3
+// An ITU reweights by exp(-delta Phi_l), resamples, sets beta <- beta + delta (exactly 1 when
+// delta took the whole remaining step) and runs n_mcmc pCN steps for exp(-beta Phi_l) mu0. An LU
+// evaluates Phi_{l+1} on all particles (reusing the J~ predictor evaluations), then bridges
+// zeta = 0 -> 1 with weights exp(-beta dzeta (Phi_{l+1} - Phi_l)), resampling and pCN steps for
+// exp(-beta((1 - zeta) Phi_l + zeta Phi_{l+1})) mu0 that solve both levels per proposal.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "handle.h"
+#include "smc_device.h"
 
 namespace mls2mc {
 
-struct Sampler {};
+struct Sampler {
+    int J = 0, K = 0;
+    double *theta = nullptr, *theta_p = nullptr, *theta_t = nullptr;
+    double *phi_c = nullptr, *phi_f = nullptr, *phi_cp = nullptr, *phi_fp = nullptr;
+    double *phi_t0 = nullptr, *phi_t1 = nullptr;
+    double *a = nullptr, *cdf = nullptr, *scal = nullptr, *mom = nullptr;
+    int *anc = nullptr, *iters = nullptr;
+    unsigned long long* n_acc = nullptr;
+    IncWork inc;
+    // host-side state
+    bool started = false;
+    int level = 0;
+    double beta = 0.0, log_z = 0.0;
+    bool prev_lu = true;
+    long long stage = 0, mcmc_event = 0;
+    long long evals[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    std::vector<smc_stage_info> path;
+};
 
-int Handle::alloc_sampler() { return SMC_OK; }
+int Handle::alloc_sampler() {
+    const int J = opts.J;
+    if (J <= 0) return SMC_OK;
+    smp = new Sampler();
+    smp->J = J;
+    smp->K = K;
+    const size_t JK = (size_t)J * K;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    A((void**)&smp->theta, JK * 8);
+    A((void**)&smp->theta_p, JK * 8);
+    A((void**)&smp->theta_t, JK * 8);
+    for (double** p : {&smp->phi_c, &smp->phi_f, &smp->phi_cp, &smp->phi_fp, &smp->phi_t0, &smp->phi_t1, &smp->a,
+                       &smp->cdf})
+        A((void**)p, (size_t)J * 8);
+    A((void**)&smp->anc, (size_t)J * 4);
+    A((void**)&smp->iters, (size_t)J * 4);
+    A((void**)&smp->scal, 64);
+    A((void**)&smp->mom, (size_t)2 * K * 8);
+    A((void**)&smp->n_acc, 8);
+    A((void**)&smp->inc.state, sizeof(IncState));
+    A((void**)&smp->inc.partials, (size_t)kIncMaxBlocks * 4 * 8);
+    if (e != cudaSuccess) return fail(SMC_ENOMEM, "sampler buffers for J = %d: %s", J, cudaGetErrorString(e));
+    return SMC_OK;
+}
 
 void Handle::free_sampler() {
+    if (!smp) return;
+    for (void* p : {(void*)smp->theta, (void*)smp->theta_p, (void*)smp->theta_t, (void*)smp->phi_c,
+                    (void*)smp->phi_f, (void*)smp->phi_cp, (void*)smp->phi_fp, (void*)smp->phi_t0,
+                    (void*)smp->phi_t1, (void*)smp->a, (void*)smp->cdf, (void*)smp->scal, (void*)smp->mom,
+                    (void*)smp->anc, (void*)smp->iters, (void*)smp->n_acc, (void*)smp->inc.state,
+                    (void*)smp->inc.partials})
+        cudaFree(p);
     delete smp;
     smp = nullptr;
 }
 
+#define CK(expr)                                              \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return cuda_fail(_e, #expr);   \
+    } while (0)
+#define RC(expr)                        \
+    do {                                \
+        int _r = (expr);                \
+        if (_r != SMC_OK) return _r;    \
+    } while (0)
+
+// likelihood of n particles on one level, counted; non-convergence checked at the end of an update
+int Handle::smp_eval(int level, int n, const double* theta, double* phi) {
+    if (n <= 0) return SMC_OK;
+    RC(eval_device(level, n, theta, nullptr, phi, smp->iters, stream));
+    smp->evals[level] += n;
+    return check_iters(n);
+}
+
+int Handle::check_iters(int n) {
+    // cheap host check of the first slot only would miss failures; copy the counts (n ints)
+    std::vector<int> its((size_t)n);
+    CK(cudaMemcpyAsync(its.data(), smp->iters, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    for (int i = 0; i < n; ++i)
+        if (its[i] < 0) return fail(SMC_ENOCONV, "forward solve of particle %d did not converge", i);
+    return SMC_OK;
+}
+
+// adaptive increment on a[0..n): Eq. Eq_cv_opt; leaves IncState on the device and a copy in st
+int Handle::increment(const double* a, int n, double dmax, IncState& st) {
+    Sampler* S = smp;
+    CK(inc_start(a, n, dmax, opts.tau_star, opts.eps, S->inc, stream));
+    for (int rounds = 0; rounds * kIncChunk < kIncMaxIter + kIncChunk; ++rounds) {
+        CK(inc_iterate(a, n, kIncChunk, S->inc, stream));
+        CK(cudaMemcpyAsync(&st, S->inc.state, sizeof(IncState), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        if (st.done == -1) return fail(SMC_ESINGULAR, "non-finite incremental weights (numerical singularity)");
+        if (st.done) return SMC_OK;
+    }
+    return fail(SMC_ENOCONV, "increment search did not finish");
+}
+
+int Handle::reweight_resample(const double* a, double dmax, bool carry_fine, IncState& st) {
+    Sampler* S = smp;
+    RC(increment(a, S->J, dmax, st));
+    S->log_z += st.log_mean_w;
+    CK(resample_launch(a, nullptr, S->J, S->inc.state, -1.0, (uint32_t)S->stage, opts.seed, S->cdf, S->anc, stream));
+    CK(gather_launch(S->anc, S->J, K, S->theta, S->theta_t, S->phi_c, S->phi_t0, carry_fine ? S->phi_f : nullptr,
+                     S->phi_t1, stream));
+    std::swap(S->theta, S->theta_t);
+    std::swap(S->phi_c, S->phi_t0);
+    if (carry_fine) std::swap(S->phi_f, S->phi_t1);
+    return SMC_OK;
+}
+
+// n_mcmc pCN steps; zeta < 0: tempering target on `level`, else bridging target on level, level+1
+int Handle::mcmc(int level, double zeta, double& rate) {
+    Sampler* S = smp;
+    const double s = opts.s_pcn, c0 = std::sqrt(1.0 - s * s);
+    CK(cudaMemsetAsync(S->n_acc, 0, 8, stream));
+    for (int m = 0; m < opts.n_mcmc; ++m) {
+        const uint32_t ev = (uint32_t)S->mcmc_event;
+        CK(normals_launch(S->theta_p, S->J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
+        RC(smp_eval(level, S->J, S->theta_p, S->phi_cp));
+        if (zeta >= 0.0) RC(smp_eval(level + 1, S->J, S->theta_p, S->phi_fp));
+        CK(pcn_accept_launch(S->J, K, S->beta, zeta, ev, opts.seed, S->theta, S->theta_p, S->phi_c, S->phi_cp,
+                             S->phi_f, S->phi_fp, S->n_acc, stream));
+        S->mcmc_event += 1;
+    }
+    unsigned long long acc = 0;
+    CK(cudaMemcpyAsync(&acc, S->n_acc, 8, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    rate = opts.n_mcmc > 0 ? (double)acc / ((double)opts.n_mcmc * S->J) : 0.0;
+    return SMC_OK;
+}
+
+void Handle::record(int type, double zeta, const IncState& st, double rate, double cv_lu, smc_stage_info* info) {
+    Sampler* S = smp;
+    smc_stage_info r;
+    std::memset(&r, 0, sizeof r);
+    r.type = type;
+    r.level = S->level + (type == 1 ? 1 : 0);
+    r.beta = S->beta;
+    r.zeta = zeta;
+    r.delta = st.delta;
+    r.cv = st.cv;
+    r.cv_lu = cv_lu;
+    r.log_z_inc = st.log_mean_w;
+    r.accept_rate = rate;
+    for (int l = 0; l < 8; ++l) r.evals_per_level[l] = S->evals[l];
+    S->path.push_back(r);
+    if (info) *info = r;
+}
+
+int Handle::itu(double cv_lu, smc_stage_info* info) {
+    Sampler* S = smp;
+    IncState st;
+    RC(reweight_resample(S->phi_c, 1.0 - S->beta, false, st));
+    S->beta = (st.delta >= 1.0 - S->beta) ? 1.0 : S->beta + st.delta;
+    double rate = 0.0;
+    RC(mcmc(S->level, -1.0, rate));
+    record(0, -1.0, st, rate, cv_lu, info);
+    S->stage += 1;
+    S->prev_lu = false;
+    return SMC_OK;
+}
+
+int Handle::lu(int head, smc_stage_info* info) {
+    Sampler* S = smp;
+    const int l = S->level;
+    RC(smp_eval(l + 1, S->J - head, S->theta + (size_t)head * K, S->phi_f + head));
+    double zeta = 0.0;
+    int nb = 0;
+    IncState st;
+    double rate = 0.0;
+    while (zeta < 1.0) {
+        CK(lu_increment_launch(S->phi_c, S->phi_f, S->J, S->beta, S->a, stream));
+        RC(reweight_resample(S->a, 1.0 - zeta, true, st));
+        zeta = (st.delta >= 1.0 - zeta) ? 1.0 : zeta + st.delta;
+        RC(mcmc(l, zeta, rate));
+        record(1, zeta, st, rate, -1.0, info);
+        S->path.back().n_bridge = ++nb;
+        if (info) info->n_bridge = nb;
+        S->stage += 1;
+    }
+    S->level = l + 1;
+    std::swap(S->phi_c, S->phi_f);
+    S->prev_lu = true;
+    return SMC_OK;
+}
+
+int Handle::sampler_start() {
+    Sampler* S = smp;
+    CK(normals_launch(S->theta, S->J, K, 0u, kPurposePrior, opts.seed, nullptr, 0.0, 0.0, stream));
+    return sampler_restart();
+}
+
+int Handle::sampler_restart() {
+    Sampler* S = smp;
+    S->level = 0;
+    S->beta = 0.0;
+    S->log_z = 0.0;
+    S->prev_lu = true;
+    S->stage = 0;
+    S->mcmc_event = 0;
+    for (auto& v : S->evals) v = 0;
+    S->path.clear();
+    S->started = true;
+    return smp_eval(0, S->J, S->theta, S->phi_c);
+}
+
+bool Handle::sampler_done() const {
+    return smp && smp->started && smp->beta >= 1.0 && smp->level == (int)levels.size() - 1;
+}
+
+int Handle::step(smc_stage_info* info) {
+    if (!smp) return fail(SMC_EINVAL, "handle was created with J = 0");
+    Sampler* S = smp;
+    if (!S->started) RC(sampler_start());
+    if (info) {
+        std::memset(info, 0, sizeof *info);
+        info->status = 1;
+    }
+    if (sampler_done()) return SMC_OK;
+    const int L = (int)levels.size();
+    if (S->level == L - 1) return itu(-1.0, info);
+    if (S->beta >= 1.0) return lu(0, info);       // beta = 1: only the level can be raised
+    if (S->prev_lu) return itu(-1.0, info);
+    const int jt = std::min(opts.J_tilde, S->J);
+    RC(smp_eval(S->level + 1, jt, S->theta, S->phi_f));
+    CK(cv_lu_launch(S->phi_c, S->phi_f, jt, S->beta, S->scal, stream));
+    double cv_lu = 0.0;
+    CK(cudaMemcpyAsync(&cv_lu, S->scal, 8, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (cv_lu < opts.tau_lu) return itu(cv_lu, info);
+    return lu(jt, info);
+}
+
 }  // namespace mls2mc
+
+using namespace mls2mc;
+
+extern "C" {
+
+int smc_step(smc_handle* hh, smc_stage_info* info) {
+    if (!hh) return SMC_EINVAL;
+    return reinterpret_cast<Handle*>(hh)->step(info);
+}
+
+int smc_run(smc_handle* hh, int max_updates, smc_stage_info* last) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->smp) return h->fail(SMC_EINVAL, "handle was created with J = 0");
+    smc_stage_info info;
+    std::memset(&info, 0, sizeof info);
+    for (int u = 0; (max_updates <= 0 || u < max_updates); ++u) {
+        if (h->smp->started && h->sampler_done()) break;
+        int rc = h->step(&info);
+        if (rc != SMC_OK) return rc;
+    }
+    if (last) *last = info;
+    return SMC_OK;
+}
+
+int smc_state(const smc_handle* hh, int* level, double* beta, double* log_evidence, int* n_updates,
+              long long* evals_per_level) {
+    if (!hh) return SMC_EINVAL;
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    if (!h->smp) return SMC_EINVAL;
+    const Sampler* S = h->smp;
+    if (level) *level = S->level;
+    if (beta) *beta = S->beta;
+    if (log_evidence) *log_evidence = S->log_z;
+    if (n_updates) *n_updates = (int)S->path.size();
+    if (evals_per_level)
+        for (int l = 0; l < 8; ++l) evals_per_level[l] = S->evals[l];
+    return SMC_OK;
+}
+
+int smc_path(const smc_handle* hh, int max_records, smc_stage_info* out, int* count) {
+    if (!hh) return SMC_EINVAL;
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    if (!h->smp) return SMC_EINVAL;
+    const int n = (int)h->smp->path.size();
+    if (count) *count = n;
+    if (out)
+        for (int i = 0; i < n && i < max_records; ++i) out[i] = h->smp->path[i];
+    return SMC_OK;
+}
+
+int smc_posterior_moments(smc_handle* hh, double* mean, double* var, double* log_evidence) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->smp || !h->smp->started) return h->fail(SMC_EINVAL, "sampler has not run");
+    Sampler* S = h->smp;
+    cudaError_t e = moments_launch(S->theta, S->J, h->K, S->mom, S->mom + h->K, h->stream);
+    std::vector<double> m((size_t)2 * h->K);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.data(), S->mom, m.size() * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "posterior moments");
+    if (mean) std::memcpy(mean, m.data(), 8 * (size_t)h->K);
+    if (var) std::memcpy(var, m.data() + h->K, 8 * (size_t)h->K);
+    if (log_evidence) *log_evidence = S->log_z;
+    return SMC_OK;
+}
+
+int smc_get_particles(const smc_handle* hh, double* theta, double* phi) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = const_cast<Handle*>(reinterpret_cast<const Handle*>(hh));
+    if (!h->smp || !h->smp->started) return h->fail(SMC_EINVAL, "sampler has not run");
+    Sampler* S = h->smp;
+    cudaError_t e = cudaSuccess;
+    if (theta) e = cudaMemcpyAsync(theta, S->theta, (size_t)S->J * h->K * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (phi && e == cudaSuccess) e = cudaMemcpyAsync(phi, S->phi_c, (size_t)S->J * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "copy particles");
+    return SMC_OK;
+}
+
+int smc_set_particles(smc_handle* hh, const double* theta) {
+    if (!hh || !theta) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->smp) return h->fail(SMC_EINVAL, "handle was created with J = 0");
+    Sampler* S = h->smp;
+    cudaError_t e = cudaMemcpyAsync(S->theta, theta, (size_t)S->J * h->K * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "copy particles");
+    return h->sampler_restart();
+}
+
+// ---- kernel-level entry points -----------------------------------------------------------------
+int smc_next_increment(smc_handle* hh, int n, const double* a, double dmax, double* out3) {
+    if (!hh || !a || !out3 || n <= 0) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->smp || n > h->smp->J) return h->fail(SMC_EINVAL, "n must be in [1, J]");
+    Sampler* S = h->smp;
+    cudaError_t e = cudaMemcpyAsync(S->a, a, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "copy a");
+    IncState st;
+    int rc = h->increment(S->a, n, dmax, st);
+    if (rc != SMC_OK) return rc;
+    out3[0] = st.delta;
+    out3[1] = st.log_mean_w;
+    out3[2] = st.cv;
+    return SMC_OK;
+}
+
+int smc_systematic_resample(smc_handle* hh, int n, const double* w, double U, int* anc) {
+    if (!hh || !w || !anc || n <= 0 || !(U >= 0.0 && U < 1.0)) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->smp || n > h->smp->J) return h->fail(SMC_EINVAL, "n must be in [1, J]");
+    Sampler* S = h->smp;
+    cudaError_t e = cudaMemcpyAsync(S->a, w, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = resample_launch(nullptr, S->a, n, S->inc.state, U, 0u, h->opts.seed, S->cdf, S->anc, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(anc, S->anc, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "systematic resampling");
+    return SMC_OK;
+}
+
+int smc_philox_normals(smc_handle* hh, int J, int K, unsigned event, unsigned purpose, double* out) {
+    if (!hh || !out || J <= 0 || K <= 0) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d, (size_t)J * K * 8);
+    if (e == cudaSuccess) e = normals_launch(d, J, K, event, purpose, h->opts.seed, nullptr, 0.0, 0.0, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)J * K * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return h->cuda_fail(e, "philox normals");
+    return SMC_OK;
+}
+
+int smc_philox_uniforms(smc_handle* hh, int J, unsigned event, unsigned purpose, double* out) {
+    if (!hh || !out || J <= 0) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d, (size_t)J * 8);
+    if (e == cudaSuccess) e = uniforms_launch(d, J, event, purpose, h->opts.seed, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)J * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return h->cuda_fail(e, "philox uniforms");
+    return SMC_OK;
+}
+
+}  // extern "C"

@@ -47,7 +47,7 @@ __host__ __device__ constexpr int arena_size(int N) { return N < 2 ? 0 : 6 * lvl
 
 template <typename Real>
 struct Lv {
-    Real *aE, *aN, *D, *e, *res, *rhs;
+    Real *aE, *aN, *iD, *e, *res, *rhs;   // iD: inverse of the stencil diagonal
 };
 
 template <typename Real, int N, int NL>
@@ -61,6 +61,15 @@ __device__ __forceinline__ Lv<Real> level_ptrs(Real* arena) {
 template <typename Real, int S>
 __device__ __forceinline__ Real offsum(const Real* aE, const Real* aN, const Real* v, int n) {
     return aE[n] * v[n + 1] + aE[n - 1] * v[n - 1] + aN[n] * v[n + S] + aN[n - S] * v[n - S];
+}
+
+// (A v)_n in edge form: sum over the four edges at n of a_e (v_n - v_nb); the diagonal is
+// the sum of the edge weights by construction
+template <typename Real, int S>
+__device__ __forceinline__ Real stencil_apply(const Real* aE, const Real* aN, const Real* v, int n) {
+    const Real vn = v[n];
+    return aE[n] * (vn - v[n + 1]) + aE[n - 1] * (vn - v[n - 1]) + aN[n] * (vn - v[n + S]) +
+           aN[n - S] * (vn - v[n - S]);
 }
 
 // ---- block reductions (every thread gets the same result, summed in a fixed order) ----
@@ -102,7 +111,7 @@ __device__ __forceinline__ void smooth_first_red(const Lv<Real>& L) {
     constexpr int M = NL - 1, S = NL + 1;
     for (int idx = threadIdx.x; idx < M * M; idx += T) {
         const int j = idx / M + 1, i = idx - (j - 1) * M + 1, n = j * S + i;
-        L.e[n] = (((i + j) & 1) == 0) ? L.rhs[n] / L.D[n] : Real(0);
+        L.e[n] = (((i + j) & 1) == 0) ? L.rhs[n] * L.iD[n] : Real(0);
     }
 }
 
@@ -111,7 +120,7 @@ __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
     constexpr int M = NL - 1, S = NL + 1;
     for (int idx = threadIdx.x; idx < M * M; idx += T) {
         const int j = idx / M + 1, i = idx - (j - 1) * M + 1, n = j * S + i;
-        if (((i + j) & 1) == color) L.e[n] = (L.rhs[n] + offsum<Real, S>(L.aE, L.aN, L.e, n)) / L.D[n];
+        if (((i + j) & 1) == color) L.e[n] = (L.rhs[n] + offsum<Real, S>(L.aE, L.aN, L.e, n)) * L.iD[n];
     }
 }
 
@@ -120,7 +129,7 @@ __device__ __forceinline__ void residual(const Lv<Real>& L) {
     constexpr int M = NL - 1, S = NL + 1;
     for (int idx = threadIdx.x; idx < M * M; idx += T) {
         const int j = idx / M + 1, i = idx - (j - 1) * M + 1, n = j * S + i;
-        L.res[n] = L.rhs[n] - (L.D[n] * L.e[n] - offsum<Real, S>(L.aE, L.aN, L.e, n));
+        L.res[n] = L.rhs[n] - stencil_apply<Real, S>(L.aE, L.aN, L.e, n);
     }
 }
 
@@ -163,7 +172,7 @@ template <typename Real, int N, int NL, int T>
 __device__ void vcycle_coarse(Real* arena) {
     Lv<Real> L = level_ptrs<Real, N, NL>(arena);
     if constexpr (NL == 2) {
-        if (threadIdx.x == 0) L.e[4] = L.rhs[4] / L.D[4];   // single interior node (1,1), S = 3
+        if (threadIdx.x == 0) L.e[4] = L.rhs[4] * L.iD[4];   // single interior node (1,1), S = 3
         __syncthreads();
     } else {
         Lv<Real> C = level_ptrs<Real, N, NL / 2>(arena);
@@ -213,7 +222,7 @@ __device__ __forceinline__ void build_diag(const Lv<Real>& L) {
         const int j = n / S, i = n - j * S;
         Real d = 0;
         if (i > 0 && j > 0 && i < NL && j < NL) d = L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S];
-        L.D[n] = (d == Real(0)) ? Real(1) : d;   // boundary entries are never used as divisors
+        L.iD[n] = (d == Real(0)) ? Real(1) : Real(1) / d;   // boundary entries are never used
     }
 }
 
@@ -300,18 +309,20 @@ fem_eval_kernel(FemArgs a) {
     }
     __syncthreads();
 
-    // fine nodes owned by this thread
-    int node[NPT];
-    bool valid[NPT], red[NPT];
+    // fine nodes owned by this thread, one packed int each: bits 0-12 padded node index n,
+    // 13-23 the coarse node c under it, 24-25 which second coarse node its P1
+    // interpolation averages with (0 none, 1 c+1, 2 c+SC, 3 c+SC+1), 26 red, 27 valid
+    constexpr int SC = N / 2 + 1;
+    int slot[NPT];
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
         const int idx = tid + T * q;
-        valid[q] = idx < NI;
-        const int jj = (valid[q] ? idx : 0) / M + 1, ii = (valid[q] ? idx : 0) - (jj - 1) * M + 1;
-        node[q] = jj * S + ii;
-        red[q] = ((ii + jj) & 1) == 0;
+        const int v = idx < NI;
+        const int jj = (v ? idx : 0) / M + 1, ii = (v ? idx : 0) - (jj - 1) * M + 1;
+        const int c = (jj >> 1) * SC + (ii >> 1);
+        const int code = (ii & 1) + 2 * (jj & 1);
+        slot[q] = (jj * S + ii) | (c << 13) | (code << 24) | ((((ii + jj) & 1) == 0) << 26) | (v << 27);
     }
-
     // right-hand side h^2 (f = 1), exact in FP32 for N a power of two
     const Real h2 = Real(1) / (Real(N) * Real(N));
     // solution x and residual r of the refinement: FP64, or double-float pairs (hi + lo)
@@ -321,7 +332,7 @@ fem_eval_kernel(FemArgs a) {
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
         xh[q] = xl[q] = rl[q] = Real(0);
-        rh[q] = valid[q] ? h2 : Real(0);
+        rh[q] = ((slot[q] >> 27) & 1) ? h2 : Real(0);
     }
     const Real bnorm2 = Real(NI) * h2 * h2;
     const Real stop_outer = Real(a.rtol * a.rtol) * bnorm2;
@@ -350,20 +361,20 @@ fem_eval_kernel(FemArgs a) {
             // z = M^{-1} r: V(1,1) cycle with the fine rhs held in registers
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
-                if (valid[q]) F.e[node[q]] = red[q] ? r[q] / F.D[node[q]] : Real(0);
+                if (((slot[q] >> 27) & 1)) F.e[(slot[q] & 0x1fff)] = ((slot[q] >> 26) & 1) ? r[q] * F.iD[(slot[q] & 0x1fff)] : Real(0);
             __syncthreads();
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
-                if (valid[q] && !red[q]) {
-                    const int n = node[q];
-                    F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) / F.D[n];
+                if (((slot[q] >> 27) & 1) && !((slot[q] >> 26) & 1)) {
+                    const int n = (slot[q] & 0x1fff);
+                    F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
                 }
             __syncthreads();
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
-                if (valid[q]) {
-                    const int n = node[q];
-                    F.res[n] = r[q] - (F.D[n] * F.e[n] - offsum<Real, S>(F.aE, F.aN, F.e, n));
+                if (((slot[q] >> 27) & 1)) {
+                    const int n = (slot[q] & 0x1fff);
+                    F.res[n] = r[q] - stencil_apply<Real, S>(F.aE, F.aN, F.e, n);
                 }
             __syncthreads();
             restrict_to<Real, N / 2, T>(F.res, C1.rhs);
@@ -371,29 +382,29 @@ fem_eval_kernel(FemArgs a) {
             vcycle_coarse<Real, N, N / 2, T>(arena);
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
-                if (valid[q]) {
-                    const int n = node[q];
-                    const int jj = n / S, ii = n - jj * S;
-                    F.e[n] += prolong_at<Real, N / 2>(C1.e, ii, jj);
+                if (((slot[q] >> 27) & 1)) {
+                    const int n = (slot[q] & 0x1fff);
+                    const int c = (slot[q] >> 13) & 0x7ff, code = (slot[q] >> 24) & 3;
+                    F.e[n] += Real(0.5) * (C1.e[c] + C1.e[c + (code & 1) + (code >> 1) * SC]);
                 }
             __syncthreads();
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
-                if (valid[q] && !red[q]) {
-                    const int n = node[q];
-                    F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) / F.D[n];
+                if (((slot[q] >> 27) & 1) && !((slot[q] >> 26) & 1)) {
+                    const int n = (slot[q] & 0x1fff);
+                    F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
                 }
             __syncthreads();
             Real rz_new = 0;
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
-                if (valid[q] && red[q]) {
-                    const int n = node[q];
-                    F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) / F.D[n];
+                if (((slot[q] >> 27) & 1) && ((slot[q] >> 26) & 1)) {
+                    const int n = (slot[q] & 0x1fff);
+                    F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
                 }
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
-                if (valid[q]) rz_new += r[q] * F.e[node[q]];
+                if (((slot[q] >> 27) & 1)) rz_new += r[q] * F.e[(slot[q] & 0x1fff)];
             block_sum<T>(rz_new, red_buf[parity]);
             parity ^= 1;
             // p = z + beta p
@@ -401,7 +412,7 @@ fem_eval_kernel(FemArgs a) {
             rz = rz_new;
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
-                if (valid[q]) P[node[q]] = (it == 0) ? F.e[node[q]] : F.e[node[q]] + beta * P[node[q]];
+                if (((slot[q] >> 27) & 1)) P[(slot[q] & 0x1fff)] = (it == 0) ? F.e[(slot[q] & 0x1fff)] : F.e[(slot[q] & 0x1fff)] + beta * P[(slot[q] & 0x1fff)];
             __syncthreads();
             // q = A p, alpha = rz / p.q
             Real qv[NPT];
@@ -409,9 +420,9 @@ fem_eval_kernel(FemArgs a) {
 #pragma unroll
             for (int q = 0; q < NPT; ++q) {
                 qv[q] = Real(0);
-                if (valid[q]) {
-                    const int n = node[q];
-                    qv[q] = F.D[n] * P[n] - offsum<Real, S>(F.aE, F.aN, P, n);
+                if (((slot[q] >> 27) & 1)) {
+                    const int n = (slot[q] & 0x1fff);
+                    qv[q] = stencil_apply<Real, S>(F.aE, F.aN, P, n);
                     pq += P[n] * qv[q];
                 }
             }
@@ -421,8 +432,8 @@ fem_eval_kernel(FemArgs a) {
             Real rr = 0;
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
-                if (valid[q]) {
-                    d[q] = fma(alpha, P[node[q]], d[q]);
+                if (((slot[q] >> 27) & 1)) {
+                    d[q] = fma(alpha, P[(slot[q] & 0x1fff)], d[q]);
                     r[q] = fma(-alpha, qv[q], r[q]);
                     rr += r[q] * r[q];
                 }
@@ -437,13 +448,13 @@ fem_eval_kernel(FemArgs a) {
         // (the rounded working-precision diagonal would act as a spurious reaction term).
 #pragma unroll
         for (int q = 0; q < NPT; ++q)
-            if (valid[q]) P[node[q]] = d[q];
+            if (((slot[q] >> 27) & 1)) P[(slot[q] & 0x1fff)] = d[q];
         __syncthreads();
         Real rr_out = 0;
 #pragma unroll
         for (int q = 0; q < NPT; ++q)
-            if (valid[q]) {
-                const int n = node[q];
+            if (((slot[q] >> 27) & 1)) {
+                const int n = (slot[q] & 0x1fff);
                 const Real di = P[n];
                 const Real w[4] = {F.aE[n], F.aE[n - 1], F.aN[n], F.aN[n - S]};
                 const Real dj[4] = {P[n + 1], P[n - 1], P[n + S], P[n - S]};
@@ -480,7 +491,7 @@ fem_eval_kernel(FemArgs a) {
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < NPT; ++q)
-        if (valid[q]) xs[node[q]] = (double)xh[q] + (double)xl[q];
+        if (((slot[q] >> 27) & 1)) xs[(slot[q] & 0x1fff)] = (double)xh[q] + (double)xl[q];
     __syncthreads();
     double misfit = 0.0;
     for (int o = tid; o < a.n_obs; o += T) {

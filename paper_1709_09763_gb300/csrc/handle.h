@@ -49,6 +49,19 @@ struct Handle {
     int eval_device(int level, int n, const double* theta, double* G, double* Phi, int* iters, cudaStream_t st);
     int alloc_sampler();
     void free_sampler();
+    // sampler (controller.cpp)
+    int smp_eval(int level, int n, const double* theta, double* phi);
+    int check_iters(int n);
+    int increment(const double* a, int n, double dmax, struct IncState& st);
+    int reweight_resample(const double* a, double dmax, bool carry_fine, struct IncState& st);
+    int mcmc(int level, double zeta, double& rate);
+    void record(int type, double zeta, const struct IncState& st, double rate, double cv_lu, smc_stage_info* info);
+    int itu(double cv_lu, smc_stage_info* info);
+    int lu(int head, smc_stage_info* info);
+    int sampler_start();
+    int sampler_restart();
+    bool sampler_done() const;
+    int step(smc_stage_info* info);
 };
 
 // G = A theta and Phi for the linear test forward model (smc_kernels.cu)

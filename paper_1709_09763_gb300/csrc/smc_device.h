@@ -1,0 +1,57 @@
+// Device state and launch wrappers of the sampler kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+namespace mls2mc {
+
+// Philox counter word 3: what the draw is for (the library's draw layout)
+constexpr uint32_t kPurposePrior = 1;
+constexpr uint32_t kPurposePcnXi = 2;
+constexpr uint32_t kPurposePcnU = 3;
+constexpr uint32_t kPurposeResample = 4;
+constexpr uint32_t kPurposeDaU = 5;
+
+constexpr int kIncMaxBlocks = 64;     // partial-sum blocks of the increment search
+constexpr int kIncMaxIter = 200;      // cap on decisions of one search
+constexpr int kIncChunk = 12;         // decisions queued between host checks
+
+// state of one adaptive-increment search, resident in device memory
+struct IncState {
+    double amin, dmin, dmax, target, tau;
+    double lo, hi, x;
+    int phase, iter, done, pad;
+    // results
+    double delta, log_mean_w, cv, S1;
+};
+
+struct IncWork {
+    IncState* state = nullptr;   // device
+    double* partials = nullptr;  // device [kIncMaxBlocks * 4]
+};
+
+int inc_blocks(int n);
+cudaError_t inc_start(const double* a, int n, double dmax, double tau, double eps, IncWork& w, cudaStream_t st);
+cudaError_t inc_iterate(const double* a, int n, int iters, IncWork& w, cudaStream_t st);
+
+cudaError_t normals_launch(double* out, int J, int K, uint32_t event, uint32_t purpose, uint64_t seed,
+                           const double* base, double c0, double c1, cudaStream_t st);
+cudaError_t uniforms_launch(double* out, int J, uint32_t event, uint32_t purpose, uint64_t seed, cudaStream_t st);
+// U >= 0: use it as the offset; U < 0: draw it from Philox (event, kPurposeResample)
+cudaError_t resample_launch(const double* a, const double* w_in, int n, const IncState* state, double U,
+                            uint32_t event, uint64_t seed, double* cdf, int* anc, cudaStream_t st);
+cudaError_t gather_launch(const int* anc, int n, int K, const double* th_in, double* th_out, const double* p0_in,
+                          double* p0_out, const double* p1_in, double* p1_out, cudaStream_t st);
+cudaError_t lu_increment_launch(const double* phi_c, const double* phi_f, int n, double beta, double* a,
+                                cudaStream_t st);
+cudaError_t cv_lu_launch(const double* phi_c, const double* phi_f, int n, double beta, double* out, cudaStream_t st);
+// zeta < 0: tempering target beta * Phi_c; else bridging target beta ((1 - zeta) Phi_c + zeta Phi_f)
+cudaError_t pcn_accept_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, double* theta,
+                              const double* theta_p, double* phi_c, const double* phi_cp, double* phi_f,
+                              const double* phi_fp, unsigned long long* n_acc, cudaStream_t st);
+cudaError_t moments_launch(const double* theta, int n, int K, double* mean, double* var, cudaStream_t st);
+
+}  // namespace mls2mc

@@ -49,7 +49,13 @@ class StageInfo(ctypes.Structure):
                 ("zeta", ctypes.c_double), ("delta", ctypes.c_double), ("cv", ctypes.c_double),
                 ("cv_lu", ctypes.c_double), ("log_z_inc", ctypes.c_double),
                 ("accept_rate", ctypes.c_double), ("da_stage1_rate", ctypes.c_double),
-                ("evals_per_level", ctypes.c_longlong * 8), ("status", ctypes.c_int)]
+                ("evals_per_level", ctypes.c_longlong * 8), ("n_bridge", ctypes.c_int), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "evals_per_level"}
+        d["evals_per_level"] = list(self.evals_per_level)
+        d["kind"] = "ITU" if self.type == 0 else "LU"
+        return d
 
 
 _lib = None
@@ -66,6 +72,18 @@ SIGNATURES = {
                                                   ctypes.c_void_p]),
     "smc_kl_table": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, _dp]),
     "smc_sizes": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip, _ip, _ip]),
+    "smc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(StageInfo)]),
+    "smc_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(StageInfo)]),
+    "smc_state": (ctypes.c_int, [ctypes.c_void_p, _ip, _dp, _dp, _ip, ctypes.POINTER(ctypes.c_longlong)]),
+    "smc_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(StageInfo), _ip]),
+    "smc_posterior_moments": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp]),
+    "smc_get_particles": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
+    "smc_set_particles": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "smc_next_increment": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_double, _dp]),
+    "smc_systematic_resample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_double, _ip]),
+    "smc_philox_normals": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint,
+                                          ctypes.c_uint, _dp]),
+    "smc_philox_uniforms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_uint, _dp]),
 }
 
 
@@ -153,6 +171,69 @@ class Handle:
         """Device pointers (ints, e.g. torch tensor data_ptr()); queued on stream, no wait."""
         self._check(self._lib.smc_eval_likelihood_device(self._h, level, n, theta_ptr, G_ptr, Phi_ptr,
                                                          iters_ptr, stream))
+
+    # ---- sampler ------------------------------------------------------------------------
+    def step(self):
+        info = StageInfo()
+        self._check(self._lib.smc_step(self._h, ctypes.byref(info)))
+        return info.as_dict()
+
+    def run(self, max_updates=0):
+        info = StageInfo()
+        self._check(self._lib.smc_run(self._h, int(max_updates), ctypes.byref(info)))
+        return info.as_dict()
+
+    def state(self):
+        lvl, beta, lz, nu = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        ev = (ctypes.c_longlong * 8)()
+        self._check(self._lib.smc_state(self._h, ctypes.byref(lvl), ctypes.byref(beta), ctypes.byref(lz),
+                                        ctypes.byref(nu), ev))
+        return dict(level=lvl.value, beta=beta.value, log_z=lz.value, n_updates=nu.value, evals=list(ev))
+
+    def path(self):
+        cnt = ctypes.c_int()
+        self._check(self._lib.smc_path(self._h, 0, None, ctypes.byref(cnt)))
+        arr = (StageInfo * max(cnt.value, 1))()
+        self._check(self._lib.smc_path(self._h, cnt.value, arr, ctypes.byref(cnt)))
+        return [arr[i].as_dict() for i in range(cnt.value)]
+
+    def posterior_moments(self):
+        m, v, lz = np.empty(self.K), np.empty(self.K), ctypes.c_double()
+        self._check(self._lib.smc_posterior_moments(self._h, _dptr(m), _dptr(v), ctypes.byref(lz)))
+        return m, v, lz.value
+
+    def particles(self):
+        th, ph = np.empty((self.J, self.K)), np.empty(self.J)
+        self._check(self._lib.smc_get_particles(self._h, _dptr(th), _dptr(ph)))
+        return th, ph
+
+    def set_particles(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(self.J, self.K)
+        self._check(self._lib.smc_set_particles(self._h, _dptr(theta)))
+
+    # ---- kernel-level entry points ---------------------------------------------------------
+    def next_increment(self, a, dmax):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        out = np.empty(3)
+        self._check(self._lib.smc_next_increment(self._h, a.size, _dptr(a), float(dmax), _dptr(out)))
+        return float(out[0]), float(out[1]), float(out[2])
+
+    def systematic_resample(self, w, U):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        anc = np.empty(w.size, dtype=np.int32)
+        self._check(self._lib.smc_systematic_resample(self._h, w.size, _dptr(w), float(U),
+                                                      anc.ctypes.data_as(_ip)))
+        return anc
+
+    def philox_normals(self, J, K, event, purpose):
+        out = np.empty((J, K))
+        self._check(self._lib.smc_philox_normals(self._h, J, K, event, purpose, _dptr(out)))
+        return out
+
+    def philox_uniforms(self, J, event, purpose):
+        out = np.empty(J)
+        self._check(self._lib.smc_philox_uniforms(self._h, J, event, purpose, _dptr(out)))
+        return out
 
     def kl_table(self, level, N):
         psi = np.empty((self.K, 2 * N * N))

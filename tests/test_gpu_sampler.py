@@ -1,0 +1,159 @@
+"""GPU parity of the sampler steps (increment search, resampling, Philox draws, pCN) and of the
+whole MLS^2MC / single-level SMC sampler against the FP64 oracle.
+
+The oracle and the library use the same counter-based draw layout, so with one seed both consume
+identical random numbers: on the FP64 path the whole update path (beta, zeta schedule, evidence,
+particles) must agree to rounding, and statistically (3 Monte Carlo standard errors) against the
+closed-form linear-Gaussian posterior.
+"""
+import numpy as np
+import pytest
+
+from oracle import gaussian, philox, smc
+from oracle import forward as ofwd
+from oracle.forward import potential
+from paper_1709_09763_gb300 import native
+from paper_1709_09763_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1709_09763_gb300 import build
+    build.build()
+
+
+def _linear(K=3, n=5, sigma=0.5, seed=0, levels=1):
+    rng = np.random.default_rng(seed)
+    A = rng.normal(0, 1, (n, K))
+    y = A @ rng.normal(0, 1, K) + sigma * rng.normal(0, 1, n)
+    B = np.random.default_rng(seed + 100).normal(0, 1, A.shape)
+    As = np.stack([A + 4.0 ** -(l + 1) * B * 8 for l in range(levels)]) if levels > 1 else A[None]
+    return As, y, sigma
+
+
+def _handle_linear(As, y, sigma, J, **kw):
+    L, n, K = As.shape
+    obs = np.full((n, 2), 0.5)
+    return native.Handle(list(range(4, 4 + L)), K, obs, y, sigma, J=J, linear_A=As, **kw)
+
+
+def test_philox_draws_match_oracle():
+    As, y, s = _linear()
+    h = _handle_linear(As, y, s, J=8, seed=0xDEADBEEF12345)
+    for (J, K, ev, pu) in [(37, 5, 0, 1), (3, 16, 123456, 2), (1000, 1, 7, 3)]:
+        g = h.philox_normals(J, K, ev, pu)
+        o = philox.normals(J, K, ev, pu, 0xDEADBEEF12345)
+        assert np.allclose(g, o, rtol=1e-14, atol=1e-15)
+    u = h.philox_uniforms(513, 99, philox.PURPOSE_PCN_U)
+    assert np.array_equal(u, philox.uniforms_open(513, 99, philox.PURPOSE_PCN_U, 0xDEADBEEF12345))
+
+
+def test_next_increment_matches_oracle():
+    As, y, s = _linear()
+    h = _handle_linear(As, y, s, J=5000, tau_star=1.0, eps=1e-6)
+    rng = np.random.default_rng(3)
+    for n, dmax in [(5000, 1.0), (1000, 0.37), (33, 1.0), (1, 1.0)]:
+        a = rng.gamma(2.0, 300.0, size=n)
+        d, lm, c = h.next_increment(a, dmax)
+        dref = smc.next_increment(a, dmax, 1.0, 1e-6)
+        assert d == pytest.approx(dref, rel=1e-12), (n, dmax)
+        assert lm == pytest.approx(smc.log_mean_weight(a, dref), rel=1e-12, abs=1e-13)
+        assert c == pytest.approx(smc.cv_of_increment(a, dref), rel=1e-9, abs=1e-12)
+    # the whole remaining step when cv stays below the target; equal potentials
+    assert h.next_increment(rng.uniform(0, 1e-3, 100), 0.3)[0] == 0.3
+    assert h.next_increment(np.full(64, 5.0), 0.25)[0] == 0.25
+    # target unreachable above eps: eps is taken
+    a = np.concatenate([np.zeros(1), np.full(99, 1e12)])
+    assert h.next_increment(a, 1.0)[0] == 1e-6
+
+
+def test_systematic_resampling():
+    As, y, s = _linear()
+    h = _handle_linear(As, y, s, J=4096)
+    rng = np.random.default_rng(5)
+    # dyadic weights: every partial sum is exact in any order, so indices match bit for bit
+    for J in (4096, 1000, 7):
+        w = 2.0 ** rng.integers(-12, 0, size=J)
+        for U in (0.0, 0.5, 0.123456789, 0.999):
+            ref = smc.systematic_resample(np.log(w), U)
+            assert np.array_equal(h.systematic_resample(w, U), ref), (J, U)
+    # general weights: offspring counts within {floor, ceil} of J W_j and nearly identical indices
+    J = 4096
+    w = np.exp(rng.normal(0, 3, J))
+    W = w / w.sum()
+    anc = h.systematic_resample(w, 0.37)
+    cnt = np.bincount(anc, minlength=J)
+    assert np.all(cnt >= np.floor(J * W) - 1e-9) and np.all(cnt <= np.ceil(J * W) + 1e-9)
+    assert np.all(np.diff(anc) >= 0)
+    assert np.mean(anc != smc.systematic_resample(np.log(w), 0.37)) < 1e-3
+
+
+def _oracle_linear(As, y, sigma, J, **kw):
+    ev = lambda l, th: potential(th @ As[l].T, y, sigma)
+    return smc.Sampler(ev, As.shape[0], As.shape[2], J, **kw).run()
+
+
+def _compare_paths(gp, op, tol):
+    assert len(gp) == len(op)
+    for g, o in zip(gp, op):
+        assert g["kind"] == o["kind"]
+        assert g["beta"] == pytest.approx(o["beta"], rel=tol, abs=tol)
+        if g["kind"] == "LU":
+            assert g["zeta"] == pytest.approx(o["zeta"], rel=tol, abs=tol)
+        assert g["delta"] == pytest.approx(o["delta"], rel=tol, abs=tol)
+
+
+def test_single_level_linear_gaussian_same_trajectory_and_closed_form():
+    As, y, s = _linear()
+    J = 4000
+    kw = dict(n_mcmc=10, s_pcn=0.5, seed=11)
+    h = _handle_linear(As, y, s, J=J, **kw)
+    h.run()
+    o = _oracle_linear(As, y, s, J, **kw)
+    _compare_paths(h.path(), o.path, 1e-9)
+    th, _ = h.particles()
+    assert np.allclose(th, o.theta, rtol=1e-8, atol=1e-9)
+    m, v, lz = h.posterior_moments()
+    assert lz == pytest.approx(o.log_z, rel=1e-10)
+    m_ex, C_ex = gaussian.posterior(As[0], y, s)
+    assert np.all(np.abs(m - m_ex) < 4 * 3 * np.sqrt(np.diag(C_ex) / J))
+    assert np.allclose(v, np.diag(C_ex), rtol=0.15)
+    assert lz == pytest.approx(gaussian.log_evidence(As[0], y, s), abs=0.15)
+
+
+def test_mls2mc_linear_same_path_and_cost_identity():
+    As, y, s = _linear(K=3, n=6, sigma=0.2, seed=3, levels=3)
+    J = 2000
+    kw = dict(J_tilde=100, n_mcmc=6, s_pcn=0.4, seed=21)
+    h = _handle_linear(As, y, s, J=J, **kw)
+    h.run()
+    o = _oracle_linear(As, y, s, J, **kw)
+    gp = h.path()
+    _compare_paths(gp, o.path, 1e-9)
+    assert any(p["kind"] == "LU" for p in gp) and gp[0]["kind"] == "ITU"
+    st = h.state()
+    assert st["evals"][:3] == list(o.evals)          # forward solves per level, exactly
+    assert st["level"] == 2 and st["beta"] == 1.0
+    assert st["log_z"] == pytest.approx(o.log_z, rel=1e-10)
+
+
+def test_fem_fp64_sampler_matches_oracle_trajectory():
+    """Two FEM levels h = 1/8, 1/16, K = 4, FP64 path: same update path and particles as the oracle."""
+    K, J = 4, 300
+    obs = wl.obs_grid(3)
+    lv = [ofwd.Level(N, 0.3, 1.0, K, obs) for N in (8, 16)]
+    th_true = np.random.default_rng(1).standard_normal(K)
+    Gt = lv[1].G(th_true)
+    sigma = 0.02 * np.abs(Gt).max()
+    y = Gt + sigma * np.random.default_rng(2).standard_normal(obs.shape[0])
+    kw = dict(J_tilde=50, n_mcmc=2, s_pcn=0.3, seed=5)
+    h = native.Handle([8, 16], K, obs, y, sigma, corr_len=0.3, J=J, precision=native.SMC_FP64, rtol=1e-13, **kw)
+    h.run()
+    ev = lambda l, th: potential(lv[l].G_batch(th), y, sigma)
+    o = smc.Sampler(ev, 2, K, J, **kw).run()
+    _compare_paths(h.path(), o.path, 1e-7)
+    th, _ = h.particles()
+    assert np.allclose(th, o.theta, rtol=1e-7, atol=1e-8)
+    assert h.state()["evals"][:2] == list(o.evals)
