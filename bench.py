@@ -179,6 +179,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-run", action="store_true", help="skip the seconds-to-posterior sampler run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -199,27 +200,27 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
     build.build()
     w = wl.WORKLOADS[WORKLOAD]
     d = load_data()
     obs = wl.obs_grid(w.obs_per_side)
     stream = torch.cuda.current_stream(dev)
-    h = native.Handle(w.inv_h, w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, variance=w.variance,
-                      precision=native.SMC_MIXED, stream=stream.cuda_stream)
     J, L, n_obs = w.J, len(w.inv_h), w.n_obs
-    theta = torch.from_numpy(wl.particles(J, w.K, 1000 + rank)).to(dev)
-    G = torch.empty((L, J, n_obs), dtype=torch.float64, device=dev)
-    Phi = torch.empty((L, J), dtype=torch.float64, device=dev)
-    iters = torch.empty((L, J), dtype=torch.int32, device=dev)
+    h = native.Handle(w.inv_h, w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, variance=w.variance, J=J,
+                      J_tilde=w.J_tilde, n_mcmc=1, s_pcn=w.s_pcn, tau_star=w.tau_star,
+                      precision=native.SMC_MIXED, seed=w.seed_sampler + 1000 * rank, stream=stream.cuda_stream)
+    theta0 = wl.particles(J, w.K, 1000 + rank)
+    h.set_particles(theta0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
-    s = stream.cuda_stream
+    n_mcmc_step = 1
+    evals_per_step = L * J * (1 + n_mcmc_step)
 
     def step(ev=None):
         for l in range(L):
             if ev is not None:
                 ev[l][0].record(stream)
-            h.eval_likelihood_device(l, J, theta.data_ptr(), G[l].data_ptr(), Phi[l].data_ptr(),
-                                     iters[l].data_ptr(), s)
+            h.tempering_update(l, 0.0, n_mcmc_step)
             if ev is not None:
                 ev[l][1].record(stream)
 
@@ -228,9 +229,13 @@ def main():
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
+    h.get_timing()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    h.set_timing(True)
+    lib = native.load()
+    launches0 = lib.smc_kernel_launches()
     step_ms, level_ms = [], [[] for _ in range(L)]
     for _ in range(args.steps):
         flush.zero_()
@@ -241,28 +246,38 @@ def main():
             level_ms[l].append(ev[l][0].elapsed_time(ev[l][1]))
         step_ms.append(ev[0][0].elapsed_time(ev[L - 1][1]))
     torch.cuda.synchronize(dev)
+    launches = lib.smc_kernel_launches() - launches0
+    h.set_timing(False)
+    kern_ms, kern_n = h.get_timing()
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
     ms = float(np.mean(step_ms))
-    it = iters.cpu().numpy()
-    if (it <= 0).any():
-        raise RuntimeError("a forward solve did not converge inside the timed region")
 
-    # e2e: the host-pointer C-ABI call; pinned host theta in, G and Phi out, every step
+    # mean CG iterations of the finest-level solve on these particles (outside the timed region)
+    th_now, _ = h.particles()
+    tdev = torch.from_numpy(th_now).to(dev)
+    Gd = torch.empty((J, n_obs), dtype=torch.float64, device=dev)
+    Pd = torch.empty(J, dtype=torch.float64, device=dev)
+    It = torch.empty(J, dtype=torch.int32, device=dev)
+    h.eval_likelihood_device(L - 1, J, tdev.data_ptr(), Gd.data_ptr(), Pd.data_ptr(), It.data_ptr(),
+                             stream.cuda_stream)
+    it = It.cpu().numpy()
+    if (it <= 0).any():
+        raise RuntimeError("a forward solve did not converge")
+
+    # e2e through the host-pointer C-ABI: particles in from pinned host memory, particles and
+    # potentials out, every step
     th_host = torch.empty((J, w.K), dtype=torch.float64, pin_memory=True)
-    th_host.copy_(theta.cpu())
-    G_host = torch.empty((J, n_obs), dtype=torch.float64, pin_memory=True)
-    Phi_host = torch.empty(J, dtype=torch.float64, pin_memory=True)
-    thn, Gn, Pn = th_host.numpy(), G_host.numpy(), Phi_host.numpy()
-    ptr = lambda a: a.ctypes.data_as(native._dp)
-    lib = native.load()
+    th_host.numpy()[:] = theta0
+    th_out = torch.empty((J, w.K), dtype=torch.float64, pin_memory=True)
+    phi_out = torch.empty(J, dtype=torch.float64, pin_memory=True)
+    ptr = lambda a: a.numpy().ctypes.data_as(native._dp)
 
     def e2e_step():
-        for l in range(L):
-            rc = lib.smc_eval_likelihood(h._h, l, J, ptr(thn), ptr(Gn), ptr(Pn))
-            if rc != 0:
-                raise native.SmcError(rc, lib.smc_last_error(h._h).decode())
+        h._check(lib.smc_set_particles(h._h, ptr(th_host)))
+        step()
+        h._check(lib.smc_get_particles(h._h, ptr(th_out), ptr(phi_out)))
     for _ in range(3):
         e2e_step()
     torch.cuda.synchronize(dev)
@@ -278,6 +293,27 @@ def main():
         torch.cuda.synchronize(dev)
         e2e_ms.append(e0.elapsed_time(e1))
     e2e = float(np.mean(e2e_ms))
+    e2e_evals = evals_per_step + J          # smc_set_particles evaluates Phi on the coarsest level
+
+    # seconds to posterior: one full MLS^2MC run of the workload (n_mcmc = 5), outside the timed region
+    run = None
+    if not args.no_run:
+        hr = native.Handle(w.inv_h, w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, variance=w.variance,
+                           J=J, J_tilde=w.J_tilde, n_mcmc=w.n_mcmc, s_pcn=w.s_pcn, tau_star=w.tau_star,
+                           precision=native.SMC_MIXED, seed=w.seed_sampler + 1000 * rank,
+                           stream=stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        hr.run()
+        torch.cuda.synchronize(dev)
+        secs = time.perf_counter() - t0
+        st = hr.state()
+        path = hr.path()
+        run = {"seconds": secs, "updates": st["n_updates"], "evals_per_level": st["evals"][:L],
+               "log_evidence": st["log_z"],
+               "n_itu": sum(p["kind"] == "ITU" for p in path), "n_bridge_steps": sum(p["kind"] == "LU" for p in path),
+               "evals_per_s": sum(st["evals"][:L]) / secs}
+        hr.close()
 
     t = torch.tensor([ms, e2e] + [float(np.mean(x)) for x in level_ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -288,33 +324,39 @@ def main():
         peaks, src = measured_peaks()
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s, FMA = 2 flops
-        mean_it = float(it[L - 1].mean())
-        passes = 2.0
-        flops = algorithmic_flops_per_eval(w.inv_h[-1], w.K, mean_it, passes) * J
-        achieved = flops / (lvl_ms[-1] * 1e-3) / 1e12
-        total_evals = J * L * world
+        mean_it = float(it.mean())
+        kl = L - 1
+        launch_ms = kern_ms[kl] / max(kern_n[kl], 1)
+        flops = algorithmic_flops_per_eval(w.inv_h[-1], w.K, mean_it, 2.0) * J
+        achieved = flops / (launch_ms * 1e-3) / 1e12
+        total_evals = evals_per_step * world
         line = {
             "metric": "likelihood evals/s per mesh level", "value": total_evals / (ms * 1e-3),
             "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "levels_inv_h": list(w.inv_h), "K": w.K, "n_obs": n_obs, "J": J,
-                       "precision": "mixed", "l2": "flushed between steps (256 MB write)",
+                       "precision": "mixed", "step": "per level: Phi on all particles, adaptive increment, "
+                       "systematic resampling, 1 pCN sweep (propose, solve, accept)",
+                       "evals_per_step": evals_per_step, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
-            "per_level": {str(N): {"evals_per_s": J * world / (lm * 1e-3), "ms": lm,
-                                   "mean_cg_iters": float(it[l].mean())}
+            "per_level": {str(N): {"evals_per_s": 2 * J * world / (lm * 1e-3), "update_ms": lm,
+                                   "solve_launch_ms": kern_ms[l] / max(kern_n[l], 1),
+                                   "solve_evals_per_s": J / (kern_ms[l] / max(kern_n[l], 1) * 1e-3)}
                           for l, (N, lm) in enumerate(zip(w.inv_h, lvl_ms))},
             "roofline": {"kernel": f"fem_eval_kernel<float,{w.inv_h[-1]},512>", "bound": "alu",
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": None,
+                         "frac": achieved / fp32_peak, "traffic": None, "launch_ms": launch_ms,
+                         "launches": kern_n[kl], "mean_cg_iters": mean_it,
                          "peak_source": f"FP32 FMA issue rate: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "
                                         f"(sm_max_mhz {src})"},
-            "e2e": {"value": total_evals / (e2e * 1e-3), "unit": "evals/s",
-                    "h2d_bytes_per_step": L * J * w.K * 8,
-                    "d2h_bytes_per_step": L * J * (n_obs * 8 + 8 + 4)},
-            "gpu_launches": args.steps * L,
+            "e2e": {"value": e2e_evals * world / (e2e * 1e-3), "unit": "evals/s",
+                    "h2d_bytes_per_step": J * w.K * 8, "d2h_bytes_per_step": J * (w.K + 1) * 8},
+            "gpu_launches": int(launches),
             "clocks": clk,
         }
+        if run is not None:
+            line["mls2mc_run"] = run
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

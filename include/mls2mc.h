@@ -110,6 +110,15 @@ int smc_eval_likelihood_device(smc_handle* h, int level, int n, const double* th
  * and the K eigenvalues lambda_k (Eq. truncKL). Either pointer may be NULL. */
 int smc_kl_table(const smc_handle* h, int level, double* psi, double* lambda);
 
+/* Opt-in timing (no counterpart in the paper; for measurement): when enabled, every forward-solve
+ * launch is bracketed by CUDA events on its stream. smc_get_timing waits for the recorded
+ * launches, returns the summed device milliseconds and launch counts per level ([8] arrays,
+ * either may be NULL) and forgets them. */
+int smc_set_timing(smc_handle* h, int enable);
+/* Number of CUDA kernels this library has launched in the process so far (all handles). */
+long long smc_kernel_launches(void);
+int smc_get_timing(smc_handle* h, double* ms_per_level, long long* launches_per_level);
+
 /* Sizes of a handle: K, n_obs, number of levels, J. Any pointer may be NULL. */
 int smc_sizes(const smc_handle* h, int* K, int* n_obs, int* n_levels, int* J);
 
@@ -164,6 +173,15 @@ int smc_get_particles(const smc_handle* h, double* theta, double* phi);
 /* Replace the particles by theta [J][K] (host), restart the sampler at beta = 0 on level 0 and
  * evaluate Phi_1 there (instead of drawing from the prior). */
 int smc_set_particles(smc_handle* h, const double* theta);
+
+/* One tempering update of the current particles on level `level` from inverse temperature beta0
+ * (Sec. 3.1 with the adaptive step of Eq. Eq_cv_opt): evaluate Phi_level on all particles, choose
+ * delta in [min(eps, 1 - beta0), 1 - beta0], reweight by exp(-delta Phi_level), resample
+ * systematically, and run n_mcmc pCN steps for exp(-(beta0 + delta) Phi_level) mu0. The particles
+ * change; the update-scheme state of smc_step (level, beta, evidence) does not. This is the building
+ * block of single-level SMC on any level (Example example_SMC) and of hand-made update schemes.
+ * info (may be NULL): type 0, the level, the new beta, delta, cv, log mean weight, accept rate. */
+int smc_tempering_update(smc_handle* h, int level, double beta0, int n_mcmc, smc_stage_info* info);
 
 /* ---- kernel-level entry points of the sampler's device steps -------------------------------- */
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -20,6 +21,9 @@
 using namespace mls2mc;
 
 namespace mls2mc {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int Handle::fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -54,6 +58,11 @@ Handle::~Handle() {
     }
     cudaFree(d_y);
     free_sampler();
+    for (auto& t : timed) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    for (auto ev : event_pool) cudaEventDestroy(ev);
     cudaFree(scratch_theta);
     cudaFree(scratch_G);
     cudaFree(scratch_phi);
@@ -78,6 +87,17 @@ int Handle::ensure_scratch(int n) {
     if (e != cudaSuccess) return fail(SMC_ENOMEM, "scratch allocation for %d particles: %s", n, cudaGetErrorString(e));
     scratch_cap = n;
     return SMC_OK;
+}
+
+cudaEvent_t Handle::take_event() {
+    if (!event_pool.empty()) {
+        cudaEvent_t e = event_pool.back();
+        event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
 }
 
 int Handle::eval_device(int level, int n, const double* theta, double* G, double* Phi, int* iters,
@@ -110,7 +130,15 @@ int Handle::eval_device(int level, int n, const double* theta, double* G, double
         a.rtol_in = precision == SMC_MIXED ? 1e-4 : std::max(0.5 * rtol, 1e-14);
         a.max_outer = precision == SMC_MIXED ? 8 : 3;
         a.max_inner = max_iter;
-        e = fem_eval_launch(a, st);
+        if (timing) {
+            TimedLaunch t{level, take_event(), take_event()};
+            cudaEventRecord(t.start, st);
+            e = fem_eval_launch(a, st);
+            cudaEventRecord(t.stop, st);
+            timed.push_back(t);
+        } else {
+            e = fem_eval_launch(a, st);
+        }
     }
     if (e != cudaSuccess) return cuda_fail(e, "forward-solve launch");
     return SMC_OK;
@@ -222,6 +250,40 @@ int smc_kl_table(const smc_handle* hh, int level, double* psi, double* lambda) {
     if (h->forward_kind != SMC_FWD_FEM) return h->fail(SMC_EINVAL, "no KL table for a linear forward model");
     if (psi) std::memcpy(psi, L.psi_host.data(), L.psi_host.size() * sizeof(double));
     if (lambda) std::memcpy(lambda, L.lambda.data(), L.lambda.size() * sizeof(double));
+    return SMC_OK;
+}
+
+long long smc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int smc_set_timing(smc_handle* hh, int enable) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    h->timing = enable != 0;
+    return SMC_OK;
+}
+
+int smc_get_timing(smc_handle* hh, double* ms_per_level, long long* launches_per_level) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    std::vector<double> ms(8, 0.0);
+    std::vector<long long> cnt(8, 0);
+    for (auto& t : h->timed) {
+        cudaError_t e = cudaEventSynchronize(t.stop);
+        float v = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&v, t.start, t.stop);
+        if (e != cudaSuccess) return h->cuda_fail(e, "read launch timing");
+        if (t.level >= 0 && t.level < 8) {
+            ms[t.level] += v;
+            cnt[t.level] += 1;
+        }
+        h->event_pool.push_back(t.start);
+        h->event_pool.push_back(t.stop);
+    }
+    h->timed.clear();
+    for (int l = 0; l < 8; ++l) {
+        if (ms_per_level) ms_per_level[l] = ms[l];
+        if (launches_per_level) launches_per_level[l] = cnt[l];
+    }
     return SMC_OK;
 }
 

@@ -177,6 +177,40 @@ void Handle::record(int type, double zeta, const IncState& st, double rate, doub
     if (info) *info = r;
 }
 
+int Handle::tempering_update(int level, double beta0, int n_mcmc, smc_stage_info* info) {
+    Sampler* S = smp;
+    RC(smp_eval(level, S->J, S->theta, S->phi_c));
+    IncState st;
+    const double log_z = S->log_z, beta = S->beta;
+    const int nm = opts.n_mcmc;
+    S->beta = beta0;
+    RC(reweight_resample(S->phi_c, 1.0 - beta0, false, st));
+    S->beta = (st.delta >= 1.0 - beta0) ? 1.0 : beta0 + st.delta;
+    opts.n_mcmc = n_mcmc;
+    double rate = 0.0;
+    const int rc = mcmc(level, -1.0, rate);
+    opts.n_mcmc = nm;
+    const double beta_new = S->beta;
+    S->beta = beta;
+    S->log_z = log_z;
+    if (rc != SMC_OK) return rc;
+    if (info) {
+        std::memset(info, 0, sizeof *info);
+        info->type = 0;
+        info->level = level;
+        info->beta = beta_new;
+        info->zeta = -1.0;
+        info->delta = st.delta;
+        info->cv = st.cv;
+        info->cv_lu = -1.0;
+        info->log_z_inc = st.log_mean_w;
+        info->accept_rate = rate;
+        for (int l = 0; l < 8; ++l) info->evals_per_level[l] = S->evals[l];
+    }
+    S->stage += 1;
+    return SMC_OK;
+}
+
 int Handle::itu(double cv_lu, smc_stage_info* info) {
     Sampler* S = smp;
     IncState st;
@@ -350,6 +384,19 @@ int smc_set_particles(smc_handle* hh, const double* theta) {
     cudaError_t e = cudaMemcpyAsync(S->theta, theta, (size_t)S->J * h->K * 8, cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "copy particles");
     return h->sampler_restart();
+}
+
+int smc_tempering_update(smc_handle* hh, int level, double beta0, int n_mcmc, smc_stage_info* info) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->smp) return h->fail(SMC_EINVAL, "handle was created with J = 0");
+    if (level < 0 || level >= (int)h->levels.size()) return h->fail(SMC_EINVAL, "level %d out of range", level);
+    if (!(beta0 >= 0.0 && beta0 < 1.0) || n_mcmc < 0) return h->fail(SMC_EINVAL, "need 0 <= beta0 < 1, n_mcmc >= 0");
+    if (!h->smp->started) {
+        int rc = h->sampler_start();
+        if (rc != SMC_OK) return rc;
+    }
+    return h->tempering_update(level, beta0, n_mcmc, info);
 }
 
 // ---- kernel-level entry points -----------------------------------------------------------------

@@ -515,6 +515,7 @@ cudaError_t launch_one(const FemArgs& a, cudaStream_t st) {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     kern<<<a.n, T, smem, st>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 

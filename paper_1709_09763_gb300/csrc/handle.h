@@ -42,6 +42,16 @@ struct Handle {
     // sampler state (smc_kernels.cu / controller.cpp)
     struct Sampler* smp = nullptr;
 
+    // opt-in CUDA-event timing of forward-solve launches, per level
+    bool timing = false;
+    struct TimedLaunch {
+        int level;
+        cudaEvent_t start, stop;
+    };
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> event_pool;
+    cudaEvent_t take_event();
+
     ~Handle();
     int fail(int code, const char* fmt, ...);
     int cuda_fail(cudaError_t e, const char* what);
@@ -57,6 +67,7 @@ struct Handle {
     int mcmc(int level, double zeta, double& rate);
     void record(int type, double zeta, const struct IncState& st, double rate, double cv_lu, smc_stage_info* info);
     int itu(double cv_lu, smc_stage_info* info);
+    int tempering_update(int level, double beta0, int n_mcmc, smc_stage_info* info);
     int lu(int head, smc_stage_info* info);
     int sampler_start();
     int sampler_restart();

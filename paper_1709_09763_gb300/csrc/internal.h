@@ -17,6 +17,9 @@ void kl_table(int N, double corr_len, double variance, int K, std::vector<double
               std::vector<double>& lambda);
 void obs_table(int N, int n_obs, const double* xy, std::vector<int>& idx, std::vector<double>& wts);
 
+// ---- kernel launch counter (api.cpp): every kernel the library launches is counted ------
+void count_launches(long long n);
+
 // ---- forward solve (fem_solve.cu) -------------------------------------------------------
 struct FemArgs {
     int N;                  // cells per side of this level (power of two, 4..64)

@@ -17,7 +17,7 @@ constexpr uint32_t kPurposeDaU = 5;
 
 constexpr int kIncMaxBlocks = 64;     // partial-sum blocks of the increment search
 constexpr int kIncMaxIter = 200;      // cap on decisions of one search
-constexpr int kIncChunk = 12;         // decisions queued between host checks
+constexpr int kIncChunk = 10;         // decisions queued between host checks
 
 // state of one adaptive-increment search, resident in device memory
 struct IncState {

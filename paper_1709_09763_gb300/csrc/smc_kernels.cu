@@ -172,8 +172,9 @@ __global__ void inc_eval_kernel(const double* a, int n, const IncState* st, doub
         for (int i = 0; i < 4; ++i) partials[blockIdx.x * 4 + i] = v[i];
 }
 
-// one decision of the search: boundary tests first, then a Newton step on
-// g(x) = log(1 + cv(x)^2) - log(1 + tau^2) safeguarded by bisection of the bracket
+// one decision of the search: boundary tests first, then Newton steps on
+// g(x) = log(1 + cv(x)^2) - log(1 + tau^2) in t = log x (the increment spans decades),
+// safeguarded by geometric bisection of the bracket [lo, hi] (lo >= eps > 0)
 __global__ void inc_decide_kernel(const double* partials, int nblk, IncState* st, int n, int max_iter) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (st->done) return;
@@ -201,15 +202,15 @@ __global__ void inc_decide_kernel(const double* partials, int nblk, IncState* st
         else {
             st->phase = 2;
             st->lo = x;
-            st->x = 0.5 * (st->lo + st->hi);
+            st->x = sqrt(st->lo * st->hi);
         }
     } else {
         if (g > 0.0) st->hi = x; else st->lo = x;
-        const double gp = 2.0 * (T1 / S1 - T2 / S2);       // dg/dx
-        double xn = x - g / gp;
         const double lo = st->lo, hi = st->hi;
-        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-        if (g == 0.0 || (hi - lo) <= 2e-16 * hi || fabs(xn - x) <= 1e-16 * x || st->iter >= max_iter) finish = true;
+        const double gp = 2.0 * (T1 / S1 - T2 / S2);       // dg/dx >= 0
+        double xn = x * exp(-g / (x * gp));                 // Newton step in log x
+        if (!(xn > lo && xn < hi)) xn = sqrt(lo * hi);
+        if (g == 0.0 || hi <= lo * (1.0 + 4e-16) || fabs(xn - x) <= 1e-15 * x || st->iter >= max_iter) finish = true;
         else st->x = xn;
     }
     if (finish) {
@@ -388,6 +389,7 @@ cudaError_t linear_eval_launch(const double* A, int n, int K, int n_obs, const d
     if (n <= 0) return cudaSuccess;
     linear_eval_kernel<<<grid_for((long long)n * 32, 256), 256, 0, st>>>(A, n, K, n_obs, theta, y, inv_sigma2, G,
                                                                          Phi, iters);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -396,12 +398,14 @@ cudaError_t normals_launch(double* out, int J, int K, uint32_t event, uint32_t p
     if (J <= 0) return cudaSuccess;
     const long long work = (long long)J * ((K + 1) / 2);
     normals_kernel<<<grid_for(work, 256), 256, 0, st>>>(out, J, K, event, purpose, seed, base, c0, c1);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t uniforms_launch(double* out, int J, uint32_t event, uint32_t purpose, uint64_t seed, cudaStream_t st) {
     if (J <= 0) return cudaSuccess;
     uniforms_kernel<<<grid_for(J, 256), 256, 0, st>>>(out, J, event, purpose, seed);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -410,7 +414,9 @@ int inc_blocks(int n) { return std::min(kIncMaxBlocks, std::max(1, (n + 255) / 2
 cudaError_t inc_start(const double* a, int n, double dmax, double tau, double eps, IncWork& w, cudaStream_t st) {
     const int nb = inc_blocks(n);
     inc_min_kernel<<<nb, 256, 0, st>>>(a, n, w.partials);
+    count_launches(1);
     inc_init_kernel<<<1, 32, 0, st>>>(w.partials, nb, w.state, dmax, tau, eps);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -418,7 +424,9 @@ cudaError_t inc_iterate(const double* a, int n, int iters, IncWork& w, cudaStrea
     const int nb = inc_blocks(n);
     for (int i = 0; i < iters; ++i) {
         inc_eval_kernel<<<nb, 256, 0, st>>>(a, n, w.state, w.partials);
+        count_launches(1);
         inc_decide_kernel<<<1, 32, 0, st>>>(w.partials, nb, w.state, n, kIncMaxIter);
+        count_launches(1);
     }
     return cudaGetLastError();
 }
@@ -427,7 +435,9 @@ cudaError_t resample_launch(const double* a, const double* w_in, int n, const In
                             uint32_t event, uint64_t seed, double* cdf, int* anc, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     cdf_kernel<<<1, 1024, 0, st>>>(a, w_in, n, state, cdf);
+    count_launches(1);
     ancestors_kernel<<<grid_for(n, 256), 256, 0, st>>>(cdf, n, U, event, seed, anc);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -436,6 +446,7 @@ cudaError_t gather_launch(const int* anc, int n, int K, const double* th_in, dou
     if (n <= 0) return cudaSuccess;
     gather_kernel<<<grid_for((long long)n * K, 256), 256, 0, st>>>(anc, n, K, th_in, th_out, p0_in, p0_out, p1_in,
                                                                    p1_out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -443,11 +454,13 @@ cudaError_t lu_increment_launch(const double* phi_c, const double* phi_f, int n,
                                 cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     lu_increment_kernel<<<grid_for(n, 256), 256, 0, st>>>(phi_c, phi_f, n, beta, a);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t cv_lu_launch(const double* phi_c, const double* phi_f, int n, double beta, double* out, cudaStream_t st) {
     cv_lu_kernel<<<1, 256, 0, st>>>(phi_c, phi_f, n, beta, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -457,11 +470,13 @@ cudaError_t pcn_accept_launch(int n, int K, double beta, double zeta, uint32_t e
     if (n <= 0) return cudaSuccess;
     pcn_accept_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, K, beta, zeta, event, seed, theta, theta_p, phi_c, phi_cp,
                                                         phi_f, phi_fp, n_acc);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t moments_launch(const double* theta, int n, int K, double* mean, double* var, cudaStream_t st) {
     moments_kernel<<<K, 256, 0, st>>>(theta, n, K, mean, var);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -79,6 +79,11 @@ SIGNATURES = {
     "smc_posterior_moments": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp]),
     "smc_get_particles": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     "smc_set_particles": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "smc_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "smc_kernel_launches": (ctypes.c_longlong, []),
+    "smc_get_timing": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "smc_tempering_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                            ctypes.POINTER(StageInfo)]),
     "smc_next_increment": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_double, _dp]),
     "smc_systematic_resample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_double, _ip]),
     "smc_philox_normals": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint,
@@ -210,6 +215,21 @@ class Handle:
     def set_particles(self, theta):
         theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(self.J, self.K)
         self._check(self._lib.smc_set_particles(self._h, _dptr(theta)))
+
+    def set_timing(self, enable=True):
+        self._check(self._lib.smc_set_timing(self._h, int(bool(enable))))
+
+    def get_timing(self):
+        ms = np.zeros(8)
+        cnt = (ctypes.c_longlong * 8)()
+        self._check(self._lib.smc_get_timing(self._h, _dptr(ms), cnt))
+        return ms, list(cnt)
+
+    def tempering_update(self, level, beta0=0.0, n_mcmc=1):
+        info = StageInfo()
+        self._check(self._lib.smc_tempering_update(self._h, int(level), float(beta0), int(n_mcmc),
+                                                   ctypes.byref(info)))
+        return info.as_dict()
 
     # ---- kernel-level entry points ---------------------------------------------------------
     def next_increment(self, a, dmax):

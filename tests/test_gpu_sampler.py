@@ -157,3 +157,23 @@ def test_fem_fp64_sampler_matches_oracle_trajectory():
     th, _ = h.particles()
     assert np.allclose(th, o.theta, rtol=1e-7, atol=1e-8)
     assert h.state()["evals"][:2] == list(o.evals)
+
+
+def test_tempering_update_equals_first_itu_of_oracle():
+    """smc_tempering_update from beta = 0 on level 0 is the scheme's first ITU: same particles."""
+    As, y, s = _linear(K=4, n=6, sigma=0.3, seed=8)
+    J = 1500
+    kw = dict(n_mcmc=3, s_pcn=0.4, seed=77)
+    h = _handle_linear(As, y, s, J=J, **kw)
+    th0 = philox.normals(J, 4, 0, philox.PURPOSE_PRIOR, 77)
+    h.set_particles(th0)
+    info = h.tempering_update(0, 0.0, 3)
+    ev = lambda l, th: potential(th @ As[l].T, y, s)
+    o = smc.Sampler(ev, 1, 4, J, theta0=th0, **kw)
+    o.step()
+    th, phi = h.particles()
+    assert info["beta"] == pytest.approx(o.beta, rel=1e-12)
+    assert info["log_z_inc"] == pytest.approx(o.log_z, rel=1e-12)
+    assert np.allclose(th, o.theta, rtol=1e-10, atol=1e-12)
+    assert np.allclose(phi, o.phi, rtol=1e-10)
+    assert h.state()["beta"] == 0.0          # the update-scheme state is untouched
