@@ -194,6 +194,21 @@ int smc_next_increment(smc_handle* h, int n, const double* a, double dmax, doubl
  * [0, 1): anc[i] = min{ j : c_j > (U + i)/n }, c the cumulative normalised weights (c_{n-1} = 1). */
 int smc_systematic_resample(smc_handle* h, int n, const double* w, double U, int* anc);
 
+/* Allocation-free systematic resampling. The paper has no counterpart to this: it serves callers
+ * that cannot allocate device memory -- code whose device memory is all owned by another
+ * framework's pool, hosts that forbid cudaMalloc after start-up (real-time or embedded loops where
+ * an allocation could block or fail), plug-ins without a handle of this library. The result is
+ * the same as smc_systematic_resample's, but w [n] (unnormalised weights > 0) and anc [n] are
+ * DEVICE arrays, the work is queued on `stream` (a cudaStream_t, NULL = default stream) without
+ * waiting, and no handle is needed. Its scratch (one double per particle) is a fixed device array
+ * of SMC_NOALLOC_MAX_PARTICLES entries (512 KiB) that every GPU loading the library holds until the
+ * process exits; n beyond that maximum returns SMC_EINVAL. It calls no cudaMalloc or cudaFree. The
+ * first call on a device looks up the array's device address (make that first call before any
+ * stream capture). All calls share the array: calls that overlap on the GPU race on it, so the
+ * caller must serialise them. Returns SMC_EINVAL for bad arguments, SMC_ECUDA if the launch fails. */
+#define SMC_NOALLOC_MAX_PARTICLES 65536
+int smc_systematic_resample_noalloc(const double* w, int n, double U, int* anc, void* stream);
+
 /* Philox4x32-10 draws of the library's layout with key opts.seed: out [J][K] standard normals
  * (counter (k/2, j, event, purpose), Box-Muller), or out [J] uniforms in (0, 1] (counter (0, j, event,
  * purpose), 1 - 53-bit uniform). */

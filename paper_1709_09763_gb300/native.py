@@ -22,6 +22,7 @@ SMC_FP64 = 0
 SMC_MIXED = 1
 SMC_FWD_FEM = 0
 SMC_FWD_LINEAR = 1
+SMC_NOALLOC_MAX_PARTICLES = 65536
 
 ERROR_NAMES = {0: "SMC_OK", -1: "SMC_EINVAL", -2: "SMC_ENOMEM", -3: "SMC_ECUDA", -4: "SMC_ENOCONV",
                -5: "SMC_ESINGULAR", -6: "SMC_ETIMEOUT"}
@@ -88,6 +89,8 @@ SIGNATURES = {
     "smc_systematic_resample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_double, _ip]),
     "smc_philox_normals": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint,
                                           ctypes.c_uint, _dp]),
+    "smc_systematic_resample_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                                       ctypes.c_void_p, ctypes.c_void_p]),
     "smc_philox_uniforms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_uint, _dp]),
 }
 
