@@ -209,6 +209,12 @@ int smc_systematic_resample(smc_handle* h, int n, const double* w, double U, int
 #define SMC_NOALLOC_MAX_PARTICLES 65536
 int smc_systematic_resample_noalloc(const double* w, int n, double U, int* anc, void* stream);
 
+/* The library's tensor-core GEMM (tcgen05, BF16 operands, FP32 accumulation) on host arrays:
+ * C[M][N] = A[M][K] . B[N][K]^T with A, B BF16 bit patterns (uint16), K a multiple of 8. It is the
+ * contraction of the surrogate network and of the KL synthesis u = theta . Psi (Eq. truncKL).
+ * Allocates and frees its own device buffers; SMC_ETIMEOUT if a bounded wait gave up. */
+int smc_gemm_bf16(int M, int N, int K, const uint16_t* A, const uint16_t* B, float* C);
+
 /* Philox4x32-10 draws of the library's layout with key opts.seed: out [J][K] standard normals
  * (counter (k/2, j, event, purpose), Box-Muller), or out [J] uniforms in (0, 1] (counter (0, j, event,
  * purpose), 1 - 53-bit uniform). */

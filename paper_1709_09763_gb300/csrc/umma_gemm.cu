@@ -1,0 +1,323 @@
+// Tensor-core GEMM for sm_103a: C[M][N] = A[M][K] . B[N][K]^T, A and B BF16 row-major (K
+// contiguous), FP32 accumulation in tensor memory, fused epilogues. Used by the surrogate network
+// (forward, backward, weight gradients) and by the KL synthesis.
+//
+// Per CTA one 128 x BN output tile:
+//  * thread 0 (producer) streams 64-wide K chunks of A (128 rows) and B (BN rows) into a ring of
+//    STAGES shared-memory slots with TMA (cp.async.bulk.tensor, 128-byte swizzle), signalling a
+//    "full" mbarrier per slot with the transaction byte count;
+//  * thread 32 (issuer) waits for a full slot, issues four tcgen05.mma.kind::f16 (K = 16 each)
+//    accumulating into TMEM, and releases the slot through tcgen05.commit on its "empty" mbarrier;
+//  * after the last chunk a commit on the "done" mbarrier hands the accumulator to all four warps,
+//    which read their 32 TMEM lanes (= tile rows) with tcgen05.ld and apply the epilogue.
+// Every wait is bounded: on time-out the CTA sets *err, stops issuing, and still frees its TMEM.
+// Out-of-range rows and K columns are zero-filled by TMA; stores are masked to M x N.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "internal.h"
+#include "umma_gemm.h"
+
+namespace mls2mc {
+
+namespace {
+
+constexpr uint32_t kSpinLimit = 1u << 22;   // bounded mbarrier waits (seconds at most)
+constexpr int BM = 128, BK = 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+// shared-memory matrix descriptor, K-major operand with 128-byte swizzle: 8-row groups of
+// 128-byte rows, 1024 bytes apart (stride byte offset); leading offset unused for this layout
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1u << 46;          // descriptor version of the 5th-generation tensor core
+    d |= (uint64_t)2u << 61;          // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 accumulator, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
+}
+
+// epilogue of one accumulator value at (row, col), inside M x N
+__device__ __forceinline__ void epilogue(const GemmEpi& e, int row, int col, float acc) {
+    switch (e.kind) {
+        case kEpiStoreF32:
+            e.out_f32[(size_t)row * e.ld_out + col] = acc + (e.bias ? e.bias[col] : 0.0f);
+            break;
+        case kEpiBiasGelu: {
+            const float z = acc + e.bias[col];
+            if (e.pre) e.pre[(size_t)row * e.ld_pre + col] = z;
+            const __nv_bfloat16 h = __float2bfloat16_rn(gelu_f(z));
+            e.act[(size_t)row * e.ld_act + col] = h;
+            if (e.act_t) e.act_t[(size_t)col * e.ld_act_t + row] = h;
+            break;
+        }
+        case kEpiGeluBackward: {
+            const __nv_bfloat16 g = __float2bfloat16_rn(acc * gelu_grad_f(e.pre_in[(size_t)row * e.ld_pre + col]));
+            e.act[(size_t)row * e.ld_act + col] = g;
+            if (e.act_t) e.act_t[(size_t)col * e.ld_act_t + row] = g;
+            break;
+        }
+        case kEpiExp:
+            e.out_f32[(size_t)row * e.ld_out + col] = expf(acc);
+            break;
+    }
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+                 int K, GemmEpi epi, int* err) {
+    constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nk = (K + BK - 1) / BK;
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&done_bar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"((uint32_t)BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (threadIdx.x == 0) {
+        // producer: TMA loads of chunk k into slot k % STAGES once the MMAs of chunk k - STAGES are done
+        for (int k = 0; k < nk; ++k) {
+            const int s = k % STAGES;
+            if (k >= STAGES && !mbar_wait(smem_u32(&empty_bar[s]), ((k / STAGES) - 1) & 1)) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            if (*(volatile int*)&abort_flag) break;
+            const uint32_t a_dst = base + s * STAGE_BYTES, b_dst = a_dst + A_BYTES;
+            mbar_expect_tx(smem_u32(&full_bar[s]), STAGE_BYTES);
+            tma_load_2d(a_dst, &tmA, smem_u32(&full_bar[s]), k * BK, m0);
+            tma_load_2d(b_dst, &tmB, smem_u32(&full_bar[s]), k * BK, n0);
+        }
+    } else if (threadIdx.x == 32) {
+        // issuer: four K = 16 MMAs per chunk; the start address advances 32 bytes per step
+        constexpr uint32_t idesc = idesc_bf16(BM, BN);
+        bool ok = true;
+        for (int k = 0; k < nk; ++k) {
+            const int s = k % STAGES;
+            if (!mbar_wait(smem_u32(&full_bar[s]), (k / STAGES) & 1)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_src = base + s * STAGE_BYTES, b_src = a_src + A_BYTES;
+#pragma unroll
+            for (int j = 0; j < BK / 16; ++j)
+                umma_bf16(tmem, sw128_desc(a_src + 32 * j), sw128_desc(b_src + 32 * j), idesc, (k | j) != 0);
+            umma_commit(smem_u32(&empty_bar[s]));
+        }
+        if (ok) umma_commit(smem_u32(&done_bar));
+        else atomicExch(&abort_flag, 1);
+    }
+    __syncwarp();
+
+    // epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w + 31
+    const bool done = mbar_wait(smem_u32(&done_bar), 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (done) {
+        const int row = m0 + 32 * warp + lane;
+        const uint32_t t_row = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(t_row + (uint32_t)c0, v);
+            if (row < M) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int col = n0 + c0 + i;
+                    if (col < N) epilogue(epi, row, col, v[i]);
+                }
+            }
+        }
+    } else if (lane == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+    }
+}
+
+// ---- host side -------------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2-D BF16 tensor map: rows x cols (cols contiguous, row stride ld elements), box 64 x box_rows
+bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    if (((uintptr_t)ptr & 15u) != 0 || (ld * 2) % 16 != 0) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES>
+cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, const GemmEpi& epi,
+                        int* err, cudaStream_t st) {
+    const size_t smem = (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024;
+    auto kern = umma_gemm_kernel<BN, STAGES>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    kern<<<grid, 128, smem, st>>>(ta, tb, M, N, K, epi, err);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t umma_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, const GemmEpi& epi,
+                      int* err, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    const int bn = N <= 64 ? 64 : 128;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, A, M, K, lda, BM) || !make_map(&tb, B, N, K, ldb, bn)) return cudaErrorInvalidValue;
+    if (bn == 64) return launch_gemm<64, 4>(ta, tb, M, N, K, epi, err, st);
+    return launch_gemm<128, 4>(ta, tb, M, N, K, epi, err, st);
+}
+
+}  // namespace mls2mc
+
+extern "C" int smc_gemm_bf16(int M, int N, int K, const uint16_t* A, const uint16_t* B, float* C) {
+    using namespace mls2mc;
+    if (M <= 0 || N <= 0 || K <= 0 || K % 8 != 0 || !A || !B || !C) return SMC_EINVAL;
+    void *dA = nullptr, *dB = nullptr;
+    float* dC = nullptr;
+    int* dErr = nullptr;
+    cudaError_t e = cudaMalloc(&dA, (size_t)M * K * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&dB, (size_t)N * K * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dC, (size_t)M * N * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dErr, 4);
+    if (e == cudaSuccess) e = cudaMemcpy(dA, A, (size_t)M * K * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dB, B, (size_t)N * K * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(dErr, 0, 4);
+    GemmEpi epi;
+    epi.kind = kEpiStoreF32;
+    epi.out_f32 = dC;
+    epi.ld_out = N;
+    if (e == cudaSuccess) e = umma_gemm(dA, K, dB, K, M, N, K, epi, dErr, nullptr);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(C, dC, (size_t)M * N * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, dErr, 4, cudaMemcpyDeviceToHost);
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dC);
+    cudaFree(dErr);
+    if (e != cudaSuccess) return SMC_ECUDA;
+    return herr ? SMC_ETIMEOUT : SMC_OK;
+}

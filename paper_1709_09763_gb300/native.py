@@ -91,6 +91,8 @@ SIGNATURES = {
                                           ctypes.c_uint, _dp]),
     "smc_systematic_resample_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "smc_gemm_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
     "smc_philox_uniforms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_uint, _dp]),
 }
 
@@ -110,6 +112,31 @@ def load():
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def bf16_bits(x):
+    """Round-to-nearest-even BF16 bit patterns (uint16) of an FP32/FP64 array."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def bf16_value(bits):
+    return (np.asarray(bits, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def gemm_bf16(A, B):
+    """C = A . B^T on the tensor cores; A (M, K), B (N, K) are rounded to BF16 first."""
+    lib = load()
+    a = bf16_bits(A)
+    b = bf16_bits(B)
+    M, K = a.shape
+    N = b.shape[0]
+    C = np.empty((M, N), dtype=np.float32)
+    rc = lib.smc_gemm_bf16(M, N, K, a.ctypes.data, b.ctypes.data, C.ctypes.data)
+    if rc != SMC_OK:
+        raise SmcError(rc, "smc_gemm_bf16")
+    return C
 
 
 class SmcError(RuntimeError):
