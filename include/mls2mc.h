@@ -183,6 +183,32 @@ int smc_set_particles(smc_handle* h, const double* theta);
  * info (may be NULL): type 0, the level, the new beta, delta, cv, log mean weight, accept rate. */
 int smc_tempering_update(smc_handle* h, int level, double beta0, int n_mcmc, smc_stage_info* info);
 
+/* ---- surrogate network (no counterpart in the paper) ------------------------------------------
+ * Per level, a network theta -> G_l(theta): K inputs, 4 hidden layers of 256 with the exact GELU
+ * z Phi(z), n_obs outputs; BF16 weights and activations, FP32 accumulation (tensor cores), FP32
+ * master weights, Adam (lr 1e-3, betas 0.9/0.999, eps 1e-8). It predicts standardised observations
+ * (G - mu) / s, mu and s the per-output mean and standard deviation of its training targets (fixed
+ * at the first training). It serves as the first stage of delayed-acceptance pCN (Christen & Fox
+ * 2005); the exact potential still judges every accepted move. Parameter arrays are flat FP32:
+ * for l = 0..4, W_l [d(l+1)][d(l)] row-major then b_l [d(l+1)], with d from smc_surrogate_dims
+ * (d0 = K rounded up to 8, d1..d4 = 256, d5 = n_obs rounded up to 16; padding rows/columns 0). */
+
+/* dims6 <- the six layer widths d0..d5. */
+int smc_surrogate_dims(smc_handle* h, int* dims6);
+/* Append n training pairs (theta [n][K], G [n][n_obs], host) to level's ring of recent pairs. */
+int smc_surrogate_add_pairs(smc_handle* h, int level, int n, const double* theta, const double* G);
+/* steps Adam steps on minibatches of `batch` pairs drawn (Philox) from the ring; *loss (may be NULL)
+ * gets the last minibatch's mean squared error in standardised units. */
+int smc_surrogate_train(smc_handle* h, int level, int steps, int batch, double* loss);
+/* Surrogate G~ [n][n_obs] (may be NULL) and Phi~ [n] (may be NULL) of theta [n][K] (host arrays). */
+int smc_surrogate_predict(smc_handle* h, int level, int n, const double* theta, double* G, double* phi);
+/* direction 1: copy the FP32 parameters (and mu, s: [2][d5], may be NULL) out; 0: copy them in. */
+int smc_surrogate_params(smc_handle* h, int level, int direction, float* params, float* mu_sd);
+/* One forward and backward pass on n pairs without an update: gradients of the mean squared error
+ * (same flat layout as the parameters) and the loss. */
+int smc_surrogate_grads(smc_handle* h, int level, int n, const double* theta, const double* G, float* grads,
+                        double* loss);
+
 /* ---- kernel-level entry points of the sampler's device steps -------------------------------- */
 
 /* The adaptive increment of Eq. Eq_cv_opt for incremental log-weights -delta * a_j, j < n <= J:

@@ -63,6 +63,8 @@ Handle::~Handle() {
         cudaEventDestroy(t.stop);
     }
     for (auto ev : event_pool) cudaEventDestroy(ev);
+    for (auto& m : mlps) m.release();
+    mwork.release();
     cudaFree(scratch_theta);
     cudaFree(scratch_G);
     cudaFree(scratch_phi);

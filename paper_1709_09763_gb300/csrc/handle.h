@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "mlp.h"
 
 namespace mls2mc {
 
@@ -51,6 +52,20 @@ struct Handle {
     std::vector<TimedLaunch> timed;
     std::vector<cudaEvent_t> event_pool;
     cudaEvent_t take_event();
+
+    // surrogate networks (mlp.cu)
+    std::vector<Mlp> mlps;
+    MlpWork mwork;
+    float mlp_lr = 1e-3f;
+    int mlp_setup(int level);
+    int mlp_sync_bf16(int level);
+    int mlp_work(int B);
+    int mlp_forward(int level, int B, const double* theta, bool training);
+    int mlp_predict(int level, int B, const double* theta, double* G, double* phi);
+    int mlp_backward(int level, int B, double* loss);
+    int mlp_adam(int level);
+    int mlp_add_pairs(int level, int n, const double* theta, const double* G);
+    int mlp_train(int level, int steps, int batch, double* last_loss);
 
     ~Handle();
     int fail(int code, const char* fmt, ...);

@@ -91,6 +91,14 @@ SIGNATURES = {
                                           ctypes.c_uint, _dp]),
     "smc_systematic_resample_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "smc_surrogate_dims": (ctypes.c_int, [ctypes.c_void_p, _ip]),
+    "smc_surrogate_add_pairs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp, _dp]),
+    "smc_surrogate_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]),
+    "smc_surrogate_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]),
+    "smc_surrogate_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
+    "smc_surrogate_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_void_p,
+                                           _dp]),
     "smc_gemm_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p]),
     "smc_philox_uniforms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_uint, _dp]),
@@ -284,6 +292,64 @@ class Handle:
         out = np.empty(J)
         self._check(self._lib.smc_philox_uniforms(self._h, J, event, purpose, _dptr(out)))
         return out
+
+    # ---- surrogate network -----------------------------------------------------------------
+    def surrogate_dims(self):
+        d = (ctypes.c_int * 6)()
+        self._check(self._lib.smc_surrogate_dims(self._h, d))
+        return list(d)
+
+    def _nparams(self):
+        d = self.surrogate_dims()
+        return sum(d[l + 1] * d[l] + d[l + 1] for l in range(5))
+
+    def unflatten(self, flat):
+        d = self.surrogate_dims()
+        W, b, off = [], [], 0
+        for l in range(5):
+            W.append(flat[off:off + d[l + 1] * d[l]].reshape(d[l + 1], d[l]))
+            off += d[l + 1] * d[l]
+            b.append(flat[off:off + d[l + 1]])
+            off += d[l + 1]
+        return W, b
+
+    def surrogate_get(self, level):
+        p = np.empty(self._nparams(), dtype=np.float32)
+        ms = np.empty(2 * self.surrogate_dims()[5], dtype=np.float32)
+        self._check(self._lib.smc_surrogate_params(self._h, level, 1, p.ctypes.data, ms.ctypes.data))
+        return p, ms
+
+    def surrogate_set(self, level, params, mu_sd):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        ms = np.ascontiguousarray(mu_sd, dtype=np.float32)
+        self._check(self._lib.smc_surrogate_params(self._h, level, 0, p.ctypes.data, ms.ctypes.data))
+
+    def surrogate_add_pairs(self, level, theta, G):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        self._check(self._lib.smc_surrogate_add_pairs(self._h, level, theta.shape[0], _dptr(theta), _dptr(G)))
+
+    def surrogate_train(self, level, steps, batch):
+        loss = ctypes.c_double()
+        self._check(self._lib.smc_surrogate_train(self._h, level, steps, batch, ctypes.byref(loss)))
+        return loss.value
+
+    def surrogate_predict(self, level, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        G = np.empty((theta.shape[0], self.n_obs))
+        phi = np.empty(theta.shape[0])
+        self._check(self._lib.smc_surrogate_predict(self._h, level, theta.shape[0], _dptr(theta), _dptr(G),
+                                                    _dptr(phi)))
+        return G, phi
+
+    def surrogate_grads(self, level, theta, G):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        g = np.empty(self._nparams(), dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self._lib.smc_surrogate_grads(self._h, level, theta.shape[0], _dptr(theta), _dptr(G),
+                                                  g.ctypes.data, ctypes.byref(loss)))
+        return g, loss.value
 
     def kl_table(self, level, N):
         psi = np.empty((self.K, 2 * N * N))
