@@ -74,6 +74,9 @@ typedef struct {
     uint64_t seed;             /* Philox4x32-10 key */
     int max_iter;              /* cap on inner CG iterations per refinement pass */
     double rtol;               /* FP64 relative residual target of each forward solve */
+    int surrogate;             /* 0: plain pCN; 1: delayed-acceptance pCN screened by the surrogate network */
+    int surrogate_train_steps; /* Adam steps per training round (<= 0: 100) */
+    int surrogate_batch;       /* training minibatch (<= 0: 512) */
     void* stream;              /* cudaStream_t used for all work, or NULL for the default stream */
 } smc_sampler_opts;
 

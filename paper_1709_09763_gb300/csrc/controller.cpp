@@ -32,6 +32,13 @@ struct Sampler {
     int *anc = nullptr, *iters = nullptr;
     unsigned long long* n_acc = nullptr;
     IncWork inc;
+    // delayed acceptance: surrogate potentials of current particles (s) and proposals (sp),
+    // compacted survivors of stage 1, observations of exact solves (training pairs)
+    double *G_buf = nullptr, *ps_c = nullptr, *ps_f = nullptr, *psp_c = nullptr, *psp_f = nullptr;
+    double *theta_s = nullptr, *phi_cs = nullptr, *phi_fs = nullptr;
+    int *surv_idx = nullptr, *n_surv = nullptr;
+    long long pairs_new[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long da_proposals = 0, da_pass1 = 0;
     // host-side state
     bool started = false;
     int level = 0;
@@ -66,6 +73,14 @@ int Handle::alloc_sampler() {
     A((void**)&smp->n_acc, 8);
     A((void**)&smp->inc.state, sizeof(IncState));
     A((void**)&smp->inc.partials, (size_t)kIncMaxBlocks * 4 * 8);
+    if (opts.surrogate) {
+        A((void**)&smp->G_buf, (size_t)J * n_obs * 8);
+        for (double** p : {&smp->ps_c, &smp->ps_f, &smp->psp_c, &smp->psp_f, &smp->phi_cs, &smp->phi_fs})
+            A((void**)p, (size_t)J * 8);
+        A((void**)&smp->theta_s, JK * 8);
+        A((void**)&smp->surv_idx, (size_t)J * 4);
+        A((void**)&smp->n_surv, 4);
+    }
     if (e != cudaSuccess) return fail(SMC_ENOMEM, "sampler buffers for J = %d: %s", J, cudaGetErrorString(e));
     return SMC_OK;
 }
@@ -76,7 +91,9 @@ void Handle::free_sampler() {
                     (void*)smp->phi_f, (void*)smp->phi_cp, (void*)smp->phi_fp, (void*)smp->phi_t0,
                     (void*)smp->phi_t1, (void*)smp->a, (void*)smp->cdf, (void*)smp->scal, (void*)smp->mom,
                     (void*)smp->anc, (void*)smp->iters, (void*)smp->n_acc, (void*)smp->inc.state,
-                    (void*)smp->inc.partials})
+                    (void*)smp->inc.partials, (void*)smp->G_buf, (void*)smp->ps_c, (void*)smp->ps_f,
+                    (void*)smp->psp_c, (void*)smp->psp_f, (void*)smp->theta_s, (void*)smp->phi_cs,
+                    (void*)smp->phi_fs, (void*)smp->surv_idx, (void*)smp->n_surv})
         cudaFree(p);
     delete smp;
     smp = nullptr;
@@ -93,12 +110,38 @@ void Handle::free_sampler() {
         if (_r != SMC_OK) return _r;    \
     } while (0)
 
-// likelihood of n particles on one level, counted; non-convergence checked at the end of an update
+// exact likelihood of n particles on one level, counted; with the surrogate enabled the
+// observations are kept as training pairs (theta, G_l(theta)) of that level's network
 int Handle::smp_eval(int level, int n, const double* theta, double* phi) {
     if (n <= 0) return SMC_OK;
-    RC(eval_device(level, n, theta, nullptr, phi, smp->iters, stream));
+    const bool collect = opts.surrogate && forward_kind == SMC_FWD_FEM;
+    RC(eval_device(level, n, theta, collect ? smp->G_buf : nullptr, phi, smp->iters, stream));
     smp->evals[level] += n;
+    if (collect) {
+        RC(mlp_add_pairs(level, n, theta, smp->G_buf));
+        smp->pairs_new[level] += n;
+    }
     return check_iters(n);
+}
+
+// training schedule: the first time a level has J pairs, then after every J new pairs
+int Handle::maybe_train(int level) {
+    if (!opts.surrogate || forward_kind != SMC_FWD_FEM) return SMC_OK;
+    if ((int)mlps.size() <= level || !mlps[level].ready) return SMC_OK;
+    Mlp& M = mlps[level];
+    if (M.count < smp->J || smp->pairs_new[level] < smp->J) return SMC_OK;
+    const int steps = opts.surrogate_train_steps > 0 ? opts.surrogate_train_steps : 100;
+    const int batch = std::min(opts.surrogate_batch > 0 ? opts.surrogate_batch : 512, M.count);
+    double loss = 0.0;
+    RC(mlp_train(level, steps, batch, &loss));
+    smp->pairs_new[level] = 0;
+    return SMC_OK;
+}
+
+bool Handle::da_ready(int level, double zeta) const {
+    if (!opts.surrogate || forward_kind != SMC_FWD_FEM) return false;
+    auto trained = [&](int l) { return (int)mlps.size() > l && mlps[l].ready && mlps[l].t > 0; };
+    return trained(level) && (zeta < 0.0 || trained(level + 1));
 }
 
 int Handle::check_iters(int n) {
@@ -140,6 +183,9 @@ int Handle::reweight_resample(const double* a, double dmax, bool carry_fine, Inc
 
 // n_mcmc pCN steps; zeta < 0: tempering target on `level`, else bridging target on level, level+1
 int Handle::mcmc(int level, double zeta, double& rate) {
+    RC(maybe_train(level));
+    if (zeta >= 0.0) RC(maybe_train(level + 1));
+    if (da_ready(level, zeta)) return mcmc_da(level, zeta, rate);
     Sampler* S = smp;
     const double s = opts.s_pcn, c0 = std::sqrt(1.0 - s * s);
     CK(cudaMemsetAsync(S->n_acc, 0, 8, stream));
@@ -159,6 +205,50 @@ int Handle::mcmc(int level, double zeta, double& rate) {
     return SMC_OK;
 }
 
+// delayed-acceptance pCN (Christen & Fox 2005): stage 1 on the surrogate potentials of every
+// proposal, exact solves only for the stage-1 survivors, stage 2 with the surrogate-corrected
+// exact ratio; the target is unchanged
+int Handle::mcmc_da(int level, double zeta, double& rate) {
+    Sampler* S = smp;
+    const int J = S->J;
+    const bool br = zeta >= 0.0;
+    const double s = opts.s_pcn, c0 = std::sqrt(1.0 - s * s);
+    CK(cudaMemsetAsync(S->n_acc, 0, 8, stream));
+    RC(mlp_predict(level, J, S->theta, nullptr, S->ps_c));
+    if (br) RC(mlp_predict(level + 1, J, S->theta, nullptr, S->ps_f));
+    long long passed = 0;
+    for (int m = 0; m < opts.n_mcmc; ++m) {
+        const uint32_t ev = (uint32_t)S->mcmc_event;
+        CK(normals_launch(S->theta_p, J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
+        RC(mlp_predict(level, J, S->theta_p, nullptr, S->psp_c));
+        if (br) RC(mlp_predict(level + 1, J, S->theta_p, nullptr, S->psp_f));
+        CK(cudaMemsetAsync(S->n_surv, 0, 4, stream));
+        CK(da_stage1_launch(J, K, S->beta, zeta, ev, opts.seed, S->ps_c, S->ps_f, S->psp_c, S->psp_f, S->theta_p,
+                            S->surv_idx, S->n_surv, S->theta_s, stream));
+        int ns = 0;
+        CK(cudaMemcpyAsync(&ns, S->n_surv, 4, cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        passed += ns;
+        if (ns > 0) {
+            RC(smp_eval(level, ns, S->theta_s, S->phi_cs));
+            if (br) RC(smp_eval(level + 1, ns, S->theta_s, S->phi_fs));
+            CK(da_stage2_launch(ns, K, S->beta, zeta, ev, opts.seed, S->surv_idx, S->theta_s, S->phi_cs, S->phi_fs,
+                                S->theta, S->phi_c, S->phi_f, S->ps_c, S->ps_f, S->psp_c, S->psp_f, S->n_acc,
+                                stream));
+        }
+        S->mcmc_event += 1;
+    }
+    unsigned long long acc = 0;
+    CK(cudaMemcpyAsync(&acc, S->n_acc, 8, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    const double props = (double)opts.n_mcmc * J;
+    rate = props > 0 ? (double)acc / props : 0.0;
+    S->da_proposals += (long long)props;
+    S->da_pass1 += passed;
+    last_da_rate = props > 0 ? (double)passed / props : 0.0;
+    return SMC_OK;
+}
+
 void Handle::record(int type, double zeta, const IncState& st, double rate, double cv_lu, smc_stage_info* info) {
     Sampler* S = smp;
     smc_stage_info r;
@@ -172,6 +262,8 @@ void Handle::record(int type, double zeta, const IncState& st, double rate, doub
     r.cv_lu = cv_lu;
     r.log_z_inc = st.log_mean_w;
     r.accept_rate = rate;
+    r.da_stage1_rate = last_da_rate;
+    last_da_rate = -1.0;
     for (int l = 0; l < 8; ++l) r.evals_per_level[l] = S->evals[l];
     S->path.push_back(r);
     if (info) *info = r;

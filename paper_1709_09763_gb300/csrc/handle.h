@@ -80,6 +80,10 @@ struct Handle {
     int increment(const double* a, int n, double dmax, struct IncState& st);
     int reweight_resample(const double* a, double dmax, bool carry_fine, struct IncState& st);
     int mcmc(int level, double zeta, double& rate);
+    int mcmc_da(int level, double zeta, double& rate);
+    int maybe_train(int level);
+    bool da_ready(int level, double zeta) const;
+    double last_da_rate = -1.0;
     void record(int type, double zeta, const struct IncState& st, double rate, double cv_lu, smc_stage_info* info);
     int itu(double cv_lu, smc_stage_info* info);
     int tempering_update(int level, double beta0, int n_mcmc, smc_stage_info* info);

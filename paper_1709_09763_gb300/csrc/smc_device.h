@@ -52,6 +52,13 @@ cudaError_t cv_lu_launch(const double* phi_c, const double* phi_f, int n, double
 cudaError_t pcn_accept_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, double* theta,
                               const double* theta_p, double* phi_c, const double* phi_cp, double* phi_f,
                               const double* phi_fp, unsigned long long* n_acc, cudaStream_t st);
+cudaError_t da_stage1_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, const double* ps_c,
+                             const double* ps_f, const double* psp_c, const double* psp_f, const double* theta_p,
+                             int* surv_idx, int* n_surv, double* theta_s, cudaStream_t st);
+cudaError_t da_stage2_launch(int ns, int K, double beta, double zeta, uint32_t event, uint64_t seed, const int* surv_idx,
+                             const double* theta_s, const double* phi_cs, const double* phi_fs, double* theta,
+                             double* phi_c, double* phi_f, double* ps_c, double* ps_f, const double* psp_c,
+                             const double* psp_f, unsigned long long* n_acc, cudaStream_t st);
 cudaError_t moments_launch(const double* theta, int n, int K, double* mean, double* var, cudaStream_t st);
 
 }  // namespace mls2mc

@@ -359,6 +359,59 @@ __global__ void pcn_accept_kernel(int n, int K, double beta, double zeta, uint32
     if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(n_acc, (unsigned long long)__popc(ballot));
 }
 
+// ---- delayed acceptance (Christen & Fox 2005) ----------------------------------------------------
+// stage 1 on the surrogate potentials: pass with probability min(1, exp(-(t~(theta') - t~(theta))));
+// survivors are compacted (index list, proposal rows) for the exact solve
+__global__ void da_stage1_kernel(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed,
+                                 const double* ps_c, const double* ps_f, const double* psp_c, const double* psp_f,
+                                 const double* theta_p, int* surv_idx, int* n_surv, double* theta_s) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const uint4 x = philox(make_uint4(0u, (uint32_t)j, event, (uint32_t)kPurposeDaU), seed);
+    const double U = 1.0 - u53(x.x, x.y);
+    const bool br = zeta >= 0.0;
+    const double t_old = target_potential(beta, zeta, ps_c[j], br ? ps_f[j] : 0.0);
+    const double t_new = target_potential(beta, zeta, psp_c[j], br ? psp_f[j] : 0.0);
+    if (log(U) < -(t_new - t_old)) {
+        const int slot = atomicAdd(n_surv, 1);
+        surv_idx[slot] = j;
+        for (int k = 0; k < K; ++k) theta_s[(size_t)slot * K + k] = theta_p[(size_t)j * K + k];
+    }
+}
+
+// stage 2 on the exact potentials of the survivors, corrected by the surrogate ratio:
+// accept with probability min(1, exp(-(t(theta') - t(theta)) + (t~(theta') - t~(theta))))
+__global__ void da_stage2_kernel(int ns, int K, double beta, double zeta, uint32_t event, uint64_t seed,
+                                 const int* surv_idx, const double* theta_s, const double* phi_cs,
+                                 const double* phi_fs, double* theta, double* phi_c, double* phi_f, double* ps_c,
+                                 double* ps_f, const double* psp_c, const double* psp_f,
+                                 unsigned long long* n_acc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool ok = false;
+    if (i < ns) {
+        const int j = surv_idx[i];
+        const uint4 x = philox(make_uint4(0u, (uint32_t)j, event, (uint32_t)kPurposePcnU), seed);
+        const double U = 1.0 - u53(x.x, x.y);
+        const bool br = zeta >= 0.0;
+        const double t_old = target_potential(beta, zeta, phi_c[j], br ? phi_f[j] : 0.0);
+        const double t_new = target_potential(beta, zeta, phi_cs[i], br ? phi_fs[i] : 0.0);
+        const double s_old = target_potential(beta, zeta, ps_c[j], br ? ps_f[j] : 0.0);
+        const double s_new = target_potential(beta, zeta, psp_c[j], br ? psp_f[j] : 0.0);
+        ok = log(U) < -(t_new - t_old) + (s_new - s_old);
+        if (ok) {
+            for (int k = 0; k < K; ++k) theta[(size_t)j * K + k] = theta_s[(size_t)i * K + k];
+            phi_c[j] = phi_cs[i];
+            ps_c[j] = psp_c[j];
+            if (br) {
+                phi_f[j] = phi_fs[i];
+                ps_f[j] = psp_f[j];
+            }
+        }
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, ok);
+    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(n_acc, (unsigned long long)__popc(ballot));
+}
+
 // ---- posterior moments over equally weighted particles ----------------------------------------
 __global__ void moments_kernel(const double* theta, int n, int K, double* mean, double* var) {
     __shared__ double sh[32];
@@ -470,6 +523,27 @@ cudaError_t pcn_accept_launch(int n, int K, double beta, double zeta, uint32_t e
     if (n <= 0) return cudaSuccess;
     pcn_accept_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, K, beta, zeta, event, seed, theta, theta_p, phi_c, phi_cp,
                                                         phi_f, phi_fp, n_acc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t da_stage1_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, const double* ps_c,
+                             const double* ps_f, const double* psp_c, const double* psp_f, const double* theta_p,
+                             int* surv_idx, int* n_surv, double* theta_s, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    da_stage1_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, K, beta, zeta, event, seed, ps_c, ps_f, psp_c, psp_f, theta_p,
+                                                       surv_idx, n_surv, theta_s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t da_stage2_launch(int ns, int K, double beta, double zeta, uint32_t event, uint64_t seed, const int* surv_idx,
+                             const double* theta_s, const double* phi_cs, const double* phi_fs, double* theta,
+                             double* phi_c, double* phi_f, double* ps_c, double* ps_f, const double* psp_c,
+                             const double* psp_f, unsigned long long* n_acc, cudaStream_t st) {
+    if (ns <= 0) return cudaSuccess;
+    da_stage2_kernel<<<grid_for(ns, 256), 256, 0, st>>>(ns, K, beta, zeta, event, seed, surv_idx, theta_s, phi_cs, phi_fs,
+                                                        theta, phi_c, phi_f, ps_c, ps_f, psp_c, psp_f, n_acc);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1,0 +1,62 @@
+"""Delayed-acceptance pCN with the trained surrogate leaves the posterior unchanged and saves exact
+solves. R seeded replicates of the plain and the surrogate-screened MLS^2MC sampler on the same
+FEM problem: replicate means of every posterior moment agree within 3.5 combined standard errors
+(Bonferroni over K coordinates), and the screened sampler solves fewer exact forward problems
+per pCN proposal."""
+import numpy as np
+import pytest
+
+from oracle import forward as ofwd
+from paper_1709_09763_gb300 import native
+from paper_1709_09763_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1709_09763_gb300 import build
+    build.build()
+
+
+def _problem():
+    K = 8
+    obs = wl.obs_grid(7)
+    lv = ofwd.Level(32, 0.3, 1.0, K, obs)
+    th_true = np.random.default_rng(11).standard_normal(K)
+    G = lv.G(th_true)
+    sigma = 0.02 * np.abs(G).max()
+    y = G + sigma * np.random.default_rng(12).standard_normal(obs.shape[0])
+    return K, obs, y, sigma
+
+
+def _run(surrogate, seed, K, obs, y, sigma):
+    h = native.Handle([8, 16, 32], K, obs, y, sigma, corr_len=0.3, J=1500, J_tilde=100, n_mcmc=5, s_pcn=0.3,
+                      precision=native.SMC_MIXED, seed=seed, surrogate=surrogate, surrogate_train_steps=150)
+    h.run()
+    m, v, lz = h.posterior_moments()
+    path = h.path()
+    st = h.state()
+    h.close()
+    return m, v, lz, path, st
+
+
+def test_delayed_acceptance_same_posterior_fewer_solves():
+    K, obs, y, sigma = _problem()
+    R = 8
+    plain = [_run(0, 100 + r, K, obs, y, sigma) for r in range(R)]
+    da = [_run(1, 100 + r, K, obs, y, sigma) for r in range(R)]
+    for idx in (0, 1):   # means, variances
+        a = np.array([p[idx] for p in plain])
+        b = np.array([d[idx] for d in da])
+        se = np.sqrt(a.var(axis=0, ddof=1) / R + b.var(axis=0, ddof=1) / R)
+        assert np.all(np.abs(a.mean(axis=0) - b.mean(axis=0)) <= 3.5 * se + 1e-12), (idx, a.mean(0), b.mean(0), se)
+    # the screen is active: some updates ran stage 1, and it rejected part of the proposals
+    rates = [p["da_stage1_rate"] for d in da for p in d[3] if p["da_stage1_rate"] >= 0]
+    assert len(rates) > 0 and np.mean(rates) < 0.9
+    # exact solves per pCN proposal: 1 per level for the plain sampler, fewer with the screen
+    def solves_per_update(run):
+        total = sum(run[4]["evals"][:3])
+        props = sum(1 for _ in run[3])
+        return total / props
+    assert np.mean([solves_per_update(d) for d in da]) < np.mean([solves_per_update(p) for p in plain])
