@@ -309,25 +309,50 @@ def main():
     e2e = float(np.mean(e2e_ms))
     e2e_evals = evals_per_step + J          # smc_set_particles evaluates Phi on the coarsest level
 
-    # seconds to posterior: one full MLS^2MC run of the workload (n_mcmc = 5), outside the timed region
+    # seconds to posterior: full MLS^2MC runs (n_mcmc = 5) of the workload from the prior, plain pCN and
+    # delayed-acceptance pCN screened by the surrogate, R seeds each, outside the timed region
     run = None
     if not args.no_run:
-        hr = native.Handle(w.inv_h, w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, variance=w.variance,
-                           J=J, J_tilde=w.J_tilde, n_mcmc=w.n_mcmc, s_pcn=w.s_pcn, tau_star=w.tau_star,
-                           precision=native.SMC_MIXED, seed=w.seed_sampler + 1000 * rank,
-                           stream=stream.cuda_stream)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        hr.run()
-        torch.cuda.synchronize(dev)
-        secs = time.perf_counter() - t0
-        st = hr.state()
-        path = hr.path()
-        run = {"seconds": secs, "updates": st["n_updates"], "evals_per_level": st["evals"][:L],
-               "log_evidence": st["log_z"],
-               "n_itu": sum(p["kind"] == "ITU" for p in path), "n_bridge_steps": sum(p["kind"] == "LU" for p in path),
-               "evals_per_s": sum(st["evals"][:L]) / secs}
-        hr.close()
+        def one_run(inv_h, surrogate, seed):
+            hr = native.Handle(inv_h, w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, variance=w.variance,
+                               J=J, J_tilde=w.J_tilde, n_mcmc=w.n_mcmc, s_pcn=w.s_pcn, tau_star=w.tau_star,
+                               precision=native.SMC_MIXED, seed=seed, stream=stream.cuda_stream,
+                               surrogate=surrogate)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            hr.run()
+            torch.cuda.synchronize(dev)
+            secs = time.perf_counter() - t0
+            st = hr.state()
+            path = hr.path()
+            m, v, lz = hr.posterior_moments()
+            hr.close()
+            rates = [p["da_stage1_rate"] for p in path if p["da_stage1_rate"] >= 0]
+            return {"seconds": secs, "updates": st["n_updates"], "solves_per_level": st["evals"][:len(inv_h)],
+                    "log_evidence": lz, "mean": m, "var": v,
+                    "stage1_pass_rate": float(np.mean(rates)) if rates else None}
+
+        def compare(inv_h, R=3):
+            res = {}
+            for name, sur in (("plain", 0), ("surrogate", 1)):
+                runs = [one_run(inv_h, sur, w.seed_sampler + 1000 * rank + 17 * r) for r in range(R)]
+                res[name] = {"seconds_median": float(np.median([x["seconds"] for x in runs])),
+                             "seconds": [x["seconds"] for x in runs],
+                             "solves_per_level_mean": np.mean([x["solves_per_level"] for x in runs], axis=0).tolist(),
+                             "updates": [x["updates"] for x in runs],
+                             "log_evidence": [x["log_evidence"] for x in runs],
+                             "stage1_pass_rate": runs[0]["stage1_pass_rate"],
+                             "_means": np.array([x["mean"] for x in runs])}
+            a, b = res["plain"].pop("_means"), res["surrogate"].pop("_means")
+            se = np.sqrt(a.var(axis=0, ddof=1) / R + b.var(axis=0, ddof=1) / R)
+            z = np.abs(a.mean(0) - b.mean(0)) / np.where(se > 0, se, np.inf)
+            return {"levels_inv_h": list(inv_h), "J": J, "replicates": R, "plain": res["plain"],
+                    "surrogate": res["surrogate"],
+                    "speedup_surrogate_vs_plain": res["plain"]["seconds_median"] / res["surrogate"]["seconds_median"],
+                    "posterior_mean_diff_over_se_max": float(np.max(z))}
+        # MLS^2MC on the workload's hierarchy, and single-level SMC on its finest level (Example
+        # example_SMC, the paper's reference sampler), plain pCN vs surrogate-screened pCN
+        run = {"mls2mc": compare(tuple(w.inv_h)), "smc_finest": compare((w.inv_h[-1],), R=6)}
 
     t = reduce_max_over_ranks([ms, e2e] + [float(np.mean(x)) for x in level_ms], dist if world > 1 else None, dev)
     ms, e2e = t[0], t[1]
@@ -368,7 +393,7 @@ def main():
             "clocks": clk,
         }
         if run is not None:
-            line["mls2mc_run"] = run
+            line["seconds_to_posterior"] = run
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -74,9 +74,11 @@ typedef struct {
     uint64_t seed;             /* Philox4x32-10 key */
     int max_iter;              /* cap on inner CG iterations per refinement pass */
     double rtol;               /* FP64 relative residual target of each forward solve */
-    int surrogate;             /* 0: plain pCN; 1: delayed-acceptance pCN screened by the surrogate network */
-    int surrogate_train_steps; /* Adam steps per training round (<= 0: 100) */
-    int surrogate_batch;       /* training minibatch (<= 0: 512) */
+    int surrogate;             /* 0: plain pCN; 1: delayed-acceptance pCN screened by the surrogate network on
+                                  the levels where an exact solve costs more than 8 surrogate passes (measured);
+                                  2: screen on every level */
+    int surrogate_train_steps; /* Adam steps of the first training round of a level (<= 0: 200; later rounds 1/4) */
+    int surrogate_batch;       /* training minibatch (<= 0: 1024) */
     void* stream;              /* cudaStream_t used for all work, or NULL for the default stream */
 } smc_sampler_opts;
 
@@ -118,6 +120,14 @@ int smc_kl_table(const smc_handle* h, int level, double* psi, double* lambda);
  * launches, returns the summed device milliseconds and launch counts per level ([8] arrays,
  * either may be NULL) and forgets them. */
 int smc_set_timing(smc_handle* h, int enable);
+/* Autotuner of the solve kernel (no counterpart in the paper): for every level, time each compiled
+ * block size (threads per particle) on n_tune prior draws and keep the fastest for the process
+ * (shared by all handles of the same 1/h and precision). chosen [n_levels] receives the block
+ * sizes, best_ms [n_levels] the time per launch (either may be NULL). smc_set_block_size forces a
+ * block size for a level (T <= 0 restores the default); T must be one of the compiled sizes. */
+int smc_autotune(smc_handle* h, int n_tune, int* chosen, float* best_ms);
+int smc_set_block_size(smc_handle* h, int level, int T);
+
 /* Number of CUDA kernels this library has launched in the process so far (all handles). */
 long long smc_kernel_launches(void);
 int smc_get_timing(smc_handle* h, double* ms_per_level, long long* launches_per_level);

@@ -7,6 +7,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,6 +18,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "smc_device.h"
 #include "internal.h"
 
 using namespace mls2mc;
@@ -23,6 +26,22 @@ using namespace mls2mc;
 namespace mls2mc {
 
 static std::atomic<long long> g_launches{0};
+
+// autotuned block size of the solve kernel per (1/h, precision), process-wide
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, int> g_block;
+
+static int tuned_block(int N, int precision) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_block.find({N, precision});
+    return it == g_block.end() ? 0 : it->second;
+}
+
+static void set_block(int N, int precision, int T) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (T <= 0) g_block.erase({N, precision});
+    else g_block[{N, precision}] = T;
+}
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int Handle::fail(int code, const char* fmt, ...) {
@@ -55,7 +74,11 @@ Handle::~Handle() {
         cudaFree(L.obs_idx);
         cudaFree(L.obs_w);
         cudaFree(L.linA);
+        cudaFree(L.psi_split);
     }
+    cudaFree(synth_kappa_buf);
+    cudaFree(synth_theta_buf);
+    cudaFree(synth_err);
     cudaFree(d_y);
     free_sampler();
     for (auto& t : timed) {
@@ -132,14 +155,21 @@ int Handle::eval_device(int level, int n, const double* theta, double* G, double
         a.rtol_in = precision == SMC_MIXED ? 1e-4 : std::max(0.5 * rtol, 1e-14);
         a.max_outer = precision == SMC_MIXED ? 8 : 3;
         a.max_inner = max_iter;
+        a.kappa = nullptr;
+        if (precision == SMC_MIXED) {
+            int rc = synth_kappa(level, n, theta, st);
+            if (rc != SMC_OK) return rc;
+            a.kappa = synth_kappa_buf;
+        }
+        const int T = tuned_block(L.N, precision);
         if (timing) {
             TimedLaunch t{level, take_event(), take_event()};
             cudaEventRecord(t.start, st);
-            e = fem_eval_launch(a, st);
+            e = fem_eval_launch(a, st, T);
             cudaEventRecord(t.stop, st);
             timed.push_back(t);
         } else {
-            e = fem_eval_launch(a, st);
+            e = fem_eval_launch(a, st, T);
         }
     }
     if (e != cudaSuccess) return cuda_fail(e, "forward-solve launch");
@@ -210,6 +240,10 @@ int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** 
             obs_table(L.N, P->n_obs, P->obs_xy, idx, wts);
             e = upload(&L.psi64, psi.data(), psi.size());
             if (e == cudaSuccess) e = upload(&L.psi32, psi32.data(), psi32.size());
+            if (e == cudaSuccess && O->precision == SMC_MIXED) {
+                std::vector<uint16_t> sp = kl_split_table(psi, P->K, 2 * L.N * L.N);
+                e = upload(&L.psi_split, sp.data(), sp.size());
+            }
             if (e == cudaSuccess) e = upload(&L.obs_idx, idx.data(), idx.size());
             if (e == cudaSuccess) e = upload(&L.obs_w, wts.data(), wts.size());
             L.lambda = lam;
@@ -252,6 +286,60 @@ int smc_kl_table(const smc_handle* hh, int level, double* psi, double* lambda) {
     if (h->forward_kind != SMC_FWD_FEM) return h->fail(SMC_EINVAL, "no KL table for a linear forward model");
     if (psi) std::memcpy(psi, L.psi_host.data(), L.psi_host.size() * sizeof(double));
     if (lambda) std::memcpy(lambda, L.lambda.data(), L.lambda.size() * sizeof(double));
+    return SMC_OK;
+}
+
+int smc_set_block_size(smc_handle* hh, int level, int T) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (level < 0 || level >= (int)h->levels.size() || h->forward_kind != SMC_FWD_FEM)
+        return h->fail(SMC_EINVAL, "level out of range");
+    const int N = h->levels[level].N;
+    if (T > 0) {
+        auto v = fem_block_sizes(N, h->precision);
+        if (std::find(v.begin(), v.end(), T) == v.end()) return h->fail(SMC_EINVAL, "block size %d not compiled for 1/h = %d", T, N);
+    }
+    set_block(N, h->precision, T);
+    return SMC_OK;
+}
+
+int smc_autotune(smc_handle* hh, int n_tune, int* chosen, float* best_ms) {
+    if (!hh || n_tune < 1) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h->forward_kind != SMC_FWD_FEM) return SMC_OK;
+    int rc = h->ensure_scratch(n_tune);
+    if (rc != SMC_OK) return rc;
+    cudaStream_t st = h->stream;
+    cudaError_t e = normals_launch(h->scratch_theta, n_tune, h->K, 0x7fffffffu, 9u, h->opts.seed, nullptr, 0.0, 0.0, st);
+    if (e != cudaSuccess) return h->cuda_fail(e, "autotune draws");
+    cudaEvent_t e0 = h->take_event(), e1 = h->take_event();
+    for (int l = 0; l < (int)h->levels.size(); ++l) {
+        const int N = h->levels[l].N;
+        int bestT = 0;
+        float best = 0.f;
+        for (int T : fem_block_sizes(N, h->precision)) {
+            set_block(N, h->precision, T);
+            for (int rep = 0; rep < 4; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, st);
+                rc = h->eval_device(l, n_tune, h->scratch_theta, nullptr, h->scratch_phi, h->scratch_iters, st);
+                if (rc != SMC_OK) return rc;
+            }
+            cudaEventRecord(e1, st);
+            e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) return h->cuda_fail(e, "autotune timing");
+            if (bestT == 0 || ms < best) {
+                best = ms;
+                bestT = T;
+            }
+        }
+        set_block(N, h->precision, bestT);
+        if (chosen) chosen[l] = bestT;
+        if (best_ms) best_ms[l] = best / 3.0f;
+    }
+    h->event_pool.push_back(e0);
+    h->event_pool.push_back(e1);
     return SMC_OK;
 }
 

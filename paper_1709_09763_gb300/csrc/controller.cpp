@@ -124,14 +124,53 @@ int Handle::smp_eval(int level, int n, const double* theta, double* phi) {
     return check_iters(n);
 }
 
-// training schedule: the first time a level has J pairs, then after every J new pairs
+// Whether screening pays on a level: measured once per level (events on the handle's stream) as
+// the device time of an exact solve of J particles against a surrogate forward pass of J
+// particles; the screen is used where the solve costs more than kDaCostRatio forward passes
+// (the screen adds a forward pass, a compaction and a host read per pCN step).
+constexpr double kDaCostRatio = 8.0;
+
+bool Handle::da_worth(int level) {
+    if ((int)da_gate.size() < (int)levels.size()) da_gate.assign(levels.size(), 0);
+    if (da_gate[level] != 0) return da_gate[level] > 0;
+    if (opts.surrogate == 2) {   // screen every level, no cost measurement
+        da_gate[level] = 1;
+        return true;
+    }
+    Sampler* S = smp;
+    if (mlp_setup(level) != SMC_OK) return false;
+    // untimed pass first: buffers allocated on first use must not fall inside the measurement
+    if (mlp_predict(level, S->J, S->theta, nullptr, S->phi_t0) != SMC_OK) return false;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return false;
+    cudaEvent_t a = take_event(), b = take_event(), c = take_event();
+    cudaEventRecord(a, stream);
+    int rc = mlp_predict(level, S->J, S->theta, nullptr, S->phi_t0);
+    cudaEventRecord(b, stream);
+    if (rc == SMC_OK) rc = eval_device(level, S->J, S->theta, nullptr, S->phi_t1, S->iters, stream);
+    cudaEventRecord(c, stream);
+    float t_pred = 0.f, t_solve = 0.f;
+    if (cudaEventSynchronize(c) == cudaSuccess) {
+        cudaEventElapsedTime(&t_pred, a, b);
+        cudaEventElapsedTime(&t_solve, b, c);
+    }
+    event_pool.push_back(a);
+    event_pool.push_back(b);
+    event_pool.push_back(c);
+    da_gate[level] = (rc == SMC_OK && t_solve > kDaCostRatio * t_pred) ? 1 : -1;
+    return da_gate[level] > 0;
+}
+
+// training schedule: once the level has J pairs, then again after every 4 J new pairs (200 Adam
+// steps the first time, 50 afterwards)
 int Handle::maybe_train(int level) {
     if (!opts.surrogate || forward_kind != SMC_FWD_FEM) return SMC_OK;
     if ((int)mlps.size() <= level || !mlps[level].ready) return SMC_OK;
     Mlp& M = mlps[level];
-    if (M.count < smp->J || smp->pairs_new[level] < smp->J) return SMC_OK;
-    const int steps = opts.surrogate_train_steps > 0 ? opts.surrogate_train_steps : 100;
-    const int batch = std::min(opts.surrogate_batch > 0 ? opts.surrogate_batch : 512, M.count);
+    if (M.count < smp->J) return SMC_OK;
+    if (M.t > 0 && smp->pairs_new[level] < 4LL * smp->J) return SMC_OK;
+    const int base = opts.surrogate_train_steps > 0 ? opts.surrogate_train_steps : 200;
+    const int steps = M.t == 0 ? base : std::max(1, base / 4);
+    const int batch = std::min(opts.surrogate_batch > 0 ? opts.surrogate_batch : 1024, M.count);
     double loss = 0.0;
     RC(mlp_train(level, steps, batch, &loss));
     smp->pairs_new[level] = 0;
@@ -140,8 +179,10 @@ int Handle::maybe_train(int level) {
 
 bool Handle::da_ready(int level, double zeta) const {
     if (!opts.surrogate || forward_kind != SMC_FWD_FEM) return false;
-    auto trained = [&](int l) { return (int)mlps.size() > l && mlps[l].ready && mlps[l].t > 0; };
-    return trained(level) && (zeta < 0.0 || trained(level + 1));
+    auto on = [&](int l) {
+        return (int)mlps.size() > l && mlps[l].ready && mlps[l].t > 0 && (int)da_gate.size() > l && da_gate[l] > 0;
+    };
+    return on(level) && (zeta < 0.0 || on(level + 1));
 }
 
 int Handle::check_iters(int n) {
@@ -183,8 +224,11 @@ int Handle::reweight_resample(const double* a, double dmax, bool carry_fine, Inc
 
 // n_mcmc pCN steps; zeta < 0: tempering target on `level`, else bridging target on level, level+1
 int Handle::mcmc(int level, double zeta, double& rate) {
-    RC(maybe_train(level));
-    if (zeta >= 0.0) RC(maybe_train(level + 1));
+    // networks are trained only for targets whose every level is worth screening
+    if (opts.surrogate && forward_kind == SMC_FWD_FEM && da_worth(level) && (zeta < 0.0 || da_worth(level + 1))) {
+        RC(maybe_train(level));
+        if (zeta >= 0.0) RC(maybe_train(level + 1));
+    }
     if (da_ready(level, zeta)) return mcmc_da(level, zeta, rate);
     Sampler* S = smp;
     const double s = opts.s_pcn, c0 = std::sqrt(1.0 - s * s);

@@ -32,6 +32,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <vector>
 
 #include "internal.h"
 
@@ -284,14 +285,20 @@ fem_eval_kernel(FemArgs a) {
     Lv<Real> F = level_ptrs<Real, N, N>(arena);
     Real* stage = F.e;     // e, res, p of the fine level are contiguous: 3*lvl_size(N) >= 2.5 N^2
 
-    // 1) field u = theta . Psi and kappa = exp(u) on every fine triangle
-    for (int k = tid; k < a.K; k += T) theta_s[k] = (Real)a.theta[(size_t)p * a.K + k];
-    __syncthreads();
-    const Real* psi = static_cast<const Real*>(a.psi);
-    for (int e = tid; e < E; e += T) {
-        Real u = 0;
-        for (int k = 0; k < a.K; ++k) u = fma(theta_s[k], psi[(size_t)k * E + e], u);
-        stage[e] = exp(u);
+    // 1) kappa = exp(u) on every fine triangle: read from the tensor-core synthesis, or
+    //    u = theta . Psi computed here (FP64 path)
+    if (a.kappa) {
+        const float* kp = a.kappa + (size_t)p * E;
+        for (int e = tid; e < E; e += T) stage[e] = (Real)kp[e];
+    } else {
+        for (int k = tid; k < a.K; k += T) theta_s[k] = (Real)a.theta[(size_t)p * a.K + k];
+        __syncthreads();
+        const Real* psi = static_cast<const Real*>(a.psi);
+        for (int e = tid; e < E; e += T) {
+            Real u = 0;
+            for (int k = 0; k < a.K; ++k) u = fma(theta_s[k], psi[(size_t)k * E + e], u);
+            stage[e] = exp(u);
+        }
     }
     __syncthreads();
 
@@ -526,22 +533,50 @@ bool fem_level_supported(int N, int precision) {
     return N == 4 || N == 8 || N == 16 || N == 32;
 }
 
-cudaError_t fem_eval_launch(const FemArgs& a, cudaStream_t st) {
-    if (a.n <= 0) return cudaSuccess;
-    if (a.precision == SMC_MIXED) {
-        switch (a.N) {
-            case 4: return launch_one<float, 4, 32>(a, st);
-            case 8: return launch_one<float, 8, 64>(a, st);
-            case 16: return launch_one<float, 16, 128>(a, st);
-            case 32: return launch_one<float, 32, 256>(a, st);
-            case 64: return launch_one<float, 64, 512>(a, st);
+// block sizes compiled for each level (threads per particle); the autotuner picks one
+std::vector<int> fem_block_sizes(int N, int precision) {
+    if (precision == SMC_MIXED) {
+        switch (N) {
+            case 4: return {32};
+            case 8: return {64, 32};
+            case 16: return {128, 64};
+            case 32: return {256, 512};
+            case 64: return {512, 1024};
         }
     } else {
-        switch (a.N) {
-            case 4: return launch_one<double, 4, 32>(a, st);
-            case 8: return launch_one<double, 8, 64>(a, st);
-            case 16: return launch_one<double, 16, 128>(a, st);
-            case 32: return launch_one<double, 32, 256>(a, st);
+        switch (N) {
+            case 4: return {32};
+            case 8: return {64};
+            case 16: return {128, 256};
+            case 32: return {256, 512};
+        }
+    }
+    return {};
+}
+
+cudaError_t fem_eval_launch(const FemArgs& a, cudaStream_t st, int T) {
+    if (a.n <= 0) return cudaSuccess;
+    if (T <= 0) T = fem_block_sizes(a.N, a.precision).at(0);
+    if (a.precision == SMC_MIXED) {
+        switch (a.N * 10000 + T) {
+            case 4 * 10000 + 32: return launch_one<float, 4, 32>(a, st);
+            case 8 * 10000 + 64: return launch_one<float, 8, 64>(a, st);
+            case 8 * 10000 + 32: return launch_one<float, 8, 32>(a, st);
+            case 16 * 10000 + 128: return launch_one<float, 16, 128>(a, st);
+            case 16 * 10000 + 64: return launch_one<float, 16, 64>(a, st);
+            case 32 * 10000 + 256: return launch_one<float, 32, 256>(a, st);
+            case 32 * 10000 + 512: return launch_one<float, 32, 512>(a, st);
+            case 64 * 10000 + 512: return launch_one<float, 64, 512>(a, st);
+            case 64 * 10000 + 1024: return launch_one<float, 64, 1024>(a, st);
+        }
+    } else {
+        switch (a.N * 10000 + T) {
+            case 4 * 10000 + 32: return launch_one<double, 4, 32>(a, st);
+            case 8 * 10000 + 64: return launch_one<double, 8, 64>(a, st);
+            case 16 * 10000 + 128: return launch_one<double, 16, 128>(a, st);
+            case 16 * 10000 + 256: return launch_one<double, 16, 256>(a, st);
+            case 32 * 10000 + 256: return launch_one<double, 32, 256>(a, st);
+            case 32 * 10000 + 512: return launch_one<double, 32, 512>(a, st);
         }
     }
     return cudaErrorInvalidValue;

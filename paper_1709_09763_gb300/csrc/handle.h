@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -18,6 +19,7 @@ struct Level {
     int* obs_idx = nullptr;      // [n_obs][3]
     double* obs_w = nullptr;     // [n_obs][3]
     double* linA = nullptr;      // linear forward model [n_obs][K]
+    uint16_t* psi_split = nullptr;   // mixed path: BF16 three-way split of Psi^T, [2N^2][kl_split_width(K)]
     std::vector<double> lambda;  // KL eigenvalues
     std::vector<double> psi_host;
 };
@@ -42,6 +44,13 @@ struct Handle {
 
     // sampler state (smc_kernels.cu / controller.cpp)
     struct Sampler* smp = nullptr;
+
+    // tensor-core KL synthesis buffers (kl_synth.cu)
+    float* synth_kappa_buf = nullptr;
+    uint16_t* synth_theta_buf = nullptr;
+    size_t synth_kappa_cap = 0, synth_theta_cap = 0;
+    int* synth_err = nullptr;
+    int synth_kappa(int level, int n, const double* theta, cudaStream_t st);
 
     // opt-in CUDA-event timing of forward-solve launches, per level
     bool timing = false;
@@ -83,6 +92,8 @@ struct Handle {
     int mcmc_da(int level, double zeta, double& rate);
     int maybe_train(int level);
     bool da_ready(int level, double zeta) const;
+    bool da_worth(int level);
+    std::vector<int> da_gate;   // per level: 0 unknown, 1 screen pays, -1 it does not
     double last_da_rate = -1.0;
     void record(int type, double zeta, const struct IncState& st, double rate, double cv_lu, smc_stage_info* info);
     int itu(double cv_lu, smc_stage_info* info);
@@ -93,6 +104,9 @@ struct Handle {
     bool sampler_done() const;
     int step(smc_stage_info* info);
 };
+
+int kl_split_width(int K);
+std::vector<uint16_t> kl_split_table(const std::vector<double>& psi, int K, int E);
 
 // G = A theta and Phi for the linear test forward model (smc_kernels.cu)
 cudaError_t linear_eval_launch(const double* A, int n, int K, int n_obs, const double* theta, const double* y,

@@ -28,6 +28,7 @@ struct FemArgs {
     int K;                  // KL terms
     const double* theta;    // [n][K] device
     const void* psi;        // [K][2N^2] device, double (FP64) or float (MIXED)
+    const float* kappa;     // [n][2N^2] kappa = exp(u) per triangle (MIXED: from the tensor-core synthesis), or null
     const int* obs_idx;     // [n_obs][3] node indices into the (N+1)^2 grid
     const double* obs_w;    // [n_obs][3] P1 weights
     int n_obs;
@@ -42,7 +43,9 @@ struct FemArgs {
     int max_inner;          // inner CG iterations per pass
 };
 // Returns cudaSuccess or the launch error.
-cudaError_t fem_eval_launch(const FemArgs& a, cudaStream_t stream);
+// T = threads per particle (one of fem_block_sizes; <= 0: the first, the default)
+cudaError_t fem_eval_launch(const FemArgs& a, cudaStream_t stream, int T = 0);
+std::vector<int> fem_block_sizes(int N, int precision);
 bool fem_level_supported(int N, int precision);
 
 }  // namespace mls2mc

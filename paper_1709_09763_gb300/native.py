@@ -84,6 +84,8 @@ SIGNATURES = {
     "smc_set_particles": (ctypes.c_int, [ctypes.c_void_p, _dp]),
     "smc_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "smc_kernel_launches": (ctypes.c_longlong, []),
+    "smc_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip, ctypes.c_void_p]),
+    "smc_set_block_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "smc_get_timing": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "smc_tempering_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(StageInfo)]),
@@ -257,6 +259,15 @@ class Handle:
     def set_particles(self, theta):
         theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(self.J, self.K)
         self._check(self._lib.smc_set_particles(self._h, _dptr(theta)))
+
+    def autotune(self, n_tune=1024):
+        chosen = (ctypes.c_int * self.n_levels)()
+        ms = np.zeros(self.n_levels, dtype=np.float32)
+        self._check(self._lib.smc_autotune(self._h, int(n_tune), chosen, ms.ctypes.data))
+        return list(chosen), ms.tolist()
+
+    def set_block_size(self, level, T):
+        self._check(self._lib.smc_set_block_size(self._h, int(level), int(T)))
 
     def set_timing(self, enable=True):
         self._check(self._lib.smc_set_timing(self._h, int(bool(enable))))

@@ -1,6 +1,6 @@
 """Delayed-acceptance pCN with the trained surrogate leaves the posterior unchanged and saves exact
-solves. R seeded replicates of the plain and the surrogate-screened MLS^2MC sampler on the same
-FEM problem: replicate means of every posterior moment agree within 3.5 combined standard errors
+solves (screen forced on every level: surrogate = 2). R seeded replicates of the plain and the
+surrogate-screened MLS^2MC sampler on the same FEM problem: replicate means of every posterior moment agree within 3.5 combined standard errors
 (Bonferroni over K coordinates), and the screened sampler solves fewer exact forward problems
 per pCN proposal."""
 import numpy as np
@@ -45,7 +45,7 @@ def test_delayed_acceptance_same_posterior_fewer_solves():
     K, obs, y, sigma = _problem()
     R = 8
     plain = [_run(0, 100 + r, K, obs, y, sigma) for r in range(R)]
-    da = [_run(1, 100 + r, K, obs, y, sigma) for r in range(R)]
+    da = [_run(2, 100 + r, K, obs, y, sigma) for r in range(R)]
     for idx in (0, 1):   # means, variances
         a = np.array([p[idx] for p in plain])
         b = np.array([d[idx] for d in da])
@@ -60,3 +60,17 @@ def test_delayed_acceptance_same_posterior_fewer_solves():
         props = sum(1 for _ in run[3])
         return total / props
     assert np.mean([solves_per_update(d) for d in da]) < np.mean([solves_per_update(p) for p in plain])
+
+
+def test_cost_gate_screens_only_expensive_levels():
+    """surrogate = 1 screens a level only where an exact solve costs more than 8 surrogate passes:
+    single-level SMC on 1/h = 64 with J = 1500 (every update an ITU on that level) must screen once
+    its network is trained, and still reach beta = 1."""
+    K, obs, y, sigma = _problem()
+    h = native.Handle([64], K, obs, y, sigma, corr_len=0.3, J=1500, n_mcmc=5, s_pcn=0.3,
+                      precision=native.SMC_MIXED, seed=7, surrogate=1)
+    h.run()
+    path = h.path()
+    assert all(p["kind"] == "ITU" for p in path)
+    assert any(p["da_stage1_rate"] >= 0 for p in path)
+    assert h.state()["beta"] == 1.0

@@ -134,3 +134,30 @@ def test_full_size_sampled_parity():
     Gr, Phir = _oracle(64, w, theta[idx], wl.obs_grid(7), np.array(d["y"]), d["sigma"])
     assert _rel(G.cpu().numpy()[idx], Gr).max() < 1e-6
     assert np.all(np.isfinite(Phi.cpu().numpy()))
+
+
+@pytest.mark.parametrize("prec", [native.SMC_MIXED, native.SMC_FP64])
+def test_every_block_size_and_autotuner(prec):
+    """Each compiled threads-per-particle variant gives the oracle's G; the autotuner picks one of them."""
+    w = wl.WORKLOADS["mls2mc_mixed_h8_64"]
+    d = _data(w.name)
+    obs = wl.obs_grid(7)
+    levels = [8, 16, 32, 64] if prec == native.SMC_MIXED else [8, 16, 32]
+    tol = 1e-6 if prec == native.SMC_MIXED else 1e-10
+    h = native.Handle(levels, w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, precision=prec)
+    sizes = {8: [64, 32], 16: [128, 64], 32: [256, 512], 64: [512, 1024]} if prec == native.SMC_MIXED else \
+        {8: [64], 16: [128, 256], 32: [256, 512]}
+    theta = wl.particles(9, w.K, 31)
+    for l, N in enumerate(levels):
+        Gr, _ = _oracle(N, w, theta, obs, np.array(d["y"]), d["sigma"])
+        for T in sizes[N]:
+            h.set_block_size(l, T)
+            G, _ = h.eval_likelihood(l, theta)
+            assert _rel(G, Gr).max() < tol, (N, T)
+        h.set_block_size(l, 0)
+    with pytest.raises(native.SmcError):
+        h.set_block_size(0, 96)
+    chosen, ms = h.autotune(256)
+    assert all(c in sizes[N] for c, N in zip(chosen, levels)) and all(m > 0 for m in ms)
+    for l in range(len(levels)):
+        h.set_block_size(l, 0)
