@@ -225,6 +225,7 @@ def main():
                       J_tilde=w.J_tilde, n_mcmc=1, s_pcn=w.s_pcn, tau_star=w.tau_star,
                       precision=native.SMC_MIXED, seed=w.seed_sampler + 1000 * rank, stream=stream.cuda_stream)
     theta0 = wl.particles(J, w.K, 1000 + rank)
+    tuned, _ = h.autotune(J)            # block size per level, chosen by the library's autotuner
     h.set_particles(theta0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
     n_mcmc_step = 1
@@ -376,12 +377,13 @@ def main():
                        "precision": "mixed", "step": "per level: Phi on all particles, adaptive increment, "
                        "systematic resampling, 1 pCN sweep (propose, solve, accept)",
                        "evals_per_step": evals_per_step, "l2": "flushed between steps (256 MB write)",
+                       "threads_per_particle": dict(zip([str(N) for N in w.inv_h], tuned)),
                        "parallelism": f"replicas x{world}"},
             "per_level": {str(N): {"evals_per_s": 2 * J * world / (lm * 1e-3), "update_ms": lm,
                                    "solve_launch_ms": kern_ms[l] / max(kern_n[l], 1),
                                    "solve_evals_per_s": J / (kern_ms[l] / max(kern_n[l], 1) * 1e-3)}
                           for l, (N, lm) in enumerate(zip(w.inv_h, lvl_ms))},
-            "roofline": {"kernel": f"fem_eval_kernel<float,{w.inv_h[-1]},512>", "bound": "alu",
+            "roofline": {"kernel": f"fem_eval_kernel<float,{w.inv_h[-1]},{tuned[-1]}>", "bound": "alu",
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": None, "launch_ms": launch_ms,
                          "launches": kern_n[kl], "mean_cg_iters": mean_it,

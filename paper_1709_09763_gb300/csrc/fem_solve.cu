@@ -87,6 +87,34 @@ __device__ __forceinline__ void block_sum(Acc& a, double* buf_raw) {
     a = s;
 }
 
+template <int T, typename Acc>
+__device__ __forceinline__ void block_sum3(Acc& a, Acc& b, Acc& c, double* buf_raw) {
+    Acc* buf = reinterpret_cast<Acc*>(buf_raw);   // 3 x 16 entries used (T <= 512 for float, 256 for double)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
+        c += __shfl_xor_sync(0xffffffffu, c, off);
+    }
+    constexpr int NW = T / 32;
+    if ((threadIdx.x & 31) == 0) {
+        buf[threadIdx.x >> 5] = a;
+        buf[NW + (threadIdx.x >> 5)] = b;
+        buf[2 * NW + (threadIdx.x >> 5)] = c;
+    }
+    __syncthreads();
+    Acc sa = 0, sb = 0, sc = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        sa += buf[i];
+        sb += buf[NW + i];
+        sc += buf[2 * NW + i];
+    }
+    a = sa;
+    b = sb;
+    c = sc;
+}
+
 // ---- error-free transformations (Knuth TwoSum, Dekker), double-float accumulation ----
 template <typename Real>
 __device__ __forceinline__ void two_sum(Real a, Real b, Real& s, Real& e) {
@@ -168,30 +196,45 @@ __device__ __forceinline__ void prolong_add(const Lv<Real>& L, const Real* ec) {
     }
 }
 
-// V(1,1) cycle on a coarse level: reads L.rhs, writes L.e
-template <typename Real, int N, int NL, int T>
+// barrier between the phases of a V-cycle: the whole block, or only warp 0 on the small levels
+template <bool WARP>
+__device__ __forceinline__ void phase_sync() {
+    if constexpr (WARP) __syncwarp();
+    else __syncthreads();
+}
+
+// V(1,1) cycle on a coarse level: reads L.rhs, writes L.e. Levels with at most 4 cells per side
+// (<= 9 unknowns) run inside warp 0 only (T = 32, warp barriers); the caller's next block
+// barrier publishes the result.
+template <typename Real, int N, int NL, int T, bool WARP = false>
 __device__ void vcycle_coarse(Real* arena) {
-    Lv<Real> L = level_ptrs<Real, N, NL>(arena);
-    if constexpr (NL == 2) {
-        if (threadIdx.x == 0) L.e[4] = L.rhs[4] * L.iD[4];   // single interior node (1,1), S = 3
+    if constexpr (!WARP && NL <= 4) {
+        if (threadIdx.x < 32) vcycle_coarse<Real, N, NL, 32, true>(arena);
         __syncthreads();
+        return;
     } else {
-        Lv<Real> C = level_ptrs<Real, N, NL / 2>(arena);
-        smooth_first_red<Real, NL, T>(L);
-        __syncthreads();
-        smooth_color<Real, NL, T>(L, 1);
-        __syncthreads();
-        residual<Real, NL, T>(L);
-        __syncthreads();
-        restrict_to<Real, NL / 2, T>(L.res, C.rhs);
-        __syncthreads();
-        vcycle_coarse<Real, N, NL / 2, T>(arena);
-        prolong_add<Real, NL, T>(L, C.e);
-        __syncthreads();
-        smooth_color<Real, NL, T>(L, 1);
-        __syncthreads();
-        smooth_color<Real, NL, T>(L, 0);
-        __syncthreads();
+        Lv<Real> L = level_ptrs<Real, N, NL>(arena);
+        if constexpr (NL == 2) {
+            if (threadIdx.x == 0) L.e[4] = L.rhs[4] * L.iD[4];   // single interior node (1,1), S = 3
+            phase_sync<WARP>();
+        } else {
+            Lv<Real> C = level_ptrs<Real, N, NL / 2>(arena);
+            smooth_first_red<Real, NL, T>(L);
+            phase_sync<WARP>();
+            smooth_color<Real, NL, T>(L, 1);
+            phase_sync<WARP>();
+            residual<Real, NL, T>(L);
+            phase_sync<WARP>();
+            restrict_to<Real, NL / 2, T>(L.res, C.rhs);
+            phase_sync<WARP>();
+            vcycle_coarse<Real, N, NL / 2, T, WARP>(arena);
+            prolong_add<Real, NL, T>(L, C.e);
+            phase_sync<WARP>();
+            smooth_color<Real, NL, T>(L, 1);
+            phase_sync<WARP>();
+            smooth_color<Real, NL, T>(L, 0);
+            phase_sync<WARP>();
+        }
     }
 }
 
@@ -361,7 +404,7 @@ fem_eval_kernel(FemArgs a) {
         }
         block_sum<T>(rr0, red_buf[parity]);
         parity ^= 1;
-        if (rr0 == Real(0)) break;
+        if (!(rr0 > Real(0))) break;
         const Real stop2 = rtol_in2 * rr0;
         Real rz = 0;
         for (int it = 0; it < a.max_inner; ++it) {

@@ -104,6 +104,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
@@ -211,17 +226,38 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     const bool done = mbar_wait(smem_u32(&done_bar), 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (done) {
-        const int row = m0 + 32 * warp + lane;
         const uint32_t t_row = tmem + ((uint32_t)(32 * warp) << 16);
+        if (epi.kind == kEpiStoreF32 || epi.kind == kEpiExp) {
+            // 32 x 32 blocks staged through shared memory (the pipeline slots are free now): each
+            // lane holds one row, then each store instruction writes 32 consecutive columns of one row
+            float* stage = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw))) + warp * (32 * 33);
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            float v[16];
-            tmem_ld16(t_row + (uint32_t)c0, v);
-            if (row < M) {
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                float v[32];
+                tmem_ld32(t_row + (uint32_t)c0, v);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int col = n0 + c0 + i;
-                    if (col < N) epilogue(epi, row, col, v[i]);
+                for (int i = 0; i < 32; ++i) stage[lane * 33 + i] = v[i];
+                __syncwarp();
+                const int col = n0 + c0 + lane;
+#pragma unroll 4
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int row = m0 + 32 * warp + rr;
+                    if (row < M && col < N) epilogue(epi, row, col, stage[rr * 33 + lane]);
+                }
+                __syncwarp();
+            }
+        } else {
+            const int row = m0 + 32 * warp + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float v[16];
+                tmem_ld16(t_row + (uint32_t)c0, v);
+                if (row < M) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int col = n0 + c0 + i;
+                        if (col < N) epilogue(epi, row, col, v[i]);
+                    }
                 }
             }
         }
