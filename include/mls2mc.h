@@ -135,6 +135,24 @@ int smc_get_timing(smc_handle* h, double* ms_per_level, long long* launches_per_
 /* Sizes of a handle: K, n_obs, number of levels, J. Any pointer may be NULL. */
 int smc_sizes(const smc_handle* h, int* K, int* n_obs, int* n_levels, int* J);
 
+/* ---- many independent problems (no counterpart in the paper) -------------------------------
+ * A batch groups handles of independent inverse problems (each its own hierarchy, K, data). One
+ * batch evaluation runs, for every problem p, the likelihood of n[p] particles (device array
+ * theta[p], [n[p]][K_p]) on its level level[p], writing phi[p] [n[p]] (device) and, if iters is
+ * not NULL, iters[p] [n[p]] (device, as in smc_eval_likelihood_device): the tensor-core KL
+ * syntheses of all mixed-precision problems, then one persistent solve launch per level size
+ * whose blocks take (problem, particle) work items from a device counter. With use_graph = 1 the
+ * sequence is captured into a CUDA graph on `stream` (which must not be the default stream) the
+ * first time and replayed afterwards, as long as levels, counts and pointers are unchanged. The
+ * call queues work on `stream` and does not wait. Handles must be distinct FEM handles and must
+ * outlive the batch. */
+typedef struct smc_batch smc_batch;
+int smc_batch_create(int n_problems, smc_handle* const* handles, smc_batch** out);
+int smc_batch_eval(smc_batch* b, const int* level, const int* n, const double* const* theta, double* const* phi,
+                   int* const* iters, void* stream, int use_graph);
+const char* smc_batch_last_error(const smc_batch* b);
+void smc_batch_destroy(smc_batch* b);
+
 /* ---- the sampler (needs opts.J > 0) ------------------------------------------------------- */
 
 /* One record per importance-sampling update: an inverse temperature update (type 0, ITU) or one

@@ -125,6 +125,35 @@ cudaEvent_t Handle::take_event() {
     return e;
 }
 
+int Handle::block_size(int N) const { return tuned_block(N, precision); }
+
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+FemArgs Handle::fem_args(int level, int n, const double* theta, double* G, double* Phi, int* iters) const {
+    const Level& L = levels[level];
+    FemArgs a{};
+    a.N = L.N;
+    a.precision = precision;
+    a.n = n;
+    a.K = K;
+    a.theta = theta;
+    a.psi = precision == SMC_MIXED ? (const void*)L.psi32 : (const void*)L.psi64;
+    a.kappa = nullptr;
+    a.obs_idx = L.obs_idx;
+    a.obs_w = L.obs_w;
+    a.n_obs = n_obs;
+    a.y = d_y;
+    a.inv_sigma2 = 1.0 / (sigma * sigma);
+    a.G = G;
+    a.Phi = Phi;
+    a.iters = iters;
+    a.rtol = rtol;
+    a.rtol_in = precision == SMC_MIXED ? 1e-4 : std::max(0.5 * rtol, 1e-14);
+    a.max_outer = precision == SMC_MIXED ? 8 : 3;
+    a.max_inner = max_iter;
+    return a;
+}
+
 int Handle::eval_device(int level, int n, const double* theta, double* G, double* Phi, int* iters,
                         cudaStream_t st) {
     if (level < 0 || level >= (int)levels.size()) return fail(SMC_EINVAL, "level %d out of range", level);
@@ -136,26 +165,7 @@ int Handle::eval_device(int level, int n, const double* theta, double* G, double
     if (forward_kind == SMC_FWD_LINEAR) {
         e = linear_eval_launch(L.linA, n, K, n_obs, theta, d_y, 1.0 / (sigma * sigma), G, Phi, iters, st);
     } else {
-        FemArgs a{};
-        a.N = L.N;
-        a.precision = precision;
-        a.n = n;
-        a.K = K;
-        a.theta = theta;
-        a.psi = precision == SMC_MIXED ? (const void*)L.psi32 : (const void*)L.psi64;
-        a.obs_idx = L.obs_idx;
-        a.obs_w = L.obs_w;
-        a.n_obs = n_obs;
-        a.y = d_y;
-        a.inv_sigma2 = 1.0 / (sigma * sigma);
-        a.G = G;
-        a.Phi = Phi;
-        a.iters = iters;
-        a.rtol = rtol;
-        a.rtol_in = precision == SMC_MIXED ? 1e-4 : std::max(0.5 * rtol, 1e-14);
-        a.max_outer = precision == SMC_MIXED ? 8 : 3;
-        a.max_inner = max_iter;
-        a.kappa = nullptr;
+        FemArgs a = fem_args(level, n, theta, G, Phi, iters);
         if (precision == SMC_MIXED) {
             int rc = synth_kappa(level, n, theta, st);
             if (rc != SMC_OK) return rc;

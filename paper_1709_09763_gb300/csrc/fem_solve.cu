@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
@@ -310,20 +311,14 @@ struct Fine {
 };
 
 // ---- the kernel ----------------------------------------------------------------------
+// the whole solve of particle p of a.n, by one thread block (all threads call it)
 template <typename Real, int N, int T>
-__global__ void __launch_bounds__(T, 1)
-fem_eval_kernel(FemArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real* arena = reinterpret_cast<Real*>(smem_raw);
-    __shared__ double red_buf[2][64];
-    __shared__ Real theta_s[256];
-
+__device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Real* arena, double (*red_buf)[64],
+                                               Real* theta_s) {
     constexpr int M = Fine<Real, N>::M, S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
     constexpr int NPT = (NI + T - 1) / T;
     constexpr int E = 2 * N * N;
     const int tid = threadIdx.x;
-    const int p = blockIdx.x;
-    if (p >= a.n) return;
 
     Lv<Real> F = level_ptrs<Real, N, N>(arena);
     Real* stage = F.e;     // e, res, p of the fine level are contiguous: 3*lvl_size(N) >= 2.5 N^2
@@ -559,6 +554,43 @@ fem_eval_kernel(FemArgs a) {
 }
 
 template <typename Real, int N, int T>
+__global__ void __launch_bounds__(T, 1)
+fem_eval_kernel(FemArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red_buf[2][64];
+    __shared__ Real theta_s[256];
+    if ((int)blockIdx.x >= a.n) return;
+    solve_particle<Real, N, T>(a, blockIdx.x, reinterpret_cast<Real*>(smem_raw), red_buf, theta_s);
+}
+
+// persistent form: grid-sized blocks pull (group, particle) items from a device counter; every
+// group is one problem's launch arguments at this level size (many independent inverse problems
+// in one launch)
+template <typename Real, int N, int T>
+__global__ void __launch_bounds__(T, 1)
+fem_eval_persistent(const FemArgs* groups, const int* offsets, int n_groups, int total, int* counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red_buf[2][64];
+    __shared__ Real theta_s[256];
+    __shared__ int item_s;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = item_s;
+        __syncthreads();
+        if (item >= total) break;
+        int lo = 0, hi = n_groups - 1;          // last group whose offset <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offsets[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        solve_particle<Real, N, T>(groups[lo], item - offsets[lo], reinterpret_cast<Real*>(smem_raw), red_buf,
+                                   theta_s);
+        __syncthreads();
+    }
+}
+
+template <typename Real, int N, int T>
 cudaError_t launch_one(const FemArgs& a, cudaStream_t st) {
     const size_t smem = sizeof(Real) * (size_t)arena_size(N);
     auto kern = fem_eval_kernel<Real, N, T>;
@@ -569,7 +601,54 @@ cudaError_t launch_one(const FemArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <typename Real, int N, int T>
+cudaError_t launch_persistent(const FemArgs* groups, const int* offsets, int n_groups, int total, int* counter,
+                              cudaStream_t st) {
+    const size_t smem = sizeof(Real) * (size_t)arena_size(N);
+    auto kern = fem_eval_persistent<Real, N, T>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
+    if (err != cudaSuccess) return err;
+    const int grid = std::max(1, std::min(total, sms * std::max(per_sm, 1)));
+    kern<<<grid, T, smem, st>>>(groups, offsets, n_groups, total, counter);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t fem_eval_persistent_launch(int N, int precision, int T, const FemArgs* groups, const int* offsets,
+                                       int n_groups, int total, int* counter, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    if (T <= 0) T = fem_block_sizes(N, precision).at(0);
+    if (precision == SMC_MIXED) {
+        switch (N * 10000 + T) {
+            case 4 * 10000 + 32: return launch_persistent<float, 4, 32>(groups, offsets, n_groups, total, counter, st);
+            case 8 * 10000 + 64: return launch_persistent<float, 8, 64>(groups, offsets, n_groups, total, counter, st);
+            case 8 * 10000 + 32: return launch_persistent<float, 8, 32>(groups, offsets, n_groups, total, counter, st);
+            case 16 * 10000 + 128: return launch_persistent<float, 16, 128>(groups, offsets, n_groups, total, counter, st);
+            case 16 * 10000 + 64: return launch_persistent<float, 16, 64>(groups, offsets, n_groups, total, counter, st);
+            case 32 * 10000 + 256: return launch_persistent<float, 32, 256>(groups, offsets, n_groups, total, counter, st);
+            case 32 * 10000 + 512: return launch_persistent<float, 32, 512>(groups, offsets, n_groups, total, counter, st);
+            case 64 * 10000 + 512: return launch_persistent<float, 64, 512>(groups, offsets, n_groups, total, counter, st);
+            case 64 * 10000 + 1024: return launch_persistent<float, 64, 1024>(groups, offsets, n_groups, total, counter, st);
+        }
+    } else {
+        switch (N * 10000 + T) {
+            case 4 * 10000 + 32: return launch_persistent<double, 4, 32>(groups, offsets, n_groups, total, counter, st);
+            case 8 * 10000 + 64: return launch_persistent<double, 8, 64>(groups, offsets, n_groups, total, counter, st);
+            case 16 * 10000 + 128: return launch_persistent<double, 16, 128>(groups, offsets, n_groups, total, counter, st);
+            case 16 * 10000 + 256: return launch_persistent<double, 16, 256>(groups, offsets, n_groups, total, counter, st);
+            case 32 * 10000 + 256: return launch_persistent<double, 32, 256>(groups, offsets, n_groups, total, counter, st);
+            case 32 * 10000 + 512: return launch_persistent<double, 32, 512>(groups, offsets, n_groups, total, counter, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
 
 bool fem_level_supported(int N, int precision) {
     if (precision == SMC_MIXED) return N == 4 || N == 8 || N == 16 || N == 32 || N == 64;

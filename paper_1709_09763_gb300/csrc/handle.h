@@ -81,6 +81,8 @@ struct Handle {
     int cuda_fail(cudaError_t e, const char* what);
     int ensure_scratch(int n);
     int eval_device(int level, int n, const double* theta, double* G, double* Phi, int* iters, cudaStream_t st);
+    FemArgs fem_args(int level, int n, const double* theta, double* G, double* Phi, int* iters) const;
+    int block_size(int N) const;
     int alloc_sampler();
     void free_sampler();
     // sampler (controller.cpp)

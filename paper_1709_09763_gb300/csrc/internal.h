@@ -19,6 +19,7 @@ void obs_table(int N, int n_obs, const double* xy, std::vector<int>& idx, std::v
 
 // ---- kernel launch counter (api.cpp): every kernel the library launches is counted ------
 void count_launches(long long n);
+long long launch_count();
 
 // ---- forward solve (fem_solve.cu) -------------------------------------------------------
 struct FemArgs {
@@ -46,6 +47,11 @@ struct FemArgs {
 // T = threads per particle (one of fem_block_sizes; <= 0: the first, the default)
 cudaError_t fem_eval_launch(const FemArgs& a, cudaStream_t stream, int T = 0);
 std::vector<int> fem_block_sizes(int N, int precision);
+// persistent multi-problem launch: groups[g] (device array) are the launch arguments of one
+// problem at level size N; offsets[g] (device) the first work item of group g; *counter (device,
+// zero before the launch) hands out the total items to the blocks
+cudaError_t fem_eval_persistent_launch(int N, int precision, int T, const FemArgs* groups, const int* offsets,
+                                       int n_groups, int total, int* counter, cudaStream_t st);
 bool fem_level_supported(int N, int precision);
 
 }  // namespace mls2mc

@@ -103,6 +103,13 @@ SIGNATURES = {
                                             ctypes.c_void_p]),
     "smc_surrogate_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_void_p,
                                            _dp]),
+    "smc_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "smc_batch_eval": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip, ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.c_void_p, ctypes.c_int]),
+    "smc_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "smc_batch_destroy": (None, [ctypes.c_void_p]),
     "smc_gemm_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p]),
     "smc_philox_uniforms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_uint, _dp]),
@@ -149,6 +156,42 @@ def gemm_bf16(A, B):
     if rc != SMC_OK:
         raise SmcError(rc, "smc_gemm_bf16")
     return C
+
+
+class Batch:
+    """Independent problems evaluated together (persistent launch per level size, CUDA graph)."""
+
+    def __init__(self, handles):
+        self._lib = load()
+        self.handles = list(handles)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h._h.value for h in self.handles])
+        out = ctypes.c_void_p()
+        rc = self._lib.smc_batch_create(len(self.handles), arr, ctypes.byref(out))
+        if rc != SMC_OK:
+            raise SmcError(rc, "smc_batch_create")
+        self._b = out
+
+    def eval(self, levels, counts, theta_ptrs, phi_ptrs, iters_ptrs=None, stream=None, use_graph=True):
+        P = len(self.handles)
+        lv = (ctypes.c_int * P)(*levels)
+        cn = (ctypes.c_int * P)(*counts)
+        th = (ctypes.c_void_p * P)(*theta_ptrs)
+        ph = (ctypes.c_void_p * P)(*phi_ptrs)
+        it = (ctypes.c_void_p * P)(*iters_ptrs) if iters_ptrs is not None else None
+        rc = self._lib.smc_batch_eval(self._b, lv, cn, th, ph, it, stream, int(use_graph))
+        if rc != SMC_OK:
+            raise SmcError(rc, self._lib.smc_batch_last_error(self._b).decode())
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            self._lib.smc_batch_destroy(self._b)
+        self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class SmcError(RuntimeError):
