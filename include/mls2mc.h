@@ -50,7 +50,8 @@ extern "C" {
 
 typedef struct {
     int n_levels;              /* N_L >= 1 */
-    const int* inv_h;          /* [n_levels] 1/h_l, coarse to fine; powers of two in [4, 64] */
+    const int* inv_h;          /* [n_levels] 1/h_l, coarse to fine; powers of two in [4, 64] (FP64),
+                                  [4, 256] (mixed; 128 and 256 keep the hierarchy in device memory) */
     int K;                     /* KL terms N_sto, 1 <= K <= 256 */
     double corr_len;           /* correlation length of the separable exponential covariance */
     double variance;           /* prior field variance */

@@ -79,6 +79,8 @@ Handle::~Handle() {
     cudaFree(synth_kappa_buf);
     cudaFree(synth_theta_buf);
     cudaFree(synth_err);
+    cudaFree(big_scratch);
+    cudaFree(big_counter);
     cudaFree(d_y);
     free_sampler();
     for (auto& t : timed) {
@@ -170,6 +172,34 @@ int Handle::eval_device(int level, int n, const double* theta, double* G, double
             int rc = synth_kappa(level, n, theta, st);
             if (rc != SMC_OK) return rc;
             a.kappa = synth_kappa_buf;
+        }
+        if (L.N >= 128) {
+            // large level: hierarchy in global memory, persistent blocks
+            const int blocks = fem_global_blocks(L.N);
+            const size_t need = (size_t)blocks * fem_global_slice(L.N);
+            if (need > big_cap) {
+                cudaFree(big_scratch);
+                big_scratch = nullptr;
+                big_cap = 0;
+                cudaError_t ea = cudaMalloc((void**)&big_scratch, need * sizeof(float));
+                if (ea != cudaSuccess) return fail(SMC_ENOMEM, "large-level scratch: %s", cudaGetErrorString(ea));
+                big_cap = need;
+            }
+            if (!big_counter && cudaMalloc((void**)&big_counter, sizeof(int)) != cudaSuccess)
+                return fail(SMC_ENOMEM, "large-level counter");
+            TimedLaunch t{level, nullptr, nullptr};
+            if (timing) {
+                t.start = take_event();
+                t.stop = take_event();
+                cudaEventRecord(t.start, st);
+            }
+            e = fem_eval_global_launch(a, big_scratch, blocks, big_counter, st);
+            if (timing) {
+                cudaEventRecord(t.stop, st);
+                timed.push_back(t);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "forward-solve launch");
+            return SMC_OK;
         }
         const int T = tuned_block(L.N, precision);
         if (timing) {

@@ -116,8 +116,9 @@ int smc_batch_eval(smc_batch* bb, const int* level, const int* n, const double* 
     std::vector<long long> sig;
     for (size_t p = 0; p < P; ++p) {
         Handle* h = b->h[p];
-        if (level[p] < 0 || level[p] >= (int)h->levels.size() || n[p] < 0 || (n[p] > 0 && (!theta[p] || !phi[p]))) {
-            b->last_error = "bad level, count or pointer for problem " + std::to_string(p);
+        if (level[p] < 0 || level[p] >= (int)h->levels.size() || n[p] < 0 || (n[p] > 0 && (!theta[p] || !phi[p])) ||
+            h->levels[level[p]].N >= 128) {
+            b->last_error = "bad level (or a 1/h >= 128 level), count or pointer for problem " + std::to_string(p);
             return SMC_EINVAL;
         }
         sig.insert(sig.end(), {(long long)level[p], (long long)n[p], (long long)(uintptr_t)theta[p],

@@ -553,6 +553,205 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     }
 }
 
+// Large levels (1/h >= 128): the same solve with the hierarchy in a per-block slice of global
+// memory (L2-resident for 1/128) and the fine-level CG and refinement vectors as arrays indexed by
+// interior node (too many nodes per thread for registers). vec: 7 arrays of NI entries after the
+// level arena: r, d, x_hi, x_lo, r_hi, r_lo, q.
+template <typename Real, int N, int T>
+__device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p, Real* arena, double (*red_buf)[64]) {
+    constexpr int M = Fine<Real, N>::M, S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
+    constexpr int E = 2 * N * N;
+    constexpr int SC = N / 2 + 1;
+    const int tid = threadIdx.x;
+    Lv<Real> F = level_ptrs<Real, N, N>(arena);
+    Real* vec = arena + arena_size(N);
+    Real *R = vec, *Dv = vec + NI, *XH = vec + 2 * NI, *XL = vec + 3 * NI, *RH = vec + 4 * NI, *RL = vec + 5 * NI,
+         *QV = vec + 6 * NI;
+    Real* stage = F.e;
+
+    const float* kp = a.kappa + (size_t)p * E;
+    for (int e = tid; e < E; e += T) stage[e] = (Real)kp[e];
+    __syncthreads();
+    setup_levels<Real, N, N, T>(arena, stage, true);
+    {
+        int off = 0;
+#pragma unroll
+        for (int NL = N; NL >= 2; NL >>= 1) {
+            const int z = ((NL + 1) * (NL + 1) + 3) & ~3;
+            for (int q = tid; q < 3 * z; q += T) arena[off + 3 * z + q] = Real(0);
+            off += 6 * z;
+        }
+    }
+    const Real h2 = Real(1) / (Real(N) * Real(N));
+    for (int i = tid; i < NI; i += T) {
+        XH[i] = XL[i] = RL[i] = Real(0);
+        RH[i] = h2;
+    }
+    __syncthreads();
+    const Real bnorm2 = Real(NI) * h2 * h2;
+    const Real stop_outer = Real(a.rtol * a.rtol) * bnorm2;
+    const Real rtol_in2 = Real(a.rtol_in * a.rtol_in);
+    int parity = 0, total_it = 0;
+    bool converged = false;
+    Lv<Real> C1 = level_ptrs<Real, N, N / 2>(arena);
+    Real* P = F.rhs;
+#define NODE_OF(i) const int jj = (i) / M + 1, ii = (i) - (jj - 1) * M + 1, n = jj * S + ii
+    for (int pass = 0; pass < a.max_outer && !converged; ++pass) {
+        Real rr0 = 0;
+        for (int i = tid; i < NI; i += T) {
+            R[i] = RH[i];
+            Dv[i] = Real(0);
+            rr0 += RH[i] * RH[i];
+        }
+        block_sum<T>(rr0, red_buf[parity]);
+        parity ^= 1;
+        if (!(rr0 > Real(0))) break;
+        const Real stop2 = rtol_in2 * rr0;
+        Real rz = 0;
+        for (int it = 0; it < a.max_inner; ++it) {
+            for (int i = tid; i < NI; i += T) {
+                NODE_OF(i);
+                F.e[n] = (((ii + jj) & 1) == 0) ? R[i] * F.iD[n] : Real(0);
+            }
+            __syncthreads();
+            for (int i = tid; i < NI; i += T) {
+                NODE_OF(i);
+                if ((ii + jj) & 1) F.e[n] = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
+            }
+            __syncthreads();
+            for (int i = tid; i < NI; i += T) {
+                NODE_OF(i);
+                F.res[n] = R[i] - stencil_apply<Real, S>(F.aE, F.aN, F.e, n);
+            }
+            __syncthreads();
+            restrict_to<Real, N / 2, T>(F.res, C1.rhs);
+            __syncthreads();
+            vcycle_coarse<Real, N, N / 2, T>(arena);
+            for (int i = tid; i < NI; i += T) {
+                NODE_OF(i);
+                const int c = (jj >> 1) * SC + (ii >> 1), code = (ii & 1) + 2 * (jj & 1);
+                F.e[n] += Real(0.5) * (C1.e[c] + C1.e[c + (code & 1) + (code >> 1) * SC]);
+            }
+            __syncthreads();
+            for (int i = tid; i < NI; i += T) {
+                NODE_OF(i);
+                if ((ii + jj) & 1) F.e[n] = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
+            }
+            __syncthreads();
+            Real rz_new = 0;
+            for (int i = tid; i < NI; i += T) {
+                NODE_OF(i);
+                if (((ii + jj) & 1) == 0) F.e[n] = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
+                rz_new += R[i] * F.e[n];
+            }
+            block_sum<T>(rz_new, red_buf[parity]);
+            parity ^= 1;
+            const Real beta = (it == 0) ? Real(0) : rz_new / rz;
+            rz = rz_new;
+            for (int i = tid; i < NI; i += T) {
+                NODE_OF(i);
+                P[n] = (it == 0) ? F.e[n] : F.e[n] + beta * P[n];
+            }
+            __syncthreads();
+            Real pq = 0;
+            for (int i = tid; i < NI; i += T) {
+                NODE_OF(i);
+                const Real q = stencil_apply<Real, S>(F.aE, F.aN, P, n);
+                QV[i] = q;
+                pq += P[n] * q;
+            }
+            block_sum<T>(pq, red_buf[parity]);
+            parity ^= 1;
+            const Real alpha = rz / pq;
+            Real rr = 0;
+            for (int i = tid; i < NI; i += T) {
+                NODE_OF(i);
+                Dv[i] = fma(alpha, P[n], Dv[i]);
+                const Real rn = fma(-alpha, QV[i], R[i]);
+                R[i] = rn;
+                rr += rn * rn;
+            }
+            block_sum<T>(rr, red_buf[parity]);
+            parity ^= 1;
+            ++total_it;
+            if (!(rr > stop2)) break;
+        }
+        for (int i = tid; i < NI; i += T) {
+            NODE_OF(i);
+            P[n] = Dv[i];
+        }
+        __syncthreads();
+        Real rr_out = 0;
+        for (int i = tid; i < NI; i += T) {
+            NODE_OF(i);
+            const Real di = P[n];
+            const Real w[4] = {F.aE[n], F.aE[n - 1], F.aN[n], F.aN[n - S]};
+            const Real dj[4] = {P[n + 1], P[n - 1], P[n + S], P[n - S]};
+            Real ah = 0, al = 0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                Real sh, sl;
+                two_sum(di, -dj[t], sh, sl);
+                const Real ph = __fmul_rn(w[t], sh);
+                Real pl = fma(w[t], sh, -ph);
+                pl = fma(w[t], sl, pl);
+                df_add(ah, al, ph, pl);
+            }
+            Real rh = RH[i], rl = RL[i], xh = XH[i], xl = XL[i];
+            df_add(rh, rl, -ah, -al);
+            df_add(xh, xl, Dv[i], Real(0));
+            RH[i] = rh;
+            RL[i] = rl;
+            XH[i] = xh;
+            XL[i] = xl;
+            rr_out += rh * rh;
+        }
+        block_sum<T>(rr_out, red_buf[parity]);
+        parity ^= 1;
+        converged = rr_out <= stop_outer;
+    }
+    double* xs = reinterpret_cast<double*>(F.e);
+    __syncthreads();
+    for (int n = tid; n < S * S; n += T) xs[n] = 0.0;
+    __syncthreads();
+    for (int i = tid; i < NI; i += T) {
+        NODE_OF(i);
+        xs[n] = (double)XH[i] + (double)XL[i];
+    }
+#undef NODE_OF
+    __syncthreads();
+    double misfit = 0.0;
+    for (int o = tid; o < a.n_obs; o += T) {
+        const double g = a.obs_w[3 * o] * xs[a.obs_idx[3 * o]] + a.obs_w[3 * o + 1] * xs[a.obs_idx[3 * o + 1]] +
+                         a.obs_w[3 * o + 2] * xs[a.obs_idx[3 * o + 2]];
+        if (a.G) a.G[(size_t)p * a.n_obs + o] = g;
+        const double rdf = a.y[o] - g;
+        misfit += rdf * rdf;
+    }
+    block_sum<T>(misfit, red_buf[parity]);
+    if (tid == 0) {
+        a.Phi[p] = 0.5 * misfit * a.inv_sigma2;
+        if (a.iters) a.iters[p] = converged ? total_it : -(total_it + 1);
+    }
+}
+
+// large levels: persistent blocks, each with its own arena slice of `scratch`
+template <int N, int T>
+__global__ void __launch_bounds__(T, 1) fem_eval_global(FemArgs a, float* scratch, size_t slice, int* counter) {
+    __shared__ double red_buf[2][64];
+    __shared__ int item_s;
+    float* arena = scratch + slice * blockIdx.x;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = item_s;
+        __syncthreads();
+        if (item >= a.n) break;
+        solve_particle_mem<float, N, T>(a, item, arena, red_buf);
+        __syncthreads();
+    }
+}
+
 template <typename Real, int N, int T>
 __global__ void __launch_bounds__(T, 1)
 fem_eval_kernel(FemArgs a) {
@@ -572,19 +771,24 @@ fem_eval_persistent(const FemArgs* groups, const int* offsets, int n_groups, int
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_buf[2][64];
     __shared__ Real theta_s[256];
-    __shared__ int item_s;
+    __shared__ int item_s, group_s;
+    __shared__ FemArgs args_s;                  // this item's launch arguments, read once per particle
     for (;;) {
-        if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+        if (threadIdx.x == 0) {
+            const int item = atomicAdd(counter, 1);
+            int lo = 0, hi = n_groups - 1;      // last group whose offset <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (offsets[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            item_s = item;
+            group_s = lo;
+            if (item < total) args_s = groups[lo];
+        }
         __syncthreads();
         const int item = item_s;
-        __syncthreads();
         if (item >= total) break;
-        int lo = 0, hi = n_groups - 1;          // last group whose offset <= item
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (offsets[mid] <= item) lo = mid; else hi = mid - 1;
-        }
-        solve_particle<Real, N, T>(groups[lo], item - offsets[lo], reinterpret_cast<Real*>(smem_raw), red_buf,
+        solve_particle<Real, N, T>(args_s, item - offsets[group_s], reinterpret_cast<Real*>(smem_raw), red_buf,
                                    theta_s);
         __syncthreads();
     }
@@ -619,7 +823,40 @@ cudaError_t launch_persistent(const FemArgs* groups, const int* offsets, int n_g
     return cudaGetLastError();
 }
 
+template <int N, int T>
+cudaError_t launch_global(const FemArgs& a, float* scratch, size_t slice, int blocks, int* counter, cudaStream_t st) {
+    fem_eval_global<N, T><<<blocks, T, 0, st>>>(a, scratch, slice, counter);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t fem_global_slice(int N) {
+    const int NI = (N - 1) * (N - 1);
+    const size_t floats = (size_t)arena_size(N) + 7 * (size_t)NI;
+    return (floats + 63) / 64 * 64;   // floats per block, 256-byte aligned slices
+}
+
+int fem_global_blocks(int N) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (N == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_global<128, 1024>, 1024, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_global<256, 1024>, 1024, 0);
+    return sms * std::max(1, per_sm);
+}
+
+cudaError_t fem_eval_global_launch(const FemArgs& a, float* scratch, int blocks, int* counter, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    const size_t slice = fem_global_slice(a.N);
+    const int grid = std::max(1, std::min(a.n, blocks));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    if (a.N == 128) return launch_global<128, 1024>(a, scratch, slice, grid, counter, st);
+    if (a.N == 256) return launch_global<256, 1024>(a, scratch, slice, grid, counter, st);
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t fem_eval_persistent_launch(int N, int precision, int T, const FemArgs* groups, const int* offsets,
                                        int n_groups, int total, int* counter, cudaStream_t st) {
@@ -651,7 +888,7 @@ cudaError_t fem_eval_persistent_launch(int N, int precision, int T, const FemArg
 }
 
 bool fem_level_supported(int N, int precision) {
-    if (precision == SMC_MIXED) return N == 4 || N == 8 || N == 16 || N == 32 || N == 64;
+    if (precision == SMC_MIXED) return N == 4 || N == 8 || N == 16 || N == 32 || N == 64 || N == 128 || N == 256;
     return N == 4 || N == 8 || N == 16 || N == 32;
 }
 
@@ -664,6 +901,8 @@ std::vector<int> fem_block_sizes(int N, int precision) {
             case 16: return {128, 64};
             case 32: return {256, 512};
             case 64: return {512, 1024};
+            case 128: return {1024};
+            case 256: return {1024};
         }
     } else {
         switch (N) {

@@ -45,6 +45,11 @@ struct Handle {
     // sampler state (smc_kernels.cu / controller.cpp)
     struct Sampler* smp = nullptr;
 
+    // large levels: per-block hierarchy slices in global memory (fem_solve.cu)
+    float* big_scratch = nullptr;
+    size_t big_cap = 0;
+    int* big_counter = nullptr;
+
     // tensor-core KL synthesis buffers (kl_synth.cu)
     float* synth_kappa_buf = nullptr;
     uint16_t* synth_theta_buf = nullptr;

@@ -161,3 +161,17 @@ def test_every_block_size_and_autotuner(prec):
     assert all(c in sizes[N] for c, N in zip(chosen, levels)) and all(m > 0 for m in ms)
     for l in range(len(levels)):
         h.set_block_size(l, 0)
+
+
+@pytest.mark.parametrize("N,n", [(128, 5), (256, 2)])
+def test_large_levels_parity(N, n):
+    """1/h = 128 and 256 (hierarchy in device memory): mixed-path G within 1e-6 of the oracle."""
+    w = wl.WORKLOADS["mls2mc_mixed_h8_64"]
+    d = _data(w.name)
+    obs = wl.obs_grid(7)
+    theta = wl.particles(n, w.K, 300 + N)
+    h = native.Handle([N], w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, precision=native.SMC_MIXED)
+    G, Phi = h.eval_likelihood(0, theta)
+    Gr, Phir = _oracle(N, w, theta, obs, np.array(d["y"]), d["sigma"])
+    assert _rel(G, Gr).max() < 1e-6
+    assert _phi_ok(Phi, Phir, Gr, d["sigma"], 1e-6)
