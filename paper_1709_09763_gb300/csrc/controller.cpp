@@ -70,7 +70,7 @@ int Handle::alloc_sampler() {
     A((void**)&smp->iters, (size_t)J * 4);
     A((void**)&smp->scal, 64);
     A((void**)&smp->mom, (size_t)2 * K * 8);
-    A((void**)&smp->n_acc, 8);
+    A((void**)&smp->n_acc, 16);   // [0] accepted moves (u64), [8] non-converged solves (u32)
     A((void**)&smp->inc.state, sizeof(IncState));
     A((void**)&smp->inc.partials, (size_t)kIncMaxBlocks * 4 * 8);
     if (opts.surrogate) {
@@ -81,6 +81,7 @@ int Handle::alloc_sampler() {
         A((void**)&smp->surv_idx, (size_t)J * 4);
         A((void**)&smp->n_surv, 4);
     }
+    if (e == cudaSuccess) e = cudaMemset(smp->n_acc, 0, 16);
     if (e != cudaSuccess) return fail(SMC_ENOMEM, "sampler buffers for J = %d: %s", J, cudaGetErrorString(e));
     return SMC_OK;
 }
@@ -121,7 +122,28 @@ int Handle::smp_eval(int level, int n, const double* theta, double* phi) {
         RC(mlp_add_pairs(level, n, theta, smp->G_buf));
         smp->pairs_new[level] += n;
     }
-    return check_iters(n);
+    // non-converged solves are counted on the device and checked when the update reads its counters
+    CK(count_bad_launch(smp->iters, n, bad_counter(), stream));
+    return SMC_OK;
+}
+
+unsigned* Handle::bad_counter() { return reinterpret_cast<unsigned*>(reinterpret_cast<char*>(smp->n_acc) + 8); }
+
+// read the accept and non-convergence counters (one device-to-host copy and wait)
+int Handle::read_counters(unsigned long long* acc) {
+    unsigned char buf[16];
+    CK(cudaMemcpyAsync(buf, smp->n_acc, 16, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    unsigned long long a;
+    unsigned bad;
+    std::memcpy(&a, buf, 8);
+    std::memcpy(&bad, buf + 8, 4);
+    if (acc) *acc = a;
+    if (bad) {
+        CK(cudaMemsetAsync(bad_counter(), 0, 4, stream));
+        return fail(SMC_ENOCONV, "%u forward solves did not reach rtol", bad);
+    }
+    return SMC_OK;
 }
 
 // Whether screening pays on a level: measured once per level (events on the handle's stream) as
@@ -243,8 +265,7 @@ int Handle::mcmc(int level, double zeta, double& rate) {
         S->mcmc_event += 1;
     }
     unsigned long long acc = 0;
-    CK(cudaMemcpyAsync(&acc, S->n_acc, 8, cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
+    RC(read_counters(&acc));
     rate = opts.n_mcmc > 0 ? (double)acc / ((double)opts.n_mcmc * S->J) : 0.0;
     return SMC_OK;
 }
@@ -283,8 +304,7 @@ int Handle::mcmc_da(int level, double zeta, double& rate) {
         S->mcmc_event += 1;
     }
     unsigned long long acc = 0;
-    CK(cudaMemcpyAsync(&acc, S->n_acc, 8, cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
+    RC(read_counters(&acc));
     const double props = (double)opts.n_mcmc * J;
     rate = props > 0 ? (double)acc / props : 0.0;
     S->da_proposals += (long long)props;

@@ -139,8 +139,9 @@ template <typename Real, int NL, int T>
 __device__ __forceinline__ void smooth_first_red(const Lv<Real>& L) {
     // starting from e = 0: red nodes get rhs/D, black nodes are zeroed
     constexpr int M = NL - 1, S = NL + 1;
-    for (int idx = threadIdx.x; idx < M * M; idx += T) {
-        const int j = idx / M + 1, i = idx - (j - 1) * M + 1, n = j * S + i;
+    for (int idx = threadIdx.x; idx < M * S; idx += T) {   // padded rows: a warp reads consecutive words
+        const int n = S + idx, j = n / S, i = n - j * S;
+        if (i == 0 || i == NL) continue;
         L.e[n] = (((i + j) & 1) == 0) ? L.rhs[n] * L.iD[n] : Real(0);
     }
 }
@@ -148,8 +149,9 @@ __device__ __forceinline__ void smooth_first_red(const Lv<Real>& L) {
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
     constexpr int M = NL - 1, S = NL + 1;
-    for (int idx = threadIdx.x; idx < M * M; idx += T) {
-        const int j = idx / M + 1, i = idx - (j - 1) * M + 1, n = j * S + i;
+    for (int idx = threadIdx.x; idx < M * S; idx += T) {
+        const int n = S + idx, j = n / S, i = n - j * S;
+        if (i == 0 || i == NL) continue;
         if (((i + j) & 1) == color) L.e[n] = (L.rhs[n] + offsum<Real, S>(L.aE, L.aN, L.e, n)) * L.iD[n];
     }
 }
@@ -157,8 +159,9 @@ __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void residual(const Lv<Real>& L) {
     constexpr int M = NL - 1, S = NL + 1;
-    for (int idx = threadIdx.x; idx < M * M; idx += T) {
-        const int j = idx / M + 1, i = idx - (j - 1) * M + 1, n = j * S + i;
+    for (int idx = threadIdx.x; idx < M * S; idx += T) {
+        const int n = S + idx, j = n / S, i = n - j * S;
+        if (i == 0 || i == NL) continue;
         L.res[n] = L.rhs[n] - stencil_apply<Real, S>(L.aE, L.aN, L.e, n);
     }
 }
@@ -191,9 +194,10 @@ __device__ __forceinline__ Real prolong_at(const Real* ec, int i, int j) {
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void prolong_add(const Lv<Real>& L, const Real* ec) {
     constexpr int M = NL - 1, S = NL + 1;
-    for (int idx = threadIdx.x; idx < M * M; idx += T) {
-        const int j = idx / M + 1, i = idx - (j - 1) * M + 1;
-        L.e[j * S + i] += prolong_at<Real, NL / 2>(ec, i, j);
+    for (int idx = threadIdx.x; idx < M * S; idx += T) {
+        const int n = S + idx, j = n / S, i = n - j * S;
+        if (i == 0 || i == NL) continue;
+        L.e[n] += prolong_at<Real, NL / 2>(ec, i, j);
     }
 }
 
@@ -316,7 +320,7 @@ template <typename Real, int N, int T>
 __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Real* arena, double (*red_buf)[64],
                                                Real* theta_s) {
     constexpr int M = Fine<Real, N>::M, S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
-    constexpr int NPT = (NI + T - 1) / T;
+    constexpr int NPT = (M * S + T - 1) / T;   // slots over the padded interior rows
     constexpr int E = 2 * N * N;
     const int tid = threadIdx.x;
 
@@ -357,16 +361,19 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     // fine nodes owned by this thread, one packed int each: bits 0-12 padded node index n,
     // 13-23 the coarse node c under it, 24-25 which second coarse node its P1
     // interpolation averages with (0 none, 1 c+1, 2 c+SC, 3 c+SC+1), 26 red, 27 valid
+    // Slots run over the padded rows 1..N-1 (boundary columns are idle slots), so the nodes of a
+    // warp are 32 consecutive words: no shared-memory bank conflicts at row ends.
     constexpr int SC = N / 2 + 1;
     int slot[NPT];
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
         const int idx = tid + T * q;
-        const int v = idx < NI;
-        const int jj = (v ? idx : 0) / M + 1, ii = (v ? idx : 0) - (jj - 1) * M + 1;
+        const int n0 = S + (idx < M * S ? idx : 0);
+        const int jj = n0 / S, ii = n0 - jj * S;
+        const int v = idx < M * S && ii >= 1 && ii <= M;
         const int c = (jj >> 1) * SC + (ii >> 1);
         const int code = (ii & 1) + 2 * (jj & 1);
-        slot[q] = (jj * S + ii) | (c << 13) | (code << 24) | ((((ii + jj) & 1) == 0) << 26) | (v << 27);
+        slot[q] = (v ? n0 : S + 1) | (c << 13) | (code << 24) | ((((ii + jj) & 1) == 0) << 26) | (v << 27);
     }
     // right-hand side h^2 (f = 1), exact in FP32 for N a power of two
     const Real h2 = Real(1) / (Real(N) * Real(N));

@@ -93,6 +93,8 @@ struct Handle {
     // sampler (controller.cpp)
     int smp_eval(int level, int n, const double* theta, double* phi);
     int check_iters(int n);
+    unsigned* bad_counter();
+    int read_counters(unsigned long long* acc);
     int increment(const double* a, int n, double dmax, struct IncState& st);
     int reweight_resample(const double* a, double dmax, bool carry_fine, struct IncState& st);
     int mcmc(int level, double zeta, double& rate);

@@ -59,6 +59,7 @@ cudaError_t da_stage2_launch(int ns, int K, double beta, double zeta, uint32_t e
                              const double* theta_s, const double* phi_cs, const double* phi_fs, double* theta,
                              double* phi_c, double* phi_f, double* ps_c, double* ps_f, const double* psp_c,
                              const double* psp_f, unsigned long long* n_acc, cudaStream_t st);
+cudaError_t count_bad_launch(const int* iters, int n, unsigned* bad, cudaStream_t st);
 cudaError_t moments_launch(const double* theta, int n, int K, double* mean, double* var, cudaStream_t st);
 
 }  // namespace mls2mc

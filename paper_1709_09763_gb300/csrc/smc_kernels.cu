@@ -412,6 +412,14 @@ __global__ void da_stage2_kernel(int ns, int K, double beta, double zeta, uint32
     if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(n_acc, (unsigned long long)__popc(ballot));
 }
 
+// number of negative iteration counts (solves that did not converge), accumulated into *bad
+__global__ void count_bad_kernel(const int* iters, int n, unsigned* bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool b = i < n && iters[i] < 0;
+    const unsigned ballot = __ballot_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(bad, (unsigned)__popc(ballot));
+}
+
 // ---- posterior moments over equally weighted particles ----------------------------------------
 __global__ void moments_kernel(const double* theta, int n, int K, double* mean, double* var) {
     __shared__ double sh[32];
@@ -544,6 +552,13 @@ cudaError_t da_stage2_launch(int ns, int K, double beta, double zeta, uint32_t e
     if (ns <= 0) return cudaSuccess;
     da_stage2_kernel<<<grid_for(ns, 256), 256, 0, st>>>(ns, K, beta, zeta, event, seed, surv_idx, theta_s, phi_cs, phi_fs,
                                                         theta, phi_c, phi_f, ps_c, ps_f, psp_c, psp_f, n_acc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t count_bad_launch(const int* iters, int n, unsigned* bad, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    count_bad_kernel<<<grid_for(n, 256), 256, 0, st>>>(iters, n, bad);
     count_launches(1);
     return cudaGetLastError();
 }
