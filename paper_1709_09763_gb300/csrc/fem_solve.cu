@@ -560,12 +560,46 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     }
 }
 
-// Large levels (1/h >= 128): the same solve with the hierarchy in a per-block slice of global
-// memory (L2-resident for 1/128) and the fine-level CG and refinement vectors as arrays indexed by
-// interior node (too many nodes per thread for registers). vec: 7 arrays of NI entries after the
-// level arena: r, d, x_hi, x_lo, r_hi, r_lo, q.
+// Two-arena hierarchy of the large levels: levels with 1/h >= 128 live in device memory (the
+// arena of a top level N), levels 1/h <= 64 in shared memory (the arena of a top level 64).
+template <typename Real, int N, int NL>
+__device__ __forceinline__ Lv<Real> ptrs2(Real* garena, Real* sarena) {
+    if constexpr (NL > 64) return level_ptrs<Real, N, NL>(garena);
+    else return level_ptrs<Real, 64, NL>(sarena);
+}
+
+template <typename Real, int N, int NL, int T>
+__device__ void vcycle2(Real* garena, Real* sarena) {
+    if constexpr (NL <= 64) {
+        vcycle_coarse<Real, 64, NL, T>(sarena);
+    } else {
+        Lv<Real> L = ptrs2<Real, N, NL>(garena, sarena);
+        Lv<Real> C = ptrs2<Real, N, NL / 2>(garena, sarena);
+        smooth_first_red<Real, NL, T>(L);
+        __syncthreads();
+        smooth_color<Real, NL, T>(L, 1);
+        __syncthreads();
+        residual<Real, NL, T>(L);
+        __syncthreads();
+        restrict_to<Real, NL / 2, T>(L.res, C.rhs);
+        __syncthreads();
+        vcycle2<Real, N, NL / 2, T>(garena, sarena);
+        prolong_add<Real, NL, T>(L, C.e);
+        __syncthreads();
+        smooth_color<Real, NL, T>(L, 1);
+        __syncthreads();
+        smooth_color<Real, NL, T>(L, 0);
+        __syncthreads();
+    }
+}
+
+// Large levels (1/h >= 128): the same solve with the levels 1/h >= 128 in a per-block slice of
+// device memory (L2-resident for 1/128), the levels 1/h <= 64 in shared memory, and the fine-level
+// CG and refinement vectors as arrays indexed by interior node (too many nodes per thread for
+// registers). vec: 7 arrays of NI entries after the level arena: r, d, x_hi, x_lo, r_hi, r_lo, q.
 template <typename Real, int N, int T>
-__device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p, Real* arena, double (*red_buf)[64]) {
+__device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p, Real* arena, Real* sarena,
+                                                   double (*red_buf)[64]) {
     constexpr int M = Fine<Real, N>::M, S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
     constexpr int E = 2 * N * N;
     constexpr int SC = N / 2 + 1;
@@ -579,13 +613,38 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
     const float* kp = a.kappa + (size_t)p * E;
     for (int e = tid; e < E; e += T) stage[e] = (Real)kp[e];
     __syncthreads();
-    setup_levels<Real, N, N, T>(arena, stage, true);
+    // device-memory levels (N, and 128 when N = 256), then the shared-memory hierarchy from 64 down;
+    // kappa is staged in the fine level's e/res/rhs region
+    {
+        Real* k1 = stage + 2 * N * N;
+        build_coeffs<Real, N, T>(F, stage);
+        coarsen_kappa<Real, N / 2, T>(stage, k1);
+        __syncthreads();
+        build_diag<Real, N, T>(F);
+        Real* k64 = k1;
+        if constexpr (N == 256) {
+            Lv<Real> L1 = level_ptrs<Real, N, 128>(arena);
+            build_coeffs<Real, 128, T>(L1, k1);
+            coarsen_kappa<Real, 64, T>(k1, stage);
+            __syncthreads();
+            build_diag<Real, 128, T>(L1);
+            k64 = stage;
+        }
+        setup_levels<Real, 64, 64, T>(sarena, k64, true);
+    }
     {
         int off = 0;
 #pragma unroll
-        for (int NL = N; NL >= 2; NL >>= 1) {
+        for (int NL = N; NL >= 128; NL >>= 1) {
             const int z = ((NL + 1) * (NL + 1) + 3) & ~3;
             for (int q = tid; q < 3 * z; q += T) arena[off + 3 * z + q] = Real(0);
+            off += 6 * z;
+        }
+        off = 0;
+#pragma unroll
+        for (int NL = 64; NL >= 2; NL >>= 1) {
+            const int z = ((NL + 1) * (NL + 1) + 3) & ~3;
+            for (int q = tid; q < 3 * z; q += T) sarena[off + 3 * z + q] = Real(0);
             off += 6 * z;
         }
     }
@@ -600,7 +659,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
     const Real rtol_in2 = Real(a.rtol_in * a.rtol_in);
     int parity = 0, total_it = 0;
     bool converged = false;
-    Lv<Real> C1 = level_ptrs<Real, N, N / 2>(arena);
+    Lv<Real> C1 = ptrs2<Real, N, N / 2>(arena, sarena);
     Real* P = F.rhs;
 #define NODE_OF(i) const int jj = (i) / M + 1, ii = (i) - (jj - 1) * M + 1, n = jj * S + ii
     for (int pass = 0; pass < a.max_outer && !converged; ++pass) {
@@ -633,7 +692,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
             __syncthreads();
             restrict_to<Real, N / 2, T>(F.res, C1.rhs);
             __syncthreads();
-            vcycle_coarse<Real, N, N / 2, T>(arena);
+            vcycle2<Real, N, N / 2, T>(arena, sarena);
             for (int i = tid; i < NI; i += T) {
                 NODE_OF(i);
                 const int c = (jj >> 1) * SC + (ii >> 1), code = (ii & 1) + 2 * (jj & 1);
@@ -745,16 +804,18 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
 // large levels: persistent blocks, each with its own arena slice of `scratch`
 template <int N, int T>
 __global__ void __launch_bounds__(T, 1) fem_eval_global(FemArgs a, float* scratch, size_t slice, int* counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_buf[2][64];
     __shared__ int item_s;
     float* arena = scratch + slice * blockIdx.x;
+    float* sarena = reinterpret_cast<float*>(smem_raw);
     for (;;) {
         if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
         __syncthreads();
         const int item = item_s;
         __syncthreads();
         if (item >= a.n) break;
-        solve_particle_mem<float, N, T>(a, item, arena, red_buf);
+        solve_particle_mem<float, N, T>(a, item, arena, sarena, red_buf);
         __syncthreads();
     }
 }
@@ -832,7 +893,10 @@ cudaError_t launch_persistent(const FemArgs* groups, const int* offsets, int n_g
 
 template <int N, int T>
 cudaError_t launch_global(const FemArgs& a, float* scratch, size_t slice, int blocks, int* counter, cudaStream_t st) {
-    fem_eval_global<N, T><<<blocks, T, 0, st>>>(a, scratch, slice, counter);
+    const size_t smem = sizeof(float) * (size_t)arena_size(64);
+    cudaError_t e = cudaFuncSetAttribute(fem_eval_global<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fem_eval_global<N, T><<<blocks, T, smem, st>>>(a, scratch, slice, counter);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -849,8 +913,14 @@ int fem_global_blocks(int N) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (N == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_global<128, 1024>, 1024, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_global<256, 1024>, 1024, 0);
+    const size_t smem = sizeof(float) * (size_t)arena_size(64);
+    if (N == 128) {
+        cudaFuncSetAttribute(fem_eval_global<128, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_global<128, 1024>, 1024, smem);
+    } else {
+        cudaFuncSetAttribute(fem_eval_global<256, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_global<256, 1024>, 1024, smem);
+    }
     return sms * std::max(1, per_sm);
 }
 
