@@ -135,14 +135,23 @@ __device__ __forceinline__ void df_add(Real& ah, Real& al, Real bh, Real bl) {
 }
 
 // ---- coarse-level multigrid pieces (rhs in shared memory) --------------------------------
+// V(1,1) with red-black Gauss-Seidel: pre-smoothing red then black from e = 0, post-smoothing
+// black then red (a symmetric preconditioner). Two identities of the red-black ordering remove
+// passes from the textbook cycle:
+//  - after the black pre-sweep every black node satisfies its equation (zero residual) and the
+//    residual of a red node is the off-diagonal sum of the new black values (the red node held
+//    its equation before), so the restriction needs residuals at red nodes only;
+//  - Gauss-Seidel overwrites a node from its neighbours alone, so the coarse correction added to
+//    the black nodes and the red nodes' pre-sweep values are never read: the black post-sweep
+//    reads its red neighbours as e + P e_c directly.
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void smooth_first_red(const Lv<Real>& L) {
-    // starting from e = 0: red nodes get rhs/D, black nodes are zeroed
+    // from e = 0: red nodes get rhs/D; black nodes are written by the black sweep before any read
     constexpr int M = NL - 1, S = NL + 1;
     for (int idx = threadIdx.x; idx < M * S; idx += T) {   // padded rows: a warp reads consecutive words
         const int n = S + idx, j = n / S, i = n - j * S;
-        if (i == 0 || i == NL) continue;
-        L.e[n] = (((i + j) & 1) == 0) ? L.rhs[n] * L.iD[n] : Real(0);
+        if (i == 0 || i == NL || ((i + j) & 1)) continue;
+        L.e[n] = L.rhs[n] * L.iD[n];
     }
 }
 
@@ -156,48 +165,53 @@ __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
     }
 }
 
-template <typename Real, int NL, int T>
-__device__ __forceinline__ void residual(const Lv<Real>& L) {
-    constexpr int M = NL - 1, S = NL + 1;
-    for (int idx = threadIdx.x; idx < M * S; idx += T) {
-        const int n = S + idx, j = n / S, i = n - j * S;
-        if (i == 0 || i == NL) continue;
-        L.res[n] = L.rhs[n] - stencil_apply<Real, S>(L.aE, L.aN, L.e, n);
-    }
-}
-
-// coarse rhs = P^T fine residual: P1 interpolation weights 1 and 1/2 along the six
-// mesh directions (+-x, +-y, and the (1,1) diagonal)
+// coarse rhs = P^T (fine residual) after the red and black pre-sweeps. P^T takes weight 1 from
+// the coincident fine node and 1/2 from its six neighbours along the mesh directions (+-x, +-y
+// and the (1,1) diagonal); of these only the coincident node and the two diagonal neighbours are
+// red, and their residuals are the off-diagonal sums of the black values.
 template <typename Real, int NC, int T>
-__device__ __forceinline__ void restrict_to(const Real* res_f, Real* rhs_c) {
+__device__ __forceinline__ void restrict_red(const Lv<Real>& F, Real* rhs_c) {
     constexpr int MC = NC - 1, SC = NC + 1, SF = 2 * NC + 1;
     for (int idx = threadIdx.x; idx < MC * MC; idx += T) {
         const int J = idx / MC + 1, I = idx - (J - 1) * MC + 1;
         const int f = (2 * J) * SF + 2 * I;
-        rhs_c[J * SC + I] = res_f[f] + Real(0.5) * (res_f[f + 1] + res_f[f - 1] + res_f[f + SF] +
-                                                     res_f[f - SF] + res_f[f + SF + 1] + res_f[f - SF - 1]);
+        rhs_c[J * SC + I] = offsum<Real, SF>(F.aE, F.aN, F.e, f) +
+                            Real(0.5) * (offsum<Real, SF>(F.aE, F.aN, F.e, f + SF + 1) +
+                                         offsum<Real, SF>(F.aE, F.aN, F.e, f - SF - 1));
     }
 }
 
-// P1 interpolation of the coarse correction at fine node (i, j)
-template <typename Real, int NC>
-__device__ __forceinline__ Real prolong_at(const Real* ec, int i, int j) {
-    constexpr int SC = NC + 1;
-    const int I = i >> 1, J = j >> 1;
-    const int c = J * SC + I;
-    if ((i & 1) == 0 && (j & 1) == 0) return ec[c];
-    if ((j & 1) == 0) return Real(0.5) * (ec[c] + ec[c + 1]);
-    if ((i & 1) == 0) return Real(0.5) * (ec[c] + ec[c + SC]);
-    return Real(0.5) * (ec[c] + ec[c + SC + 1]);
+// off-diagonal sum at black node n = (i, j) with its red neighbours read as e + P e_c (P1
+// interpolation of the coarse correction ec). c0 = (j/2) SC + i/2 (integer halves) is the
+// coarse node at or below-left of n; jeven selects which neighbours coincide with coarse nodes.
+template <typename Real, int S, int SC>
+__device__ __forceinline__ Real offsum_prolong(const Real* aE, const Real* aN, const Real* e, const Real* ec, int n,
+                                               int c0, bool jeven) {
+    Real pE, pW, pN, pS;
+    if (jeven) {   // i odd: E, W coincide with coarse nodes, N, S lie on coarse diagonals
+        pE = ec[c0 + 1];
+        pW = ec[c0];
+        pN = Real(0.5) * (ec[c0] + ec[c0 + SC + 1]);
+        pS = Real(0.5) * (ec[c0 - SC] + ec[c0 + 1]);
+    } else {       // i even: N, S coincide, E, W on diagonals
+        pE = Real(0.5) * (ec[c0] + ec[c0 + SC + 1]);
+        pW = Real(0.5) * (ec[c0 - 1] + ec[c0 + SC]);
+        pN = ec[c0 + SC];
+        pS = ec[c0];
+    }
+    return aE[n] * (e[n + 1] + pE) + aE[n - 1] * (e[n - 1] + pW) + aN[n] * (e[n + S] + pN) +
+           aN[n - S] * (e[n - S] + pS);
 }
 
+// black post-sweep with the coarse correction of level NL / 2 folded in
 template <typename Real, int NL, int T>
-__device__ __forceinline__ void prolong_add(const Lv<Real>& L, const Real* ec) {
-    constexpr int M = NL - 1, S = NL + 1;
+__device__ __forceinline__ void black_prolong(const Lv<Real>& L, const Real* ec) {
+    constexpr int M = NL - 1, S = NL + 1, SC = NL / 2 + 1;
     for (int idx = threadIdx.x; idx < M * S; idx += T) {
         const int n = S + idx, j = n / S, i = n - j * S;
-        if (i == 0 || i == NL) continue;
-        L.e[n] += prolong_at<Real, NL / 2>(ec, i, j);
+        if (i == 0 || i == NL || !((i + j) & 1)) continue;
+        const int c0 = (j >> 1) * SC + (i >> 1);
+        L.e[n] = (L.rhs[n] + offsum_prolong<Real, S, SC>(L.aE, L.aN, L.e, ec, n, c0, (j & 1) == 0)) * L.iD[n];
     }
 }
 
@@ -228,14 +242,10 @@ __device__ void vcycle_coarse(Real* arena) {
             phase_sync<WARP>();
             smooth_color<Real, NL, T>(L, 1);
             phase_sync<WARP>();
-            residual<Real, NL, T>(L);
-            phase_sync<WARP>();
-            restrict_to<Real, NL / 2, T>(L.res, C.rhs);
+            restrict_red<Real, NL / 2, T>(L, C.rhs);
             phase_sync<WARP>();
             vcycle_coarse<Real, N, NL / 2, T, WARP>(arena);
-            prolong_add<Real, NL, T>(L, C.e);
-            phase_sync<WARP>();
-            smooth_color<Real, NL, T>(L, 1);
+            black_prolong<Real, NL, T>(L, C.e);
             phase_sync<WARP>();
             smooth_color<Real, NL, T>(L, 0);
             phase_sync<WARP>();
@@ -410,10 +420,12 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
         const Real stop2 = rtol_in2 * rr0;
         Real rz = 0;
         for (int it = 0; it < a.max_inner; ++it) {
-            // z = M^{-1} r: V(1,1) cycle with the fine rhs held in registers
+            // z = M^{-1} r: V(1,1) cycle with the fine rhs held in registers (red pre-sweep
+            // from zero, black pre-sweep, restriction of the red residuals, coarse cycle, black
+            // post-sweep with the prolongation folded in, red post-sweep)
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
-                if (((slot[q] >> 27) & 1)) F.e[(slot[q] & 0x1fff)] = ((slot[q] >> 26) & 1) ? r[q] * F.iD[(slot[q] & 0x1fff)] : Real(0);
+                if (((slot[q] >> 27) & 1) && ((slot[q] >> 26) & 1)) F.e[(slot[q] & 0x1fff)] = r[q] * F.iD[(slot[q] & 0x1fff)];
             __syncthreads();
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
@@ -422,29 +434,15 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
                     F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
                 }
             __syncthreads();
-#pragma unroll
-            for (int q = 0; q < NPT; ++q)
-                if (((slot[q] >> 27) & 1)) {
-                    const int n = (slot[q] & 0x1fff);
-                    F.res[n] = r[q] - stencil_apply<Real, S>(F.aE, F.aN, F.e, n);
-                }
-            __syncthreads();
-            restrict_to<Real, N / 2, T>(F.res, C1.rhs);
+            restrict_red<Real, N / 2, T>(F, C1.rhs);
             __syncthreads();
             vcycle_coarse<Real, N, N / 2, T>(arena);
 #pragma unroll
             for (int q = 0; q < NPT; ++q)
-                if (((slot[q] >> 27) & 1)) {
-                    const int n = (slot[q] & 0x1fff);
-                    const int c = (slot[q] >> 13) & 0x7ff, code = (slot[q] >> 24) & 3;
-                    F.e[n] += Real(0.5) * (C1.e[c] + C1.e[c + (code & 1) + (code >> 1) * SC]);
-                }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < NPT; ++q)
                 if (((slot[q] >> 27) & 1) && !((slot[q] >> 26) & 1)) {
                     const int n = (slot[q] & 0x1fff);
-                    F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
+                    const int c = (slot[q] >> 13) & 0x7ff, code = (slot[q] >> 24) & 3;
+                    F.e[n] = (r[q] + offsum_prolong<Real, S, SC>(F.aE, F.aN, F.e, C1.e, n, c, code == 1)) * F.iD[n];
                 }
             __syncthreads();
             Real rz_new = 0;
@@ -579,14 +577,10 @@ __device__ void vcycle2(Real* garena, Real* sarena) {
         __syncthreads();
         smooth_color<Real, NL, T>(L, 1);
         __syncthreads();
-        residual<Real, NL, T>(L);
-        __syncthreads();
-        restrict_to<Real, NL / 2, T>(L.res, C.rhs);
+        restrict_red<Real, NL / 2, T>(L, C.rhs);
         __syncthreads();
         vcycle2<Real, N, NL / 2, T>(garena, sarena);
-        prolong_add<Real, NL, T>(L, C.e);
-        __syncthreads();
-        smooth_color<Real, NL, T>(L, 1);
+        black_prolong<Real, NL, T>(L, C.e);
         __syncthreads();
         smooth_color<Real, NL, T>(L, 0);
         __syncthreads();
@@ -677,7 +671,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
         for (int it = 0; it < a.max_inner; ++it) {
             for (int i = tid; i < NI; i += T) {
                 NODE_OF(i);
-                F.e[n] = (((ii + jj) & 1) == 0) ? R[i] * F.iD[n] : Real(0);
+                if (((ii + jj) & 1) == 0) F.e[n] = R[i] * F.iD[n];
             }
             __syncthreads();
             for (int i = tid; i < NI; i += T) {
@@ -685,23 +679,15 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
                 if ((ii + jj) & 1) F.e[n] = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
             }
             __syncthreads();
-            for (int i = tid; i < NI; i += T) {
-                NODE_OF(i);
-                F.res[n] = R[i] - stencil_apply<Real, S>(F.aE, F.aN, F.e, n);
-            }
-            __syncthreads();
-            restrict_to<Real, N / 2, T>(F.res, C1.rhs);
+            restrict_red<Real, N / 2, T>(F, C1.rhs);
             __syncthreads();
             vcycle2<Real, N, N / 2, T>(arena, sarena);
             for (int i = tid; i < NI; i += T) {
                 NODE_OF(i);
-                const int c = (jj >> 1) * SC + (ii >> 1), code = (ii & 1) + 2 * (jj & 1);
-                F.e[n] += Real(0.5) * (C1.e[c] + C1.e[c + (code & 1) + (code >> 1) * SC]);
-            }
-            __syncthreads();
-            for (int i = tid; i < NI; i += T) {
-                NODE_OF(i);
-                if ((ii + jj) & 1) F.e[n] = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
+                if ((ii + jj) & 1) {
+                    const int c = (jj >> 1) * SC + (ii >> 1);
+                    F.e[n] = (R[i] + offsum_prolong<Real, S, SC>(F.aE, F.aN, F.e, C1.e, n, c, (jj & 1) == 0)) * F.iD[n];
+                }
             }
             __syncthreads();
             Real rz_new = 0;
