@@ -227,6 +227,13 @@ int smc_tempering_update(smc_handle* h, int level, double beta0, int n_mcmc, smc
 
 /* dims6 <- the six layer widths d0..d5. */
 int smc_surrogate_dims(smc_handle* h, int* dims6);
+
+/* The screening gate of surrogate = 1 on one level: *decision 0 not measured yet, 1 the level is
+ * screened, -1 it is not; *solve_ms and *predict_ms the device times it compared (an exact solve
+ * of J particles against a surrogate forward pass of J particles; the level is screened when the
+ * solve costs more than 8 passes). Zero times when not measured or when surrogate = 2 forces the
+ * screen. Any output pointer may be NULL. SMC_EINVAL for a null handle or a bad level. */
+int smc_surrogate_gate(const smc_handle* h, int level, int* decision, double* solve_ms, double* predict_ms);
 /* Append n training pairs (theta [n][K], G [n][n_obs], host) to level's ring of recent pairs. */
 int smc_surrogate_add_pairs(smc_handle* h, int level, int n, const double* theta, const double* G);
 /* steps Adam steps on minibatches of `batch` pairs drawn (Philox) from the ring; *loss (may be NULL)

@@ -153,7 +153,11 @@ int Handle::read_counters(unsigned long long* acc) {
 constexpr double kDaCostRatio = 8.0;
 
 bool Handle::da_worth(int level) {
-    if ((int)da_gate.size() < (int)levels.size()) da_gate.assign(levels.size(), 0);
+    if ((int)da_gate.size() < (int)levels.size()) {
+        da_gate.assign(levels.size(), 0);
+        da_t_solve.assign(levels.size(), 0.f);
+        da_t_pred.assign(levels.size(), 0.f);
+    }
     if (da_gate[level] != 0) return da_gate[level] > 0;
     if (opts.surrogate == 2) {   // screen every level, no cost measurement
         da_gate[level] = 1;
@@ -178,6 +182,8 @@ bool Handle::da_worth(int level) {
     event_pool.push_back(a);
     event_pool.push_back(b);
     event_pool.push_back(c);
+    da_t_solve[level] = t_solve;
+    da_t_pred[level] = t_pred;
     da_gate[level] = (rc == SMC_OK && t_solve > kDaCostRatio * t_pred) ? 1 : -1;
     return da_gate[level] > 0;
 }
@@ -489,6 +495,17 @@ int smc_state(const smc_handle* hh, int* level, double* beta, double* log_eviden
     if (n_updates) *n_updates = (int)S->path.size();
     if (evals_per_level)
         for (int l = 0; l < 8; ++l) evals_per_level[l] = S->evals[l];
+    return SMC_OK;
+}
+
+int smc_surrogate_gate(const smc_handle* hh, int level, int* decision, double* solve_ms, double* predict_ms) {
+    if (!hh) return SMC_EINVAL;
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    if (level < 0 || level >= (int)h->levels.size()) return SMC_EINVAL;
+    const bool known = level < (int)h->da_gate.size();
+    if (decision) *decision = known ? h->da_gate[level] : 0;
+    if (solve_ms) *solve_ms = known ? (double)h->da_t_solve[level] : 0.0;
+    if (predict_ms) *predict_ms = known ? (double)h->da_t_pred[level] : 0.0;
     return SMC_OK;
 }
 

@@ -30,6 +30,8 @@
 // registers: every fine node belongs to one thread for the whole solve.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <cmath>
 #include <algorithm>
 #include <cstdint>
@@ -42,7 +44,7 @@ namespace mls2mc {
 namespace {
 
 __host__ __device__ constexpr int padded(int n) { return (n + 3) & ~3; }
-__host__ __device__ constexpr int lvl_size(int NL) { return padded((NL + 1) * (NL + 1)); }
+__host__ __device__ constexpr int lvl_size(int NL) { return padded((NL + 1) * fem_row_stride(NL)); }
 // element offset of level NL inside the shared arena of a hierarchy with top level N
 __host__ __device__ constexpr int lvl_offset(int N, int NL) { return N == NL ? 0 : 6 * lvl_size(N) + lvl_offset(N / 2, NL); }
 __host__ __device__ constexpr int arena_size(int N) { return N < 2 ? 0 : 6 * lvl_size(N) + arena_size(N / 2); }
@@ -147,20 +149,20 @@ __device__ __forceinline__ void df_add(Real& ah, Real& al, Real bh, Real bl) {
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void smooth_first_red(const Lv<Real>& L) {
     // from e = 0: red nodes get rhs/D; black nodes are written by the black sweep before any read
-    constexpr int M = NL - 1, S = NL + 1;
+    constexpr int M = NL - 1, S = fem_row_stride(NL);
     for (int idx = threadIdx.x; idx < M * S; idx += T) {   // padded rows: a warp reads consecutive words
         const int n = S + idx, j = n / S, i = n - j * S;
-        if (i == 0 || i == NL || ((i + j) & 1)) continue;
+        if (i == 0 || i >= NL || ((i + j) & 1)) continue;
         L.e[n] = L.rhs[n] * L.iD[n];
     }
 }
 
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
-    constexpr int M = NL - 1, S = NL + 1;
+    constexpr int M = NL - 1, S = fem_row_stride(NL);
     for (int idx = threadIdx.x; idx < M * S; idx += T) {
         const int n = S + idx, j = n / S, i = n - j * S;
-        if (i == 0 || i == NL) continue;
+        if (i == 0 || i >= NL) continue;
         if (((i + j) & 1) == color) L.e[n] = (L.rhs[n] + offsum<Real, S>(L.aE, L.aN, L.e, n)) * L.iD[n];
     }
 }
@@ -171,7 +173,7 @@ __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
 // red, and their residuals are the off-diagonal sums of the black values.
 template <typename Real, int NC, int T>
 __device__ __forceinline__ void restrict_red(const Lv<Real>& F, Real* rhs_c) {
-    constexpr int MC = NC - 1, SC = NC + 1, SF = 2 * NC + 1;
+    constexpr int MC = NC - 1, SC = fem_row_stride(NC), SF = fem_row_stride(2 * NC);
     for (int idx = threadIdx.x; idx < MC * MC; idx += T) {
         const int J = idx / MC + 1, I = idx - (J - 1) * MC + 1;
         const int f = (2 * J) * SF + 2 * I;
@@ -187,18 +189,12 @@ __device__ __forceinline__ void restrict_red(const Lv<Real>& F, Real* rhs_c) {
 template <typename Real, int S, int SC>
 __device__ __forceinline__ Real offsum_prolong(const Real* aE, const Real* aN, const Real* e, const Real* ec, int n,
                                                int c0, bool jeven) {
-    Real pE, pW, pN, pS;
-    if (jeven) {   // i odd: E, W coincide with coarse nodes, N, S lie on coarse diagonals
-        pE = ec[c0 + 1];
-        pW = ec[c0];
-        pN = Real(0.5) * (ec[c0] + ec[c0 + SC + 1]);
-        pS = Real(0.5) * (ec[c0 - SC] + ec[c0 + 1]);
-    } else {       // i even: N, S coincide, E, W on diagonals
-        pE = Real(0.5) * (ec[c0] + ec[c0 + SC + 1]);
-        pW = Real(0.5) * (ec[c0 - 1] + ec[c0 + SC]);
-        pN = ec[c0 + SC];
-        pS = ec[c0];
-    }
+    // both cases read ec at c0 and c0 + SC + 1 (the diagonal pair) and at two more nodes
+    const Real e0 = ec[c0], e1 = ec[c0 + SC + 1];
+    const Real eu = ec[jeven ? c0 + 1 : c0 + SC], ev = ec[jeven ? c0 - SC : c0 - 1];
+    const Real dg = Real(0.5) * (e0 + e1), hf = Real(0.5) * (ev + eu);
+    // i odd (j even): E, W coincide with coarse nodes, N, S lie on coarse diagonals; i even: the reverse
+    const Real pE = jeven ? eu : dg, pW = jeven ? e0 : hf, pN = jeven ? dg : eu, pS = jeven ? hf : e0;
     return aE[n] * (e[n + 1] + pE) + aE[n - 1] * (e[n - 1] + pW) + aN[n] * (e[n + S] + pN) +
            aN[n - S] * (e[n - S] + pS);
 }
@@ -206,10 +202,10 @@ __device__ __forceinline__ Real offsum_prolong(const Real* aE, const Real* aN, c
 // black post-sweep with the coarse correction of level NL / 2 folded in
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void black_prolong(const Lv<Real>& L, const Real* ec) {
-    constexpr int M = NL - 1, S = NL + 1, SC = NL / 2 + 1;
+    constexpr int M = NL - 1, S = fem_row_stride(NL), SC = fem_row_stride(NL / 2);
     for (int idx = threadIdx.x; idx < M * S; idx += T) {
         const int n = S + idx, j = n / S, i = n - j * S;
-        if (i == 0 || i == NL || !((i + j) & 1)) continue;
+        if (i == 0 || i >= NL || !((i + j) & 1)) continue;
         const int c0 = (j >> 1) * SC + (i >> 1);
         L.e[n] = (L.rhs[n] + offsum_prolong<Real, S, SC>(L.aE, L.aN, L.e, ec, n, c0, (j & 1) == 0)) * L.iD[n];
     }
@@ -234,7 +230,8 @@ __device__ void vcycle_coarse(Real* arena) {
     } else {
         Lv<Real> L = level_ptrs<Real, N, NL>(arena);
         if constexpr (NL == 2) {
-            if (threadIdx.x == 0) L.e[4] = L.rhs[4] * L.iD[4];   // single interior node (1,1), S = 3
+            constexpr int n11 = fem_row_stride(2) + 1;           // single interior node (1,1)
+            if (threadIdx.x == 0) L.e[n11] = L.rhs[n11] * L.iD[n11];
             phase_sync<WARP>();
         } else {
             Lv<Real> C = level_ptrs<Real, N, NL / 2>(arena);
@@ -257,10 +254,14 @@ __device__ void vcycle_coarse(Real* arena) {
 // kappa in element order e = 2*(j*NL+i) + t (t = 0 lower, 1 upper half of cell (i, j))
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void build_coeffs(const Lv<Real>& L, const Real* kap) {
-    constexpr int S = NL + 1;
-    for (int n = threadIdx.x; n < S * S; n += T) {
+    constexpr int S = fem_row_stride(NL);
+    for (int n = threadIdx.x; n < (NL + 1) * S; n += T) {
         const int j = n / S, i = n - j * S;
         Real ae = 0, an = 0;
+        if (i > NL) {   // padding column
+            L.aE[n] = L.aN[n] = Real(0);
+            continue;
+        }
         if (i < NL) {   // horizontal edge (i,j)-(i+1,j): lower of cell (i,j), upper of cell (i,j-1)
             if (j < NL) ae += kap[2 * (j * NL + i)];
             if (j > 0) ae += kap[2 * ((j - 1) * NL + i) + 1];
@@ -276,8 +277,8 @@ __device__ __forceinline__ void build_coeffs(const Lv<Real>& L, const Real* kap)
 
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void build_diag(const Lv<Real>& L) {
-    constexpr int S = NL + 1;
-    for (int n = threadIdx.x; n < S * S; n += T) {
+    constexpr int S = fem_row_stride(NL);
+    for (int n = threadIdx.x; n < (NL + 1) * S; n += T) {
         const int j = n / S, i = n - j * S;
         Real d = 0;
         if (i > 0 && j > 0 && i < NL && j < NL) d = L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S];
@@ -321,7 +322,7 @@ __device__ void setup_levels(Real* arena, Real* stage, bool ping) {
 
 template <typename Real, int N>
 struct Fine {
-    static constexpr int M = N - 1, S = N + 1, NI = M * M;
+    static constexpr int M = N - 1, S = fem_row_stride(N), NI = M * M;
 };
 
 // ---- the kernel ----------------------------------------------------------------------
@@ -330,7 +331,9 @@ template <typename Real, int N, int T>
 __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Real* arena, double (*red_buf)[64],
                                                Real* theta_s) {
     constexpr int M = Fine<Real, N>::M, S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
-    constexpr int NPT = (M * S + T - 1) / T;   // slots over the padded interior rows
+    constexpr int NCOL = N * N / 2;                    // slot positions per colour (see below)
+    constexpr int NPH = (NCOL + T - 1) / T;            // slots per colour and thread
+    constexpr int NPT = 2 * NPH;
     constexpr int E = 2 * N * N;
     const int tid = threadIdx.x;
 
@@ -361,29 +364,38 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
         int off = 0;
 #pragma unroll
         for (int NL = N; NL >= 2; NL >>= 1) {
-            const int z = ((NL + 1) * (NL + 1) + 3) & ~3;
+            const int z = lvl_size(NL);
             for (int q = tid; q < 3 * z; q += T) arena[off + 3 * z + q] = Real(0);
             off += 6 * z;
         }
     }
     __syncthreads();
 
-    // fine nodes owned by this thread, one packed int each: bits 0-12 padded node index n,
-    // 13-23 the coarse node c under it, 24-25 which second coarse node its P1
-    // interpolation averages with (0 none, 1 c+1, 2 c+SC, 3 c+SC+1), 26 red, 27 valid
-    // Slots run over the padded rows 1..N-1 (boundary columns are idle slots), so the nodes of a
-    // warp are 32 consecutive words: no shared-memory bank conflicts at row ends.
-    constexpr int SC = N / 2 + 1;
+    // fine nodes owned by this thread, one packed int each: bits 0-12 node index n, 13-23 the
+    // coarse node c under it ((j/2) SC + i/2), 24-25 (i & 1) + 2 (j & 1), 26 red, 27 valid.
+    // Slots 0..NPH-1 hold red nodes (i + j even), NPH..NPT-1 black ones, so that every lane has
+    // a node in each colour sweep. A colour has N/2 positions per row (the last one idle in rows
+    // with N/2 - 1 nodes of that colour); 2G consecutive slots (G = min(16, N/2)) take G
+    // positions of row 2R + 1 and the same positions of row 2R + 2: with the even row stride the
+    // two rows' nodes of one colour lie on banks of opposite parity, and a warp's 32 accesses
+    // hit 32 distinct banks.
+    constexpr int G = N / 2 < 16 ? N / 2 : 16;
+    constexpr int SC = fem_row_stride(N / 2);
     int slot[NPT];
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
-        const int idx = tid + T * q;
-        const int n0 = S + (idx < M * S ? idx : 0);
-        const int jj = n0 / S, ii = n0 - jj * S;
-        const int v = idx < M * S && ii >= 1 && ii <= M;
+        const bool red = q < NPH;
+        const int k = tid + T * (red ? q : q - NPH);
+        const int blk = k / (2 * G), l = k - blk * 2 * G;
+        const int R = blk / (N / 2 / G), sg = blk - R * (N / 2 / G);
+        int jj = 2 * R + 1 + l / G;
+        int ii = (((jj & 1) ^ (red ? 0 : 1)) ? 1 : 2) + 2 * (sg * G + l % G);
+        const int v = k < NCOL && jj <= M && ii <= M;
+        if (!v) ii = jj = 1;
+        const int n0 = jj * S + ii;
         const int c = (jj >> 1) * SC + (ii >> 1);
         const int code = (ii & 1) + 2 * (jj & 1);
-        slot[q] = (v ? n0 : S + 1) | (c << 13) | (code << 24) | ((((ii + jj) & 1) == 0) << 26) | (v << 27);
+        slot[q] = n0 | (c << 13) | (code << 24) | ((red ? 1 : 0) << 26) | (v << 27);
     }
     // right-hand side h^2 (f = 1), exact in FP32 for N a power of two
     const Real h2 = Real(1) / (Real(N) * Real(N));
@@ -424,12 +436,12 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
             // from zero, black pre-sweep, restriction of the red residuals, coarse cycle, black
             // post-sweep with the prolongation folded in, red post-sweep)
 #pragma unroll
-            for (int q = 0; q < NPT; ++q)
-                if (((slot[q] >> 27) & 1) && ((slot[q] >> 26) & 1)) F.e[(slot[q] & 0x1fff)] = r[q] * F.iD[(slot[q] & 0x1fff)];
+            for (int q = 0; q < NPH; ++q)
+                if (((slot[q] >> 27) & 1)) F.e[(slot[q] & 0x1fff)] = r[q] * F.iD[(slot[q] & 0x1fff)];
             __syncthreads();
 #pragma unroll
-            for (int q = 0; q < NPT; ++q)
-                if (((slot[q] >> 27) & 1) && !((slot[q] >> 26) & 1)) {
+            for (int q = NPH; q < NPT; ++q)
+                if (((slot[q] >> 27) & 1)) {
                     const int n = (slot[q] & 0x1fff);
                     F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
                 }
@@ -438,8 +450,8 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
             __syncthreads();
             vcycle_coarse<Real, N, N / 2, T>(arena);
 #pragma unroll
-            for (int q = 0; q < NPT; ++q)
-                if (((slot[q] >> 27) & 1) && !((slot[q] >> 26) & 1)) {
+            for (int q = NPH; q < NPT; ++q)
+                if (((slot[q] >> 27) & 1)) {
                     const int n = (slot[q] & 0x1fff);
                     const int c = (slot[q] >> 13) & 0x7ff, code = (slot[q] >> 24) & 3;
                     F.e[n] = (r[q] + offsum_prolong<Real, S, SC>(F.aE, F.aN, F.e, C1.e, n, c, code == 1)) * F.iD[n];
@@ -447,8 +459,8 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
             __syncthreads();
             Real rz_new = 0;
 #pragma unroll
-            for (int q = 0; q < NPT; ++q)
-                if (((slot[q] >> 27) & 1) && ((slot[q] >> 26) & 1)) {
+            for (int q = 0; q < NPH; ++q)
+                if (((slot[q] >> 27) & 1)) {
                     const int n = (slot[q] & 0x1fff);
                     F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
                 }
@@ -536,25 +548,42 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     }
 
     // ---- observations and misfit (FP64) ----
-    double* xs = reinterpret_cast<double*>(F.e);   // e and res: 2*lvl_size(N) Real >= (N+1)^2 doubles
-    for (int n = tid; n < S * S; n += T) xs[n] = 0.0;
-    __syncthreads();
+    // the solution goes to shared memory as stored (double, or the double-float pair as float2,
+    // so that FP64 arithmetic runs only at the observed nodes); the boundary ring reads as zero
+    using Node = typename std::conditional<sizeof(Real) == 8, double, float2>::type;
+    Node* xs = reinterpret_cast<Node*>(F.e);   // e and res: 2*lvl_size(N) Real >= (N+1) S Nodes
+    for (int k = tid; k < 4 * N; k += T) {   // rows 0 and N (N + 1 nodes each), then columns 0 and N
+        const int n = k <= N ? k : k <= 2 * N + 1 ? N * S + (k - N - 1)
+                                                 : (1 + ((k - 2 * N - 2) >> 1)) * S + (((k - 2 * N - 2) & 1) ? N : 0);
+        if constexpr (sizeof(Real) == 8) xs[n] = 0.0;
+        else xs[n] = make_float2(0.f, 0.f);
+    }
 #pragma unroll
     for (int q = 0; q < NPT; ++q)
-        if (((slot[q] >> 27) & 1)) xs[(slot[q] & 0x1fff)] = (double)xh[q] + (double)xl[q];
+        if (((slot[q] >> 27) & 1)) {
+            if constexpr (sizeof(Real) == 8) xs[(slot[q] & 0x1fff)] = (double)xh[q];
+            else xs[(slot[q] & 0x1fff)] = make_float2((float)xh[q], (float)xl[q]);
+        }
     __syncthreads();
-    double misfit = 0.0;
-    for (int o = tid; o < a.n_obs; o += T) {
-        const double g = a.obs_w[3 * o] * xs[a.obs_idx[3 * o]] + a.obs_w[3 * o + 1] * xs[a.obs_idx[3 * o + 1]] +
-                         a.obs_w[3 * o + 2] * xs[a.obs_idx[3 * o + 2]];
-        if (a.G) a.G[(size_t)p * a.n_obs + o] = g;
-        const double rdf = a.y[o] - g;
-        misfit += rdf * rdf;
-    }
-    block_sum<T>(misfit, red_buf[parity]);
-    if (tid == 0) {
-        a.Phi[p] = 0.5 * misfit * a.inv_sigma2;
-        if (a.iters) a.iters[p] = converged ? total_it : -(total_it + 1);
+    if (tid < 32) {   // one warp gathers and reduces the misfit (no block-wide FP64 work)
+        auto val = [&](int n) -> double {
+            if constexpr (sizeof(Real) == 8) return xs[n];
+            else return (double)xs[n].x + (double)xs[n].y;
+        };
+        double misfit = 0.0;
+        for (int o = tid; o < a.n_obs; o += 32) {
+            const double g = a.obs_w[3 * o] * val(a.obs_idx[3 * o]) + a.obs_w[3 * o + 1] * val(a.obs_idx[3 * o + 1]) +
+                             a.obs_w[3 * o + 2] * val(a.obs_idx[3 * o + 2]);
+            if (a.G) a.G[(size_t)p * a.n_obs + o] = g;
+            const double rdf = a.y[o] - g;
+            misfit += rdf * rdf;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) misfit += __shfl_xor_sync(0xffffffffu, misfit, off);
+        if (tid == 0) {
+            a.Phi[p] = 0.5 * misfit * a.inv_sigma2;
+            if (a.iters) a.iters[p] = converged ? total_it : -(total_it + 1);
+        }
     }
 }
 
@@ -596,7 +625,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
                                                    double (*red_buf)[64]) {
     constexpr int M = Fine<Real, N>::M, S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
     constexpr int E = 2 * N * N;
-    constexpr int SC = N / 2 + 1;
+    constexpr int SC = fem_row_stride(N / 2);
     const int tid = threadIdx.x;
     Lv<Real> F = level_ptrs<Real, N, N>(arena);
     Real* vec = arena + arena_size(N);
@@ -630,14 +659,14 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
         int off = 0;
 #pragma unroll
         for (int NL = N; NL >= 128; NL >>= 1) {
-            const int z = ((NL + 1) * (NL + 1) + 3) & ~3;
+            const int z = lvl_size(NL);
             for (int q = tid; q < 3 * z; q += T) arena[off + 3 * z + q] = Real(0);
             off += 6 * z;
         }
         off = 0;
 #pragma unroll
         for (int NL = 64; NL >= 2; NL >>= 1) {
-            const int z = ((NL + 1) * (NL + 1) + 3) & ~3;
+            const int z = lvl_size(NL);
             for (int q = tid; q < 3 * z; q += T) sarena[off + 3 * z + q] = Real(0);
             off += 6 * z;
         }
@@ -762,28 +791,29 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
         parity ^= 1;
         converged = rr_out <= stop_outer;
     }
-    double* xs = reinterpret_cast<double*>(F.e);
-    __syncthreads();
-    for (int n = tid; n < S * S; n += T) xs[n] = 0.0;
-    __syncthreads();
-    for (int i = tid; i < NI; i += T) {
-        NODE_OF(i);
-        xs[n] = (double)XH[i] + (double)XL[i];
-    }
 #undef NODE_OF
     __syncthreads();
-    double misfit = 0.0;
-    for (int o = tid; o < a.n_obs; o += T) {
-        const double g = a.obs_w[3 * o] * xs[a.obs_idx[3 * o]] + a.obs_w[3 * o + 1] * xs[a.obs_idx[3 * o + 1]] +
-                         a.obs_w[3 * o + 2] * xs[a.obs_idx[3 * o + 2]];
-        if (a.G) a.G[(size_t)p * a.n_obs + o] = g;
-        const double rdf = a.y[o] - g;
-        misfit += rdf * rdf;
-    }
-    block_sum<T>(misfit, red_buf[parity]);
-    if (tid == 0) {
-        a.Phi[p] = 0.5 * misfit * a.inv_sigma2;
-        if (a.iters) a.iters[p] = converged ? total_it : -(total_it + 1);
+    if (tid < 32) {   // the observed nodes straight from the interior arrays; one warp reduces
+        auto val = [&](int n) -> double {
+            const int j = n / S, i = n - j * S;
+            if (i < 1 || i > M || j < 1 || j > M) return 0.0;
+            const int k = (j - 1) * M + (i - 1);
+            return (double)XH[k] + (double)XL[k];
+        };
+        double misfit = 0.0;
+        for (int o = tid; o < a.n_obs; o += 32) {
+            const double g = a.obs_w[3 * o] * val(a.obs_idx[3 * o]) + a.obs_w[3 * o + 1] * val(a.obs_idx[3 * o + 1]) +
+                             a.obs_w[3 * o + 2] * val(a.obs_idx[3 * o + 2]);
+            if (a.G) a.G[(size_t)p * a.n_obs + o] = g;
+            const double rdf = a.y[o] - g;
+            misfit += rdf * rdf;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) misfit += __shfl_xor_sync(0xffffffffu, misfit, off);
+        if (tid == 0) {
+            a.Phi[p] = 0.5 * misfit * a.inv_sigma2;
+            if (a.iters) a.iters[p] = converged ? total_it : -(total_it + 1);
+        }
     }
 }
 

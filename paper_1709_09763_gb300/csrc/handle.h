@@ -103,6 +103,7 @@ struct Handle {
     bool da_ready(int level, double zeta) const;
     bool da_worth(int level);
     std::vector<int> da_gate;   // per level: 0 unknown, 1 screen pays, -1 it does not
+    std::vector<float> da_t_solve, da_t_pred;   // per level: the gate's measured device times (ms)
     double last_da_rate = -1.0;
     void record(int type, double zeta, const struct IncState& st, double rate, double cv_lu, smc_stage_info* info);
     int itu(double cv_lu, smc_stage_info* info);

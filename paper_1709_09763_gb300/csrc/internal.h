@@ -15,6 +15,11 @@ namespace mls2mc {
 void kl_eig_1d(double corr_len, int n_modes, std::vector<double>& lam, std::vector<double>& omega);
 void kl_table(int N, double corr_len, double variance, int K, std::vector<double>& psi,
               std::vector<double>& lambda);
+// Nodes of a level with NL cells per side are stored row by row with row stride NL + 2 (one
+// padding word per row, never read): with an even stride, nodes of one red-black colour in two
+// adjacent rows fall on shared-memory banks of opposite parity.
+__host__ __device__ constexpr int fem_row_stride(int NL) { return NL + 2; }
+// node indices j * fem_row_stride(N) + i of the three P1 vertices of each observation
 void obs_table(int N, int n_obs, const double* xy, std::vector<int>& idx, std::vector<double>& wts);
 
 // ---- kernel launch counter (api.cpp): every kernel the library launches is counted ------
@@ -30,7 +35,7 @@ struct FemArgs {
     const double* theta;    // [n][K] device
     const void* psi;        // [K][2N^2] device, double (FP64) or float (MIXED)
     const float* kappa;     // [n][2N^2] kappa = exp(u) per triangle (MIXED: from the tensor-core synthesis), or null
-    const int* obs_idx;     // [n_obs][3] node indices into the (N+1)^2 grid
+    const int* obs_idx;     // [n_obs][3] node indices j * fem_row_stride(N) + i
     const double* obs_w;    // [n_obs][3] P1 weights
     int n_obs;
     const double* y;        // [n_obs]

@@ -104,7 +104,7 @@ void kl_table(int N, double corr_len, double variance, int K, std::vector<double
 
 void obs_table(int N, int n_obs, const double* xy, std::vector<int>& idx, std::vector<double>& wts) {
     // P1 interpolation: locate the cell, then the triangle (lower when dx >= dy),
-    // then barycentric weights of its three vertices (node index j*(N+1)+i).
+    // then barycentric weights of its three vertices (node index j * fem_row_stride(N) + i).
     const double h = 1.0 / N;
     idx.resize((size_t)n_obs * 3);
     wts.resize((size_t)n_obs * 3);
@@ -114,7 +114,8 @@ void obs_table(int N, int n_obs, const double* xy, std::vector<int>& idx, std::v
         i = std::min(std::max(i, 0), N - 1);
         j = std::min(std::max(j, 0), N - 1);
         const double dx = x / h - i, dy = y / h - j;   // local coordinates in [0,1]^2
-        const int v00 = j * (N + 1) + i, v10 = v00 + 1, v01 = v00 + N + 1, v11 = v01 + 1;
+        const int SR = fem_row_stride(N);
+        const int v00 = j * SR + i, v10 = v00 + 1, v01 = v00 + SR, v11 = v01 + 1;
         if (dx >= dy) {  // lower triangle (0,0),(1,0),(1,1): weights 1-dx, dx-dy, dy
             idx[3 * r] = v00; wts[3 * r] = 1.0 - dx;
             idx[3 * r + 1] = v10; wts[3 * r + 1] = dx - dy;

@@ -78,6 +78,7 @@ SIGNATURES = {
     "smc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(StageInfo)]),
     "smc_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(StageInfo)]),
     "smc_state": (ctypes.c_int, [ctypes.c_void_p, _ip, _dp, _dp, _ip, ctypes.POINTER(ctypes.c_longlong)]),
+    "smc_surrogate_gate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip, _dp, _dp]),
     "smc_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(StageInfo), _ip]),
     "smc_posterior_moments": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp, _dp]),
     "smc_get_particles": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
@@ -281,6 +282,13 @@ class Handle:
         self._check(self._lib.smc_state(self._h, ctypes.byref(lvl), ctypes.byref(beta), ctypes.byref(lz),
                                         ctypes.byref(nu), ev))
         return dict(level=lvl.value, beta=beta.value, log_z=lz.value, n_updates=nu.value, evals=list(ev))
+
+    def surrogate_gate(self, level):
+        """The screening gate of one level: (decision 0/1/-1, solve ms, surrogate pass ms)."""
+        dec, ts, tp = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.smc_surrogate_gate(self._h, int(level), ctypes.byref(dec), ctypes.byref(ts),
+                                                 ctypes.byref(tp)))
+        return dec.value, ts.value, tp.value
 
     def path(self):
         cnt = ctypes.c_int()

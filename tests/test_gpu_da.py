@@ -62,15 +62,33 @@ def test_delayed_acceptance_same_posterior_fewer_solves():
     assert np.mean([solves_per_update(d) for d in da]) < np.mean([solves_per_update(p) for p in plain])
 
 
-def test_cost_gate_screens_only_expensive_levels():
-    """surrogate = 1 screens a level only where an exact solve costs more than 8 surrogate passes:
-    single-level SMC on 1/h = 64 with J = 1500 (every update an ITU on that level) must screen once
-    its network is trained, and still reach beta = 1."""
+def test_cost_gate_follows_measured_costs():
+    """surrogate = 1 screens a level exactly when its measured exact solve of J particles costs more
+    than 8 surrogate passes: single-level SMC on 1/h = 64 with J = 1500 (every update an ITU on that
+    level) measures the gate once, screens its updates iff the gate says so, and reaches beta = 1."""
     K, obs, y, sigma = _problem()
     h = native.Handle([64], K, obs, y, sigma, corr_len=0.3, J=1500, n_mcmc=5, s_pcn=0.3,
                       precision=native.SMC_MIXED, seed=7, surrogate=1)
     h.run()
     path = h.path()
     assert all(p["kind"] == "ITU" for p in path)
-    assert any(p["da_stage1_rate"] >= 0 for p in path)
+    dec, t_solve, t_pred = h.surrogate_gate(0)
+    assert dec != 0 and t_solve > 0 and t_pred > 0
+    assert (dec > 0) == (t_solve > 8 * t_pred)
+    screened = [p["da_stage1_rate"] >= 0 for p in path]
+    if dec > 0:
+        assert any(screened)
+    else:
+        assert not any(screened)
     assert h.state()["beta"] == 1.0
+
+
+def test_gate_forced_and_unmeasured():
+    """surrogate = 2 screens without a measurement (zero times); a plain sampler never measures."""
+    K, obs, y, sigma = _problem()
+    h = native.Handle([8, 16], K, obs, y, sigma, corr_len=0.3, J=300, n_mcmc=2, s_pcn=0.3,
+                      precision=native.SMC_MIXED, seed=3, surrogate=0)
+    h.run()
+    assert h.surrogate_gate(0) == (0, 0.0, 0.0) and h.surrogate_gate(1) == (0, 0.0, 0.0)
+    with pytest.raises(native.SmcError):
+        h.surrogate_gate(2)
