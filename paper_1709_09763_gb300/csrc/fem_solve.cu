@@ -136,6 +136,23 @@ __device__ __forceinline__ void df_add(Real& ah, Real& al, Real bh, Real bl) {
     al = e - (ah - s);
 }
 
+// ---- red/black enumeration -----------------------------------------------------------------
+// Position k of colour col (0 red: i + j even, 1 black) on a level with NL cells per side. A
+// colour has NL/2 positions per row (the last one idle in rows with NL/2 - 1 nodes of that
+// colour); 2G consecutive positions (G = min(16, NL/2)) take G positions of row 2R + 1 and the
+// same positions of row 2R + 2. With the even row stride the two rows' nodes of one colour lie on
+// banks of opposite parity, so for NL >= 32 a warp's 32 accesses hit 32 distinct banks. All
+// divisions are by powers of two. Returns false for idle positions.
+template <int NL>
+__device__ __forceinline__ bool colour_node(int k, int col, int& i, int& j) {
+    constexpr int G = NL / 2 < 16 ? NL / 2 : 16;
+    const int blk = k / (2 * G), l = k - blk * 2 * G;
+    const int R = blk / (NL / 2 / G), sg = blk - R * (NL / 2 / G);
+    j = 2 * R + 1 + l / G;
+    i = (((j & 1) ^ col) ? 1 : 2) + 2 * (sg * G + l % G);
+    return k < NL * NL / 2 && j <= NL - 1 && i <= NL - 1;
+}
+
 // ---- coarse-level multigrid pieces (rhs in shared memory) --------------------------------
 // V(1,1) with red-black Gauss-Seidel: pre-smoothing red then black from e = 0, post-smoothing
 // black then red (a symmetric preconditioner). Two identities of the red-black ordering remove
@@ -149,21 +166,23 @@ __device__ __forceinline__ void df_add(Real& ah, Real& al, Real bh, Real bl) {
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void smooth_first_red(const Lv<Real>& L) {
     // from e = 0: red nodes get rhs/D; black nodes are written by the black sweep before any read
-    constexpr int M = NL - 1, S = fem_row_stride(NL);
-    for (int idx = threadIdx.x; idx < M * S; idx += T) {   // padded rows: a warp reads consecutive words
-        const int n = S + idx, j = n / S, i = n - j * S;
-        if (i == 0 || i >= NL || ((i + j) & 1)) continue;
+    constexpr int S = fem_row_stride(NL);
+    for (int k = threadIdx.x; k < NL * NL / 2; k += T) {
+        int i, j;
+        if (!colour_node<NL>(k, 0, i, j)) continue;
+        const int n = j * S + i;
         L.e[n] = L.rhs[n] * L.iD[n];
     }
 }
 
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
-    constexpr int M = NL - 1, S = fem_row_stride(NL);
-    for (int idx = threadIdx.x; idx < M * S; idx += T) {
-        const int n = S + idx, j = n / S, i = n - j * S;
-        if (i == 0 || i >= NL) continue;
-        if (((i + j) & 1) == color) L.e[n] = (L.rhs[n] + offsum<Real, S>(L.aE, L.aN, L.e, n)) * L.iD[n];
+    constexpr int S = fem_row_stride(NL);
+    for (int k = threadIdx.x; k < NL * NL / 2; k += T) {
+        int i, j;
+        if (!colour_node<NL>(k, color, i, j)) continue;
+        const int n = j * S + i;
+        L.e[n] = (L.rhs[n] + offsum<Real, S>(L.aE, L.aN, L.e, n)) * L.iD[n];
     }
 }
 
@@ -202,10 +221,11 @@ __device__ __forceinline__ Real offsum_prolong(const Real* aE, const Real* aN, c
 // black post-sweep with the coarse correction of level NL / 2 folded in
 template <typename Real, int NL, int T>
 __device__ __forceinline__ void black_prolong(const Lv<Real>& L, const Real* ec) {
-    constexpr int M = NL - 1, S = fem_row_stride(NL), SC = fem_row_stride(NL / 2);
-    for (int idx = threadIdx.x; idx < M * S; idx += T) {
-        const int n = S + idx, j = n / S, i = n - j * S;
-        if (i == 0 || i >= NL || !((i + j) & 1)) continue;
+    constexpr int S = fem_row_stride(NL), SC = fem_row_stride(NL / 2);
+    for (int k = threadIdx.x; k < NL * NL / 2; k += T) {
+        int i, j;
+        if (!colour_node<NL>(k, 1, i, j)) continue;
+        const int n = j * S + i;
         const int c0 = (j >> 1) * SC + (i >> 1);
         L.e[n] = (L.rhs[n] + offsum_prolong<Real, S, SC>(L.aE, L.aN, L.e, ec, n, c0, (j & 1) == 0)) * L.iD[n];
     }
@@ -330,7 +350,7 @@ struct Fine {
 template <typename Real, int N, int T>
 __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Real* arena, double (*red_buf)[64],
                                                Real* theta_s) {
-    constexpr int M = Fine<Real, N>::M, S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
+    constexpr int S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
     constexpr int NCOL = N * N / 2;                    // slot positions per colour (see below)
     constexpr int NPH = (NCOL + T - 1) / T;            // slots per colour and thread
     constexpr int NPT = 2 * NPH;
@@ -373,24 +393,16 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
 
     // fine nodes owned by this thread, one packed int each: bits 0-12 node index n, 13-23 the
     // coarse node c under it ((j/2) SC + i/2), 24-25 (i & 1) + 2 (j & 1), 26 red, 27 valid.
-    // Slots 0..NPH-1 hold red nodes (i + j even), NPH..NPT-1 black ones, so that every lane has
-    // a node in each colour sweep. A colour has N/2 positions per row (the last one idle in rows
-    // with N/2 - 1 nodes of that colour); 2G consecutive slots (G = min(16, N/2)) take G
-    // positions of row 2R + 1 and the same positions of row 2R + 2: with the even row stride the
-    // two rows' nodes of one colour lie on banks of opposite parity, and a warp's 32 accesses
-    // hit 32 distinct banks.
-    constexpr int G = N / 2 < 16 ? N / 2 : 16;
+    // Slots 0..NPH-1 hold red nodes (i + j even), NPH..NPT-1 black ones (colour_node
+    // enumeration), so that every lane has a node in each colour sweep, without bank conflicts.
     constexpr int SC = fem_row_stride(N / 2);
     int slot[NPT];
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
         const bool red = q < NPH;
         const int k = tid + T * (red ? q : q - NPH);
-        const int blk = k / (2 * G), l = k - blk * 2 * G;
-        const int R = blk / (N / 2 / G), sg = blk - R * (N / 2 / G);
-        int jj = 2 * R + 1 + l / G;
-        int ii = (((jj & 1) ^ (red ? 0 : 1)) ? 1 : 2) + 2 * (sg * G + l % G);
-        const int v = k < NCOL && jj <= M && ii <= M;
+        int ii, jj;
+        const int v = colour_node<N>(k, red ? 0 : 1, ii, jj);
         if (!v) ii = jj = 1;
         const int n0 = jj * S + ii;
         const int c = (jj >> 1) * SC + (ii >> 1);
