@@ -76,6 +76,13 @@ __device__ __forceinline__ Real stencil_apply(const Real* aE, const Real* aN, co
            aN[n - S] * (vn - v[n - S]);
 }
 
+// the same with the value at n supplied by the caller (held in a register)
+template <typename Real, int S>
+__device__ __forceinline__ Real stencil_apply_at(const Real* aE, const Real* aN, const Real* v, int n, Real vn) {
+    return aE[n] * (vn - v[n + 1]) + aE[n - 1] * (vn - v[n - 1]) + aN[n] * (vn - v[n + S]) +
+           aN[n - S] * (vn - v[n - S]);
+}
+
 // ---- block reductions (every thread gets the same result, summed in a fixed order) ----
 template <int T, typename Acc>
 __device__ __forceinline__ void block_sum(Acc& a, double* buf_raw) {
@@ -345,15 +352,20 @@ struct Fine {
     static constexpr int M = N - 1, S = fem_row_stride(N), NI = M * M;
 };
 
+// fine-level slots per thread (half red, half black) of the on-chip solve
+__host__ __device__ constexpr int fine_slots(int N, int T) { return 2 * ((N * N / 2 + T - 1) / T); }
+// dynamic shared memory of the on-chip solve, in Reals: the level arena, then the refinement
+// state (x and r, each a hi/lo pair) of every thread's slots
+__host__ __device__ constexpr int solve_smem_reals(int N, int T) { return arena_size(N) + 4 * fine_slots(N, T) * T; }
+
 // ---- the kernel ----------------------------------------------------------------------
 // the whole solve of particle p of a.n, by one thread block (all threads call it)
 template <typename Real, int N, int T>
 __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Real* arena, double (*red_buf)[64],
                                                Real* theta_s) {
     constexpr int S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
-    constexpr int NCOL = N * N / 2;                    // slot positions per colour (see below)
-    constexpr int NPH = (NCOL + T - 1) / T;            // slots per colour and thread
-    constexpr int NPT = 2 * NPH;
+    constexpr int NPT = fine_slots(N, T);              // slots per thread (colour_node positions)
+    constexpr int NPH = NPT / 2;                       // per colour
     constexpr int E = 2 * N * N;
     const int tid = threadIdx.x;
 
@@ -411,15 +423,23 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     }
     // right-hand side h^2 (f = 1), exact in FP32 for N a power of two
     const Real h2 = Real(1) / (Real(N) * Real(N));
-    // solution x and residual r of the refinement: FP64, or double-float pairs (hi + lo)
-    // of FP32 numbers on the mixed path so that no FP64 instruction runs in the solve
-    Real xh[NPT], xl[NPT], rh[NPT], rl[NPT];
-    Real r[NPT], d[NPT];
+    // solution x and residual r of the refinement: FP64, or double-float pairs (hi + lo) of FP32
+    // numbers on the mixed path so that no FP64 instruction runs in the solve. They are touched
+    // once per refinement pass, so they live in shared memory after the arena ([4][NPT][T]:
+    // x hi, x lo, r hi, r lo), conflict-free per slot.
+    Real* ref = arena + arena_size(N);
+    auto XH = [&](int q) -> Real& { return ref[(0 * NPT + q) * T + tid]; };
+    auto XL = [&](int q) -> Real& { return ref[(1 * NPT + q) * T + tid]; };
+    auto RH = [&](int q) -> Real& { return ref[(2 * NPT + q) * T + tid]; };
+    auto RL = [&](int q) -> Real& { return ref[(3 * NPT + q) * T + tid]; };
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
-        xh[q] = xl[q] = rl[q] = Real(0);
-        rh[q] = ((slot[q] >> 27) & 1) ? h2 : Real(0);
+        XH(q) = XL(q) = RL(q) = Real(0);
+        RH(q) = ((slot[q] >> 27) & 1) ? h2 : Real(0);
     }
+    // inner CG state of this thread's nodes: residual r, correction d, preconditioned residual z
+    // and search direction p (p is also published in shared memory for the stencil)
+    Real r[NPT], d[NPT], z[NPT], pv[NPT];
     const Real bnorm2 = Real(NI) * h2 * h2;
     const Real stop_outer = Real(a.rtol * a.rtol) * bnorm2;
     const Real rtol_in2 = Real(a.rtol_in * a.rtol_in);
@@ -427,15 +447,16 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     int total_it = 0;
     bool converged = false;
     Lv<Real> C1 = level_ptrs<Real, N, N / 2>(arena);
-    Real* P = F.rhs;   // fine-level CG direction
+    Real* P = F.rhs;   // fine-level CG direction (the fine rhs is r, held in registers)
 
     for (int pass = 0; pass < a.max_outer && !converged; ++pass) {
         // ---- inner multigrid-preconditioned CG on A d = r (working precision) ----
         Real rr0 = 0;
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
-            r[q] = rh[q];
+            r[q] = RH(q);
             d[q] = Real(0);
+            pv[q] = Real(0);
             rr0 += r[q] * r[q];
         }
         block_sum<T>(rr0, red_buf[parity]);
@@ -446,7 +467,8 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
         for (int it = 0; it < a.max_inner; ++it) {
             // z = M^{-1} r: V(1,1) cycle with the fine rhs held in registers (red pre-sweep
             // from zero, black pre-sweep, restriction of the red residuals, coarse cycle, black
-            // post-sweep with the prolongation folded in, red post-sweep)
+            // post-sweep with the prolongation folded in, red post-sweep). The red post-sweep
+            // values are read by nothing but this thread, so they stay in registers.
 #pragma unroll
             for (int q = 0; q < NPH; ++q)
                 if (((slot[q] >> 27) & 1)) F.e[(slot[q] & 0x1fff)] = r[q] * F.iD[(slot[q] & 0x1fff)];
@@ -462,31 +484,37 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
             __syncthreads();
             vcycle_coarse<Real, N, N / 2, T>(arena);
 #pragma unroll
-            for (int q = NPH; q < NPT; ++q)
+            for (int q = NPH; q < NPT; ++q) {
+                z[q] = Real(0);
                 if (((slot[q] >> 27) & 1)) {
                     const int n = (slot[q] & 0x1fff);
                     const int c = (slot[q] >> 13) & 0x7ff, code = (slot[q] >> 24) & 3;
-                    F.e[n] = (r[q] + offsum_prolong<Real, S, SC>(F.aE, F.aN, F.e, C1.e, n, c, code == 1)) * F.iD[n];
+                    z[q] = (r[q] + offsum_prolong<Real, S, SC>(F.aE, F.aN, F.e, C1.e, n, c, code == 1)) * F.iD[n];
+                    F.e[n] = z[q];
                 }
+            }
             __syncthreads();
             Real rz_new = 0;
 #pragma unroll
-            for (int q = 0; q < NPH; ++q)
+            for (int q = 0; q < NPH; ++q) {
+                z[q] = Real(0);
                 if (((slot[q] >> 27) & 1)) {
                     const int n = (slot[q] & 0x1fff);
-                    F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
+                    z[q] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
                 }
+            }
 #pragma unroll
-            for (int q = 0; q < NPT; ++q)
-                if (((slot[q] >> 27) & 1)) rz_new += r[q] * F.e[(slot[q] & 0x1fff)];
+            for (int q = 0; q < NPT; ++q) rz_new += r[q] * z[q];   // idle slots hold r = z = 0
             block_sum<T>(rz_new, red_buf[parity]);
             parity ^= 1;
             // p = z + beta p
             const Real beta = (it == 0) ? Real(0) : rz_new / rz;
             rz = rz_new;
 #pragma unroll
-            for (int q = 0; q < NPT; ++q)
-                if (((slot[q] >> 27) & 1)) P[(slot[q] & 0x1fff)] = (it == 0) ? F.e[(slot[q] & 0x1fff)] : F.e[(slot[q] & 0x1fff)] + beta * P[(slot[q] & 0x1fff)];
+            for (int q = 0; q < NPT; ++q) {
+                pv[q] = (it == 0) ? z[q] : z[q] + beta * pv[q];
+                if (((slot[q] >> 27) & 1)) P[(slot[q] & 0x1fff)] = pv[q];
+            }
             __syncthreads();
             // q = A p, alpha = rz / p.q
             Real qv[NPT];
@@ -496,8 +524,8 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
                 qv[q] = Real(0);
                 if (((slot[q] >> 27) & 1)) {
                     const int n = (slot[q] & 0x1fff);
-                    qv[q] = stencil_apply<Real, S>(F.aE, F.aN, P, n);
-                    pq += P[n] * qv[q];
+                    qv[q] = stencil_apply_at<Real, S>(F.aE, F.aN, P, n, pv[q]);
+                    pq += pv[q] * qv[q];
                 }
             }
             block_sum<T>(pq, red_buf[parity]);
@@ -505,12 +533,11 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
             const Real alpha = rz / pq;
             Real rr = 0;
 #pragma unroll
-            for (int q = 0; q < NPT; ++q)
-                if (((slot[q] >> 27) & 1)) {
-                    d[q] = fma(alpha, P[(slot[q] & 0x1fff)], d[q]);
-                    r[q] = fma(-alpha, qv[q], r[q]);
-                    rr += r[q] * r[q];
-                }
+            for (int q = 0; q < NPT; ++q) {
+                d[q] = fma(alpha, pv[q], d[q]);
+                r[q] = fma(-alpha, qv[q], r[q]);
+                rr += r[q] * r[q];
+            }
             block_sum<T>(rr, red_buf[parity]);
             parity ^= 1;
             ++total_it;
@@ -536,8 +563,8 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
                     Real Ad = 0;
 #pragma unroll
                     for (int t = 0; t < 4; ++t) Ad = fma(w[t], di - dj[t], Ad);
-                    rh[q] -= Ad;
-                    xh[q] += d[q];
+                    RH(q) -= Ad;
+                    XH(q) += d[q];
                 } else {
                     Real ah = 0, al = 0;
 #pragma unroll
@@ -549,10 +576,15 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
                         pl = fma(w[t], sl, pl);
                         df_add(ah, al, ph, pl);
                     }
-                    df_add(rh[q], rl[q], -ah, -al);
-                    df_add(xh[q], xl[q], d[q], Real(0));
+                    Real rh = RH(q), rl = RL(q), xh = XH(q), xl = XL(q);
+                    df_add(rh, rl, -ah, -al);
+                    df_add(xh, xl, d[q], Real(0));
+                    RH(q) = rh;
+                    RL(q) = rl;
+                    XH(q) = xh;
+                    XL(q) = xl;
                 }
-                rr_out += rh[q] * rh[q];
+                rr_out += RH(q) * RH(q);
             }
         block_sum<T>(rr_out, red_buf[parity]);
         parity ^= 1;
@@ -573,8 +605,8 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
 #pragma unroll
     for (int q = 0; q < NPT; ++q)
         if (((slot[q] >> 27) & 1)) {
-            if constexpr (sizeof(Real) == 8) xs[(slot[q] & 0x1fff)] = (double)xh[q];
-            else xs[(slot[q] & 0x1fff)] = make_float2((float)xh[q], (float)xl[q]);
+            if constexpr (sizeof(Real) == 8) xs[(slot[q] & 0x1fff)] = (double)XH(q);
+            else xs[(slot[q] & 0x1fff)] = make_float2((float)XH(q), (float)XL(q));
         }
     __syncthreads();
     if (tid < 32) {   // one warp gathers and reduces the misfit (no block-wide FP64 work)
@@ -892,7 +924,7 @@ fem_eval_persistent(const FemArgs* groups, const int* offsets, int n_groups, int
 
 template <typename Real, int N, int T>
 cudaError_t launch_one(const FemArgs& a, cudaStream_t st) {
-    const size_t smem = sizeof(Real) * (size_t)arena_size(N);
+    const size_t smem = sizeof(Real) * (size_t)solve_smem_reals(N, T);
     auto kern = fem_eval_kernel<Real, N, T>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -904,7 +936,7 @@ cudaError_t launch_one(const FemArgs& a, cudaStream_t st) {
 template <typename Real, int N, int T>
 cudaError_t launch_persistent(const FemArgs* groups, const int* offsets, int n_groups, int total, int* counter,
                               cudaStream_t st) {
-    const size_t smem = sizeof(Real) * (size_t)arena_size(N);
+    const size_t smem = sizeof(Real) * (size_t)solve_smem_reals(N, T);
     auto kern = fem_eval_persistent<Real, N, T>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
