@@ -209,6 +209,32 @@ __device__ __forceinline__ void restrict_red(const Lv<Real>& F, Real* rhs_c) {
     }
 }
 
+// the same restriction from red residuals stored in res (fine level of the on-chip solve, where
+// each thread computes the residuals of its own red nodes first)
+template <typename Real, int NC, int T>
+__device__ __forceinline__ void restrict_gather(const Real* res, Real* rhs_c) {
+    constexpr int MC = NC - 1, SC = fem_row_stride(NC), SF = fem_row_stride(2 * NC);
+    for (int idx = threadIdx.x; idx < MC * MC; idx += T) {
+        const int J = idx / MC + 1, I = idx - (J - 1) * MC + 1;
+        const int f = (2 * J) * SF + 2 * I;
+        rhs_c[J * SC + I] = res[f] + Real(0.5) * (res[f + SF + 1] + res[f - SF - 1]);
+    }
+}
+
+// zero the boundary rings of e, res, rhs on every level from NL down (interior values are always
+// written before they are read; the rings must read as zero)
+template <typename Real, int N, int NL, int T>
+__device__ __forceinline__ void zero_rings(Real* arena) {
+    constexpr int S = fem_row_stride(NL);
+    const Lv<Real> L = level_ptrs<Real, N, NL>(arena);
+    for (int k = threadIdx.x; k < 4 * NL; k += T) {   // rows 0 and NL, then columns 0 and NL
+        const int n = k <= NL ? k : k <= 2 * NL + 1 ? NL * S + (k - NL - 1)
+                                                     : (1 + ((k - 2 * NL - 2) >> 1)) * S + (((k - 2 * NL - 2) & 1) ? NL : 0);
+        L.e[n] = L.res[n] = L.rhs[n] = Real(0);
+    }
+    if constexpr (NL > 2) zero_rings<Real, N, NL / 2, T>(arena);
+}
+
 // off-diagonal sum at black node n = (i, j) with its red neighbours read as e + P e_c (P1
 // interpolation of the coarse correction ec). c0 = (j/2) SC + i/2 (integer halves) is the
 // coarse node at or below-left of n; jeven selects which neighbours coincide with coarse nodes.
@@ -238,6 +264,86 @@ __device__ __forceinline__ void black_prolong(const Lv<Real>& L, const Real* ec)
     }
 }
 
+// ---- exact solve on the coarsest level kept ------------------------------------------------
+// The multigrid recursion stops at level direct_level(N) (1/4 for N >= 16; below that the
+// setup costs more than the cycles it saves): there the Galerkin operator (the same 5-point stencil,
+// m = (NL - 1)^2 = 9 unknowns) is inverted once per particle and applied as a dense
+// matrix-vector product, replacing the cycles of the levels below it. (An exact solve one level
+// higher, m = 49, lowers the iteration count by about 8 % but its m^3 setup costs more than that.)
+// The FP64 path keeps the full cycle: its Gauss-Jordan setup would run on the FP64 pipe, which
+// on this part costs more than the cycles it saves.
+template <typename Real>
+__host__ __device__ constexpr int direct_level(int N) {
+    return sizeof(Real) == 8 ? 0 : (N >= 16 ? 4 : 0);
+}
+template <typename Real>
+__host__ __device__ constexpr int dense_reals(int N) {
+    return direct_level<Real>(N) ? padded((direct_level<Real>(N) - 1) * (direct_level<Real>(N) - 1) *
+                                          ((direct_level<Real>(N) - 1) * (direct_level<Real>(N) - 1) + 4))
+                                 : 0;
+}
+
+// Ainv [m][m] := A^{-1} by in-place Gauss-Jordan elimination without pivoting (A is symmetric
+// positive definite). Step k turns row k into row k / a_kk, column k into -column k / a_kk, the
+// pivot into 1 / a_kk and every other entry into a_uv - a_uk a_kv / a_kk; the old row and column
+// k are read from a buffer that step k - 1 filled, so one barrier per step suffices.
+// Ainv is followed by that buffer: [2][row | column], 4m Reals.
+template <typename Real, int NL, int T>
+__device__ void dense_setup(const Lv<Real>& L, Real* Ainv) {
+    constexpr int MM = NL - 1, m = MM * MM, S = fem_row_stride(NL);
+    Real* buf = Ainv + m * m;
+    for (int idx = threadIdx.x; idx < m * m; idx += T) {
+        const int u = idx / m, v = idx - u * m;
+        const int ui = u % MM, uj = u / MM, vi = v % MM, vj = v / MM;
+        const int n = (uj + 1) * S + ui + 1;
+        Real val = 0;
+        if (u == v) val = L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S];
+        else if (uj == vj && vi == ui + 1) val = -L.aE[n];
+        else if (uj == vj && vi == ui - 1) val = -L.aE[n - 1];
+        else if (ui == vi && vj == uj + 1) val = -L.aN[n];
+        else if (ui == vi && vj == uj - 1) val = -L.aN[n - S];
+        Ainv[idx] = val;
+        if (u == 0) buf[v] = val;
+        if (v == 0) buf[m + u] = val;
+    }
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        const Real* rowk = buf + (k & 1) * 2 * m;
+        const Real* colk = rowk + m;
+        Real* rown = buf + ((k + 1) & 1) * 2 * m;
+        Real* coln = rown + m;
+        const Real ip = Real(1) / rowk[k];
+        for (int idx = threadIdx.x; idx < m * m; idx += T) {
+            const int u = idx / m, v = idx - u * m;
+            Real val;
+            if (u == k) val = (v == k) ? ip : rowk[v] * ip;
+            else if (v == k) val = -colk[u] * ip;
+            else val = Ainv[idx] - colk[u] * rowk[v] * ip;
+            Ainv[idx] = val;
+            if (u == k + 1) rown[v] = val;
+            if (v == k + 1) coln[u] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// L.e = Ainv L.rhs on the interior nodes: 8 lanes per row, reduced by warp shuffles
+template <typename Real, int NL, int T>
+__device__ __forceinline__ void dense_solve(const Lv<Real>& L, const Real* Ainv) {
+    constexpr int MM = NL - 1, m = MM * MM, S = fem_row_stride(NL);
+    constexpr int W = (m * 8 + 31) / 32 * 32;   // whole warps: every lane takes part in the shuffles
+    for (int w = threadIdx.x; w < W; w += T) {
+        const int u = w >> 3, part = w & 7;
+        Real acc = 0;
+        if (u < m)
+            for (int v = part; v < m; v += 8) acc = fma(Ainv[u * m + v], L.rhs[(v / MM + 1) * S + v % MM + 1], acc);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (part == 0 && u < m) L.e[(u / MM + 1) * S + u % MM + 1] = acc;
+    }
+}
+
 // barrier between the phases of a V-cycle: the whole block, or only warp 0 on the small levels
 template <bool WARP>
 __device__ __forceinline__ void phase_sync() {
@@ -249,9 +355,12 @@ __device__ __forceinline__ void phase_sync() {
 // (<= 9 unknowns) run inside warp 0 only (T = 32, warp barriers); the caller's next block
 // barrier publishes the result.
 template <typename Real, int N, int NL, int T, bool WARP = false>
-__device__ void vcycle_coarse(Real* arena) {
-    if constexpr (!WARP && NL <= 4) {
-        if (threadIdx.x < 32) vcycle_coarse<Real, N, NL, 32, true>(arena);
+__device__ void vcycle_coarse(Real* arena, const Real* dinv) {
+    if constexpr (NL == direct_level<Real>(N)) {
+        dense_solve<Real, NL, T>(level_ptrs<Real, N, NL>(arena), dinv);
+        phase_sync<WARP>();
+    } else if constexpr (!WARP && NL <= 4) {
+        if (threadIdx.x < 32) vcycle_coarse<Real, N, NL, 32, true>(arena, dinv);
         __syncthreads();
         return;
     } else {
@@ -268,7 +377,7 @@ __device__ void vcycle_coarse(Real* arena) {
             phase_sync<WARP>();
             restrict_red<Real, NL / 2, T>(L, C.rhs);
             phase_sync<WARP>();
-            vcycle_coarse<Real, N, NL / 2, T, WARP>(arena);
+            vcycle_coarse<Real, N, NL / 2, T, WARP>(arena, dinv);
             black_prolong<Real, NL, T>(L, C.e);
             phase_sync<WARP>();
             smooth_color<Real, NL, T>(L, 0);
@@ -355,8 +464,12 @@ struct Fine {
 // fine-level slots per thread (half red, half black) of the on-chip solve
 __host__ __device__ constexpr int fine_slots(int N, int T) { return 2 * ((N * N / 2 + T - 1) / T); }
 // dynamic shared memory of the on-chip solve, in Reals: the level arena, then the refinement
-// state (x and r, each a hi/lo pair) of every thread's slots
-__host__ __device__ constexpr int solve_smem_reals(int N, int T) { return arena_size(N) + 4 * fine_slots(N, T) * T; }
+// state (x and r, each a hi/lo pair) of every thread's slots, then the dense inverse of the
+// coarsest level kept
+template <typename Real>
+__host__ __device__ constexpr int solve_smem_reals(int N, int T) {
+    return arena_size(N) + 4 * fine_slots(N, T) * T + dense_reals<Real>(N);
+}
 
 // ---- the kernel ----------------------------------------------------------------------
 // the whole solve of particle p of a.n, by one thread block (all threads call it)
@@ -391,17 +504,11 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
 
     // 2) stencil hierarchy
     setup_levels<Real, N, N, T>(arena, stage, true);
-    // zero every vector e, res, rhs of every level (their boundary rings must read as zero)
-    {
-        int off = 0;
-#pragma unroll
-        for (int NL = N; NL >= 2; NL >>= 1) {
-            const int z = lvl_size(NL);
-            for (int q = tid; q < 3 * z; q += T) arena[off + 3 * z + q] = Real(0);
-            off += 6 * z;
-        }
-    }
+    zero_rings<Real, N, N, T>(arena);
     __syncthreads();
+    Real* dinv = arena + arena_size(N) + 4 * NPT * T;
+    if constexpr (direct_level<Real>(N) != 0)
+        dense_setup<Real, direct_level<Real>(N), T>(level_ptrs<Real, N, direct_level<Real>(N)>(arena), dinv);
 
     // fine nodes owned by this thread, one packed int each: bits 0-12 node index n, 13-23 the
     // coarse node c under it ((j/2) SC + i/2), 24-25 (i & 1) + 2 (j & 1), 26 red, 27 valid.
@@ -480,9 +587,16 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
                     F.e[n] = (r[q] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
                 }
             __syncthreads();
-            restrict_red<Real, N / 2, T>(F, C1.rhs);
+#pragma unroll
+            for (int q = 0; q < NPH; ++q)   // red residuals: off-diagonal sums of the new black values
+                if (((slot[q] >> 27) & 1)) {
+                    const int n = (slot[q] & 0x1fff);
+                    F.res[n] = offsum<Real, S>(F.aE, F.aN, F.e, n);
+                }
             __syncthreads();
-            vcycle_coarse<Real, N, N / 2, T>(arena);
+            restrict_gather<Real, N / 2, T>(F.res, C1.rhs);
+            __syncthreads();
+            vcycle_coarse<Real, N, N / 2, T>(arena, dinv);
 #pragma unroll
             for (int q = NPH; q < NPT; ++q) {
                 z[q] = Real(0);
@@ -640,9 +754,9 @@ __device__ __forceinline__ Lv<Real> ptrs2(Real* garena, Real* sarena) {
 }
 
 template <typename Real, int N, int NL, int T>
-__device__ void vcycle2(Real* garena, Real* sarena) {
+__device__ void vcycle2(Real* garena, Real* sarena, const Real* dinv) {
     if constexpr (NL <= 64) {
-        vcycle_coarse<Real, 64, NL, T>(sarena);
+        vcycle_coarse<Real, 64, NL, T>(sarena, dinv);
     } else {
         Lv<Real> L = ptrs2<Real, N, NL>(garena, sarena);
         Lv<Real> C = ptrs2<Real, N, NL / 2>(garena, sarena);
@@ -652,7 +766,7 @@ __device__ void vcycle2(Real* garena, Real* sarena) {
         __syncthreads();
         restrict_red<Real, NL / 2, T>(L, C.rhs);
         __syncthreads();
-        vcycle2<Real, N, NL / 2, T>(garena, sarena);
+        vcycle2<Real, N, NL / 2, T>(garena, sarena, dinv);
         black_prolong<Real, NL, T>(L, C.e);
         __syncthreads();
         smooth_color<Real, NL, T>(L, 0);
@@ -715,6 +829,9 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
             off += 6 * z;
         }
     }
+    __syncthreads();
+    Real* dinv = sarena + arena_size(64);
+    dense_setup<Real, direct_level<Real>(64), T>(level_ptrs<Real, 64, direct_level<Real>(64)>(sarena), dinv);
     const Real h2 = Real(1) / (Real(N) * Real(N));
     for (int i = tid; i < NI; i += T) {
         XH[i] = XL[i] = RL[i] = Real(0);
@@ -754,7 +871,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
             __syncthreads();
             restrict_red<Real, N / 2, T>(F, C1.rhs);
             __syncthreads();
-            vcycle2<Real, N, N / 2, T>(arena, sarena);
+            vcycle2<Real, N, N / 2, T>(arena, sarena, dinv);
             for (int i = tid; i < NI; i += T) {
                 NODE_OF(i);
                 if ((ii + jj) & 1) {
@@ -924,7 +1041,7 @@ fem_eval_persistent(const FemArgs* groups, const int* offsets, int n_groups, int
 
 template <typename Real, int N, int T>
 cudaError_t launch_one(const FemArgs& a, cudaStream_t st) {
-    const size_t smem = sizeof(Real) * (size_t)solve_smem_reals(N, T);
+    const size_t smem = sizeof(Real) * (size_t)solve_smem_reals<Real>(N, T);
     auto kern = fem_eval_kernel<Real, N, T>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -936,7 +1053,7 @@ cudaError_t launch_one(const FemArgs& a, cudaStream_t st) {
 template <typename Real, int N, int T>
 cudaError_t launch_persistent(const FemArgs* groups, const int* offsets, int n_groups, int total, int* counter,
                               cudaStream_t st) {
-    const size_t smem = sizeof(Real) * (size_t)solve_smem_reals(N, T);
+    const size_t smem = sizeof(Real) * (size_t)solve_smem_reals<Real>(N, T);
     auto kern = fem_eval_persistent<Real, N, T>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -953,7 +1070,7 @@ cudaError_t launch_persistent(const FemArgs* groups, const int* offsets, int n_g
 
 template <int N, int T>
 cudaError_t launch_global(const FemArgs& a, float* scratch, size_t slice, int blocks, int* counter, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)arena_size(64);
+    const size_t smem = sizeof(float) * (size_t)(arena_size(64) + dense_reals<float>(64));
     cudaError_t e = cudaFuncSetAttribute(fem_eval_global<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fem_eval_global<N, T><<<blocks, T, smem, st>>>(a, scratch, slice, counter);
@@ -973,7 +1090,7 @@ int fem_global_blocks(int N) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = sizeof(float) * (size_t)arena_size(64);
+    const size_t smem = sizeof(float) * (size_t)(arena_size(64) + dense_reals<float>(64));
     if (N == 128) {
         cudaFuncSetAttribute(fem_eval_global<128, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_global<128, 1024>, 1024, smem);
