@@ -171,18 +171,6 @@ __device__ __forceinline__ bool colour_node(int k, int col, int& i, int& j) {
 //    the black nodes and the red nodes' pre-sweep values are never read: the black post-sweep
 //    reads its red neighbours as e + P e_c directly.
 template <typename Real, int NL, int T>
-__device__ __forceinline__ void smooth_first_red(const Lv<Real>& L) {
-    // from e = 0: red nodes get rhs/D; black nodes are written by the black sweep before any read
-    constexpr int S = fem_row_stride(NL);
-    for (int k = threadIdx.x; k < NL * NL / 2; k += T) {
-        int i, j;
-        if (!colour_node<NL>(k, 0, i, j)) continue;
-        const int n = j * S + i;
-        L.e[n] = L.rhs[n] * L.iD[n];
-    }
-}
-
-template <typename Real, int NL, int T>
 __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
     constexpr int S = fem_row_stride(NL);
     for (int k = threadIdx.x; k < NL * NL / 2; k += T) {
@@ -197,27 +185,34 @@ __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
 // the coincident fine node and 1/2 from its six neighbours along the mesh directions (+-x, +-y
 // and the (1,1) diagonal); of these only the coincident node and the two diagonal neighbours are
 // red, and their residuals are the off-diagonal sums of the black values.
+//
+// The coarse level's red pre-sweep from zero (e = rhs / D at red nodes) is folded in: it needs
+// nothing but the node's own rhs.
 template <typename Real, int NC, int T>
-__device__ __forceinline__ void restrict_red(const Lv<Real>& F, Real* rhs_c) {
+__device__ __forceinline__ void restrict_red(const Lv<Real>& F, const Lv<Real>& C) {
     constexpr int MC = NC - 1, SC = fem_row_stride(NC), SF = fem_row_stride(2 * NC);
     for (int idx = threadIdx.x; idx < MC * MC; idx += T) {
         const int J = idx / MC + 1, I = idx - (J - 1) * MC + 1;
-        const int f = (2 * J) * SF + 2 * I;
-        rhs_c[J * SC + I] = offsum<Real, SF>(F.aE, F.aN, F.e, f) +
-                            Real(0.5) * (offsum<Real, SF>(F.aE, F.aN, F.e, f + SF + 1) +
-                                         offsum<Real, SF>(F.aE, F.aN, F.e, f - SF - 1));
+        const int f = (2 * J) * SF + 2 * I, c = J * SC + I;
+        const Real v = offsum<Real, SF>(F.aE, F.aN, F.e, f) +
+                       Real(0.5) * (offsum<Real, SF>(F.aE, F.aN, F.e, f + SF + 1) +
+                                    offsum<Real, SF>(F.aE, F.aN, F.e, f - SF - 1));
+        C.rhs[c] = v;
+        if (((I + J) & 1) == 0) C.e[c] = v * C.iD[c];
     }
 }
 
 // the same restriction from red residuals stored in res (fine level of the on-chip solve, where
 // each thread computes the residuals of its own red nodes first)
 template <typename Real, int NC, int T>
-__device__ __forceinline__ void restrict_gather(const Real* res, Real* rhs_c) {
+__device__ __forceinline__ void restrict_gather(const Real* res, const Lv<Real>& C) {
     constexpr int MC = NC - 1, SC = fem_row_stride(NC), SF = fem_row_stride(2 * NC);
     for (int idx = threadIdx.x; idx < MC * MC; idx += T) {
         const int J = idx / MC + 1, I = idx - (J - 1) * MC + 1;
-        const int f = (2 * J) * SF + 2 * I;
-        rhs_c[J * SC + I] = res[f] + Real(0.5) * (res[f + SF + 1] + res[f - SF - 1]);
+        const int f = (2 * J) * SF + 2 * I, c = J * SC + I;
+        const Real v = res[f] + Real(0.5) * (res[f + SF + 1] + res[f - SF - 1]);
+        C.rhs[c] = v;
+        if (((I + J) & 1) == 0) C.e[c] = v * C.iD[c];
     }
 }
 
@@ -371,11 +366,9 @@ __device__ void vcycle_coarse(Real* arena, const Real* dinv) {
             phase_sync<WARP>();
         } else {
             Lv<Real> C = level_ptrs<Real, N, NL / 2>(arena);
-            smooth_first_red<Real, NL, T>(L);
+            smooth_color<Real, NL, T>(L, 1);   // red pre-sweep done by the restriction above
             phase_sync<WARP>();
-            smooth_color<Real, NL, T>(L, 1);
-            phase_sync<WARP>();
-            restrict_red<Real, NL / 2, T>(L, C.rhs);
+            restrict_red<Real, NL / 2, T>(L, C);
             phase_sync<WARP>();
             vcycle_coarse<Real, N, NL / 2, T, WARP>(arena, dinv);
             black_prolong<Real, NL, T>(L, C.e);
@@ -566,6 +559,9 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
             pv[q] = Real(0);
             rr0 += r[q] * r[q];
         }
+#pragma unroll
+        for (int q = 0; q < NPH; ++q)   // red pre-sweep of the first cycle (see the r update below)
+            if (((slot[q] >> 27) & 1)) F.e[(slot[q] & 0x1fff)] = r[q] * F.iD[(slot[q] & 0x1fff)];
         block_sum<T>(rr0, red_buf[parity]);
         parity ^= 1;
         if (!(rr0 > Real(0))) break;
@@ -573,13 +569,10 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
         Real rz = 0;
         for (int it = 0; it < a.max_inner; ++it) {
             // z = M^{-1} r: V(1,1) cycle with the fine rhs held in registers (red pre-sweep
-            // from zero, black pre-sweep, restriction of the red residuals, coarse cycle, black
-            // post-sweep with the prolongation folded in, red post-sweep). The red post-sweep
-            // values are read by nothing but this thread, so they stay in registers.
-#pragma unroll
-            for (int q = 0; q < NPH; ++q)
-                if (((slot[q] >> 27) & 1)) F.e[(slot[q] & 0x1fff)] = r[q] * F.iD[(slot[q] & 0x1fff)];
-            __syncthreads();
+            // from zero, written where r was last updated; black pre-sweep, restriction of the
+            // red residuals, coarse cycle, black post-sweep with the prolongation folded in, red
+            // post-sweep). The red post-sweep values are read by nothing but this thread, so they
+            // stay in registers.
 #pragma unroll
             for (int q = NPH; q < NPT; ++q)
                 if (((slot[q] >> 27) & 1)) {
@@ -594,7 +587,7 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
                     F.res[n] = offsum<Real, S>(F.aE, F.aN, F.e, n);
                 }
             __syncthreads();
-            restrict_gather<Real, N / 2, T>(F.res, C1.rhs);
+            restrict_gather<Real, N / 2, T>(F.res, C1);
             __syncthreads();
             vcycle_coarse<Real, N, N / 2, T>(arena, dinv);
 #pragma unroll
@@ -652,6 +645,9 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
                 r[q] = fma(-alpha, qv[q], r[q]);
                 rr += r[q] * r[q];
             }
+#pragma unroll
+            for (int q = 0; q < NPH; ++q)   // red pre-sweep of the next cycle (nothing reads F.e now)
+                if (((slot[q] >> 27) & 1)) F.e[(slot[q] & 0x1fff)] = r[q] * F.iD[(slot[q] & 0x1fff)];
             block_sum<T>(rr, red_buf[parity]);
             parity ^= 1;
             ++total_it;
@@ -760,11 +756,9 @@ __device__ void vcycle2(Real* garena, Real* sarena, const Real* dinv) {
     } else {
         Lv<Real> L = ptrs2<Real, N, NL>(garena, sarena);
         Lv<Real> C = ptrs2<Real, N, NL / 2>(garena, sarena);
-        smooth_first_red<Real, NL, T>(L);
+        smooth_color<Real, NL, T>(L, 1);   // red pre-sweep done by the restriction above
         __syncthreads();
-        smooth_color<Real, NL, T>(L, 1);
-        __syncthreads();
-        restrict_red<Real, NL / 2, T>(L, C.rhs);
+        restrict_red<Real, NL / 2, T>(L, C);
         __syncthreads();
         vcycle2<Real, N, NL / 2, T>(garena, sarena, dinv);
         black_prolong<Real, NL, T>(L, C.e);
@@ -869,7 +863,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
                 if ((ii + jj) & 1) F.e[n] = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
             }
             __syncthreads();
-            restrict_red<Real, N / 2, T>(F, C1.rhs);
+            restrict_red<Real, N / 2, T>(F, C1);
             __syncthreads();
             vcycle2<Real, N, N / 2, T>(arena, sarena, dinv);
             for (int i = tid; i < NI; i += T) {
