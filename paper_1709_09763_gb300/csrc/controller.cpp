@@ -36,7 +36,7 @@ struct Sampler {
     // compacted survivors of stage 1, observations of exact solves (training pairs)
     double *G_buf = nullptr, *ps_c = nullptr, *ps_f = nullptr, *psp_c = nullptr, *psp_f = nullptr;
     double *theta_s = nullptr, *phi_cs = nullptr, *phi_fs = nullptr;
-    int *surv_idx = nullptr, *n_surv = nullptr;
+    int *surv_idx = nullptr, *n_surv = nullptr, *da_pass = nullptr;
     long long pairs_new[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long da_proposals = 0, da_pass1 = 0;
     // host-side state
@@ -72,13 +72,16 @@ int Handle::alloc_sampler() {
     A((void**)&smp->mom, (size_t)2 * K * 8);
     A((void**)&smp->n_acc, 16);   // [0] accepted moves (u64), [8] non-converged solves (u32)
     A((void**)&smp->inc.state, sizeof(IncState));
-    A((void**)&smp->inc.partials, (size_t)kIncMaxBlocks * 4 * 8);
+    A((void**)&smp->inc.partials, kIncPartials * 8);
+    A((void**)&smp->inc.bar, 2 * sizeof(unsigned));
+    smp->inc.err = reinterpret_cast<int*>(smp->inc.bar + 1);
     if (opts.surrogate) {
         A((void**)&smp->G_buf, (size_t)J * n_obs * 8);
         for (double** p : {&smp->ps_c, &smp->ps_f, &smp->psp_c, &smp->psp_f, &smp->phi_cs, &smp->phi_fs})
             A((void**)p, (size_t)J * 8);
         A((void**)&smp->theta_s, JK * 8);
         A((void**)&smp->surv_idx, (size_t)J * 4);
+        A((void**)&smp->da_pass, (size_t)J * 4);
         A((void**)&smp->n_surv, 4);
     }
     if (e == cudaSuccess) e = cudaMemset(smp->n_acc, 0, 16);
@@ -92,9 +95,10 @@ void Handle::free_sampler() {
                     (void*)smp->phi_f, (void*)smp->phi_cp, (void*)smp->phi_fp, (void*)smp->phi_t0,
                     (void*)smp->phi_t1, (void*)smp->a, (void*)smp->cdf, (void*)smp->scal, (void*)smp->mom,
                     (void*)smp->anc, (void*)smp->iters, (void*)smp->n_acc, (void*)smp->inc.state,
-                    (void*)smp->inc.partials, (void*)smp->G_buf, (void*)smp->ps_c, (void*)smp->ps_f,
+                    (void*)smp->inc.partials, (void*)smp->inc.bar, (void*)smp->G_buf, (void*)smp->ps_c, (void*)smp->ps_f,
                     (void*)smp->psp_c, (void*)smp->psp_f, (void*)smp->theta_s, (void*)smp->phi_cs,
-                    (void*)smp->phi_fs, (void*)smp->surv_idx, (void*)smp->n_surv})
+                    (void*)smp->phi_fs, (void*)smp->surv_idx, (void*)smp->n_surv,
+                    (void*)smp->da_pass})
         cudaFree(p);
     delete smp;
     smp = nullptr;
@@ -223,18 +227,19 @@ int Handle::check_iters(int n) {
     return SMC_OK;
 }
 
-// adaptive increment on a[0..n): Eq. Eq_cv_opt; leaves IncState on the device and a copy in st
+// adaptive increment on a[0..n): Eq. Eq_cv_opt, one cooperative launch; leaves IncState on the
+// device and a copy in st
 int Handle::increment(const double* a, int n, double dmax, IncState& st) {
     Sampler* S = smp;
-    CK(inc_start(a, n, dmax, opts.tau_star, opts.eps, S->inc, stream));
-    for (int rounds = 0; rounds * kIncChunk < kIncMaxIter + kIncChunk; ++rounds) {
-        CK(inc_iterate(a, n, kIncChunk, S->inc, stream));
-        CK(cudaMemcpyAsync(&st, S->inc.state, sizeof(IncState), cudaMemcpyDeviceToHost, stream));
-        CK(cudaStreamSynchronize(stream));
-        if (st.done == -1) return fail(SMC_ESINGULAR, "non-finite incremental weights (numerical singularity)");
-        if (st.done) return SMC_OK;
-    }
-    return fail(SMC_ENOCONV, "increment search did not finish");
+    CK(inc_search_launch(a, n, dmax, opts.tau_star, opts.eps, kIncMaxIter, S->inc, stream));
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, S->inc.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(&st, S->inc.state, sizeof(IncState), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (err) return fail(SMC_ETIMEOUT, "increment search: a block gave up waiting at the grid barrier");
+    if (st.done == -1) return fail(SMC_ESINGULAR, "non-finite incremental weights (numerical singularity)");
+    if (st.done != 1) return fail(SMC_ENOCONV, "increment search did not finish");
+    return SMC_OK;
 }
 
 int Handle::reweight_resample(const double* a, double dmax, bool carry_fine, IncState& st) {
@@ -293,9 +298,8 @@ int Handle::mcmc_da(int level, double zeta, double& rate) {
         CK(normals_launch(S->theta_p, J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
         RC(mlp_predict(level, J, S->theta_p, nullptr, S->psp_c));
         if (br) RC(mlp_predict(level + 1, J, S->theta_p, nullptr, S->psp_f));
-        CK(cudaMemsetAsync(S->n_surv, 0, 4, stream));
         CK(da_stage1_launch(J, K, S->beta, zeta, ev, opts.seed, S->ps_c, S->ps_f, S->psp_c, S->psp_f, S->theta_p,
-                            S->surv_idx, S->n_surv, S->theta_s, stream));
+                            S->da_pass, S->surv_idx, S->n_surv, S->theta_s, stream));
         int ns = 0;
         CK(cudaMemcpyAsync(&ns, S->n_surv, 4, cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));

@@ -15,27 +15,33 @@ constexpr uint32_t kPurposePcnU = 3;
 constexpr uint32_t kPurposeResample = 4;
 constexpr uint32_t kPurposeDaU = 5;
 
-constexpr int kIncMaxBlocks = 64;     // partial-sum blocks of the increment search
+constexpr int kIncMaxBlocks = 128;    // blocks of the increment search (one cooperative launch)
+constexpr int kIncThreads = 64;       // two warps a block: short FP64 reductions
+constexpr int kIncSums = 6;           // sums per block and decision
 constexpr int kIncMaxIter = 200;      // cap on decisions of one search
-constexpr int kIncChunk = 10;         // decisions queued between host checks
 
 // state of one adaptive-increment search, resident in device memory
 struct IncState {
     double amin, dmin, dmax, target, tau;
-    double lo, hi, x;
+    double lo, hi, x;                 // bracket and current point
+    double glo, ghi;                  // g at the bracket ends
     int phase, iter, done, pad;
     // results
     double delta, log_mean_w, cv, S1;
 };
 
 struct IncWork {
-    IncState* state = nullptr;   // device
-    double* partials = nullptr;  // device [kIncMaxBlocks * 4]
+    IncState* state = nullptr;   // device: the result
+    double* partials = nullptr;  // device [kIncMaxBlocks] minima, then [2][kIncMaxBlocks][kIncSums] sums
+    unsigned* bar = nullptr;     // device: grid-barrier counter, then (as int) the error flag
+    int* err = nullptr;          // = (int*)(bar + 1): a block gave up waiting at the grid barrier
 };
+constexpr size_t kIncPartials = (size_t)kIncMaxBlocks * (1 + 2 * kIncSums);
 
 int inc_blocks(int n);
-cudaError_t inc_start(const double* a, int n, double dmax, double tau, double eps, IncWork& w, cudaStream_t st);
-cudaError_t inc_iterate(const double* a, int n, int iters, IncWork& w, cudaStream_t st);
+// the whole search on a[0..n) into *w.state (w.err set if a grid barrier timed out)
+cudaError_t inc_search_launch(const double* a, int n, double dmax, double tau, double eps, int max_iter, IncWork& w,
+                              cudaStream_t st);
 
 cudaError_t normals_launch(double* out, int J, int K, uint32_t event, uint32_t purpose, uint64_t seed,
                            const double* base, double c0, double c1, cudaStream_t st);
@@ -54,7 +60,7 @@ cudaError_t pcn_accept_launch(int n, int K, double beta, double zeta, uint32_t e
                               const double* phi_fp, unsigned long long* n_acc, cudaStream_t st);
 cudaError_t da_stage1_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, const double* ps_c,
                              const double* ps_f, const double* psp_c, const double* psp_f, const double* theta_p,
-                             int* surv_idx, int* n_surv, double* theta_s, cudaStream_t st);
+                             int* pass, int* surv_idx, int* n_surv, double* theta_s, cudaStream_t st);
 cudaError_t da_stage2_launch(int ns, int K, double beta, double zeta, uint32_t event, uint64_t seed, const int* surv_idx,
                              const double* theta_s, const double* phi_cs, const double* phi_fs, double* theta,
                              double* phi_c, double* phi_f, double* ps_c, double* ps_f, const double* psp_c,

@@ -122,105 +122,246 @@ __device__ __forceinline__ void block_reduce_sum(double (&v)[NV], double* sh /*[
 }
 
 // ---- adaptive increment (Eq. Eq_cv_opt) --------------------------------------------------
-__global__ void inc_min_kernel(const double* a, int n, double* pmin) {
-    __shared__ double sh[32];
+// One cooperative launch runs the whole search. Every block sums its slice of the particles, the
+// blocks meet at a grid barrier, and then every block reduces all partial sums in the same fixed
+// order and takes the same decision on its own copy of the search state, so one barrier per
+// decision suffices. Partial sums are double-buffered by decision parity: a block can be at most
+// one decision ahead of the slowest one.
+//
+// The search solves g(x) = log(1 + cv(x)^2) - log(1 + tau^2) = 0 for the increment x, where
+// cv(x) is the coefficient of variation of w_j = exp(-x a~_j), a~_j = a_j - min a (population
+// moments: 1 + cv^2 = n S2 / S1^2 with S1 = sum w, S2 = sum w^2); g is non-decreasing in x.
+// Decision 1 evaluates both ends of [dmin, dmax] (dmin = min(eps, dmax)): g(dmax) <= 0 takes
+// the whole remaining step, g(dmin) >= 0 the smallest one (the constrained minimiser of
+// (cv - tau)^2, Eqs. Eq_ESS_opt, Eq_cv_opt). Otherwise the root is bracketed and found in
+// t = log x (the increment spans decades) from a regula-falsi start by Halley steps, kept inside
+// the bracket (Newton, then bisection in t, as fallbacks). Only g itself needs FP64: the step is
+// a correction, computed in FP32 (FP64 instructions are expensive on this part).
+//
+// Sums at a point x: S1, S2, T1 = sum a~ w, T2 = sum a~ w^2, U1 = sum a~^2 w, U2 = sum a~^2 w^2;
+// dS1/dx = -T1, dS2/dx = -2 T2, d2S1/dx2 = U1, d2S2/dx2 = 4 U2.
+
+// state after the minimum of the potentials is known
+__device__ void inc_init(IncState& st, double amin, double dmax, double tau, double eps) {
+    st.amin = amin;
+    st.dmax = dmax;
+    st.dmin = fmin(eps, dmax);
+    st.target = log1p(tau * tau);   // log(1 + tau^2)
+    st.tau = tau;
+    st.x = dmax;
+    st.phase = 0;
+    st.iter = 0;
+    st.done = (amin == INFINITY || !(amin == amin)) ? -1 : 0;   // -1: empty or NaN potentials
+}
+
+__device__ void inc_finish(IncState& st, double x, double S1, double ratio, int n) {
+    st.delta = x;
+    st.S1 = S1;
+    st.log_mean_w = -x * st.amin + log(S1 / (double)n);
+    const double c2 = ratio - 1.0;
+    st.cv = c2 > 0.0 ? sqrt(c2) : 0.0;
+    st.done = 1;
+}
+
+// one decision from the block-reduced sums v[kIncSums]. Decision 1: S1, S2 at dmax, S1, S2 at
+// dmin, then sum a~ and sum a~^2 (unweighted, for the starting point). Later decisions: the six
+// sums at x.
+__device__ void inc_decide(IncState& st, const double* v, int n, int max_iter) {
+    st.iter += 1;
+    if (st.phase == 0) {
+        const double r_hi = (double)n * v[1] / (v[0] * v[0]);
+        const double g_hi = log(r_hi) - st.target;
+        if (!(g_hi > 0.0)) {                                   // cv(dmax) <= tau (also: all a equal)
+            inc_finish(st, st.dmax, v[0], r_hi, n);
+            return;
+        }
+        const double r_lo = (double)n * v[3] / (v[2] * v[2]);
+        const double g_lo = log(r_lo) - st.target;
+        if (g_lo >= 0.0 || st.dmin >= st.dmax) {
+            inc_finish(st, st.dmin, v[2], r_lo, n);
+            return;
+        }
+        st.phase = 1;
+        st.lo = st.dmin;
+        st.hi = st.dmax;
+        st.glo = g_lo;
+        st.ghi = g_hi;
+        // small increments: w ~ 1 - x a~, so cv(x)^2 ~ x^2 var(a~) and the root is near tau / sd(a~)
+        const double mean = v[4] / n, var = v[5] / n - mean * mean;
+        double x0 = var > 0.0 ? st.tau / sqrt(var) : 0.0;
+        if (!(x0 > st.lo && x0 < st.hi)) {
+            const double tlo = log(st.lo), thi = log(st.hi);
+            x0 = exp(tlo + (thi - tlo) * (-g_lo / (g_hi - g_lo)));   // regula falsi in t
+            if (!(x0 > st.lo && x0 < st.hi)) x0 = sqrt(st.lo * st.hi);
+        }
+        st.x = x0;
+        return;
+    }
+    const double x = st.x, S1 = v[0], S2 = v[1];
+    const double ratio = (double)n * S2 / (S1 * S1);
+    const double g = log(ratio) - st.target;
+    if (g > 0.0) {
+        st.hi = x;
+        st.ghi = g;
+    } else {
+        st.lo = x;
+        st.glo = g;
+    }
+    if (g == 0.0 || st.hi <= st.lo * (1.0 + 4e-16) || st.iter >= max_iter) {
+        inc_finish(st, x, S1, ratio, n);
+        return;
+    }
+    // derivatives in t = log x, in FP32
+    const float fx = (float)x;
+    const float m1 = (float)v[2] / (float)S1, m2 = (float)v[3] / (float)S2;     // T1/S1, T2/S2
+    const float q1 = (float)v[4] / (float)S1, q2 = (float)v[5] / (float)S2;     // U1/S1, U2/S2
+    const float gp = 2.f * (m1 - m2);                                          // dg/dx
+    const float gpp = 4.f * (q2 - m2 * m2) - 2.f * (q1 - m1 * m1);             // d2g/dx2
+    const float G = (float)g, Gp = fx * gp, Gpp = fx * gp + fx * fx * gpp;
+    const double tlo = log(st.lo), thi = log(st.hi), t = log(x);
+    bool local = true;
+    float dt = -2.f * G * Gp / (2.f * Gp * Gp - G * Gpp);                      // Halley
+    if (!(t + dt > tlo && t + dt < thi)) dt = -G / Gp;                          // Newton
+    double tn = t + (double)dt;
+    if (!(tn > tlo && tn < thi)) {                                              // secant on the bracket
+        local = false;
+        tn = tlo + (thi - tlo) * (-st.glo / (st.ghi - st.glo));
+        if (!(tn > tlo && tn < thi)) tn = 0.5 * (tlo + thi);
+    }
+    const double xn = exp(tn);
+    if (local && fabs(tn - t) <= 1e-7) {
+        // the step lands within rounding of the root (the next Halley correction would be of
+        // order dt^3): finish at xn, its sums extrapolated to second order in xn - x (the
+        // neglected terms are of order ((xn - x) a~)^3)
+        const double d = xn - x;
+        const double S1n = S1 - v[2] * d + 0.5 * v[4] * d * d;
+        const double S2n = S2 - 2.0 * v[3] * d + 2.0 * v[5] * d * d;
+        inc_finish(st, xn, S1n, (double)n * S2n / (S1n * S1n), n);
+        return;
+    }
+    st.x = xn;
+}
+
+// grid barrier on a counter zeroed before the launch (thread 0 of each block; the caller
+// synchronises the block around it). Bounded: after about a second of waiting (or once another
+// block has given up) it raises *err and returns false.
+__device__ bool grid_barrier(unsigned* bar, int* err, unsigned nblocks, unsigned& generation) {
+    __threadfence();
+    const unsigned target = (++generation) * nblocks;
+    atomicAdd(bar, 1u);
+    const long long t0 = clock64();
+    while (true) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+        if (v >= target) break;
+        if (*(volatile int*)err) return false;
+        if (clock64() - t0 > 2000000000LL) {
+            atomicExch(err, 1);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    return true;
+}
+
+// sum of v[kIncSums] over the block into thread 0 (warp shuffles, then warp 0 over the warps)
+__device__ __forceinline__ void inc_block_sum(double (&v)[kIncSums], double* sh /*[kIncSums][32]*/) {
+#pragma unroll
+    for (int i = 0; i < kIncSums; ++i)
+        for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+    constexpr int nw = kIncThreads / 32;
+    if (nw > 1) {
+        if ((threadIdx.x & 31) == 0 && threadIdx.x > 0)
+#pragma unroll
+            for (int i = 0; i < kIncSums; ++i) sh[i * 32 + (threadIdx.x >> 5)] = v[i];
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int k = 1; k < nw; ++k)
+#pragma unroll
+                for (int i = 0; i < kIncSums; ++i) v[i] += sh[i * 32 + k];
+    }
+}
+
+__global__ void __launch_bounds__(kIncThreads) inc_search_kernel(const double* a, int n, double dmax, double tau,
+                                                                 double eps, int max_iter, IncWork w) {
+    __shared__ double sh[kIncSums * 32];
+    __shared__ IncState st;
+    __shared__ int ok_s;
+    const unsigned nb = gridDim.x;
+    const int lane = threadIdx.x & 31;
+    unsigned generation = 0;
+    // minimum of the potentials (the weights are formed relative to it)
     double m = INFINITY;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) m = fmin(m, a[j]);
     for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    if (lane == 0) sh[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double r = INFINITY;
-        for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) r = fmin(r, sh[k]);
-        pmin[blockIdx.x] = r;
+        for (int k = 1; k < kIncThreads / 32; ++k) m = fmin(m, sh[k]);
+        w.partials[blockIdx.x] = m;
+        ok_s = grid_barrier(w.bar, w.err, nb, generation);
     }
-}
-
-__global__ void inc_init_kernel(const double* pmin, int nblk, IncState* st, double dmax, double tau, double eps) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double m = INFINITY;
-    for (int k = 0; k < nblk; ++k) m = fmin(m, pmin[k]);
-    st->amin = m;
-    st->dmax = dmax;
-    st->dmin = fmin(eps, dmax);
-    st->target = log1p(tau * tau);   // log(1 + tau^2)
-    st->tau = tau;
-    st->x = dmax;                     // first test: the whole remaining step
-    st->phase = 0;
-    st->iter = 0;
-    st->done = (m == INFINITY || !(m == m)) ? -1 : 0;   // -1: empty or NaN potentials
-}
-
-// sums at x = st->x over w_j = exp(-x (a_j - amin)): S1, S2, T1 = sum a~ w, T2 = sum a~ w^2
-__global__ void inc_eval_kernel(const double* a, int n, const IncState* st, double* partials) {
-    __shared__ double sh[4 * 32];
-    if (st->done) return;
-    const double x = st->x, amin = st->amin;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const double at = a[j] - amin;
-        const double w = exp(-x * at);
-        const double w2 = w * w;
-        v[0] += w;
-        v[1] += w2;
-        v[2] += at * w;
-        v[3] += at * w2;
+    __syncthreads();
+    if (!ok_s) return;
+    if (threadIdx.x < 32) {   // warp 0: minimum over the blocks
+        double mm = INFINITY;
+        for (unsigned k = lane; k < nb; k += 32) mm = fmin(mm, __ldcg(&w.partials[k]));
+        for (int off = 16; off > 0; off >>= 1) mm = fmin(mm, __shfl_xor_sync(0xffffffffu, mm, off));
+        if (lane == 0) inc_init(st, mm, dmax, tau, eps);
     }
-    block_reduce_sum<4>(v, sh);
-    if (threadIdx.x == 0)
+    __syncthreads();
+    for (int dec = 0; st.done == 0; ++dec) {
+        double* part = w.partials + kIncMaxBlocks + (dec & 1) * kIncSums * kIncMaxBlocks;
+        const double amin = st.amin;
+        double v[kIncSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (st.phase == 0) {   // both ends of the interval
+            const double xh = st.dmax, xl = st.dmin;
+            for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+                const double at = a[j] - amin;
+                const double wh = exp(-xh * at), wl = exp(-xl * at);
+                v[0] += wh;
+                v[1] += wh * wh;
+                v[2] += wl;
+                v[3] += wl * wl;
+                v[4] += at;
+                v[5] += at * at;
+            }
+        } else {
+            const double x = st.x;
+            for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+                const double at = a[j] - amin;
+                const double wj = exp(-x * at);
+                const double w2 = wj * wj;
+                v[0] += wj;
+                v[1] += w2;
+                v[2] += at * wj;
+                v[3] += at * w2;
+                v[4] += at * at * wj;
+                v[5] += at * at * w2;
+            }
+        }
+        inc_block_sum(v, sh);
+        if (threadIdx.x == 0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) partials[blockIdx.x * 4 + i] = v[i];
-}
-
-// one decision of the search: boundary tests first, then Newton steps on
-// g(x) = log(1 + cv(x)^2) - log(1 + tau^2) in t = log x (the increment spans decades),
-// safeguarded by geometric bisection of the bracket [lo, hi] (lo >= eps > 0)
-__global__ void inc_decide_kernel(const double* partials, int nblk, IncState* st, int n, int max_iter) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (st->done) return;
-    double S1 = 0, S2 = 0, T1 = 0, T2 = 0;
-    for (int k = 0; k < nblk; ++k) {
-        S1 += partials[4 * k];
-        S2 += partials[4 * k + 1];
-        T1 += partials[4 * k + 2];
-        T2 += partials[4 * k + 3];
-    }
-    const double x = st->x;
-    const double ratio = (double)n * S2 / (S1 * S1);      // 1 + cv^2
-    const double g = log(ratio) - st->target;
-    st->iter += 1;
-    bool finish = false;
-    if (st->phase == 0) {                    // x = dmax
-        if (!(g > 0.0)) finish = true;       // cv(dmax) <= tau (also: all a equal)
-        else {
-            st->phase = 1;
-            st->x = st->dmin;
-            st->hi = x;
+            for (int i = 0; i < kIncSums; ++i) part[blockIdx.x * kIncSums + i] = v[i];
+            ok_s = grid_barrier(w.bar, w.err, nb, generation);
         }
-    } else if (st->phase == 1) {             // x = dmin
-        if (g >= 0.0 || st->dmin >= st->dmax) finish = true;
-        else {
-            st->phase = 2;
-            st->lo = x;
-            st->x = sqrt(st->lo * st->hi);
+        __syncthreads();
+        if (!ok_s) return;
+        if (threadIdx.x < 32) {   // warp 0: sums over the blocks in a fixed order, then the decision
+            double t[kIncSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (unsigned k = lane; k < nb; k += 32)
+#pragma unroll
+                for (int i = 0; i < kIncSums; ++i) t[i] += __ldcg(&part[k * kIncSums + i]);
+#pragma unroll
+            for (int i = 0; i < kIncSums; ++i)
+                for (int off = 16; off > 0; off >>= 1) t[i] += __shfl_xor_sync(0xffffffffu, t[i], off);
+            if (lane == 0) inc_decide(st, t, n, max_iter);
         }
-    } else {
-        if (g > 0.0) st->hi = x; else st->lo = x;
-        const double lo = st->lo, hi = st->hi;
-        const double gp = 2.0 * (T1 / S1 - T2 / S2);       // dg/dx >= 0
-        double xn = x * exp(-g / (x * gp));                 // Newton step in log x
-        if (!(xn > lo && xn < hi)) xn = sqrt(lo * hi);
-        if (g == 0.0 || hi <= lo * (1.0 + 4e-16) || fabs(xn - x) <= 1e-15 * x || st->iter >= max_iter) finish = true;
-        else st->x = xn;
+        __syncthreads();
     }
-    if (finish) {
-        st->delta = x;
-        st->S1 = S1;
-        st->log_mean_w = -x * st->amin + log(S1 / (double)n);
-        const double c2 = ratio - 1.0;
-        st->cv = c2 > 0.0 ? sqrt(c2) : 0.0;
-        st->done = 1;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *w.state = st;
 }
 
 // ---- systematic resampling -----------------------------------------------------------------
@@ -361,10 +502,11 @@ __global__ void pcn_accept_kernel(int n, int K, double beta, double zeta, uint32
 
 // ---- delayed acceptance (Christen & Fox 2005) ----------------------------------------------------
 // stage 1 on the surrogate potentials: pass with probability min(1, exp(-(t~(theta') - t~(theta))));
-// survivors are compacted (index list, proposal rows) for the exact solve
-__global__ void da_stage1_kernel(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed,
+// the survivors are then compacted in particle order (deterministic: the exact solves, and the
+// training pairs they add to the surrogate's set, come in the same order on every run)
+__global__ void da_stage1_kernel(int n, double beta, double zeta, uint32_t event, uint64_t seed,
                                  const double* ps_c, const double* ps_f, const double* psp_c, const double* psp_f,
-                                 const double* theta_p, int* surv_idx, int* n_surv, double* theta_s) {
+                                 int* pass) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const uint4 x = philox(make_uint4(0u, (uint32_t)j, event, (uint32_t)kPurposeDaU), seed);
@@ -372,11 +514,49 @@ __global__ void da_stage1_kernel(int n, int K, double beta, double zeta, uint32_
     const bool br = zeta >= 0.0;
     const double t_old = target_potential(beta, zeta, ps_c[j], br ? ps_f[j] : 0.0);
     const double t_new = target_potential(beta, zeta, psp_c[j], br ? psp_f[j] : 0.0);
-    if (log(U) < -(t_new - t_old)) {
-        const int slot = atomicAdd(n_surv, 1);
-        surv_idx[slot] = j;
-        for (int k = 0; k < K; ++k) theta_s[(size_t)slot * K + k] = theta_p[(size_t)j * K + k];
+    pass[j] = log(U) < -(t_new - t_old);
+}
+
+// surv_idx = the indices j with pass[j] set, increasing; *n_surv = their number (one block of
+// 1024 threads: warp ballots, warp totals scanned by warp 0, a running base per chunk)
+__global__ void __launch_bounds__(1024) compact_kernel(const int* pass, int n, int* surv_idx, int* n_surv) {
+    __shared__ int warp_off[32];
+    __shared__ int base_s, total_s;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) base_s = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        const int j = base + tid;
+        const bool f = j < n && pass[j];
+        const unsigned ballot = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) warp_off[wid] = __popc(ballot);
+        __syncthreads();
+        if (wid == 0) {
+            const int c = warp_off[lane];
+            int incl = c;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += u;
+            }
+            warp_off[lane] = incl - c;          // exclusive offset of each warp
+            if (lane == 31) total_s = incl;
+        }
+        __syncthreads();
+        if (f) surv_idx[base_s + warp_off[wid] + __popc(ballot & ((1u << lane) - 1u))] = j;
+        __syncthreads();
+        if (tid == 0) base_s += total_s;
+        __syncthreads();
     }
+    if (tid == 0) *n_surv = base_s;
+}
+
+// rows dst[i] = src[idx[i]] (K doubles) for i < *n_rows (grid over nmax rows)
+__global__ void gather_rows_kernel(const int* idx, const int* n_rows, int nmax, int K, const double* src,
+                                   double* dst) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nmax * K) return;
+    const int i = (int)(t / K), k = (int)(t - (long long)i * K);
+    if (i < *n_rows) dst[t] = src[(size_t)idx[i] * K + k];
 }
 
 // stage 2 on the exact potentials of the survivors, corrected by the surrogate ratio:
@@ -470,26 +650,17 @@ cudaError_t uniforms_launch(double* out, int J, uint32_t event, uint32_t purpose
     return cudaGetLastError();
 }
 
-int inc_blocks(int n) { return std::min(kIncMaxBlocks, std::max(1, (n + 255) / 256)); }
+int inc_blocks(int n) { return std::min(kIncMaxBlocks, std::max(1, (n + 63) / 64)); }
 
-cudaError_t inc_start(const double* a, int n, double dmax, double tau, double eps, IncWork& w, cudaStream_t st) {
+cudaError_t inc_search_launch(const double* a, int n, double dmax, double tau, double eps, int max_iter, IncWork& w,
+                              cudaStream_t st) {
     const int nb = inc_blocks(n);
-    inc_min_kernel<<<nb, 256, 0, st>>>(a, n, w.partials);
+    cudaError_t e = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);   // barrier counter, error flag
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&a, (void*)&n, (void*)&dmax, (void*)&tau, (void*)&eps, (void*)&max_iter, (void*)&w};
+    e = cudaLaunchCooperativeKernel((const void*)inc_search_kernel, dim3(nb), dim3(kIncThreads), args, 0, st);
     count_launches(1);
-    inc_init_kernel<<<1, 32, 0, st>>>(w.partials, nb, w.state, dmax, tau, eps);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t inc_iterate(const double* a, int n, int iters, IncWork& w, cudaStream_t st) {
-    const int nb = inc_blocks(n);
-    for (int i = 0; i < iters; ++i) {
-        inc_eval_kernel<<<nb, 256, 0, st>>>(a, n, w.state, w.partials);
-        count_launches(1);
-        inc_decide_kernel<<<1, 32, 0, st>>>(w.partials, nb, w.state, n, kIncMaxIter);
-        count_launches(1);
-    }
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t resample_launch(const double* a, const double* w_in, int n, const IncState* state, double U,
@@ -537,11 +708,12 @@ cudaError_t pcn_accept_launch(int n, int K, double beta, double zeta, uint32_t e
 
 cudaError_t da_stage1_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, const double* ps_c,
                              const double* ps_f, const double* psp_c, const double* psp_f, const double* theta_p,
-                             int* surv_idx, int* n_surv, double* theta_s, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    da_stage1_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, K, beta, zeta, event, seed, ps_c, ps_f, psp_c, psp_f, theta_p,
-                                                       surv_idx, n_surv, theta_s);
-    count_launches(1);
+                             int* pass, int* surv_idx, int* n_surv, double* theta_s, cudaStream_t st) {
+    if (n <= 0) return cudaMemsetAsync(n_surv, 0, sizeof(int), st);
+    da_stage1_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, beta, zeta, event, seed, ps_c, ps_f, psp_c, psp_f, pass);
+    compact_kernel<<<1, 1024, 0, st>>>(pass, n, surv_idx, n_surv);
+    gather_rows_kernel<<<grid_for((long long)n * K, 256), 256, 0, st>>>(surv_idx, n_surv, n, K, theta_p, theta_s);
+    count_launches(3);
     return cudaGetLastError();
 }
 
