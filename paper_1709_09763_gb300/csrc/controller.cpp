@@ -133,11 +133,15 @@ int Handle::smp_eval(int level, int n, const double* theta, double* phi) {
 
 unsigned* Handle::bad_counter() { return reinterpret_cast<unsigned*>(reinterpret_cast<char*>(smp->n_acc) + 8); }
 
-// read the accept and non-convergence counters (one device-to-host copy and wait)
+// read the accept and non-convergence counters and the grid-barrier flag of the last resampling
+// (one wait)
 int Handle::read_counters(unsigned long long* acc) {
     unsigned char buf[16];
+    int rs_err = 0;
     CK(cudaMemcpyAsync(buf, smp->n_acc, 16, cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(&rs_err, smp->inc.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
+    if (rs_err) return fail(SMC_ETIMEOUT, "resampling: a block gave up waiting at the grid barrier");
     unsigned long long a;
     unsigned bad;
     std::memcpy(&a, buf, 8);
@@ -246,9 +250,9 @@ int Handle::reweight_resample(const double* a, double dmax, bool carry_fine, Inc
     Sampler* S = smp;
     RC(increment(a, S->J, dmax, st));
     S->log_z += st.log_mean_w;
-    CK(resample_launch(a, nullptr, S->J, S->inc.state, -1.0, (uint32_t)S->stage, opts.seed, S->cdf, S->anc, stream));
-    CK(gather_launch(S->anc, S->J, K, S->theta, S->theta_t, S->phi_c, S->phi_t0, carry_fine ? S->phi_f : nullptr,
-                     S->phi_t1, stream));
+    CK(resample_gather_launch(a, S->J, S->inc.state, (uint32_t)S->stage, opts.seed, K, S->theta, S->theta_t,
+                              S->phi_c, S->phi_t0, carry_fine ? S->phi_f : nullptr, S->phi_t1, S->cdf, S->anc,
+                              S->inc, stream));
     std::swap(S->theta, S->theta_t);
     std::swap(S->phi_c, S->phi_t0);
     if (carry_fine) std::swap(S->phi_f, S->phi_t1);

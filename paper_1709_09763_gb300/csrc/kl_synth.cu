@@ -30,12 +30,14 @@ __global__ void theta_split_kernel(const double* theta, int n, int K, int Kp, __
     const int blk = c / K, k = c - blk * K;
     float v = 0.0f;
     if (blk < 6) {
-        const double x = theta[(size_t)j * K + k];
-        const __nv_bfloat16 p1 = __float2bfloat16_rn((float)x);
-        const double r1 = x - (double)__bfloat162float(p1);
-        const __nv_bfloat16 p2 = __float2bfloat16_rn((float)r1);
-        const double r2 = r1 - (double)__bfloat162float(p2);
-        const __nv_bfloat16 p3 = __float2bfloat16_rn((float)r2);
+        // split of theta rounded to FP32 (24 bits, all that three BF16 pieces carry); each remainder
+        // is exact in FP32, so no FP64 arithmetic is needed
+        const float x = (float)theta[(size_t)j * K + k];
+        const __nv_bfloat16 p1 = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(p1);
+        const __nv_bfloat16 p2 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(p2);
+        const __nv_bfloat16 p3 = __float2bfloat16_rn(r2);
         // A' blocks: t1 t1 t2 t2 t1 t3
         const __nv_bfloat16 sel[6] = {p1, p1, p2, p2, p1, p3};
         out[t] = sel[blk];

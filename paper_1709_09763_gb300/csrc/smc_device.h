@@ -24,6 +24,7 @@ constexpr int kIncMaxIter = 200;      // cap on decisions of one search
 struct IncState {
     double amin, dmin, dmax, target, tau;
     double lo, hi, x;                 // bracket and current point
+    double tlo, thi, t;               // their logarithms
     double glo, ghi;                  // g at the bracket ends
     int phase, iter, done, pad;
     // results
@@ -49,6 +50,13 @@ cudaError_t uniforms_launch(double* out, int J, uint32_t event, uint32_t purpose
 // U >= 0: use it as the offset; U < 0: draw it from Philox (event, kPurposeResample)
 cudaError_t resample_launch(const double* a, const double* w_in, int n, const IncState* state, double U,
                             uint32_t event, uint64_t seed, double* cdf, int* anc, cudaStream_t st);
+// weights of the increment in *state, systematic resampling (U from Philox (event, kPurposeResample))
+// and the gather of theta rows and up to two potential caches, in one cooperative launch; uses
+// w's barrier and scratch (w.err set if a grid barrier timed out)
+cudaError_t resample_gather_launch(const double* a, int n, const IncState* state, uint32_t event, uint64_t seed,
+                                   int K, const double* th_in, double* th_out, const double* p0_in, double* p0_out,
+                                   const double* p1_in, double* p1_out, double* cdf, int* anc, IncWork& w,
+                                   cudaStream_t st);
 cudaError_t gather_launch(const int* anc, int n, int K, const double* th_in, double* th_out, const double* p0_in,
                           double* p0_out, const double* p1_in, double* p1_out, cudaStream_t st);
 cudaError_t lu_increment_launch(const double* phi_c, const double* phi_f, int n, double beta, double* a,

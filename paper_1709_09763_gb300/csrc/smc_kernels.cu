@@ -184,27 +184,30 @@ __device__ void inc_decide(IncState& st, const double* v, int n, int max_iter) {
         st.phase = 1;
         st.lo = st.dmin;
         st.hi = st.dmax;
+        st.tlo = log(st.lo);
+        st.thi = log(st.hi);
         st.glo = g_lo;
         st.ghi = g_hi;
         // small increments: w ~ 1 - x a~, so cv(x)^2 ~ x^2 var(a~) and the root is near tau / sd(a~)
         const double mean = v[4] / n, var = v[5] / n - mean * mean;
-        double x0 = var > 0.0 ? st.tau / sqrt(var) : 0.0;
-        if (!(x0 > st.lo && x0 < st.hi)) {
-            const double tlo = log(st.lo), thi = log(st.hi);
-            x0 = exp(tlo + (thi - tlo) * (-g_lo / (g_hi - g_lo)));   // regula falsi in t
-            if (!(x0 > st.lo && x0 < st.hi)) x0 = sqrt(st.lo * st.hi);
-        }
-        st.x = x0;
+        const double x0 = var > 0.0 ? st.tau / sqrt(var) : 0.0;
+        double t0 = x0 > st.lo && x0 < st.hi ? log(x0) : st.tlo + (st.thi - st.tlo) * (-g_lo / (g_hi - g_lo));
+        if (!(t0 > st.tlo && t0 < st.thi)) t0 = 0.5 * (st.tlo + st.thi);   // regula falsi in t, bisection
+        st.t = t0;
+        st.x = exp(t0);
         return;
     }
     const double x = st.x, S1 = v[0], S2 = v[1];
     const double ratio = (double)n * S2 / (S1 * S1);
     const double g = log(ratio) - st.target;
+    const double t = st.t;
     if (g > 0.0) {
         st.hi = x;
+        st.thi = t;
         st.ghi = g;
     } else {
         st.lo = x;
+        st.tlo = t;
         st.glo = g;
     }
     if (g == 0.0 || st.hi <= st.lo * (1.0 + 4e-16) || st.iter >= max_iter) {
@@ -218,7 +221,7 @@ __device__ void inc_decide(IncState& st, const double* v, int n, int max_iter) {
     const float gp = 2.f * (m1 - m2);                                          // dg/dx
     const float gpp = 4.f * (q2 - m2 * m2) - 2.f * (q1 - m1 * m1);             // d2g/dx2
     const float G = (float)g, Gp = fx * gp, Gpp = fx * gp + fx * fx * gpp;
-    const double tlo = log(st.lo), thi = log(st.hi), t = log(x);
+    const double tlo = st.tlo, thi = st.thi;
     bool local = true;
     float dt = -2.f * G * Gp / (2.f * Gp * Gp - G * Gpp);                      // Halley
     if (!(t + dt > tlo && t + dt < thi)) dt = -G / Gp;                          // Newton
@@ -239,6 +242,7 @@ __device__ void inc_decide(IncState& st, const double* v, int n, int max_iter) {
         inc_finish(st, xn, S1n, (double)n * S2n / (S1n * S1n), n);
         return;
     }
+    st.t = tn;
     st.x = xn;
 }
 
@@ -362,6 +366,98 @@ __global__ void __launch_bounds__(kIncThreads) inc_search_kernel(const double* a
         __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *w.state = st;
+}
+
+// ---- systematic resampling with the gather, one cooperative launch ------------------------------
+// The weights w_j = exp(-delta (a_j - amin)) of the increment just found, their normalised inclusive
+// prefix sums (cdf, last entry 1 exactly), the ancestors min{j : cdf_j > (U + i)/n} and the gather
+// of theta rows and potential caches, with the FP64 work spread over the blocks: each block scans a
+// contiguous range, and after a grid barrier adds the prefix of the block totals (summed in the same
+// fixed order by every block). Deterministic for given n and grid.
+constexpr int kRsThreads = 128;
+
+__global__ void __launch_bounds__(kRsThreads) resample_gather_kernel(
+    const double* a, int n, const IncState* state, uint32_t event, uint64_t seed, int K, const double* th_in,
+    double* th_out, const double* p0_in, double* p0_out, const double* p1_in, double* p1_out, double* cdf, int* anc,
+    double* btot, unsigned* bar, int* err) {
+    __shared__ double warp_tot[kRsThreads / 32];
+    __shared__ double run_s, off_s, inv_s;
+    __shared__ int ok_s;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned nb = gridDim.x;
+    unsigned generation = 0;
+    const int chunk = (n + (int)nb - 1) / (int)nb;
+    const int j0 = min(n, (int)blockIdx.x * chunk), j1 = min(n, j0 + chunk);
+    const double delta = state->delta, amin = state->amin;
+    if (tid == 0) run_s = 0.0;
+    __syncthreads();
+    for (int base = j0; base < j1; base += kRsThreads) {
+        const int j = base + tid;
+        const double w = j < j1 ? exp(-delta * (a[j] - amin)) : 0.0;
+        double incl = w;
+        for (int off = 1; off < 32; off <<= 1) {
+            const double u = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += u;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        double before = run_s;
+        for (int k = 0; k < wid; ++k) before += warp_tot[k];
+        if (j < j1) cdf[j] = before + incl;
+        __syncthreads();
+        if (tid == kRsThreads - 1) run_s = before + incl;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        btot[blockIdx.x] = run_s;
+        ok_s = grid_barrier(bar, err, nb, generation);
+    }
+    __syncthreads();
+    if (!ok_s) return;
+    if (wid == 0) {   // offset of this block and the total, in a fixed order
+        double off = 0.0, tot = 0.0;
+        for (unsigned k = lane; k < nb; k += 32) {
+            const double v = __ldcg(&btot[k]);
+            tot += v;
+            if (k < blockIdx.x) off += v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if (lane == 0) {
+            off_s = off;
+            inv_s = 1.0 / tot;
+        }
+    }
+    __syncthreads();
+    for (int j = j0 + tid; j < j1; j += kRsThreads) cdf[j] = j == n - 1 ? 1.0 : (cdf[j] + off_s) * inv_s;
+    if (tid == 0) ok_s = grid_barrier(bar, err, nb, generation);
+    __syncthreads();
+    if (!ok_s) return;
+    const uint4 x = philox(make_uint4(0u, 0u, event, (uint32_t)kPurposeResample), seed);
+    const double U = u53(x.x, x.y);
+    for (int i = blockIdx.x * kRsThreads + tid; i < n; i += nb * kRsThreads) {
+        const double pos = (U + (double)i) / (double)n;
+        int lo = 0, hi = n - 1;   // cdf[n-1] = 1 > pos always
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldcg(&cdf[mid]) > pos) hi = mid; else lo = mid + 1;
+        }
+        anc[i] = lo;
+    }
+    if (tid == 0) ok_s = grid_barrier(bar, err, nb, generation);
+    __syncthreads();
+    if (!ok_s) return;
+    for (long long t = (long long)blockIdx.x * kRsThreads + tid; t < (long long)n * K; t += (long long)nb * kRsThreads) {
+        const int i = (int)(t / K), k = (int)(t - (long long)i * K);
+        const int src = __ldcg(&anc[i]);
+        th_out[t] = th_in[(size_t)src * K + k];
+        if (k == 0) {
+            if (p0_in) p0_out[i] = p0_in[src];
+            if (p1_in) p1_out[i] = p1_in[src];
+        }
+    }
 }
 
 // ---- systematic resampling -----------------------------------------------------------------
@@ -671,6 +767,23 @@ cudaError_t resample_launch(const double* a, const double* w_in, int n, const In
     ancestors_kernel<<<grid_for(n, 256), 256, 0, st>>>(cdf, n, U, event, seed, anc);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t resample_gather_launch(const double* a, int n, const IncState* state, uint32_t event, uint64_t seed,
+                                   int K, const double* th_in, double* th_out, const double* p0_in, double* p0_out,
+                                   const double* p1_in, double* p1_out, double* cdf, int* anc, IncWork& w,
+                                   cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int nb = std::min(kIncMaxBlocks, std::max(1, (n + kRsThreads - 1) / kRsThreads));
+    cudaError_t e = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    double* btot = w.partials;   // the search is finished: its scratch is free
+    void* args[] = {(void*)&a,     (void*)&n,      (void*)&state,  (void*)&event, (void*)&seed, (void*)&K,
+                    (void*)&th_in, (void*)&th_out, (void*)&p0_in,  (void*)&p0_out, (void*)&p1_in,
+                    (void*)&p1_out, (void*)&cdf,   (void*)&anc,    (void*)&btot,  (void*)&w.bar, (void*)&w.err};
+    e = cudaLaunchCooperativeKernel((const void*)resample_gather_kernel, dim3(nb), dim3(kRsThreads), args, 0, st);
+    count_launches(1);
+    return e;
 }
 
 cudaError_t gather_launch(const int* anc, int n, int K, const double* th_in, double* th_out, const double* p0_in,

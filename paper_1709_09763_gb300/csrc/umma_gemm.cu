@@ -151,7 +151,7 @@ __device__ __forceinline__ void epilogue(const GemmEpi& e, int row, int col, flo
 }
 
 template <int BN, int STAGES>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 3)
 umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                  int K, GemmEpi epi, int* err) {
     constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
@@ -323,8 +323,10 @@ cudaError_t umma_gemm(const void* A, int lda, const void* B, int ldb, int M, int
     const int bn = N <= 64 ? 64 : 128;
     CUtensorMap ta, tb;
     if (!make_map(&ta, A, M, K, lda, BM) || !make_map(&tb, B, N, K, ldb, bn)) return cudaErrorInvalidValue;
-    if (bn == 64) return launch_gemm<64, 4>(ta, tb, M, N, K, epi, err, st);
-    return launch_gemm<128, 4>(ta, tb, M, N, K, epi, err, st);
+    // two stages (65 KB of shared memory): three CTAs per SM, so that one CTA's epilogue overlaps
+    // the loads and MMAs of the others (the contractions here have short K)
+    if (bn == 64) return launch_gemm<64, 2>(ta, tb, M, N, K, epi, err, st);
+    return launch_gemm<128, 2>(ta, tb, M, N, K, epi, err, st);
 }
 
 }  // namespace mls2mc
