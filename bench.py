@@ -31,19 +31,27 @@ import numpy as np  # noqa: E402
 WORKLOAD = "mls2mc_mixed_h8_64"
 
 
-def algorithmic_flops_per_eval(N, K, iters, passes):
+# DRAM bytes per particle of the 1/64 solve kernel (kappa in, G and Phi out), measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on a 304-particle launch of the same kernel and
+# scaled by the particle count (the traffic is per particle: nothing is shared between blocks)
+FEM64_DRAM_BYTES_PER_PARTICLE = 10.050048e6 / 304
+
+
+def algorithmic_flops_per_eval(N, K, iters, passes, synthesis=False):
     """FP32 operations of one likelihood evaluation on level 1/h = N, counted from the algorithm.
 
     Per fine interior node and CG iteration: V(1,1) fine-level work (red/black smoothing
     before and after: 2 x (0.5 x 1 + 0.5 x 10), residual 11, restriction 2, prolongation
     1.5) = 24.5, coarse levels 1/3 of that, CG vector work 22 -> 54.7. Per refinement pass:
     the residual update in double-float arithmetic, ~100 FP32 operations per node. Set-up:
-    KL synthesis 2*K*E, exp E, coefficients ~10 per node.
+    coefficients ~10 per node, and with synthesis=True the KL synthesis 2*K*E and exp E (on the
+    mixed path the synthesis runs in the tensor-core GEMM, not in the solve kernel).
     """
     n = (N - 1) ** 2
     E = 2 * N * N
     per_iter = (24.5 * 4.0 / 3.0 + 22.0) * n
-    return iters * per_iter + passes * 100.0 * n + 2.0 * K * E + E + 10.0 * (N + 1) ** 2
+    synth = 2.0 * K * E + E if synthesis else 0.0
+    return iters * per_iter + passes * 100.0 * n + synth + 10.0 * (N + 1) ** 2
 
 
 class ClockSampler:
@@ -451,7 +459,9 @@ def main():
                           for l, (N, lm) in enumerate(zip(w.inv_h, lvl_ms))},
             "roofline": {"kernel": f"fem_eval_kernel<float,{w.inv_h[-1]},{tuned[-1]}>", "bound": "alu",
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": None, "launch_ms": launch_ms,
+                         "frac": achieved / fp32_peak,
+                         "traffic": FEM64_DRAM_BYTES_PER_PARTICLE * J if w.inv_h[-1] == 64 else None,
+                         "launch_ms": launch_ms,
                          "launches": kern_n[kl], "mean_cg_iters": mean_it,
                          "peak_source": f"FP32 FMA issue rate: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "
                                         f"(sm_max_mhz {src})"},
