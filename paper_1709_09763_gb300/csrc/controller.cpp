@@ -119,7 +119,9 @@ void Handle::free_sampler() {
 // observations are kept as training pairs (theta, G_l(theta)) of that level's network
 int Handle::smp_eval(int level, int n, const double* theta, double* phi) {
     if (n <= 0) return SMC_OK;
-    const bool collect = opts.surrogate && forward_kind == SMC_FWD_FEM;
+    // no pairs for a level whose screening gate has been measured and said no
+    const bool collect = opts.surrogate && forward_kind == SMC_FWD_FEM &&
+                         !(level < (int)da_gate.size() && da_gate[level] < 0);
     RC(eval_device(level, n, theta, collect ? smp->G_buf : nullptr, phi, smp->iters, stream));
     smp->evals[level] += n;
     if (collect) {
@@ -196,17 +198,18 @@ bool Handle::da_worth(int level) {
     return da_gate[level] > 0;
 }
 
-// training schedule: once the level has J pairs, then again after every 4 J new pairs (200 Adam
-// steps the first time, 50 afterwards)
+// training schedule: once the level has J pairs, then again after every 4 J new pairs (25 Adam
+// steps the first time, a quarter of that afterwards) on minibatches of up to 8192 pairs: the
+// small GEMMs of a step are latency-bound, so few large steps train for less than many small ones
 int Handle::maybe_train(int level) {
     if (!opts.surrogate || forward_kind != SMC_FWD_FEM) return SMC_OK;
     if ((int)mlps.size() <= level || !mlps[level].ready) return SMC_OK;
     Mlp& M = mlps[level];
     if (M.count < smp->J) return SMC_OK;
     if (M.t > 0 && smp->pairs_new[level] < 4LL * smp->J) return SMC_OK;
-    const int base = opts.surrogate_train_steps > 0 ? opts.surrogate_train_steps : 200;
+    const int base = opts.surrogate_train_steps > 0 ? opts.surrogate_train_steps : 25;
     const int steps = M.t == 0 ? base : std::max(1, base / 4);
-    const int batch = std::min(opts.surrogate_batch > 0 ? opts.surrogate_batch : 1024, M.count);
+    const int batch = std::min(opts.surrogate_batch > 0 ? opts.surrogate_batch : 8192, M.count);
     double loss = 0.0;
     RC(mlp_train(level, steps, batch, &loss));
     smp->pairs_new[level] = 0;

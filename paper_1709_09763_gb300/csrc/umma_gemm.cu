@@ -18,7 +18,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <atomic>
 #include <mutex>
+#include <unordered_map>
 
 #include "internal.h"
 #include "umma_gemm.h"
@@ -302,13 +304,51 @@ bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int
     return r == CUDA_SUCCESS;
 }
 
+// encoded maps of this thread, keyed by everything a map encodes (address, shape, stride, box):
+// a key fully determines its map, so entries never go stale
+struct MapKey {
+    const void* ptr;
+    int rows, cols, ld, box_rows;
+    bool operator==(const MapKey& o) const {
+        return ptr == o.ptr && rows == o.rows && cols == o.cols && ld == o.ld && box_rows == o.box_rows;
+    }
+};
+struct MapKeyHash {
+    size_t operator()(const MapKey& k) const {
+        size_t h = std::hash<const void*>()(k.ptr);
+        for (int v : {k.rows, k.cols, k.ld, k.box_rows}) h = h * 1000003u ^ (size_t)(unsigned)v;
+        return h;
+    }
+};
+
+bool cached_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows) {
+    thread_local std::unordered_map<MapKey, CUtensorMap, MapKeyHash> cache;
+    const MapKey key{ptr, rows, cols, ld, box_rows};
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *map = it->second;
+        return true;
+    }
+    if (!make_map(map, ptr, rows, cols, ld, box_rows)) return false;
+    if (cache.size() >= 512) cache.clear();
+    cache.emplace(key, *map);
+    return true;
+}
+
 template <int BN, int STAGES>
 cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, const GemmEpi& epi,
                         int* err, cudaStream_t st) {
     const size_t smem = (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024;
     auto kern = umma_gemm_kernel<BN, STAGES>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    static std::atomic<unsigned long long> attr_set{0};   // one bit per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(attr_set.load() & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set.fetch_or(bit);
+    }
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     kern<<<grid, 128, smem, st>>>(ta, tb, M, N, K, epi, err);
     count_launches(1);
@@ -322,7 +362,7 @@ cudaError_t umma_gemm(const void* A, int lda, const void* B, int ldb, int M, int
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     const int bn = N <= 64 ? 64 : 128;
     CUtensorMap ta, tb;
-    if (!make_map(&ta, A, M, K, lda, BM) || !make_map(&tb, B, N, K, ldb, bn)) return cudaErrorInvalidValue;
+    if (!cached_map(&ta, A, M, K, lda, BM) || !cached_map(&tb, B, N, K, ldb, bn)) return cudaErrorInvalidValue;
     // two stages (65 KB of shared memory): three CTAs per SM, so that one CTA's epilogue overlaps
     // the loads and MMAs of the others (the contractions here have short K)
     if (bn == 64) return launch_gemm<64, 2>(ta, tb, M, N, K, epi, err, st);
