@@ -26,6 +26,7 @@ struct Batch {
         std::vector<int> offsets;
         FemArgs* d_args = nullptr;
         int* d_offsets = nullptr;
+        int* d_item_group = nullptr;   // group of each work item
     };
     std::vector<Group> groups;
     int* d_counters = nullptr;
@@ -39,6 +40,7 @@ struct Batch {
         for (auto& g : groups) {
             cudaFree(g.d_args);
             cudaFree(g.d_offsets);
+            cudaFree(g.d_item_group);
         }
         groups.clear();
         cudaFree(d_counters);
@@ -67,7 +69,7 @@ int enqueue(Batch* b, const int* level, const int* n, const double* const* theta
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->groups.size(), st);
     for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g) {
         const auto& G = b->groups[g];
-        e = fem_eval_persistent_launch(G.N, G.precision, G.T, G.d_args, G.d_offsets, (int)G.args.size(), G.total,
+        e = fem_eval_persistent_launch(G.N, G.precision, G.T, G.d_args, G.d_offsets, G.d_item_group, G.total,
                                        b->d_counters + g, st);
     }
     return e == cudaSuccess ? SMC_OK : SMC_ECUDA;
@@ -166,6 +168,14 @@ int smc_batch_eval(smc_batch* bb, const int* level, const int* n, const double* 
                 e = cudaMemcpy(G.d_args, G.args.data(), sizeof(FemArgs) * G.args.size(), cudaMemcpyHostToDevice);
             if (e == cudaSuccess)
                 e = cudaMemcpy(G.d_offsets, G.offsets.data(), sizeof(int) * G.offsets.size(), cudaMemcpyHostToDevice);
+            std::vector<int> ig((size_t)std::max(G.total, 1), 0);
+            for (size_t q = 0; q < G.offsets.size(); ++q) {
+                const int end = q + 1 < G.offsets.size() ? G.offsets[q + 1] : G.total;
+                for (int i = G.offsets[q]; i < end; ++i) ig[(size_t)i] = (int)q;
+            }
+            if (e == cudaSuccess) e = cudaMalloc((void**)&G.d_item_group, sizeof(int) * ig.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(G.d_item_group, ig.data(), sizeof(int) * ig.size(), cudaMemcpyHostToDevice);
         }
         if (e != cudaSuccess) {
             b->last_error = cudaGetErrorString(e);

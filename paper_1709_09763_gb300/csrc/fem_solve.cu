@@ -1004,31 +1004,37 @@ fem_eval_kernel(FemArgs a) {
 // persistent form: grid-sized blocks pull (group, particle) items from a device counter; every
 // group is one problem's launch arguments at this level size (many independent inverse problems
 // in one launch)
+// blocks per SM the register file can hold at 128 registers a thread (the per-problem kernels
+// compile below that; without the bound the persistent form took 143 at N = 32, T = 256, which
+// halved its occupancy)
+__host__ __device__ constexpr int min_blocks_128(int T) { return T >= 512 ? 1 : 65536 / (T * 128); }
+
 template <typename Real, int N, int T>
-__global__ void __launch_bounds__(T, 1)
-fem_eval_persistent(const FemArgs* groups, const int* offsets, int n_groups, int total, int* counter) {
+__global__ void __launch_bounds__(T, min_blocks_128(T))
+fem_eval_persistent(const FemArgs* groups, const int* offsets, const int* item_group, int total, int* counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_buf[2][64];
     __shared__ Real theta_s[256];
-    __shared__ int item_s, group_s;
+    __shared__ int item_s, p_s;
     __shared__ FemArgs args_s;                  // this item's launch arguments, read once per particle
+    // thread 0 takes the ticket of the next item before each solve: the atomic's latency overlaps
+    // the solve, and item_group maps an item to its group in one load
+    int next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
     for (;;) {
         if (threadIdx.x == 0) {
-            const int item = atomicAdd(counter, 1);
-            int lo = 0, hi = n_groups - 1;      // last group whose offset <= item
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (offsets[mid] <= item) lo = mid; else hi = mid - 1;
-            }
+            const int item = next;
             item_s = item;
-            group_s = lo;
-            if (item < total) args_s = groups[lo];
+            if (item < total) {
+                const int g = item_group[item];
+                args_s = groups[g];
+                p_s = item - offsets[g];
+                next = atomicAdd(counter, 1);
+            }
         }
         __syncthreads();
-        const int item = item_s;
-        if (item >= total) break;
-        solve_particle<Real, N, T>(args_s, item - offsets[group_s], reinterpret_cast<Real*>(smem_raw), red_buf,
-                                   theta_s);
+        if (item_s >= total) break;
+        solve_particle<Real, N, T>(args_s, p_s, reinterpret_cast<Real*>(smem_raw), red_buf, theta_s);
         __syncthreads();
     }
 }
@@ -1045,7 +1051,7 @@ cudaError_t launch_one(const FemArgs& a, cudaStream_t st) {
 }
 
 template <typename Real, int N, int T>
-cudaError_t launch_persistent(const FemArgs* groups, const int* offsets, int n_groups, int total, int* counter,
+cudaError_t launch_persistent(const FemArgs* groups, const int* offsets, const int* item_group, int total, int* counter,
                               cudaStream_t st) {
     const size_t smem = sizeof(Real) * (size_t)solve_smem_reals<Real>(N, T);
     auto kern = fem_eval_persistent<Real, N, T>;
@@ -1057,7 +1063,7 @@ cudaError_t launch_persistent(const FemArgs* groups, const int* offsets, int n_g
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
     if (err != cudaSuccess) return err;
     const int grid = std::max(1, std::min(total, sms * std::max(per_sm, 1)));
-    kern<<<grid, T, smem, st>>>(groups, offsets, n_groups, total, counter);
+    kern<<<grid, T, smem, st>>>(groups, offsets, item_group, total, counter);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1107,29 +1113,29 @@ cudaError_t fem_eval_global_launch(const FemArgs& a, float* scratch, int blocks,
 }
 
 cudaError_t fem_eval_persistent_launch(int N, int precision, int T, const FemArgs* groups, const int* offsets,
-                                       int n_groups, int total, int* counter, cudaStream_t st) {
+                                       const int* item_group, int total, int* counter, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     if (T <= 0) T = fem_block_sizes(N, precision).at(0);
     if (precision == SMC_MIXED) {
         switch (N * 10000 + T) {
-            case 4 * 10000 + 32: return launch_persistent<float, 4, 32>(groups, offsets, n_groups, total, counter, st);
-            case 8 * 10000 + 64: return launch_persistent<float, 8, 64>(groups, offsets, n_groups, total, counter, st);
-            case 8 * 10000 + 32: return launch_persistent<float, 8, 32>(groups, offsets, n_groups, total, counter, st);
-            case 16 * 10000 + 128: return launch_persistent<float, 16, 128>(groups, offsets, n_groups, total, counter, st);
-            case 16 * 10000 + 64: return launch_persistent<float, 16, 64>(groups, offsets, n_groups, total, counter, st);
-            case 32 * 10000 + 256: return launch_persistent<float, 32, 256>(groups, offsets, n_groups, total, counter, st);
-            case 32 * 10000 + 512: return launch_persistent<float, 32, 512>(groups, offsets, n_groups, total, counter, st);
-            case 64 * 10000 + 512: return launch_persistent<float, 64, 512>(groups, offsets, n_groups, total, counter, st);
-            case 64 * 10000 + 1024: return launch_persistent<float, 64, 1024>(groups, offsets, n_groups, total, counter, st);
+            case 4 * 10000 + 32: return launch_persistent<float, 4, 32>(groups, offsets, item_group, total, counter, st);
+            case 8 * 10000 + 64: return launch_persistent<float, 8, 64>(groups, offsets, item_group, total, counter, st);
+            case 8 * 10000 + 32: return launch_persistent<float, 8, 32>(groups, offsets, item_group, total, counter, st);
+            case 16 * 10000 + 128: return launch_persistent<float, 16, 128>(groups, offsets, item_group, total, counter, st);
+            case 16 * 10000 + 64: return launch_persistent<float, 16, 64>(groups, offsets, item_group, total, counter, st);
+            case 32 * 10000 + 256: return launch_persistent<float, 32, 256>(groups, offsets, item_group, total, counter, st);
+            case 32 * 10000 + 512: return launch_persistent<float, 32, 512>(groups, offsets, item_group, total, counter, st);
+            case 64 * 10000 + 512: return launch_persistent<float, 64, 512>(groups, offsets, item_group, total, counter, st);
+            case 64 * 10000 + 1024: return launch_persistent<float, 64, 1024>(groups, offsets, item_group, total, counter, st);
         }
     } else {
         switch (N * 10000 + T) {
-            case 4 * 10000 + 32: return launch_persistent<double, 4, 32>(groups, offsets, n_groups, total, counter, st);
-            case 8 * 10000 + 64: return launch_persistent<double, 8, 64>(groups, offsets, n_groups, total, counter, st);
-            case 16 * 10000 + 128: return launch_persistent<double, 16, 128>(groups, offsets, n_groups, total, counter, st);
-            case 16 * 10000 + 256: return launch_persistent<double, 16, 256>(groups, offsets, n_groups, total, counter, st);
-            case 32 * 10000 + 256: return launch_persistent<double, 32, 256>(groups, offsets, n_groups, total, counter, st);
-            case 32 * 10000 + 512: return launch_persistent<double, 32, 512>(groups, offsets, n_groups, total, counter, st);
+            case 4 * 10000 + 32: return launch_persistent<double, 4, 32>(groups, offsets, item_group, total, counter, st);
+            case 8 * 10000 + 64: return launch_persistent<double, 8, 64>(groups, offsets, item_group, total, counter, st);
+            case 16 * 10000 + 128: return launch_persistent<double, 16, 128>(groups, offsets, item_group, total, counter, st);
+            case 16 * 10000 + 256: return launch_persistent<double, 16, 256>(groups, offsets, item_group, total, counter, st);
+            case 32 * 10000 + 256: return launch_persistent<double, 32, 256>(groups, offsets, item_group, total, counter, st);
+            case 32 * 10000 + 512: return launch_persistent<double, 32, 512>(groups, offsets, item_group, total, counter, st);
         }
     }
     return cudaErrorInvalidValue;

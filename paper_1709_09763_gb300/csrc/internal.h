@@ -52,16 +52,17 @@ struct FemArgs {
 // T = threads per particle (one of fem_block_sizes; <= 0: the first, the default)
 cudaError_t fem_eval_launch(const FemArgs& a, cudaStream_t stream, int T = 0);
 std::vector<int> fem_block_sizes(int N, int precision);
-// persistent multi-problem launch: groups[g] (device array) are the launch arguments of one
-// problem at level size N; offsets[g] (device) the first work item of group g; *counter (device,
-// zero before the launch) hands out the total items to the blocks
 // large levels (1/h = 128, 256; mixed precision, kappa from the synthesis): hierarchy in global
 // scratch, blocks x fem_global_slice(N) floats; *counter (device) is reset by the launch
 size_t fem_global_slice(int N);
 int fem_global_blocks(int N);
 cudaError_t fem_eval_global_launch(const FemArgs& a, float* scratch, int blocks, int* counter, cudaStream_t st);
+// persistent multi-problem launch: groups[g] (device array) are the launch arguments of one
+// problem at level size N; offsets[g] (device) the first work item of group g; item_group[i]
+// (device) the group of item i; *counter (device, zero before the launch) hands out the total
+// items to the blocks
 cudaError_t fem_eval_persistent_launch(int N, int precision, int T, const FemArgs* groups, const int* offsets,
-                                       int n_groups, int total, int* counter, cudaStream_t st);
+                                       const int* item_group, int total, int* counter, cudaStream_t st);
 bool fem_level_supported(int N, int precision);
 
 }  // namespace mls2mc
