@@ -840,12 +840,16 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
     Lv<Real> C1 = ptrs2<Real, N, N / 2>(arena, sarena);
     Real* P = F.rhs;
 #define NODE_OF(i) const int jj = (i) / M + 1, ii = (i) - (jj - 1) * M + 1, n = jj * S + ii
+    // colour sweeps run over colour_node positions (every lane busy), the vector updates over the
+    // interior index (coalesced); the red pre-sweep from zero is written where R is updated
     for (int pass = 0; pass < a.max_outer && !converged; ++pass) {
         Real rr0 = 0;
         for (int i = tid; i < NI; i += T) {
+            NODE_OF(i);
             R[i] = RH[i];
             Dv[i] = Real(0);
             rr0 += RH[i] * RH[i];
+            if (((ii + jj) & 1) == 0) F.e[n] = RH[i] * F.iD[n];
         }
         block_sum<T>(rr0, red_buf[parity]);
         parity ^= 1;
@@ -853,32 +857,41 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
         const Real stop2 = rtol_in2 * rr0;
         Real rz = 0;
         for (int it = 0; it < a.max_inner; ++it) {
-            for (int i = tid; i < NI; i += T) {
-                NODE_OF(i);
-                if (((ii + jj) & 1) == 0) F.e[n] = R[i] * F.iD[n];
+            for (int k = tid; k < N * N / 2; k += T) {   // black pre-sweep
+                int ii, jj;
+                if (!colour_node<N>(k, 1, ii, jj)) continue;
+                const int n = jj * S + ii, i = (jj - 1) * M + ii - 1;
+                F.e[n] = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
             }
             __syncthreads();
-            for (int i = tid; i < NI; i += T) {
-                NODE_OF(i);
-                if ((ii + jj) & 1) F.e[n] = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
+            for (int k = tid; k < N * N / 2; k += T) {   // red residuals
+                int ii, jj;
+                if (!colour_node<N>(k, 0, ii, jj)) continue;
+                const int n = jj * S + ii;
+                F.res[n] = offsum<Real, S>(F.aE, F.aN, F.e, n);
             }
             __syncthreads();
-            restrict_red<Real, N / 2, T>(F, C1);
+            restrict_gather<Real, N / 2, T>(F.res, C1);
             __syncthreads();
             vcycle2<Real, N, N / 2, T>(arena, sarena, dinv);
-            for (int i = tid; i < NI; i += T) {
-                NODE_OF(i);
-                if ((ii + jj) & 1) {
-                    const int c = (jj >> 1) * SC + (ii >> 1);
-                    F.e[n] = (R[i] + offsum_prolong<Real, S, SC>(F.aE, F.aN, F.e, C1.e, n, c, (jj & 1) == 0)) * F.iD[n];
-                }
+            Real rz_new = 0;
+            for (int k = tid; k < N * N / 2; k += T) {   // black post-sweep with the prolongation
+                int ii, jj;
+                if (!colour_node<N>(k, 1, ii, jj)) continue;
+                const int n = jj * S + ii, i = (jj - 1) * M + ii - 1;
+                const int c = (jj >> 1) * SC + (ii >> 1);
+                const Real z = (R[i] + offsum_prolong<Real, S, SC>(F.aE, F.aN, F.e, C1.e, n, c, (jj & 1) == 0)) * F.iD[n];
+                F.e[n] = z;
+                rz_new += R[i] * z;
             }
             __syncthreads();
-            Real rz_new = 0;
-            for (int i = tid; i < NI; i += T) {
-                NODE_OF(i);
-                if (((ii + jj) & 1) == 0) F.e[n] = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
-                rz_new += R[i] * F.e[n];
+            for (int k = tid; k < N * N / 2; k += T) {   // red post-sweep
+                int ii, jj;
+                if (!colour_node<N>(k, 0, ii, jj)) continue;
+                const int n = jj * S + ii, i = (jj - 1) * M + ii - 1;
+                const Real z = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
+                F.e[n] = z;
+                rz_new += R[i] * z;
             }
             block_sum<T>(rz_new, red_buf[parity]);
             parity ^= 1;
@@ -906,6 +919,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
                 const Real rn = fma(-alpha, QV[i], R[i]);
                 R[i] = rn;
                 rr += rn * rn;
+                if (((ii + jj) & 1) == 0) F.e[n] = rn * F.iD[n];   // red pre-sweep of the next cycle
             }
             block_sum<T>(rr, red_buf[parity]);
             parity ^= 1;
