@@ -1005,8 +1005,16 @@ __global__ void __launch_bounds__(T, 1) fem_eval_global(FemArgs a, float* scratc
     }
 }
 
+// blocks per SM the register bound aims for: three 256-thread blocks at 1/32 (85 registers; the
+// shared memory of 64 KB a block allows three), otherwise what the shared memory and 128
+// registers a thread allow
 template <typename Real, int N, int T>
-__global__ void __launch_bounds__(T, 1)
+__host__ __device__ constexpr int solve_min_blocks() {
+    return (sizeof(Real) == 4 && N == 32 && T == 256) ? 3 : 1;
+}
+
+template <typename Real, int N, int T>
+__global__ void __launch_bounds__(T, (solve_min_blocks<Real, N, T>()))
 fem_eval_kernel(FemArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_buf[2][64];
