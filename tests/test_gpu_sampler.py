@@ -177,3 +177,40 @@ def test_tempering_update_equals_first_itu_of_oracle():
     assert np.allclose(th, o.theta, rtol=1e-10, atol=1e-12)
     assert np.allclose(phi, o.phi, rtol=1e-10)
     assert h.state()["beta"] == 0.0          # the update-scheme state is untouched
+
+
+@pytest.mark.parametrize("n", [8193, 20000, 100000])
+def test_next_increment_many_particles_and_spreads(n):
+    """The one-launch search with several particles per thread (n > 128 blocks x 64 threads) and
+    potentials of very different spread (the increment then ranges over decades), against the
+    oracle's bisection."""
+    As, y, s = _linear()
+    h = _handle_linear(As, y, s, J=n, tau_star=1.0, eps=1e-6)
+    rng = np.random.default_rng(n)
+    for a, dmax in [(rng.gamma(2.0, 3.0, n), 1.0), (rng.gamma(0.5, 3000.0, n), 1.0),
+                    (rng.lognormal(3.0, 2.0, n), 0.01), (rng.normal(1e4, 1.0, n), 1.0)]:
+        d, lm, c = h.next_increment(a, dmax)
+        dref = smc.next_increment(a, dmax, 1.0, 1e-6)
+        assert d == pytest.approx(dref, rel=1e-12), (n, dmax, d, dref)
+        assert lm == pytest.approx(smc.log_mean_weight(a, dref), rel=1e-12, abs=1e-13)
+        assert c == pytest.approx(smc.cv_of_increment(a, dref), rel=1e-9, abs=1e-12)
+
+
+@pytest.mark.parametrize("J", [7, 40001])
+def test_tempering_update_small_and_large_populations(J):
+    """The one-launch resampling with one block (J = 7) and with several scan rounds per block and
+    a ragged last block (J = 40001 over 128 blocks): same particles as the oracle's first ITU."""
+    As, y, s = _linear(K=4, n=6, sigma=0.3, seed=8)
+    kw = dict(n_mcmc=2, s_pcn=0.4, seed=91)
+    h = _handle_linear(As, y, s, J=J, **kw)
+    th0 = philox.normals(J, 4, 0, philox.PURPOSE_PRIOR, 91)
+    h.set_particles(th0)
+    info = h.tempering_update(0, 0.0, 2)
+    ev = lambda l, th: potential(th @ As[l].T, y, s)
+    o = smc.Sampler(ev, 1, 4, J, theta0=th0, **kw)
+    o.step()
+    th, phi = h.particles()
+    assert info["beta"] == pytest.approx(o.beta, rel=1e-12)
+    assert info["log_z_inc"] == pytest.approx(o.log_z, rel=1e-12, abs=1e-14)
+    assert np.allclose(th, o.theta, rtol=1e-10, atol=1e-12)
+    assert np.allclose(phi, o.phi, rtol=1e-10)
