@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
@@ -135,15 +136,18 @@ int Handle::smp_eval(int level, int n, const double* theta, double* phi) {
 
 unsigned* Handle::bad_counter() { return reinterpret_cast<unsigned*>(reinterpret_cast<char*>(smp->n_acc) + 8); }
 
-// read the accept and non-convergence counters and the grid-barrier flag of the last resampling
-// (one wait)
-int Handle::read_counters(unsigned long long* acc) {
+// read the accept and non-convergence counters and the grid-barrier flag of the last increment
+// search and resampling, and (pending != null) the state of a search whose result the host has
+// not waited for (one wait)
+int Handle::read_counters(unsigned long long* acc, IncState* pending) {
     unsigned char buf[16];
     int rs_err = 0;
     CK(cudaMemcpyAsync(buf, smp->n_acc, 16, cudaMemcpyDeviceToHost, stream));
     CK(cudaMemcpyAsync(&rs_err, smp->inc.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    if (pending) CK(cudaMemcpyAsync(pending, smp->inc.state, sizeof(IncState), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
-    if (rs_err) return fail(SMC_ETIMEOUT, "resampling: a block gave up waiting at the grid barrier");
+    if (rs_err) return fail(SMC_ETIMEOUT, "increment search or resampling: a block gave up at a grid barrier");
+    if (pending) RC(check_increment(*pending));
     unsigned long long a;
     unsigned bad;
     std::memcpy(&a, buf, 8);
@@ -234,25 +238,32 @@ int Handle::check_iters(int n) {
     return SMC_OK;
 }
 
-// adaptive increment on a[0..n): Eq. Eq_cv_opt, one cooperative launch; leaves IncState on the
-// device and a copy in st
-int Handle::increment(const double* a, int n, double dmax, IncState& st) {
-    Sampler* S = smp;
-    CK(inc_search_launch(a, n, dmax, opts.tau_star, opts.eps, kIncMaxIter, S->inc, stream));
-    int err = 0;
-    CK(cudaMemcpyAsync(&err, S->inc.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    CK(cudaMemcpyAsync(&st, S->inc.state, sizeof(IncState), cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
-    if (err) return fail(SMC_ETIMEOUT, "increment search: a block gave up waiting at the grid barrier");
+int Handle::check_increment(const IncState& st) {
     if (st.done == -1) return fail(SMC_ESINGULAR, "non-finite incremental weights (numerical singularity)");
     if (st.done != 1) return fail(SMC_ENOCONV, "increment search did not finish");
     return SMC_OK;
 }
 
-int Handle::reweight_resample(const double* a, double dmax, bool carry_fine, IncState& st) {
+// adaptive increment on a[0..n): Eq. Eq_cv_opt, one cooperative launch. The device state also
+// holds the next parameter, next = delta >= dmax ? 1 : base + delta. wait: copy the state to st
+// and check it now; otherwise the caller resolves it later (read_counters with pending = &st).
+int Handle::increment(const double* a, int n, double dmax, double base, IncState& st, bool wait) {
     Sampler* S = smp;
-    RC(increment(a, S->J, dmax, st));
-    S->log_z += st.log_mean_w;
+    CK(inc_search_launch(a, n, dmax, opts.tau_star, opts.eps, kIncMaxIter, base, 1.0, S->inc, stream));
+    if (!wait) return SMC_OK;
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, S->inc.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaMemcpyAsync(&st, S->inc.state, sizeof(IncState), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (err) return fail(SMC_ETIMEOUT, "increment search: a block gave up waiting at the grid barrier");
+    return check_increment(st);
+}
+
+// increment, evidence factor (when waited for), resampling and gather
+int Handle::reweight_resample(const double* a, double dmax, double base, bool carry_fine, IncState& st, bool wait) {
+    Sampler* S = smp;
+    RC(increment(a, S->J, dmax, base, st, wait));
+    if (wait) S->log_z += st.log_mean_w;
     CK(resample_gather_launch(a, S->J, S->inc.state, (uint32_t)S->stage, opts.seed, K, S->theta, S->theta_t,
                               S->phi_c, S->phi_t0, carry_fine ? S->phi_f : nullptr, S->phi_t1, S->cdf, S->anc,
                               S->inc, stream));
@@ -262,8 +273,12 @@ int Handle::reweight_resample(const double* a, double dmax, bool carry_fine, Inc
     return SMC_OK;
 }
 
+const double* Handle::next_param_device() const {
+    return reinterpret_cast<const double*>(reinterpret_cast<const char*>(smp->inc.state) + offsetof(IncState, next));
+}
+
 // n_mcmc pCN steps; zeta < 0: tempering target on `level`, else bridging target on level, level+1
-int Handle::mcmc(int level, double zeta, double& rate) {
+int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, IncState* pending) {
     // networks are trained only for targets whose every level is worth screening
     if (opts.surrogate && forward_kind == SMC_FWD_FEM && da_worth(level) && (zeta < 0.0 || da_worth(level + 1))) {
         RC(maybe_train(level));
@@ -278,12 +293,12 @@ int Handle::mcmc(int level, double zeta, double& rate) {
         CK(normals_launch(S->theta_p, S->J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
         RC(smp_eval(level, S->J, S->theta_p, S->phi_cp));
         if (zeta >= 0.0) RC(smp_eval(level + 1, S->J, S->theta_p, S->phi_fp));
-        CK(pcn_accept_launch(S->J, K, S->beta, zeta, ev, opts.seed, S->theta, S->theta_p, S->phi_c, S->phi_cp,
-                             S->phi_f, S->phi_fp, S->n_acc, stream));
+        CK(pcn_accept_launch(S->J, K, S->beta, beta_p, zeta, ev, opts.seed, S->theta, S->theta_p, S->phi_c,
+                             S->phi_cp, S->phi_f, S->phi_fp, S->n_acc, stream));
         S->mcmc_event += 1;
     }
     unsigned long long acc = 0;
-    RC(read_counters(&acc));
+    RC(read_counters(&acc, pending));
     rate = opts.n_mcmc > 0 ? (double)acc / ((double)opts.n_mcmc * S->J) : 0.0;
     return SMC_OK;
 }
@@ -350,20 +365,23 @@ void Handle::record(int type, double zeta, const IncState& st, double rate, doub
     if (info) *info = r;
 }
 
+// The plain sampler does not wait for the increment search: the pCN accept reads the new beta
+// from the device and the search state comes back with the update's counters (one host wait per
+// update). With the surrogate the host needs beta earlier (screening), so it waits.
 int Handle::tempering_update(int level, double beta0, int n_mcmc, smc_stage_info* info) {
     Sampler* S = smp;
     RC(smp_eval(level, S->J, S->theta, S->phi_c));
     IncState st;
     const double log_z = S->log_z, beta = S->beta;
     const int nm = opts.n_mcmc;
+    const bool wait = opts.surrogate != 0;
     S->beta = beta0;
-    RC(reweight_resample(S->phi_c, 1.0 - beta0, false, st));
-    S->beta = (st.delta >= 1.0 - beta0) ? 1.0 : beta0 + st.delta;
+    RC(reweight_resample(S->phi_c, 1.0 - beta0, beta0, false, st, wait));
+    if (wait) S->beta = st.next;
     opts.n_mcmc = n_mcmc;
     double rate = 0.0;
-    const int rc = mcmc(level, -1.0, rate);
+    const int rc = mcmc(level, -1.0, rate, wait ? nullptr : next_param_device(), wait ? nullptr : &st);
     opts.n_mcmc = nm;
-    const double beta_new = S->beta;
     S->beta = beta;
     S->log_z = log_z;
     if (rc != SMC_OK) return rc;
@@ -371,7 +389,7 @@ int Handle::tempering_update(int level, double beta0, int n_mcmc, smc_stage_info
         std::memset(info, 0, sizeof *info);
         info->type = 0;
         info->level = level;
-        info->beta = beta_new;
+        info->beta = st.next;
         info->zeta = -1.0;
         info->delta = st.delta;
         info->cv = st.cv;
@@ -387,10 +405,15 @@ int Handle::tempering_update(int level, double beta0, int n_mcmc, smc_stage_info
 int Handle::itu(double cv_lu, smc_stage_info* info) {
     Sampler* S = smp;
     IncState st;
-    RC(reweight_resample(S->phi_c, 1.0 - S->beta, false, st));
-    S->beta = (st.delta >= 1.0 - S->beta) ? 1.0 : S->beta + st.delta;
+    const bool wait = opts.surrogate != 0;
+    RC(reweight_resample(S->phi_c, 1.0 - S->beta, S->beta, false, st, wait));
+    if (wait) S->beta = st.next;
     double rate = 0.0;
-    RC(mcmc(S->level, -1.0, rate));
+    RC(mcmc(S->level, -1.0, rate, wait ? nullptr : next_param_device(), wait ? nullptr : &st));
+    if (!wait) {
+        S->beta = st.next;
+        S->log_z += st.log_mean_w;
+    }
     record(0, -1.0, st, rate, cv_lu, info);
     S->stage += 1;
     S->prev_lu = false;
@@ -407,8 +430,8 @@ int Handle::lu(int head, smc_stage_info* info) {
     double rate = 0.0;
     while (zeta < 1.0) {
         CK(lu_increment_launch(S->phi_c, S->phi_f, S->J, S->beta, S->a, stream));
-        RC(reweight_resample(S->a, 1.0 - zeta, true, st));
-        zeta = (st.delta >= 1.0 - zeta) ? 1.0 : zeta + st.delta;
+        RC(reweight_resample(S->a, 1.0 - zeta, zeta, true, st, true));
+        zeta = st.next;
         RC(mcmc(l, zeta, rate));
         record(1, zeta, st, rate, -1.0, info);
         S->path.back().n_bridge = ++nb;
@@ -592,7 +615,7 @@ int smc_next_increment(smc_handle* hh, int n, const double* a, double dmax, doub
     cudaError_t e = cudaMemcpyAsync(S->a, a, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "copy a");
     IncState st;
-    int rc = h->increment(S->a, n, dmax, st);
+    int rc = h->increment(S->a, n, dmax, 0.0, st, true);
     if (rc != SMC_OK) return rc;
     out3[0] = st.delta;
     out3[1] = st.log_mean_w;

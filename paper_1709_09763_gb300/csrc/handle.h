@@ -94,10 +94,12 @@ struct Handle {
     int smp_eval(int level, int n, const double* theta, double* phi);
     int check_iters(int n);
     unsigned* bad_counter();
-    int read_counters(unsigned long long* acc);
-    int increment(const double* a, int n, double dmax, struct IncState& st);
-    int reweight_resample(const double* a, double dmax, bool carry_fine, struct IncState& st);
-    int mcmc(int level, double zeta, double& rate);
+    int read_counters(unsigned long long* acc, struct IncState* pending = nullptr);
+    int check_increment(const struct IncState& st);
+    const double* next_param_device() const;
+    int increment(const double* a, int n, double dmax, double base, struct IncState& st, bool wait);
+    int reweight_resample(const double* a, double dmax, double base, bool carry_fine, struct IncState& st, bool wait);
+    int mcmc(int level, double zeta, double& rate, const double* beta_p = nullptr, struct IncState* pending = nullptr);
     int mcmc_da(int level, double zeta, double& rate);
     int maybe_train(int level);
     bool da_ready(int level, double zeta) const;

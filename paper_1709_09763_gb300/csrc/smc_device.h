@@ -26,9 +26,10 @@ struct IncState {
     double lo, hi, x;                 // bracket and current point
     double tlo, thi, t;               // their logarithms
     double glo, ghi;                  // g at the bracket ends
+    double base, top;                 // next = delta >= dmax ? top : base + delta
     int phase, iter, done, pad;
     // results
-    double delta, log_mean_w, cv, S1;
+    double delta, log_mean_w, cv, S1, next;
 };
 
 struct IncWork {
@@ -41,8 +42,8 @@ constexpr size_t kIncPartials = (size_t)kIncMaxBlocks * (1 + 2 * kIncSums);
 
 int inc_blocks(int n);
 // the whole search on a[0..n) into *w.state (w.err set if a grid barrier timed out)
-cudaError_t inc_search_launch(const double* a, int n, double dmax, double tau, double eps, int max_iter, IncWork& w,
-                              cudaStream_t st);
+cudaError_t inc_search_launch(const double* a, int n, double dmax, double tau, double eps, int max_iter, double base,
+                              double top, IncWork& w, cudaStream_t st);
 
 cudaError_t normals_launch(double* out, int J, int K, uint32_t event, uint32_t purpose, uint64_t seed,
                            const double* base, double c0, double c1, cudaStream_t st);
@@ -63,9 +64,11 @@ cudaError_t lu_increment_launch(const double* phi_c, const double* phi_f, int n,
                                 cudaStream_t st);
 cudaError_t cv_lu_launch(const double* phi_c, const double* phi_f, int n, double beta, double* out, cudaStream_t st);
 // zeta < 0: tempering target beta * Phi_c; else bridging target beta ((1 - zeta) Phi_c + zeta Phi_f)
-cudaError_t pcn_accept_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, double* theta,
-                              const double* theta_p, double* phi_c, const double* phi_cp, double* phi_f,
-                              const double* phi_fp, unsigned long long* n_acc, cudaStream_t st);
+// beta_p (device, or null): read beta there instead (the tempering parameter the increment search
+// left on the device, so the host need not wait for it)
+cudaError_t pcn_accept_launch(int n, int K, double beta, const double* beta_p, double zeta, uint32_t event,
+                              uint64_t seed, double* theta, const double* theta_p, double* phi_c, const double* phi_cp,
+                              double* phi_f, const double* phi_fp, unsigned long long* n_acc, cudaStream_t st);
 cudaError_t da_stage1_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, const double* ps_c,
                              const double* ps_f, const double* psp_c, const double* psp_f, const double* theta_p,
                              int* pass, int* surv_idx, int* n_surv, double* theta_s, cudaStream_t st);

@@ -142,8 +142,10 @@ __device__ __forceinline__ void block_reduce_sum(double (&v)[NV], double* sh /*[
 // dS1/dx = -T1, dS2/dx = -2 T2, d2S1/dx2 = U1, d2S2/dx2 = 4 U2.
 
 // state after the minimum of the potentials is known
-__device__ void inc_init(IncState& st, double amin, double dmax, double tau, double eps) {
+__device__ void inc_init(IncState& st, double amin, double dmax, double tau, double eps, double base, double top) {
     st.amin = amin;
+    st.base = base;
+    st.top = top;
     st.dmax = dmax;
     st.dmin = fmin(eps, dmax);
     st.target = log1p(tau * tau);   // log(1 + tau^2)
@@ -156,6 +158,7 @@ __device__ void inc_init(IncState& st, double amin, double dmax, double tau, dou
 
 __device__ void inc_finish(IncState& st, double x, double S1, double ratio, int n) {
     st.delta = x;
+    st.next = x >= st.dmax ? st.top : st.base + x;
     st.S1 = S1;
     st.log_mean_w = -x * st.amin + log(S1 / (double)n);
     const double c2 = ratio - 1.0;
@@ -288,7 +291,8 @@ __device__ __forceinline__ void inc_block_sum(double (&v)[kIncSums], double* sh 
 }
 
 __global__ void __launch_bounds__(kIncThreads) inc_search_kernel(const double* a, int n, double dmax, double tau,
-                                                                 double eps, int max_iter, IncWork w) {
+                                                                 double eps, int max_iter, double base, double top,
+                                                                 IncWork w) {
     __shared__ double sh[kIncSums * 32];
     __shared__ IncState st;
     __shared__ int ok_s;
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(kIncThreads) inc_search_kernel(const double* a
         double mm = INFINITY;
         for (unsigned k = lane; k < nb; k += 32) mm = fmin(mm, __ldcg(&w.partials[k]));
         for (int off = 16; off > 0; off >>= 1) mm = fmin(mm, __shfl_xor_sync(0xffffffffu, mm, off));
-        if (lane == 0) inc_init(st, mm, dmax, tau, eps);
+        if (lane == 0) inc_init(st, mm, dmax, tau, eps, base, top);
     }
     __syncthreads();
     for (int dec = 0; st.done == 0; ++dec) {
@@ -575,10 +579,12 @@ __device__ __forceinline__ double target_potential(double beta, double zeta, dou
     return __dmul_rn(beta, __dadd_rn(__dmul_rn(1.0 - zeta, pc), __dmul_rn(zeta, pf)));
 }
 
-__global__ void pcn_accept_kernel(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed,
-                                  double* theta, const double* theta_p, double* phi_c, const double* phi_cp,
-                                  double* phi_f, const double* phi_fp, unsigned long long* n_acc) {
+__global__ void pcn_accept_kernel(int n, int K, double beta, const double* beta_p, double zeta, uint32_t event,
+                                  uint64_t seed, double* theta, const double* theta_p, double* phi_c,
+                                  const double* phi_cp, double* phi_f, const double* phi_fp,
+                                  unsigned long long* n_acc) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (beta_p) beta = *beta_p;
     bool ok = false;
     if (j < n) {
         const uint4 x = philox(make_uint4(0u, (uint32_t)j, event, (uint32_t)kPurposePcnU), seed);
@@ -748,12 +754,13 @@ cudaError_t uniforms_launch(double* out, int J, uint32_t event, uint32_t purpose
 
 int inc_blocks(int n) { return std::min(kIncMaxBlocks, std::max(1, (n + 63) / 64)); }
 
-cudaError_t inc_search_launch(const double* a, int n, double dmax, double tau, double eps, int max_iter, IncWork& w,
-                              cudaStream_t st) {
+cudaError_t inc_search_launch(const double* a, int n, double dmax, double tau, double eps, int max_iter, double base,
+                              double top, IncWork& w, cudaStream_t st) {
     const int nb = inc_blocks(n);
     cudaError_t e = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);   // barrier counter, error flag
     if (e != cudaSuccess) return e;
-    void* args[] = {(void*)&a, (void*)&n, (void*)&dmax, (void*)&tau, (void*)&eps, (void*)&max_iter, (void*)&w};
+    void* args[] = {(void*)&a,        (void*)&n,    (void*)&dmax, (void*)&tau, (void*)&eps,
+                    (void*)&max_iter, (void*)&base, (void*)&top,  (void*)&w};
     e = cudaLaunchCooperativeKernel((const void*)inc_search_kernel, dim3(nb), dim3(kIncThreads), args, 0, st);
     count_launches(1);
     return e;
@@ -809,12 +816,13 @@ cudaError_t cv_lu_launch(const double* phi_c, const double* phi_f, int n, double
     return cudaGetLastError();
 }
 
-cudaError_t pcn_accept_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, double* theta,
-                              const double* theta_p, double* phi_c, const double* phi_cp, double* phi_f,
-                              const double* phi_fp, unsigned long long* n_acc, cudaStream_t st) {
+cudaError_t pcn_accept_launch(int n, int K, double beta, const double* beta_p, double zeta, uint32_t event,
+                              uint64_t seed, double* theta, const double* theta_p, double* phi_c, const double* phi_cp,
+                              double* phi_f, const double* phi_fp, unsigned long long* n_acc, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    pcn_accept_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, K, beta, zeta, event, seed, theta, theta_p, phi_c, phi_cp,
-                                                        phi_f, phi_fp, n_acc);
+    // 64-thread blocks: the FP64 work (log U, target potentials) spread over many SMs
+    pcn_accept_kernel<<<grid_for(n, 64), 64, 0, st>>>(n, K, beta, beta_p, zeta, event, seed, theta, theta_p, phi_c,
+                                                      phi_cp, phi_f, phi_fp, n_acc);
     count_launches(1);
     return cudaGetLastError();
 }
