@@ -175,3 +175,17 @@ def test_large_levels_parity(N, n):
     Gr, Phir = _oracle(N, w, theta, obs, np.array(d["y"]), d["sigma"])
     assert _rel(G, Gr).max() < 1e-6
     assert _phi_ok(Phi, Phir, Gr, d["sigma"], 1e-6)
+
+
+@pytest.mark.parametrize("N,K,corr,nobs,n", [(128, 64, 0.1, 7, 3), (256, 128, 0.05, 12, 2)])
+def test_large_level_workload_shapes(N, K, corr, nobs, n):
+    """The surrogate workload's finest level (1/128, K = 64) and the large workload's (1/256,
+    K = 128, correlation length 0.05, 12 x 12 observations interpolated at (i/13, j/13)): mixed-path
+    G within 1e-6 of the oracle."""
+    obs = wl.obs_grid(nobs)
+    theta = wl.particles(n, K, 900 + N)
+    y = np.zeros(obs.shape[0])
+    h = native.Handle([N], K, obs, y, 1.0, corr_len=corr, precision=native.SMC_MIXED)
+    G, _ = h.eval_likelihood(0, theta)
+    Gr = ofwd.Level(N, corr, 1.0, K, obs).G_batch(theta)
+    assert _rel(G, Gr).max() < 1e-6, _rel(G, Gr)
