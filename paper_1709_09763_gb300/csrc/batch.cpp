@@ -30,6 +30,8 @@ struct Batch {
     };
     std::vector<Group> groups;
     int* d_counters = nullptr;
+    float* big_scratch = nullptr;    // per-block slices for the groups of large levels (1/h >= 128)
+    int big_blocks = 0;
     std::vector<long long> signature;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -45,6 +47,9 @@ struct Batch {
         groups.clear();
         cudaFree(d_counters);
         d_counters = nullptr;
+        cudaFree(big_scratch);
+        big_scratch = nullptr;
+        big_blocks = 0;
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         exec = nullptr;
@@ -69,8 +74,12 @@ int enqueue(Batch* b, const int* level, const int* n, const double* const* theta
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->groups.size(), st);
     for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g) {
         const auto& G = b->groups[g];
-        e = fem_eval_persistent_launch(G.N, G.precision, G.T, G.d_args, G.d_offsets, G.d_item_group, G.total,
-                                       b->d_counters + g, st);
+        if (G.N >= 128)
+            e = fem_eval_global_multi_launch(G.N, G.d_args, G.d_offsets, G.d_item_group, G.total, b->big_scratch,
+                                             b->big_blocks, b->d_counters + g, st);
+        else
+            e = fem_eval_persistent_launch(G.N, G.precision, G.T, G.d_args, G.d_offsets, G.d_item_group, G.total,
+                                           b->d_counters + g, st);
     }
     return e == cudaSuccess ? SMC_OK : SMC_ECUDA;
 }
@@ -118,9 +127,8 @@ int smc_batch_eval(smc_batch* bb, const int* level, const int* n, const double* 
     std::vector<long long> sig;
     for (size_t p = 0; p < P; ++p) {
         Handle* h = b->h[p];
-        if (level[p] < 0 || level[p] >= (int)h->levels.size() || n[p] < 0 || (n[p] > 0 && (!theta[p] || !phi[p])) ||
-            h->levels[level[p]].N >= 128) {
-            b->last_error = "bad level (or a 1/h >= 128 level), count or pointer for problem " + std::to_string(p);
+        if (level[p] < 0 || level[p] >= (int)h->levels.size() || n[p] < 0 || (n[p] > 0 && (!theta[p] || !phi[p]))) {
+            b->last_error = "bad level, count or pointer for problem " + std::to_string(p);
             return SMC_EINVAL;
         }
         sig.insert(sig.end(), {(long long)level[p], (long long)n[p], (long long)(uintptr_t)theta[p],
@@ -161,6 +169,14 @@ int smc_batch_eval(smc_batch* bb, const int* level, const int* n, const double* 
             G.total += n[p];
         }
         cudaError_t e = cudaMalloc((void**)&b->d_counters, sizeof(int) * std::max<size_t>(1, b->groups.size()));
+        size_t big_need = 0;   // one scratch for all large groups: they run one after another
+        for (auto& G : b->groups)
+            if (G.N >= 128) {
+                const int blocks = fem_global_blocks(G.N);
+                b->big_blocks = std::max(b->big_blocks, blocks);
+                big_need = std::max(big_need, (size_t)blocks * fem_global_slice(G.N));
+            }
+        if (e == cudaSuccess && big_need) e = cudaMalloc((void**)&b->big_scratch, big_need * sizeof(float));
         for (auto& G : b->groups) {
             if (e == cudaSuccess) e = cudaMalloc((void**)&G.d_args, sizeof(FemArgs) * G.args.size());
             if (e == cudaSuccess) e = cudaMalloc((void**)&G.d_offsets, sizeof(int) * G.offsets.size());

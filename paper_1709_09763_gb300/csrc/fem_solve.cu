@@ -1005,12 +1005,48 @@ __global__ void __launch_bounds__(T, 1) fem_eval_global(FemArgs a, float* scratc
     }
 }
 
-// blocks per SM the register bound aims for: three 256-thread blocks at 1/32 (85 registers; the
-// shared memory of 64 KB a block allows three), otherwise what the shared memory and 128
-// registers a thread allow
+// large levels of many problems: the same persistent loop over (problem, particle) items, the
+// item's problem found in a per-item table and its launch arguments copied to shared memory
+template <int N, int T>
+__global__ void __launch_bounds__(T, 1)
+fem_eval_global_multi(const FemArgs* groups, const int* offsets, const int* item_group, int total, float* scratch,
+                      size_t slice, int* counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red_buf[2][64];
+    __shared__ int item_s, p_s;
+    __shared__ FemArgs args_s;
+    float* arena = scratch + slice * blockIdx.x;
+    float* sarena = reinterpret_cast<float*>(smem_raw);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int item = atomicAdd(counter, 1);
+            item_s = item;
+            if (item < total) {
+                const int g = item_group[item];
+                args_s = groups[g];
+                p_s = item - offsets[g];
+            }
+        }
+        __syncthreads();
+        if (item_s >= total) break;
+        solve_particle_mem<float, N, T>(args_s, p_s, arena, sarena, red_buf);
+        __syncthreads();
+    }
+}
+
+// blocks per SM the register file can hold at 128 registers a thread (the per-problem kernels
+// compile below that; without the bound the persistent form took 143 at N = 32, T = 256, which
+// halved its occupancy)
+__host__ __device__ constexpr int min_blocks_128(int T) { return T >= 512 ? 1 : 65536 / (T * 128); }
+
+// blocks per SM the register bound aims for, the same for the per-problem and the persistent
+// forms: FP32 blocks are compiled for at most 85 registers a thread (three 256-thread blocks at
+// 1/32, whose 64 KB of shared memory allow three; twelve 64-thread blocks at 1/16), FP64 blocks
+// for 128
 template <typename Real, int N, int T>
 __host__ __device__ constexpr int solve_min_blocks() {
-    return (sizeof(Real) == 4 && N == 32 && T == 256) ? 3 : 1;
+    return sizeof(Real) == 4 ? (65536 / (T * 85) > 1 ? (65536 / (T * 85) < 32 ? 65536 / (T * 85) : 32) : 1)
+                             : min_blocks_128(T);
 }
 
 template <typename Real, int N, int T>
@@ -1026,13 +1062,9 @@ fem_eval_kernel(FemArgs a) {
 // persistent form: grid-sized blocks pull (group, particle) items from a device counter; every
 // group is one problem's launch arguments at this level size (many independent inverse problems
 // in one launch)
-// blocks per SM the register file can hold at 128 registers a thread (the per-problem kernels
-// compile below that; without the bound the persistent form took 143 at N = 32, T = 256, which
-// halved its occupancy)
-__host__ __device__ constexpr int min_blocks_128(int T) { return T >= 512 ? 1 : 65536 / (T * 128); }
 
 template <typename Real, int N, int T>
-__global__ void __launch_bounds__(T, min_blocks_128(T))
+__global__ void __launch_bounds__(T, (solve_min_blocks<Real, N, T>()))
 fem_eval_persistent(const FemArgs* groups, const int* offsets, const int* item_group, int total, int* counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_buf[2][64];
@@ -1100,6 +1132,18 @@ cudaError_t launch_global(const FemArgs& a, float* scratch, size_t slice, int bl
     return cudaGetLastError();
 }
 
+template <int N, int T>
+cudaError_t launch_global_multi(const FemArgs* groups, const int* offsets, const int* item_group, int total,
+                                float* scratch, size_t slice, int blocks, int* counter, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (size_t)(arena_size(64) + dense_reals<float>(64));
+    cudaError_t e =
+        cudaFuncSetAttribute(fem_eval_global_multi<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fem_eval_global_multi<N, T><<<blocks, T, smem, st>>>(groups, offsets, item_group, total, scratch, slice, counter);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t fem_global_slice(int N) {
@@ -1131,6 +1175,16 @@ cudaError_t fem_eval_global_launch(const FemArgs& a, float* scratch, int blocks,
     if (e != cudaSuccess) return e;
     if (a.N == 128) return launch_global<128, 1024>(a, scratch, slice, grid, counter, st);
     if (a.N == 256) return launch_global<256, 1024>(a, scratch, slice, grid, counter, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t fem_eval_global_multi_launch(int N, const FemArgs* groups, const int* offsets, const int* item_group,
+                                         int total, float* scratch, int blocks, int* counter, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    const size_t slice = fem_global_slice(N);
+    const int grid = std::max(1, std::min(total, blocks));
+    if (N == 128) return launch_global_multi<128, 1024>(groups, offsets, item_group, total, scratch, slice, grid, counter, st);
+    if (N == 256) return launch_global_multi<256, 1024>(groups, offsets, item_group, total, scratch, slice, grid, counter, st);
     return cudaErrorInvalidValue;
 }
 

@@ -57,6 +57,10 @@ std::vector<int> fem_block_sizes(int N, int precision);
 size_t fem_global_slice(int N);
 int fem_global_blocks(int N);
 cudaError_t fem_eval_global_launch(const FemArgs& a, float* scratch, int blocks, int* counter, cudaStream_t st);
+// large levels of many problems (groups, offsets, item_group as for fem_eval_persistent_launch;
+// *counter zero before the launch), blocks x fem_global_slice(N) floats of scratch
+cudaError_t fem_eval_global_multi_launch(int N, const FemArgs* groups, const int* offsets, const int* item_group,
+                                         int total, float* scratch, int blocks, int* counter, cudaStream_t st);
 // persistent multi-problem launch: groups[g] (device array) are the launch arguments of one
 // problem at level size N; offsets[g] (device) the first work item of group g; item_group[i]
 // (device) the group of item i; *counter (device, zero before the launch) hands out the total

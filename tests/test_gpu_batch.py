@@ -1,4 +1,5 @@
-"""Many independent problems in one persistent launch per level size, captured in a CUDA graph:
+"""Many independent problems in one persistent launch per level size (1/128 and 1/256 in their
+device-memory form), captured in a CUDA graph:
 every problem's potentials equal its own single-problem evaluation bit for bit (same per-particle
 solve), in eager mode, on the first graph launch and on replays with new particle values."""
 import numpy as np
@@ -21,7 +22,9 @@ def _problems():
     rng = np.random.default_rng(7)
     specs = [((8, 16, 32), 16, 0.3, native.SMC_MIXED), ((16, 32, 64), 32, 0.1, native.SMC_MIXED),
              ((8, 16), 8, 0.3, native.SMC_FP64), ((16, 64), 64, 0.1, native.SMC_MIXED),
-             ((32,), 16, 0.3, native.SMC_MIXED), ((8, 32), 32, 0.1, native.SMC_FP64)]
+             ((32,), 16, 0.3, native.SMC_MIXED), ((8, 32), 32, 0.1, native.SMC_FP64),
+             ((16, 128), 16, 0.3, native.SMC_MIXED), ((32, 128), 32, 0.1, native.SMC_MIXED),
+             ((256,), 32, 0.1, native.SMC_MIXED)]
     hs = []
     for levels, K, lc, prec in specs:
         obs = wl.obs_grid(7)
@@ -33,8 +36,8 @@ def _problems():
 def test_batch_matches_single_problem_evaluations():
     hs, rng = _problems()
     stream = torch.cuda.Stream()
-    levels = [2, 1, 1, 1, 0, 1]
-    counts = [37, 400, 129, 250, 1, 77]
+    levels = [2, 1, 1, 1, 0, 1, 1, 1, 0]
+    counts = [37, 400, 129, 250, 1, 77, 9, 300, 2]
     b = native.Batch(hs)
     with torch.cuda.stream(stream):
         th = [torch.from_numpy(rng.normal(0, 1, (n, h.K))).cuda() for h, n in zip(hs, counts)]
