@@ -119,8 +119,8 @@ def job_throughput(units_per_rank, world, ms_max):
     return units_per_rank * world / (ms_max * 1e-3)
 
 
-def load_data():
-    with open(os.path.join(ROOT, "tests", "golden", f"data_{WORKLOAD}.json")) as f:
+def load_data(name=WORKLOAD):
+    with open(os.path.join(ROOT, "tests", "golden", f"data_{name}.json")) as f:
         return json.load(f)
 
 
@@ -386,11 +386,12 @@ def main():
     # delayed-acceptance pCN screened by the surrogate, R seeds each, outside the timed region
     run = None
     if not args.no_run:
-        def one_run(inv_h, surrogate, seed):
-            hr = native.Handle(inv_h, w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, variance=w.variance,
-                               J=J, J_tilde=w.J_tilde, n_mcmc=w.n_mcmc, s_pcn=w.s_pcn, tau_star=w.tau_star,
-                               precision=native.SMC_MIXED, seed=seed, stream=stream.cuda_stream,
-                               surrogate=surrogate)
+        def one_run(wk, dk, inv_h, surrogate, seed):
+            ob = wl.obs_grid(wk.obs_per_side)
+            hr = native.Handle(inv_h, wk.K, ob, dk["y"], dk["sigma"], corr_len=wk.corr_len, variance=wk.variance,
+                               J=wk.J, J_tilde=wk.J_tilde, n_mcmc=wk.n_mcmc, s_pcn=wk.s_pcn,
+                               tau_star=wk.tau_star, precision=native.SMC_MIXED, seed=seed,
+                               stream=stream.cuda_stream, surrogate=surrogate)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             hr.run()
@@ -405,10 +406,10 @@ def main():
                     "log_evidence": lz, "mean": m, "var": v,
                     "stage1_pass_rate": float(np.mean(rates)) if rates else None}
 
-        def compare(inv_h, R=3):
+        def compare(wk, dk, inv_h, R=3):
             res = {}
             for name, sur in (("plain", 0), ("surrogate", 1)):
-                runs = [one_run(inv_h, sur, w.seed_sampler + 1000 * rank + 17 * r) for r in range(R)]
+                runs = [one_run(wk, dk, inv_h, sur, wk.seed_sampler + 1000 * rank + 17 * r) for r in range(R)]
                 res[name] = {"seconds_median": float(np.median([x["seconds"] for x in runs])),
                              "seconds": [x["seconds"] for x in runs],
                              "solves_per_level_mean": np.mean([x["solves_per_level"] for x in runs], axis=0).tolist(),
@@ -419,13 +420,17 @@ def main():
             a, b = res["plain"].pop("_means"), res["surrogate"].pop("_means")
             se = np.sqrt(a.var(axis=0, ddof=1) / R + b.var(axis=0, ddof=1) / R)
             z = np.abs(a.mean(0) - b.mean(0)) / np.where(se > 0, se, np.inf)
-            return {"levels_inv_h": list(inv_h), "J": J, "replicates": R, "plain": res["plain"],
-                    "surrogate": res["surrogate"],
+            return {"workload": wk.name, "levels_inv_h": list(inv_h), "K": wk.K, "J": wk.J, "n_mcmc": wk.n_mcmc,
+                    "replicates": R, "plain": res["plain"], "surrogate": res["surrogate"],
                     "speedup_surrogate_vs_plain": res["plain"]["seconds_median"] / res["surrogate"]["seconds_median"],
                     "posterior_mean_diff_over_se_max": float(np.max(z))}
-        # MLS^2MC on the workload's hierarchy, and single-level SMC on its finest level (Example
-        # example_SMC, the paper's reference sampler), plain pCN vs surrogate-screened pCN
-        run = {"mls2mc": compare(tuple(w.inv_h)), "smc_finest": compare((w.inv_h[-1],), R=6)}
+        # MLS^2MC on the workload's hierarchy, single-level SMC on its finest level (Example
+        # example_SMC, the paper's reference sampler), and the surrogate workload (5 levels to 1/128,
+        # K = 64, J = 8000, 10 pCN steps): plain pCN vs surrogate-screened pCN
+        wda = wl.WORKLOADS["da_mixed_h8_128"]
+        dda = load_data(wda.name)
+        run = {"mls2mc": compare(w, d, tuple(w.inv_h)), "smc_finest": compare(w, d, (w.inv_h[-1],), R=6),
+               "mls2mc_surrogate_workload": compare(wda, dda, tuple(wda.inv_h))}
 
     batched = None if args.no_run else batched_measurement(native, wl, torch, dev)
 

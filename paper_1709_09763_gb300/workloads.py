@@ -46,6 +46,15 @@ WORKLOADS = {
     "mls2mc_mixed_h8_64": Workload("mls2mc_mixed_h8_64", (8, 16, 32, 64), 256, 32, 0.1, 7,
                                    4000, 5, seed_true=11, seed_noise=12, seed_sampler=13,
                                    precision="mixed"),
+    # surrogate-screened MLS^2MC, 5 levels h = 1/8 .. 1/128, K = 64, J = 8000, 10 pCN steps
+    "da_mixed_h8_128": Workload("da_mixed_h8_128", (8, 16, 32, 64, 128), 512, 64, 0.1, 7,
+                                8000, 10, seed_true=21, seed_noise=22, seed_sampler=23,
+                                precision="mixed"),
+    # large: 5 levels h = 1/16 .. 1/256, K = 128, correlation length 0.05, 12 x 12 observations,
+    # J = 16384, 10 pCN steps
+    "large_mixed_h16_256": Workload("large_mixed_h16_256", (16, 32, 64, 128, 256), 1024, 128, 0.05,
+                                    12, 16384, 10, seed_true=31, seed_noise=32, seed_sampler=33,
+                                    precision="mixed"),
 }
 
 
