@@ -42,7 +42,8 @@ extern "C" {
 
 /* precision of the forward solve */
 #define SMC_FP64   0   /* FP64 field, FP64 multigrid-preconditioned CG */
-#define SMC_MIXED  1   /* FP32 field + FP32 multigrid-PCG, FP64 residual refinement */
+#define SMC_MIXED  1   /* FP32 field + FP32 multigrid-PCG, residual refinement in double-float
+                          arithmetic (pairs of FP32 numbers, FP64-grade) */
 
 /* forward model kind */
 #define SMC_FWD_FEM     0  /* the PDE of Sec. 5 */
@@ -50,8 +51,8 @@ extern "C" {
 
 typedef struct {
     int n_levels;              /* N_L >= 1 */
-    const int* inv_h;          /* [n_levels] 1/h_l, coarse to fine; powers of two in [4, 64] (FP64),
-                                  [4, 256] (mixed; 128 and 256 keep the hierarchy in device memory) */
+    const int* inv_h;          /* [n_levels] 1/h_l, coarse to fine; powers of two in [4, 32] (FP64),
+                                  [4, 256] (mixed; 128 and 256 keep their fine levels in device memory) */
     int K;                     /* KL terms N_sto, 1 <= K <= 256 */
     double corr_len;           /* correlation length of the separable exponential covariance */
     double variance;           /* prior field variance */
@@ -182,7 +183,9 @@ typedef struct {
 /* One step of the update scheme u of Eq. eq_updatescheme_final (Sec. 4.4): an ITU, or a whole LU
  * with all its bridging steps. The first call draws the prior particles (Philox, see the
  * library documentation) and evaluates Phi_1 on them. info (may be NULL) receives the last
- * update's record; info->status = 1 when there was nothing left to do. */
+ * update's record; info->status = 1 when there was nothing left to do. A failure of an ITU's
+ * increment search (SMC_ESINGULAR, SMC_ETIMEOUT) is reported when the update ends; the particles
+ * are then unspecified. */
 int smc_step(smc_handle* h, smc_stage_info* info);
 
 /* Steps until beta = 1 on the finest level, or max_updates steps (<= 0: no cap). */
@@ -213,7 +216,9 @@ int smc_set_particles(smc_handle* h, const double* theta);
  * systematically, and run n_mcmc pCN steps for exp(-(beta0 + delta) Phi_level) mu0. The particles
  * change; the update-scheme state of smc_step (level, beta, evidence) does not. This is the building
  * block of single-level SMC on any level (Example example_SMC) and of hand-made update schemes.
- * info (may be NULL): type 0, the level, the new beta, delta, cv, log mean weight, accept rate. */
+ * info (may be NULL): type 0, the level, the new beta, delta, cv, log mean weight, accept rate.
+ * Without the surrogate the host does not wait for the increment search: its failures
+ * (SMC_ESINGULAR, SMC_ETIMEOUT) are reported when the update ends, the particles then unspecified. */
 int smc_tempering_update(smc_handle* h, int level, double beta0, int n_mcmc, smc_stage_info* info);
 
 /* ---- surrogate network (no counterpart in the paper) ------------------------------------------

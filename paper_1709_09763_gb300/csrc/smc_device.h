@@ -58,8 +58,6 @@ cudaError_t resample_gather_launch(const double* a, int n, const IncState* state
                                    int K, const double* th_in, double* th_out, const double* p0_in, double* p0_out,
                                    const double* p1_in, double* p1_out, double* cdf, int* anc, IncWork& w,
                                    cudaStream_t st);
-cudaError_t gather_launch(const int* anc, int n, int K, const double* th_in, double* th_out, const double* p0_in,
-                          double* p0_out, const double* p1_in, double* p1_out, cudaStream_t st);
 cudaError_t lu_increment_launch(const double* phi_c, const double* phi_f, int n, double beta, double* a,
                                 cudaStream_t st);
 cudaError_t cv_lu_launch(const double* phi_c, const double* phi_f, int n, double beta, double* out, cudaStream_t st);

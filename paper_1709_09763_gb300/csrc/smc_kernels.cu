@@ -527,20 +527,6 @@ __global__ void ancestors_kernel(const double* cdf, int n, double U, uint32_t ev
     anc[i] = lo;
 }
 
-// gather theta rows and up to two potential caches by ancestor index
-__global__ void gather_kernel(const int* anc, int n, int K, const double* th_in, double* th_out,
-                              const double* p0_in, double* p0_out, const double* p1_in, double* p1_out) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)n * K) return;
-    const int i = (int)(t / K), k = (int)(t - (long long)i * K);
-    const int src = anc[i];
-    th_out[t] = th_in[(size_t)src * K + k];
-    if (k == 0) {
-        if (p0_in) p0_out[i] = p0_in[src];
-        if (p1_in) p1_out[i] = p1_in[src];
-    }
-}
-
 // ---- increments of a level update and the cv^LU predictor ------------------------------------
 __global__ void lu_increment_kernel(const double* phi_c, const double* phi_f, int n, double beta, double* a) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -791,15 +777,6 @@ cudaError_t resample_gather_launch(const double* a, int n, const IncState* state
     e = cudaLaunchCooperativeKernel((const void*)resample_gather_kernel, dim3(nb), dim3(kRsThreads), args, 0, st);
     count_launches(1);
     return e;
-}
-
-cudaError_t gather_launch(const int* anc, int n, int K, const double* th_in, double* th_out, const double* p0_in,
-                          double* p0_out, const double* p1_in, double* p1_out, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    gather_kernel<<<grid_for((long long)n * K, 256), 256, 0, st>>>(anc, n, K, th_in, th_out, p0_in, p0_out, p1_in,
-                                                                   p1_out);
-    count_launches(1);
-    return cudaGetLastError();
 }
 
 cudaError_t lu_increment_launch(const double* phi_c, const double* phi_f, int n, double beta, double* a,
