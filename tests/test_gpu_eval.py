@@ -189,3 +189,29 @@ def test_large_level_workload_shapes(N, K, corr, nobs, n):
     G, _ = h.eval_likelihood(0, theta)
     Gr = ofwd.Level(N, corr, 1.0, K, obs).G_batch(theta)
     assert _rel(G, Gr).max() < 1e-6, _rel(G, Gr)
+
+
+@pytest.mark.parametrize("name", ["da_mixed_h8_128", "large_mixed_h16_256"])
+def test_full_size_sampled_parity_large_workloads(name):
+    """The finest-level launch of the surrogate workload (J = 8000 on 1/128, K = 64) and of the large
+    workload (J = 16384 on 1/256, K = 128, 12 x 12 interpolated observations): every solve
+    converges, sampled particles (first, last, inner) match the oracle within 1e-6."""
+    import torch
+    w = wl.WORKLOADS[name]
+    d = _data(w.name)
+    obs = wl.obs_grid(w.obs_per_side)
+    h = native.Handle(w.inv_h, w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, precision=native.SMC_MIXED)
+    theta = wl.particles(w.J, w.K, 5151)
+    th = torch.from_numpy(theta).cuda()
+    G = torch.empty((w.J, w.n_obs), dtype=torch.float64, device="cuda")
+    Phi = torch.empty(w.J, dtype=torch.float64, device="cuda")
+    it = torch.empty(w.J, dtype=torch.int32, device="cuda")
+    L = len(w.inv_h) - 1
+    h.eval_likelihood_device(L, w.J, th.data_ptr(), G.data_ptr(), Phi.data_ptr(), it.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert int(it.min()) > 0
+    idx = np.array([0, 1, w.J // 3, w.J - 1])
+    Gr, Phir = _oracle(w.inv_h[-1], w, theta[idx], obs, np.array(d["y"]), d["sigma"])
+    assert _rel(G.cpu().numpy()[idx], Gr).max() < 1e-6
+    assert _phi_ok(Phi.cpu().numpy()[idx], Phir, Gr, d["sigma"], 1e-6)
