@@ -31,10 +31,16 @@ import numpy as np  # noqa: E402
 WORKLOAD = "mls2mc_mixed_h8_64"
 
 
-# DRAM bytes per particle of the 1/64 solve kernel (kappa in, G and Phi out), measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on a 304-particle launch of the same kernel and
-# scaled by the particle count (the traffic is per particle: nothing is shared between blocks)
-FEM64_DRAM_BYTES_PER_PARTICLE = 10.050048e6 / 304
+# DRAM bytes per particle of the 1/64 solve kernels by threads per particle (kappa in, G and Phi
+# out), measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on one launch of the same
+# kernel and scaled by the particle count (the traffic is per particle: nothing is shared between
+# blocks); None where no capture of the current build exists
+FEM64_DRAM_BYTES_PER_PARTICLE = {512: None, 1024: None, -512: (20.04736e6 + 3.955456e6) / 608}
+
+
+def solve_kernel_name(N, T):
+    """Name of the solve kernel that runs level 1/h = N with T threads per particle."""
+    return f"fem_eval_compact<{N},{-T}>" if T < 0 else f"fem_eval_kernel<float,{N},{T}>"
 
 
 def algorithmic_flops_per_eval(N, K, iters, passes, synthesis=False):
@@ -444,6 +450,8 @@ def main():
         mean_it = float(it.mean())
         kl = L - 1
         launch_ms = kern_ms[kl] / max(kern_n[kl], 1)
+        per_particle = FEM64_DRAM_BYTES_PER_PARTICLE.get(tuned[-1]) if w.inv_h[-1] == 64 else None
+        traffic = per_particle * J if per_particle is not None else None
         flops = algorithmic_flops_per_eval(w.inv_h[-1], w.K, mean_it, 2.0) * J
         achieved = flops / (launch_ms * 1e-3) / 1e12
         total_evals = evals_per_step * world
@@ -462,10 +470,10 @@ def main():
                                    "solve_launch_ms": kern_ms[l] / max(kern_n[l], 1),
                                    "solve_evals_per_s": J / (kern_ms[l] / max(kern_n[l], 1) * 1e-3)}
                           for l, (N, lm) in enumerate(zip(w.inv_h, lvl_ms))},
-            "roofline": {"kernel": f"fem_eval_kernel<float,{w.inv_h[-1]},{tuned[-1]}>", "bound": "alu",
+            "roofline": {"kernel": solve_kernel_name(w.inv_h[-1], tuned[-1]), "bound": "alu",
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak,
-                         "traffic": FEM64_DRAM_BYTES_PER_PARTICLE * J if w.inv_h[-1] == 64 else None,
+                         "traffic": traffic,
                          "launch_ms": launch_ms,
                          "launches": kern_n[kl], "mean_cg_iters": mean_it,
                          "peak_source": f"FP32 FMA issue rate: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "

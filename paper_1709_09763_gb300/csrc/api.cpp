@@ -37,9 +37,10 @@ static int tuned_block(int N, int precision) {
     return it == g_block.end() ? 0 : it->second;
 }
 
+// T = 0: the default; T < 0: the compact form with -T threads (where compiled)
 static void set_block(int N, int precision, int T) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    if (T <= 0) g_block.erase({N, precision});
+    if (T == 0) g_block.erase({N, precision});
     else g_block[{N, precision}] = T;
 }
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -80,6 +81,7 @@ Handle::~Handle() {
     cudaFree(synth_theta_buf);
     cudaFree(synth_err);
     cudaFree(big_scratch);
+    cudaFree(cp_scratch);
     cudaFree(big_counter);
     cudaFree(d_y);
     free_sampler();
@@ -202,7 +204,32 @@ int Handle::eval_device(int level, int n, const double* theta, double* G, double
             return SMC_OK;
         }
         const int T = tuned_block(L.N, precision);
-        if (timing) {
+        if (T < 0) {   // compact form: persistent blocks with their refinement state in device memory
+            const int blocks = fem_compact_blocks(-T);
+            if (blocks <= 0) return fail(SMC_EINVAL, "no compact form with %d threads", -T);
+            const size_t need = (size_t)blocks * fem_compact_ref_floats(-T);
+            if (need > cp_cap) {
+                cudaFree(cp_scratch);
+                cp_scratch = nullptr;
+                cp_cap = 0;
+                cudaError_t ea = cudaMalloc((void**)&cp_scratch, need * sizeof(float));
+                if (ea != cudaSuccess) return fail(SMC_ENOMEM, "compact-form scratch: %s", cudaGetErrorString(ea));
+                cp_cap = need;
+            }
+            if (!big_counter && cudaMalloc((void**)&big_counter, sizeof(int)) != cudaSuccess)
+                return fail(SMC_ENOMEM, "work counter");
+            TimedLaunch t{level, nullptr, nullptr};
+            if (timing) {
+                t.start = take_event();
+                t.stop = take_event();
+                cudaEventRecord(t.start, st);
+            }
+            e = fem_eval_compact_launch(a, -T, cp_scratch, blocks, big_counter, st);
+            if (timing) {
+                cudaEventRecord(t.stop, st);
+                timed.push_back(t);
+            }
+        } else if (timing) {
             TimedLaunch t{level, take_event(), take_event()};
             cudaEventRecord(t.start, st);
             e = fem_eval_launch(a, st, T);
@@ -335,7 +362,7 @@ int smc_set_block_size(smc_handle* hh, int level, int T) {
     if (level < 0 || level >= (int)h->levels.size() || h->forward_kind != SMC_FWD_FEM)
         return h->fail(SMC_EINVAL, "level out of range");
     const int N = h->levels[level].N;
-    if (T > 0) {
+    if (T != 0) {
         auto v = fem_block_sizes(N, h->precision);
         if (std::find(v.begin(), v.end(), T) == v.end()) return h->fail(SMC_EINVAL, "block size %d not compiled for 1/h = %d", T, N);
     }

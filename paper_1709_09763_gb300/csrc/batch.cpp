@@ -158,7 +158,7 @@ int smc_batch_eval(smc_batch* bb, const int* level, const int* n, const double* 
                 Batch::Group G;
                 G.N = L.N;
                 G.precision = h->precision;
-                G.T = h->block_size(L.N);
+                G.T = std::max(0, h->block_size(L.N));   // the persistent form has no compact variant
                 b->groups.push_back(G);
             }
             Batch::Group& G = b->groups[gidx[key]];

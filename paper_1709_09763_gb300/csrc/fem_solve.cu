@@ -54,11 +54,37 @@ struct Lv {
     Real *aE, *aN, *iD, *e, *res, *rhs;   // iD: inverse of the stencil diagonal
 };
 
-template <typename Real, int N, int NL>
+// Compact hierarchy (two blocks per SM at 1/64): the top level keeps five arrays (res shares
+// the storage of rhs, which holds the CG direction p: p is dead while the V-cycle runs, its
+// values live in registers), the coarse levels four (aE, aN, e, rhs: no res, and the inverse
+// diagonal is formed from the edge weights where a sweep needs it).
+__host__ __device__ constexpr int coarse_size_cp(int NL) { return NL < 2 ? 0 : 4 * lvl_size(NL) + coarse_size_cp(NL / 2); }
+__host__ __device__ constexpr int coarse_offset_cp(int NL, int NC) {
+    return NL == NC ? 0 : 4 * lvl_size(NL) + coarse_offset_cp(NL / 2, NC);
+}
+__host__ __device__ constexpr int arena_size_cp(int N) { return 5 * lvl_size(N) + coarse_size_cp(N / 2); }
+
+template <typename Real, int N, int NL, bool CP = false>
 __device__ __forceinline__ Lv<Real> level_ptrs(Real* arena) {
-    Real* b = arena + lvl_offset(N, NL);
     constexpr int z = lvl_size(NL);
-    return Lv<Real>{b, b + z, b + 2 * z, b + 3 * z, b + 4 * z, b + 5 * z};
+    if constexpr (!CP) {
+        Real* b = arena + lvl_offset(N, NL);
+        return Lv<Real>{b, b + z, b + 2 * z, b + 3 * z, b + 4 * z, b + 5 * z};
+    } else if constexpr (NL == N) {
+        Real* b = arena;
+        return Lv<Real>{b, b + z, b + 2 * z, b + 3 * z, b + 4 * z, b + 4 * z};
+    } else {
+        Real* b = arena + 5 * lvl_size(N) + coarse_offset_cp(N / 2, NL);
+        return Lv<Real>{b, b + z, nullptr, b + 2 * z, nullptr, b + 3 * z};
+    }
+}
+
+// inverse stencil diagonal at interior node n: stored, or formed from the four edge weights
+// (the same expression and order as where it is stored)
+template <typename Real, int S>
+__device__ __forceinline__ Real inv_diag(const Lv<Real>& L, int n) {
+    if (L.iD) return L.iD[n];
+    return Real(1) / (L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S]);
 }
 
 // sum of a_nb * v_nb over the four stencil neighbours of padded node n (row stride S)
@@ -177,7 +203,7 @@ __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
         int i, j;
         if (!colour_node<NL>(k, color, i, j)) continue;
         const int n = j * S + i;
-        L.e[n] = (L.rhs[n] + offsum<Real, S>(L.aE, L.aN, L.e, n)) * L.iD[n];
+        L.e[n] = (L.rhs[n] + offsum<Real, S>(L.aE, L.aN, L.e, n)) * inv_diag<Real, S>(L, n);
     }
 }
 
@@ -198,7 +224,7 @@ __device__ __forceinline__ void restrict_red(const Lv<Real>& F, const Lv<Real>& 
                        Real(0.5) * (offsum<Real, SF>(F.aE, F.aN, F.e, f + SF + 1) +
                                     offsum<Real, SF>(F.aE, F.aN, F.e, f - SF - 1));
         C.rhs[c] = v;
-        if (((I + J) & 1) == 0) C.e[c] = v * C.iD[c];
+        if (((I + J) & 1) == 0) C.e[c] = v * inv_diag<Real, SC>(C, c);
     }
 }
 
@@ -212,22 +238,23 @@ __device__ __forceinline__ void restrict_gather(const Real* res, const Lv<Real>&
         const int f = (2 * J) * SF + 2 * I, c = J * SC + I;
         const Real v = res[f] + Real(0.5) * (res[f + SF + 1] + res[f - SF - 1]);
         C.rhs[c] = v;
-        if (((I + J) & 1) == 0) C.e[c] = v * C.iD[c];
+        if (((I + J) & 1) == 0) C.e[c] = v * inv_diag<Real, SC>(C, c);
     }
 }
 
 // zero the boundary rings of e, res, rhs on every level from NL down (interior values are always
 // written before they are read; the rings must read as zero)
-template <typename Real, int N, int NL, int T>
+template <typename Real, int N, int NL, int T, bool CP = false>
 __device__ __forceinline__ void zero_rings(Real* arena) {
     constexpr int S = fem_row_stride(NL);
-    const Lv<Real> L = level_ptrs<Real, N, NL>(arena);
+    const Lv<Real> L = level_ptrs<Real, N, NL, CP>(arena);
     for (int k = threadIdx.x; k < 4 * NL; k += T) {   // rows 0 and NL, then columns 0 and NL
         const int n = k <= NL ? k : k <= 2 * NL + 1 ? NL * S + (k - NL - 1)
                                                      : (1 + ((k - 2 * NL - 2) >> 1)) * S + (((k - 2 * NL - 2) & 1) ? NL : 0);
-        L.e[n] = L.res[n] = L.rhs[n] = Real(0);
+        L.e[n] = L.rhs[n] = Real(0);
+        if (L.res) L.res[n] = Real(0);
     }
-    if constexpr (NL > 2) zero_rings<Real, N, NL / 2, T>(arena);
+    if constexpr (NL > 2) zero_rings<Real, N, NL / 2, T, CP>(arena);
 }
 
 // off-diagonal sum at black node n = (i, j) with its red neighbours read as e + P e_c (P1
@@ -255,7 +282,8 @@ __device__ __forceinline__ void black_prolong(const Lv<Real>& L, const Real* ec)
         if (!colour_node<NL>(k, 1, i, j)) continue;
         const int n = j * S + i;
         const int c0 = (j >> 1) * SC + (i >> 1);
-        L.e[n] = (L.rhs[n] + offsum_prolong<Real, S, SC>(L.aE, L.aN, L.e, ec, n, c0, (j & 1) == 0)) * L.iD[n];
+        L.e[n] = (L.rhs[n] + offsum_prolong<Real, S, SC>(L.aE, L.aN, L.e, ec, n, c0, (j & 1) == 0)) *
+                 inv_diag<Real, S>(L, n);
     }
 }
 
@@ -349,28 +377,28 @@ __device__ __forceinline__ void phase_sync() {
 // V(1,1) cycle on a coarse level: reads L.rhs, writes L.e. Levels with at most 4 cells per side
 // (<= 9 unknowns) run inside warp 0 only (T = 32, warp barriers); the caller's next block
 // barrier publishes the result.
-template <typename Real, int N, int NL, int T, bool WARP = false>
+template <typename Real, int N, int NL, int T, bool WARP = false, bool CP = false>
 __device__ void vcycle_coarse(Real* arena, const Real* dinv) {
     if constexpr (NL == direct_level<Real>(N)) {
-        dense_solve<Real, NL, T>(level_ptrs<Real, N, NL>(arena), dinv);
+        dense_solve<Real, NL, T>(level_ptrs<Real, N, NL, CP>(arena), dinv);
         phase_sync<WARP>();
     } else if constexpr (!WARP && NL <= 4) {
-        if (threadIdx.x < 32) vcycle_coarse<Real, N, NL, 32, true>(arena, dinv);
+        if (threadIdx.x < 32) vcycle_coarse<Real, N, NL, 32, true, CP>(arena, dinv);
         __syncthreads();
         return;
     } else {
-        Lv<Real> L = level_ptrs<Real, N, NL>(arena);
+        Lv<Real> L = level_ptrs<Real, N, NL, CP>(arena);
         if constexpr (NL == 2) {
             constexpr int n11 = fem_row_stride(2) + 1;           // single interior node (1,1)
-            if (threadIdx.x == 0) L.e[n11] = L.rhs[n11] * L.iD[n11];
+            if (threadIdx.x == 0) L.e[n11] = L.rhs[n11] * inv_diag<Real, fem_row_stride(2)>(L, n11);
             phase_sync<WARP>();
         } else {
-            Lv<Real> C = level_ptrs<Real, N, NL / 2>(arena);
+            Lv<Real> C = level_ptrs<Real, N, NL / 2, CP>(arena);
             smooth_color<Real, NL, T>(L, 1);   // red pre-sweep done by the restriction above
             phase_sync<WARP>();
             restrict_red<Real, NL / 2, T>(L, C);
             phase_sync<WARP>();
-            vcycle_coarse<Real, N, NL / 2, T, WARP>(arena, dinv);
+            vcycle_coarse<Real, N, NL / 2, T, WARP, CP>(arena, dinv);
             black_prolong<Real, NL, T>(L, C.e);
             phase_sync<WARP>();
             smooth_color<Real, NL, T>(L, 0);
@@ -449,6 +477,21 @@ __device__ void setup_levels(Real* arena, Real* stage, bool ping) {
     }
 }
 
+// compact hierarchy: coefficients of coarse level NL from kappa in kin, coarser kappa into kout,
+// then recurse with the buffers swapped (no stored inverse diagonal)
+template <typename Real, int N, int NL, int T>
+__device__ void setup_levels_cp(Real* arena, Real* kin, Real* kout) {
+    Lv<Real> L = level_ptrs<Real, N, NL, true>(arena);
+    build_coeffs<Real, NL, T>(L, kin);
+    if constexpr (NL > 2) {
+        coarsen_kappa<Real, NL / 2, T>(kin, kout);
+        __syncthreads();
+        setup_levels_cp<Real, N, NL / 2, T>(arena, kout, kin);
+    } else {
+        __syncthreads();
+    }
+}
+
 template <typename Real, int N>
 struct Fine {
     static constexpr int M = N - 1, S = fem_row_stride(N), NI = M * M;
@@ -466,21 +509,24 @@ __host__ __device__ constexpr int solve_smem_reals(int N, int T) {
 
 // ---- the kernel ----------------------------------------------------------------------
 // the whole solve of particle p of a.n, by one thread block (all threads call it)
-template <typename Real, int N, int T>
+// CP: compact hierarchy (mixed path, kappa from the synthesis) with the refinement state at
+// ref_ext (device memory) instead of shared memory
+template <typename Real, int N, int T, bool CP = false>
 __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Real* arena, double (*red_buf)[64],
-                                               Real* theta_s) {
+                                               Real* theta_s, Real* ref_ext = nullptr) {
     constexpr int S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
     constexpr int NPT = fine_slots(N, T);              // slots per thread (colour_node positions)
     constexpr int NPH = NPT / 2;                       // per colour
     constexpr int E = 2 * N * N;
     const int tid = threadIdx.x;
 
-    Lv<Real> F = level_ptrs<Real, N, N>(arena);
+    Lv<Real> F = level_ptrs<Real, N, N, CP>(arena);
     Real* stage = F.e;     // e, res, p of the fine level are contiguous: 3*lvl_size(N) >= 2.5 N^2
+                           // (compact: e and p, 2*lvl_size(N) >= 2 N^2)
 
     // 1) kappa = exp(u) on every fine triangle: read from the tensor-core synthesis, or
     //    u = theta . Psi computed here (FP64 path)
-    if (a.kappa) {
+    if (CP || a.kappa) {
         const float* kp = a.kappa + (size_t)p * E;
         for (int e = tid; e < E; e += T) stage[e] = (Real)kp[e];
     } else {
@@ -496,12 +542,22 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     __syncthreads();
 
     // 2) stencil hierarchy
-    setup_levels<Real, N, N, T>(arena, stage, true);
-    zero_rings<Real, N, N, T>(arena);
+    if constexpr (CP) {
+        // kappa ping-pongs between the fine level's e/p storage and its inverse-diagonal storage,
+        // which is filled last
+        build_coeffs<Real, N, T>(F, stage);
+        coarsen_kappa<Real, N / 2, T>(stage, F.iD);
+        __syncthreads();
+        setup_levels_cp<Real, N, N / 2, T>(arena, F.iD, stage);
+        build_diag<Real, N, T>(F);
+    } else {
+        setup_levels<Real, N, N, T>(arena, stage, true);
+    }
+    zero_rings<Real, N, N, T, CP>(arena);
     __syncthreads();
-    Real* dinv = arena + arena_size(N) + 4 * NPT * T;
+    Real* dinv = CP ? arena + arena_size_cp(N) : arena + arena_size(N) + 4 * NPT * T;
     if constexpr (direct_level<Real>(N) != 0)
-        dense_setup<Real, direct_level<Real>(N), T>(level_ptrs<Real, N, direct_level<Real>(N)>(arena), dinv);
+        dense_setup<Real, direct_level<Real>(N), T>(level_ptrs<Real, N, direct_level<Real>(N), CP>(arena), dinv);
 
     // fine nodes owned by this thread, one packed int each: bits 0-12 node index n, 13-23 the
     // coarse node c under it ((j/2) SC + i/2), 24-25 (i & 1) + 2 (j & 1), 26 red, 27 valid.
@@ -527,7 +583,7 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     // numbers on the mixed path so that no FP64 instruction runs in the solve. They are touched
     // once per refinement pass, so they live in shared memory after the arena ([4][NPT][T]:
     // x hi, x lo, r hi, r lo), conflict-free per slot.
-    Real* ref = arena + arena_size(N);
+    Real* ref = CP ? ref_ext : arena + arena_size(N);
     auto XH = [&](int q) -> Real& { return ref[(0 * NPT + q) * T + tid]; };
     auto XL = [&](int q) -> Real& { return ref[(1 * NPT + q) * T + tid]; };
     auto RH = [&](int q) -> Real& { return ref[(2 * NPT + q) * T + tid]; };
@@ -546,7 +602,7 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     int parity = 0;
     int total_it = 0;
     bool converged = false;
-    Lv<Real> C1 = level_ptrs<Real, N, N / 2>(arena);
+    Lv<Real> C1 = level_ptrs<Real, N, N / 2, CP>(arena);
     Real* P = F.rhs;   // fine-level CG direction (the fine rhs is r, held in registers)
 
     for (int pass = 0; pass < a.max_outer && !converged; ++pass) {
@@ -589,7 +645,7 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
             __syncthreads();
             restrict_gather<Real, N / 2, T>(F.res, C1);
             __syncthreads();
-            vcycle_coarse<Real, N, N / 2, T>(arena, dinv);
+            vcycle_coarse<Real, N, N / 2, T, false, CP>(arena, dinv);
 #pragma unroll
             for (int q = NPH; q < NPT; ++q) {
                 z[q] = Real(0);
@@ -1059,6 +1115,25 @@ fem_eval_kernel(FemArgs a) {
     solve_particle<Real, N, T>(a, blockIdx.x, reinterpret_cast<Real*>(smem_raw), red_buf, theta_s);
 }
 
+// compact form at 1/h = 64 (mixed): two blocks per SM, persistent over the particles; each block
+// keeps its refinement state in its own slice of ref_scratch (L2-resident)
+template <int N, int T>
+__global__ void __launch_bounds__(T, 2) fem_eval_compact(FemArgs a, float* ref_scratch, int* counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red_buf[2][64];
+    __shared__ int item_s;
+    float* ref = ref_scratch + (size_t)blockIdx.x * (4 * fine_slots(N, T) * T);
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = item_s;
+        __syncthreads();
+        if (item >= a.n) break;
+        solve_particle<float, N, T, true>(a, item, reinterpret_cast<float*>(smem_raw), red_buf, nullptr, ref);
+        __syncthreads();
+    }
+}
+
 // persistent form: grid-sized blocks pull (group, particle) items from a device counter; every
 // group is one problem's launch arguments at this level size (many independent inverse problems
 // in one launch)
@@ -1144,7 +1219,46 @@ cudaError_t launch_global_multi(const FemArgs* groups, const int* offsets, const
     return cudaGetLastError();
 }
 
+template <int T>
+cudaError_t launch_compact(const FemArgs& a, float* ref_scratch, int blocks, int* counter, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (size_t)(arena_size_cp(64) + dense_reals<float>(64));
+    cudaError_t e = cudaFuncSetAttribute(fem_eval_compact<64, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fem_eval_compact<64, T><<<blocks, T, smem, st>>>(a, ref_scratch, counter);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+int fem_compact_blocks(int T) {
+    // resident blocks of the 512-thread compact kernel, queried once per device
+    static int cached[64] = {0};
+    if (T != 512) return 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = sizeof(float) * (size_t)(arena_size_cp(64) + dense_reals<float>(64));
+    cudaFuncSetAttribute(fem_eval_compact<64, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_compact<64, 512>, 512, smem);
+    const int blocks = sms * std::max(1, per_sm);
+    if (dev >= 0 && dev < 64) cached[dev] = blocks;
+    return blocks;
+}
+size_t fem_compact_ref_floats(int T) { return (size_t)4 * fine_slots(64, T) * T; }
+
+cudaError_t fem_eval_compact_launch(const FemArgs& a, int T, float* ref_scratch, int blocks, int* counter,
+                                    cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    if (a.N != 64 || a.precision != SMC_MIXED || !a.kappa) return cudaErrorInvalidValue;
+    const int grid = std::max(1, std::min(a.n, blocks));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    if (T == 512) return launch_compact<512>(a, ref_scratch, grid, counter, st);
+    return cudaErrorInvalidValue;
+}
 
 size_t fem_global_slice(int N) {
     const int NI = (N - 1) * (N - 1);
@@ -1230,7 +1344,7 @@ std::vector<int> fem_block_sizes(int N, int precision) {
             case 8: return {64, 32};
             case 16: return {128, 64};
             case 32: return {256, 512};
-            case 64: return {512, 1024};
+            case 64: return {512, 1024, -512};   // -512: compact form, two blocks per SM
             case 128: return {1024};
             case 256: return {1024};
         }

@@ -1,7 +1,9 @@
 """One small launch of the likelihood kernel, for profiler captures (ncu) of a single kernel.
 
 python -m paper_1709_09763_gb300.profile_case [--inv-h 64] [--J 304] [--launches 2] [--precision mixed]
-Uses the MLS^2MC workload's KL settings and observation grid with seeded particles.
+                                             [--block 0]
+Uses the MLS^2MC workload's KL settings and observation grid with seeded particles; --block forces
+the threads per particle (0: the library default; -512 at 1/h = 64: the compact form).
 """
 import argparse
 import json
@@ -19,6 +21,7 @@ def main():
     ap.add_argument("--J", type=int, default=304)
     ap.add_argument("--launches", type=int, default=2)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--block", type=int, default=0)
     a = ap.parse_args()
     import torch
     build.build()
@@ -28,6 +31,8 @@ def main():
         d = json.load(f)
     prec = native.SMC_MIXED if a.precision == "mixed" else native.SMC_FP64
     h = native.Handle([a.inv_h], w.K, wl.obs_grid(7), d["y"], d["sigma"], corr_len=w.corr_len, precision=prec)
+    if a.block:
+        h.set_block_size(0, a.block)
     th = torch.from_numpy(wl.particles(a.J, w.K, 5)).cuda()
     G = torch.empty((a.J, 49), dtype=torch.float64, device="cuda")
     Phi = torch.empty(a.J, dtype=torch.float64, device="cuda")
@@ -38,7 +43,7 @@ def main():
     torch.cuda.synchronize()
     its = it.cpu().numpy()
     assert (its > 0).all(), "non-converged solve"
-    print(json.dumps({"inv_h": a.inv_h, "J": a.J, "mean_iters": float(np.mean(its))}))
+    print(json.dumps({"inv_h": a.inv_h, "J": a.J, "block": a.block, "mean_iters": float(np.mean(its))}))
 
 
 if __name__ == "__main__":
