@@ -200,12 +200,12 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def batched_measurement(native, wl, torch, dev, reps=5):
-    """64 independent problems of uneven size (finest 1/h in {16, 32, 64, 128}), each evaluating its J
-    particles on its finest level:
+def batched_measurement(native, wl, torch, dev, reps=5, n_problems=64, max_inv_h=128, j_range=(500, 8000)):
+    """n_problems independent problems of uneven size (finest 1/h in {16, 32, 64, 128} up to
+    max_inv_h, J log-uniform in j_range), each evaluating its J particles on its finest level:
     sequential per-problem launches against one batch (persistent launch per level size) replayed
     as a CUDA graph. Data: y = G(theta_true) on the finest level + 1 % noise, from the library."""
-    specs = wl.batched_uneven(max_inv_h=128)
+    specs = wl.batched_uneven(n_problems=n_problems, max_inv_h=max_inv_h, j_range=j_range)
     stream = torch.cuda.Stream(dev)
     obs = wl.obs_grid(7)
     hs, th, ph, it = [], [], [], []
@@ -439,6 +439,9 @@ def main():
                "mls2mc_surrogate_workload": compare(wda, dda, tuple(wda.inv_h))}
 
     batched = None if args.no_run else batched_measurement(native, wl, torch, dev)
+    # many small problems: each per-problem launch fills a fraction of the GPU
+    batched_small = None if args.no_run else batched_measurement(native, wl, torch, dev, n_problems=256,
+                                                                 max_inv_h=64, j_range=(16, 256))
 
     t = reduce_max_over_ranks([ms, e2e] + [float(np.mean(x)) for x in level_ms], dist if world > 1 else None, dev)
     ms, e2e = t[0], t[1]
@@ -487,6 +490,8 @@ def main():
             line["seconds_to_posterior"] = run
         if batched is not None:
             line["batched_uneven"] = batched
+        if batched_small is not None:
+            line["batched_small_problems"] = batched_small
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

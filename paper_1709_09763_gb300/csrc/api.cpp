@@ -205,9 +205,9 @@ int Handle::eval_device(int level, int n, const double* theta, double* G, double
         }
         const int T = tuned_block(L.N, precision);
         if (T < 0) {   // compact form: persistent blocks with their refinement state in device memory
-            const int blocks = fem_compact_blocks(-T);
-            if (blocks <= 0) return fail(SMC_EINVAL, "no compact form with %d threads", -T);
-            const size_t need = (size_t)blocks * fem_compact_ref_floats(-T);
+            const int blocks = fem_compact_blocks(L.N, -T);
+            if (blocks <= 0) return fail(SMC_EINVAL, "no compact form with %d threads at 1/h = %d", -T, L.N);
+            const size_t need = (size_t)blocks * fem_compact_ref_floats(L.N, -T);
             if (need > cp_cap) {
                 cudaFree(cp_scratch);
                 cp_scratch = nullptr;

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <cstdlib>
 #include <map>
 #include <string>
 #include <vector>
@@ -158,7 +159,9 @@ int smc_batch_eval(smc_batch* bb, const int* level, const int* n, const double* 
                 Batch::Group G;
                 G.N = L.N;
                 G.precision = h->precision;
-                G.T = std::max(0, h->block_size(L.N));   // the persistent form has no compact variant
+                // the persistent form has no compact variant: a compact size -T runs with T threads,
+                // the same arithmetic
+                G.T = std::abs(h->block_size(L.N));
                 b->groups.push_back(G);
             }
             Batch::Group& G = b->groups[gidx[key]];

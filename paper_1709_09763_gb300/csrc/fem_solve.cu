@@ -1115,10 +1115,10 @@ fem_eval_kernel(FemArgs a) {
     solve_particle<Real, N, T>(a, blockIdx.x, reinterpret_cast<Real*>(smem_raw), red_buf, theta_s);
 }
 
-// compact form at 1/h = 64 (mixed): two blocks per SM, persistent over the particles; each block
-// keeps its refinement state in its own slice of ref_scratch (L2-resident)
-template <int N, int T>
-__global__ void __launch_bounds__(T, 2) fem_eval_compact(FemArgs a, float* ref_scratch, int* counter) {
+// compact form (mixed, kappa from the synthesis): MINB blocks per SM, persistent over the
+// particles; each block keeps its refinement state in its own slice of ref_scratch (L2-resident)
+template <int N, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) fem_eval_compact(FemArgs a, float* ref_scratch, int* counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_buf[2][64];
     __shared__ int item_s;
@@ -1219,44 +1219,64 @@ cudaError_t launch_global_multi(const FemArgs* groups, const int* offsets, const
     return cudaGetLastError();
 }
 
-template <int T>
+// compiled compact configurations: blocks per SM that the registers are sized for (0: none)
+constexpr int compact_min_blocks(int N, int T) {
+    return (N == 64 && T == 512) ? 2 : (N == 32 && T == 256) ? 4 : 0;
+}
+
+template <int N>
+constexpr size_t compact_smem() {
+    return sizeof(float) * (size_t)(arena_size_cp(N) + dense_reals<float>(N));
+}
+
+template <int N, int T>
 cudaError_t launch_compact(const FemArgs& a, float* ref_scratch, int blocks, int* counter, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)(arena_size_cp(64) + dense_reals<float>(64));
-    cudaError_t e = cudaFuncSetAttribute(fem_eval_compact<64, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr int MINB = compact_min_blocks(N, T);
+    cudaError_t e = cudaFuncSetAttribute(fem_eval_compact<N, T, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)compact_smem<N>());
     if (e != cudaSuccess) return e;
-    fem_eval_compact<64, T><<<blocks, T, smem, st>>>(a, ref_scratch, counter);
+    fem_eval_compact<N, T, MINB><<<blocks, T, compact_smem<N>(), st>>>(a, ref_scratch, counter);
     count_launches(1);
     return cudaGetLastError();
 }
 
+template <int N, int T>
+int compact_resident_blocks() {
+    constexpr int MINB = compact_min_blocks(N, T);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(fem_eval_compact<N, T, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)compact_smem<N>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_compact<N, T, MINB>, T, compact_smem<N>());
+    return sms * std::max(1, per_sm);
+}
+
 }  // namespace
 
-int fem_compact_blocks(int T) {
-    // resident blocks of the 512-thread compact kernel, queried once per device
-    static int cached[64] = {0};
-    if (T != 512) return 0;
+int fem_compact_blocks(int N, int T) {
+    // resident blocks of a compact kernel, queried once per device and configuration
+    static int cached[64][2] = {};
+    const int c = (N == 64 && T == 512) ? 0 : (N == 32 && T == 256) ? 1 : -1;
+    if (c < 0) return 0;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = sizeof(float) * (size_t)(arena_size_cp(64) + dense_reals<float>(64));
-    cudaFuncSetAttribute(fem_eval_compact<64, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_compact<64, 512>, 512, smem);
-    const int blocks = sms * std::max(1, per_sm);
-    if (dev >= 0 && dev < 64) cached[dev] = blocks;
+    if (dev >= 0 && dev < 64 && cached[dev][c] > 0) return cached[dev][c];
+    const int blocks = c == 0 ? compact_resident_blocks<64, 512>() : compact_resident_blocks<32, 256>();
+    if (dev >= 0 && dev < 64) cached[dev][c] = blocks;
     return blocks;
 }
-size_t fem_compact_ref_floats(int T) { return (size_t)4 * fine_slots(64, T) * T; }
+size_t fem_compact_ref_floats(int N, int T) { return (size_t)4 * fine_slots(N, T) * T; }
 
 cudaError_t fem_eval_compact_launch(const FemArgs& a, int T, float* ref_scratch, int blocks, int* counter,
                                     cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    if (a.N != 64 || a.precision != SMC_MIXED || !a.kappa) return cudaErrorInvalidValue;
+    if (a.precision != SMC_MIXED || !a.kappa || compact_min_blocks(a.N, T) == 0) return cudaErrorInvalidValue;
     const int grid = std::max(1, std::min(a.n, blocks));
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    if (T == 512) return launch_compact<512>(a, ref_scratch, grid, counter, st);
+    if (a.N == 64 && T == 512) return launch_compact<64, 512>(a, ref_scratch, grid, counter, st);
+    if (a.N == 32 && T == 256) return launch_compact<32, 256>(a, ref_scratch, grid, counter, st);
     return cudaErrorInvalidValue;
 }
 
@@ -1343,8 +1363,8 @@ std::vector<int> fem_block_sizes(int N, int precision) {
             case 4: return {32};
             case 8: return {64, 32};
             case 16: return {128, 64};
-            case 32: return {256, 512};
-            case 64: return {512, 1024, -512};   // -512: compact form, two blocks per SM
+            case 32: return {256, 512, -256};   // -256: compact form, four blocks per SM
+            case 64: return {512, 1024, -512};  // -512: compact form, two blocks per SM
             case 128: return {1024};
             case 256: return {1024};
         }

@@ -47,7 +47,7 @@ struct Handle {
 
     // large levels: per-block hierarchy slices in global memory (fem_solve.cu)
     float* big_scratch = nullptr;
-    float* cp_scratch = nullptr;   // refinement state of the compact 1/64 form's blocks
+    float* cp_scratch = nullptr;   // refinement state of the compact form's blocks
     size_t cp_cap = 0;
     size_t big_cap = 0;
     int* big_counter = nullptr;

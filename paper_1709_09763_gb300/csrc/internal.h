@@ -67,12 +67,12 @@ cudaError_t fem_eval_global_multi_launch(int N, const FemArgs* groups, const int
 // items to the blocks
 cudaError_t fem_eval_persistent_launch(int N, int precision, int T, const FemArgs* groups, const int* offsets,
                                        const int* item_group, int total, int* counter, cudaStream_t st);
-// compact form of the 1/64 mixed solve (block size -512 of fem_block_sizes, T = 512 threads): two
-// blocks per SM, fem_compact_blocks(T) persistent blocks (0 for an unsupported T) with
-// fem_compact_ref_floats(T) floats of device scratch each for the refinement state; *counter
-// (device) is reset by the launch
-int fem_compact_blocks(int T);
-size_t fem_compact_ref_floats(int T);
+// compact form of the mixed solve (negative block sizes of fem_block_sizes: -512 at 1/h = 64,
+// -256 at 1/h = 32): two or four blocks per SM, fem_compact_blocks(N, T) persistent blocks
+// (0 for a configuration that is not compiled) with fem_compact_ref_floats(N, T) floats of device
+// scratch each for the refinement state; *counter (device) is reset by the launch
+int fem_compact_blocks(int N, int T);
+size_t fem_compact_ref_floats(int N, int T);
 cudaError_t fem_eval_compact_launch(const FemArgs& a, int T, float* ref_scratch, int blocks, int* counter,
                                     cudaStream_t st);
 bool fem_level_supported(int N, int precision);

@@ -82,11 +82,12 @@ def particles(J, K, seed):
     return standard_normals((J, K), seed)
 
 
-def batched_uneven(n_problems=64, seed=7, max_inv_h=64):
+def batched_uneven(n_problems=64, seed=7, max_inv_h=64, j_range=(500, 8000)):
     """Independent problems of uneven size: finest mesh 1/h drawn from {16, 32, 64} (and 128 when
     max_inv_h allows), hierarchy from 1/8 up to it, K from {16, 32, 64} (correlation length 0.3,
-    0.1, 0.1), J log-uniform in [500, 8000]; problem p uses theta_true seed 100 + p and noise seed
-    200 + p. Returns a list of dicts (levels, K, corr_len, J, seed_true, seed_noise)."""
+    0.1, 0.1), J log-uniform in j_range (default [500, 8000]); problem p uses theta_true seed
+    100 + p and noise seed 200 + p. Returns a list of dicts (levels, K, corr_len, J, seed_true,
+    seed_noise)."""
     rng = np.random.default_rng(seed)
     finest = [h for h in (16, 32, 64, 128) if h <= max_inv_h]
     out = []
@@ -94,7 +95,7 @@ def batched_uneven(n_problems=64, seed=7, max_inv_h=64):
         f = int(rng.choice(finest))
         K = int(rng.choice([16, 32, 64]))
         lc = 0.3 if K == 16 else 0.1
-        J = int(round(np.exp(rng.uniform(np.log(500), np.log(8000)))))
+        J = int(round(np.exp(rng.uniform(np.log(j_range[0]), np.log(j_range[1])))))
         levels = tuple(h for h in (8, 16, 32, 64, 128) if h <= f)
         out.append(dict(levels=levels, K=K, corr_len=lc, J=J, seed_true=100 + p, seed_noise=200 + p))
     return out

@@ -145,7 +145,7 @@ def test_every_block_size_and_autotuner(prec):
     levels = [8, 16, 32, 64] if prec == native.SMC_MIXED else [8, 16, 32]
     tol = 1e-6 if prec == native.SMC_MIXED else 1e-10
     h = native.Handle(levels, w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, precision=prec)
-    sizes = {8: [64, 32], 16: [128, 64], 32: [256, 512], 64: [512, 1024, -512]} if prec == native.SMC_MIXED else \
+    sizes = {8: [64, 32], 16: [128, 64], 32: [256, 512, -256], 64: [512, 1024, -512]} if prec == native.SMC_MIXED else \
         {8: [64], 16: [128, 256], 32: [256, 512]}
     theta = wl.particles(9, w.K, 31)
     for l, N in enumerate(levels):
@@ -217,26 +217,27 @@ def test_full_size_sampled_parity_large_workloads(name):
     assert _phi_ok(Phi.cpu().numpy()[idx], Phir, Gr, d["sigma"], 1e-6)
 
 
-def test_compact_form_equals_shared_memory_form():
-    """The compact 1/64 form (two blocks per SM: five fine-level arrays, four per coarse level,
+@pytest.mark.parametrize("inv_h,T", [(64, 512), (32, 256)])
+def test_compact_form_equals_shared_memory_form(inv_h, T):
+    """The compact form (several blocks per SM: five fine-level arrays, four per coarse level,
     refinement state in device memory) does the same arithmetic as the form with the whole state
-    in shared memory: with the same threads per particle the potentials are bit-identical, at the
-    benchmark's launch size."""
+    in shared memory: with the same threads per particle the potentials and iteration counts are
+    bit-identical, at the benchmark's launch size."""
     import torch
     w = wl.WORKLOADS["mls2mc_mixed_h8_64"]
     d = _data(w.name)
-    h = native.Handle([64], w.K, wl.obs_grid(7), d["y"], d["sigma"], corr_len=w.corr_len,
+    h = native.Handle([inv_h], w.K, wl.obs_grid(7), d["y"], d["sigma"], corr_len=w.corr_len,
                       precision=native.SMC_MIXED)
     theta = torch.from_numpy(wl.particles(w.J, w.K, 808)).cuda()
     out = {}
-    for T in (512, -512):
-        h.set_block_size(0, T)
+    for B in (T, -T):
+        h.set_block_size(0, B)
         Phi = torch.empty(w.J, dtype=torch.float64, device="cuda")
         it = torch.empty(w.J, dtype=torch.int32, device="cuda")
         h.eval_likelihood_device(0, w.J, theta.data_ptr(), 0, Phi.data_ptr(), it.data_ptr(),
                                  torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         assert int(it.min()) > 0
-        out[T] = (Phi.cpu().numpy(), it.cpu().numpy())
+        out[B] = (Phi.cpu().numpy(), it.cpu().numpy())
     h.set_block_size(0, 0)
-    assert np.array_equal(out[512][0], out[-512][0]) and np.array_equal(out[512][1], out[-512][1])
+    assert np.array_equal(out[T][0], out[-T][0]) and np.array_equal(out[T][1], out[-T][1])
