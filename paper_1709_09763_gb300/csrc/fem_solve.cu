@@ -30,8 +30,6 @@
 // registers: every fine node belongs to one thread for the whole solve.
 #include <cuda_runtime.h>
 
-#include <type_traits>
-
 #include <cmath>
 #include <algorithm>
 #include <cstdint>
@@ -79,12 +77,16 @@ __device__ __forceinline__ Lv<Real> level_ptrs(Real* arena) {
     }
 }
 
+// 1 / x rounded to nearest (the same value as the IEEE division 1 / x)
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+
 // inverse stencil diagonal at interior node n: stored, or formed from the four edge weights
 // (the same expression and order as where it is stored)
 template <typename Real, int S>
 __device__ __forceinline__ Real inv_diag(const Lv<Real>& L, int n) {
     if (L.iD) return L.iD[n];
-    return Real(1) / (L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S]);
+    return recip(L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S]);
 }
 
 // sum of a_nb * v_nb over the four stencil neighbours of padded node n (row stride S)
@@ -121,34 +123,6 @@ __device__ __forceinline__ void block_sum(Acc& a, double* buf_raw) {
 #pragma unroll
     for (int i = 0; i < T / 32; ++i) s += buf[i];
     a = s;
-}
-
-template <int T, typename Acc>
-__device__ __forceinline__ void block_sum3(Acc& a, Acc& b, Acc& c, double* buf_raw) {
-    Acc* buf = reinterpret_cast<Acc*>(buf_raw);   // 3 x 16 entries used (T <= 512 for float, 256 for double)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, off);
-        b += __shfl_xor_sync(0xffffffffu, b, off);
-        c += __shfl_xor_sync(0xffffffffu, c, off);
-    }
-    constexpr int NW = T / 32;
-    if ((threadIdx.x & 31) == 0) {
-        buf[threadIdx.x >> 5] = a;
-        buf[NW + (threadIdx.x >> 5)] = b;
-        buf[2 * NW + (threadIdx.x >> 5)] = c;
-    }
-    __syncthreads();
-    Acc sa = 0, sb = 0, sc = 0;
-#pragma unroll
-    for (int i = 0; i < NW; ++i) {
-        sa += buf[i];
-        sb += buf[NW + i];
-        sc += buf[2 * NW + i];
-    }
-    a = sa;
-    b = sb;
-    c = sc;
 }
 
 // ---- error-free transformations (Knuth TwoSum, Dekker), double-float accumulation ----
@@ -439,7 +413,7 @@ __device__ __forceinline__ void build_diag(const Lv<Real>& L) {
         const int j = n / S, i = n - j * S;
         Real d = 0;
         if (i > 0 && j > 0 && i < NL && j < NL) d = L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S];
-        L.iD[n] = (d == Real(0)) ? Real(1) : Real(1) / d;   // boundary entries are never used
+        L.iD[n] = (d == Real(0)) ? Real(1) : recip(d);   // boundary entries are never used
     }
 }
 

@@ -157,6 +157,11 @@ def test_every_block_size_and_autotuner(prec):
         h.set_block_size(l, 0)
     with pytest.raises(native.SmcError):
         h.set_block_size(0, 96)
+    with pytest.raises(native.SmcError):   # no compact form at 1/8, none with 128 threads at 1/32
+        h.set_block_size(0, -32)
+    if prec == native.SMC_MIXED:
+        with pytest.raises(native.SmcError):
+            h.set_block_size(2, -128)
     chosen, ms = h.autotune(256)
     assert all(c in sizes[N] for c, N in zip(chosen, levels)) and all(m > 0 for m in ms)
     for l in range(len(levels)):
