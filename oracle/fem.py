@@ -16,6 +16,8 @@ factorisation (scipy SuperLU), so the only error is FP64 rounding.
 """
 import functools
 
+import math
+
 import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
@@ -114,6 +116,16 @@ def load_vector(N, f=None):
         for a in range(3):
             b[tri[a]] += area / 3.0 * sum(0.5 * fm[q] for q in touching[a])
     return b
+
+
+def nine_sources(x, y):
+    """Source term of Example 5.1 (Sec. 5): nine smoothed point sources, the products of 1-D
+    Gaussian densities N(x1; 0.25 n, 0.001) N(x2; 0.25 m, 0.001), n, m = 1..3."""
+    var = 0.001
+    norm = 1.0 / math.sqrt(2.0 * math.pi * var)
+    gx = sum(norm * math.exp(-(x - 0.25 * n) ** 2 / (2.0 * var)) for n in (1, 2, 3))
+    gy = sum(norm * math.exp(-(y - 0.25 * m) ** 2 / (2.0 * var)) for m in (1, 2, 3))
+    return gx * gy
 
 
 def interior_nodes(N):

@@ -13,14 +13,23 @@ import numpy as np
 
 from . import fem
 from . import kl
+from . import matern
 
 
 class Level:
-    """One discretisation level: mesh N = 1/h, KL table and observation operator."""
+    """One discretisation level: mesh N = 1/h, KL table and observation operator.
 
-    def __init__(self, N, corr_len, variance, K, obs_xy, f=None):
+    cov: "sep_exp" (separable exponential, analytic KL) or "matern" (nu = 3/2, Nystrom KL);
+    f: source term f(x, y), None for f = 1."""
+
+    def __init__(self, N, corr_len, variance, K, obs_xy, f=None, cov="sep_exp"):
         self.N = N
-        self.psi = kl.kl_table(N, corr_len, variance, K)
+        if cov == "sep_exp":
+            self.psi = kl.kl_table(N, corr_len, variance, K)
+        elif cov == "matern":
+            self.psi = matern.kl_table(N, corr_len, variance, K)
+        else:
+            raise ValueError("cov must be 'sep_exp' or 'matern'")
         self.O = fem.observation_operator(N, obs_xy)
         self.f = f
 

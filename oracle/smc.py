@@ -90,6 +90,17 @@ def pcn_propose(theta, xi, s):
     return math.sqrt(1.0 - s * s) * theta + s * xi
 
 
+def rwm_propose(theta, xi, s):
+    """theta' = theta + s xi: the Gaussian random walk of Sec. 5 (proposal covariance s^2 I,
+    s^2 = 2.38^2 / N_sto in the paper)."""
+    return theta + s * xi
+
+
+def log_prior_ratio(theta_new, theta):
+    """log mu0(theta') - log mu0(theta) for mu0 = N(0, I), one value per row."""
+    return -0.5 * (np.sum(theta_new * theta_new, axis=1) - np.sum(theta * theta, axis=1))
+
+
 class Sampler:
     """MLS^2MC (Sec. 4) on a hierarchy of levels; single-level SMC when there is one level.
 
@@ -99,7 +110,7 @@ class Sampler:
     """
 
     def __init__(self, evaluate, n_levels, K, J, J_tilde=100, n_mcmc=5, tau_star=1.0,
-                 tau_lu=None, eps=1e-6, s_pcn=0.2, seed=0, theta0=None):
+                 tau_lu=None, eps=1e-6, s_pcn=0.2, seed=0, theta0=None, proposal="pcn"):
         self.evaluate_raw = evaluate
         self.L = n_levels
         self.K = K
@@ -110,6 +121,9 @@ class Sampler:
         self.tau_lu = tau_star if tau_lu is None else tau_lu
         self.eps = eps
         self.s = s_pcn
+        if proposal not in ("pcn", "rwm"):
+            raise ValueError("proposal must be 'pcn' or 'rwm'")
+        self.proposal = proposal
         self.seed = seed
         self.evals = np.zeros(n_levels, dtype=np.int64)
         self.level = 0
@@ -143,15 +157,21 @@ class Sampler:
         return delta, anc, cv(w)
 
     def _mcmc(self, target):
-        """n_mcmc pCN steps; target(theta) -> (Phi_target, caches) evaluates the proposal."""
+        """n_mcmc pCN (or random-walk) Metropolis steps; target(theta) -> (Phi_target, caches)
+        evaluates the proposal."""
         acc = 0
         phi_t, caches = target(None)
         for _ in range(self.n_mcmc):
             xi = philox.normals(self.J, self.K, self.mcmc_event, philox.PURPOSE_PCN_XI, self.seed)
             u = philox.uniforms_open(self.J, self.mcmc_event, philox.PURPOSE_PCN_U, self.seed)
-            prop = pcn_propose(self.theta, xi, self.s)
-            phi_t_new, caches_new = target(prop)
-            ok = np.log(u) < -(phi_t_new - phi_t)
+            if self.proposal == "pcn":
+                prop = pcn_propose(self.theta, xi, self.s)
+                phi_t_new, caches_new = target(prop)
+                ok = np.log(u) < -(phi_t_new - phi_t)
+            else:   # random walk: the prior ratio enters the acceptance
+                prop = rwm_propose(self.theta, xi, self.s)
+                phi_t_new, caches_new = target(prop)
+                ok = np.log(u) < -(phi_t_new - phi_t) + log_prior_ratio(prop, self.theta)
             self.theta[ok] = prop[ok]
             phi_t = np.where(ok, phi_t_new, phi_t)
             for c, cn in zip(caches, caches_new):
