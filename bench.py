@@ -397,7 +397,8 @@ def main():
             hr = native.Handle(inv_h, wk.K, ob, dk["y"], dk["sigma"], corr_len=wk.corr_len, variance=wk.variance,
                                J=wk.J, J_tilde=wk.J_tilde, n_mcmc=wk.n_mcmc, s_pcn=wk.s_pcn,
                                tau_star=wk.tau_star, precision=native.SMC_MIXED, seed=seed,
-                               stream=stream.cuda_stream, surrogate=surrogate)
+                               stream=stream.cuda_stream, surrogate=surrogate, cov=wk.cov, source=wk.source,
+                               proposal=wk.proposal)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             hr.run()
@@ -437,6 +438,31 @@ def main():
         dda = load_data(wda.name)
         run = {"mls2mc": compare(w, d, tuple(w.inv_h)), "smc_finest": compare(w, d, (w.inv_h[-1],), R=6),
                "mls2mc_surrogate_workload": compare(wda, dda, tuple(wda.inv_h))}
+
+        def paper_example(name, R=3):
+            """Examples 5.1/5.2 (Matern prior, nine sources, one random-walk step per update):
+            MLS^2MC on 1/8..1/128 against single-level SMC on 1/128, R seeded runs each; cost in
+            the paper's unit sum_l evals_l 4^(l - L) (one finest-level solve = 1)."""
+            wk, dk = wl.WORKLOADS[name], load_data(name)
+            res = {"workload": name, "levels_inv_h": list(wk.inv_h), "K": wk.K, "J": wk.J, "sigma": dk["sigma"],
+                   "tau_star": wk.tau_star, "proposal": wk.proposal}
+            for label, inv_h in (("mls2mc", tuple(wk.inv_h)), ("smc_finest", (wk.inv_h[-1],))):
+                runs = [one_run(wk, dk, inv_h, 0, wk.seed_sampler + 1000 * rank + 17 * r) for r in range(R)]
+                L = len(inv_h)
+                cost = [float(sum(e * 4.0 ** (l - (L - 1)) for l, e in enumerate(x["solves_per_level"]))) for x in runs]
+                res[label] = {"seconds_median": float(np.median([x["seconds"] for x in runs])),
+                              "seconds": [x["seconds"] for x in runs],
+                              "solves_per_level_mean": np.mean([x["solves_per_level"] for x in runs], axis=0).tolist(),
+                              "cost_finest_solves_mean": float(np.mean(cost)),
+                              "updates": [x["updates"] for x in runs],
+                              "log_evidence": [x["log_evidence"] for x in runs],
+                              "posterior_mean_first3": np.mean([x["mean"][:3] for x in runs], axis=0).tolist()}
+            res["speedup_mls2mc_vs_smc"] = res["smc_finest"]["seconds_median"] / res["mls2mc"]["seconds_median"]
+            res["cost_ratio_smc_over_mls2mc"] = (res["smc_finest"]["cost_finest_solves_mean"] /
+                                                 res["mls2mc"]["cost_finest_solves_mean"])
+            return res
+        run["paper_example_5_1"] = paper_example("example_5_1")
+        run["paper_example_5_2"] = paper_example("example_5_2")
 
     batched = None if args.no_run else batched_measurement(native, wl, torch, dev)
     # many small problems: each per-problem launch fills a fraction of the GPU

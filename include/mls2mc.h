@@ -49,6 +49,23 @@ extern "C" {
 #define SMC_FWD_FEM     0  /* the PDE of Sec. 5 */
 #define SMC_FWD_LINEAR  1  /* G_l(theta) = A_l theta (linear-Gaussian test problems) */
 
+/* prior covariance of the log-diffusion field (Sec. 5, Eq. truncKL) */
+#define SMC_COV_SEP_EXP 0  /* variance exp(-|x1-x1'|/lc - |x2-x2'|/lc); analytic KL pairs */
+#define SMC_COV_MATERN  1  /* Matern, smoothness 3/2: variance (1 + z) exp(-z), z = sqrt(6) |x - x'| / lc
+                              (Minasny & McBratney 2005); KL by the Nystrom method on the midpoint
+                              rule of a 32 x 32 cell grid, eigenvectors of definite parity under
+                              x -> 1-x and y -> 1-y (the library documentation gives the order and
+                              sign rules); K <= 64 */
+/* source term f of the PDE */
+#define SMC_SRC_ONE     0  /* f = 1 */
+#define SMC_SRC_NINE    1  /* the nine smoothed point sources of Example 5.1: products of 1-D Gaussian
+                              densities N(x1; 0.25 n, 0.001) N(x2; 0.25 m, 0.001), n, m = 1..3; load
+                              vector by the edge-midpoint rule on every triangle */
+/* Markov kernel of the sampler */
+#define SMC_PROP_PCN    0  /* theta' = sqrt(1 - s^2) theta + s xi */
+#define SMC_PROP_RWM    1  /* theta' = theta + s xi (random walk of Sec. 5; s^2 = 2.38^2 / K there),
+                              accepted with the prior ratio N(0, I) included */
+
 typedef struct {
     int n_levels;              /* N_L >= 1 */
     const int* inv_h;          /* [n_levels] 1/h_l, coarse to fine; powers of two in [4, 32] (FP64),
@@ -62,6 +79,8 @@ typedef struct {
     double sigma;              /* noise standard deviation, Gamma = sigma^2 I */
     int forward_kind;          /* SMC_FWD_FEM or SMC_FWD_LINEAR */
     const double* linear_A;    /* SMC_FWD_LINEAR only: [n_levels][n_obs][K] */
+    int cov_kind;              /* SMC_COV_SEP_EXP (0, the default) or SMC_COV_MATERN */
+    int source_kind;           /* SMC_SRC_ONE (0, the default) or SMC_SRC_NINE */
 } smc_problem_desc;
 
 typedef struct {
@@ -71,7 +90,7 @@ typedef struct {
     double tau_star;           /* target cv of the incremental weights (Eq. Eq_cv_opt) */
     double tau_lu;             /* cv^LU threshold of the update scheme (Eq. eq_updatescheme_final) */
     double eps;                /* minimum increment of beta or zeta (Eq. Eq_ESS_opt) */
-    double s_pcn;              /* pCN step size s: theta' = sqrt(1-s^2) theta + s xi */
+    double s_pcn;              /* step size s of the Markov kernel (see proposal) */
     int precision;             /* SMC_FP64 or SMC_MIXED */
     uint64_t seed;             /* Philox4x32-10 key */
     int max_iter;              /* cap on inner CG iterations per refinement pass */
@@ -82,6 +101,8 @@ typedef struct {
     int surrogate_train_steps; /* Adam steps of the first training round of a level (<= 0: 25; later rounds 1/4) */
     int surrogate_batch;       /* training minibatch, at most the pairs held (<= 0: 8192) */
     void* stream;              /* cudaStream_t used for all work, or NULL for the default stream */
+    int proposal;              /* SMC_PROP_PCN (0, the default) or SMC_PROP_RWM (step s = s_pcn; not with
+                                  the surrogate screen) */
 } smc_sampler_opts;
 
 typedef struct smc_handle smc_handle;

@@ -76,6 +76,7 @@ Handle::~Handle() {
         cudaFree(L.obs_w);
         cudaFree(L.linA);
         cudaFree(L.psi_split);
+        cudaFree(L.rhs);
     }
     cudaFree(synth_kappa_buf);
     cudaFree(synth_theta_buf);
@@ -155,6 +156,8 @@ FemArgs Handle::fem_args(int level, int n, const double* theta, double* G, doubl
     a.rtol_in = precision == SMC_MIXED ? 1e-4 : std::max(0.5 * rtol, 1e-14);
     a.max_outer = precision == SMC_MIXED ? 8 : 3;
     a.max_inner = max_iter;
+    a.rhs = L.rhs;
+    a.bnorm2 = L.bnorm2;
     return a;
 }
 
@@ -269,9 +272,18 @@ int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** 
         return bail(h->fail(SMC_EINVAL, "linear_A required for SMC_FWD_LINEAR"));
     if (O->precision != SMC_FP64 && O->precision != SMC_MIXED) return bail(h->fail(SMC_EINVAL, "unknown precision"));
     if (O->J < 0) return bail(h->fail(SMC_EINVAL, "J must be >= 0"));
+    if (O->proposal != SMC_PROP_PCN && O->proposal != SMC_PROP_RWM) return bail(h->fail(SMC_EINVAL, "unknown proposal"));
+    if (O->proposal == SMC_PROP_RWM && O->surrogate)
+        return bail(h->fail(SMC_EINVAL, "the surrogate screen runs with the pCN kernel only"));
     if (P->forward_kind == SMC_FWD_FEM) {
         if (!(P->corr_len > 0.0) || !(P->variance > 0.0))
             return bail(h->fail(SMC_EINVAL, "corr_len and variance must be positive"));
+        if (P->cov_kind != SMC_COV_SEP_EXP && P->cov_kind != SMC_COV_MATERN)
+            return bail(h->fail(SMC_EINVAL, "unknown cov_kind"));
+        if (P->cov_kind == SMC_COV_MATERN && P->K > matern_max_terms())
+            return bail(h->fail(SMC_EINVAL, "the Matern KL keeps at most %d terms", matern_max_terms()));
+        if (P->source_kind != SMC_SRC_ONE && P->source_kind != SMC_SRC_NINE)
+            return bail(h->fail(SMC_EINVAL, "unknown source_kind"));
         for (int l = 0; l < P->n_levels; ++l) {
             if (!fem_level_supported(P->inv_h[l], O->precision))
                 return bail(h->fail(SMC_EINVAL, "level %d: 1/h = %d not supported at this precision", l, P->inv_h[l]));
@@ -300,7 +312,8 @@ int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** 
         if (P->forward_kind == SMC_FWD_FEM) {
             L.N = P->inv_h[l];
             std::vector<double> psi, lam;
-            kl_table(L.N, P->corr_len, P->variance, P->K, psi, lam);
+            if (P->cov_kind == SMC_COV_MATERN) matern_kl_table(L.N, P->corr_len, P->variance, P->K, psi, lam);
+            else kl_table(L.N, P->corr_len, P->variance, P->K, psi, lam);
             std::vector<float> psi32(psi.begin(), psi.end());
             std::vector<int> idx;
             std::vector<double> wts;
@@ -313,6 +326,24 @@ int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** 
             }
             if (e == cudaSuccess) e = upload(&L.obs_idx, idx.data(), idx.size());
             if (e == cudaSuccess) e = upload(&L.obs_w, wts.data(), wts.size());
+            if (e == cudaSuccess && P->source_kind == SMC_SRC_NINE) {
+                std::vector<double> b;
+                nine_source_load(L.N, b, L.bnorm2);
+                if (O->precision == SMC_MIXED) {   // (hi, lo) float pairs: hi + lo = b to ~2^-48
+                    std::vector<float> b2(2 * b.size());
+                    for (size_t i = 0; i < b.size(); ++i) {
+                        b2[2 * i] = (float)b[i];
+                        b2[2 * i + 1] = (float)(b[i] - (double)b2[2 * i]);
+                    }
+                    float* d = nullptr;
+                    e = upload(&d, b2.data(), b2.size());
+                    L.rhs = d;
+                } else {
+                    double* d = nullptr;
+                    e = upload(&d, b.data(), b.size());
+                    L.rhs = d;
+                }
+            }
             L.lambda = lam;
             L.psi_host = std::move(psi);
         } else {

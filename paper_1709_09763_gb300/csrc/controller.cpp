@@ -277,7 +277,8 @@ const double* Handle::next_param_device() const {
     return reinterpret_cast<const double*>(reinterpret_cast<const char*>(smp->inc.state) + offsetof(IncState, next));
 }
 
-// n_mcmc pCN steps; zeta < 0: tempering target on `level`, else bridging target on level, level+1
+// n_mcmc pCN (or random-walk) Metropolis steps; zeta < 0: tempering target on `level`, else
+// bridging target on level, level+1
 int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, IncState* pending) {
     // networks are trained only for targets whose every level is worth screening
     if (opts.surrogate && forward_kind == SMC_FWD_FEM && da_worth(level) && (zeta < 0.0 || da_worth(level + 1))) {
@@ -286,7 +287,8 @@ int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, Inc
     }
     if (da_ready(level, zeta)) return mcmc_da(level, zeta, rate);
     Sampler* S = smp;
-    const double s = opts.s_pcn, c0 = std::sqrt(1.0 - s * s);
+    const bool rwm = opts.proposal == SMC_PROP_RWM;
+    const double s = opts.s_pcn, c0 = rwm ? 1.0 : std::sqrt(1.0 - s * s);
     CK(cudaMemsetAsync(S->n_acc, 0, 8, stream));
     for (int m = 0; m < opts.n_mcmc; ++m) {
         const uint32_t ev = (uint32_t)S->mcmc_event;
@@ -294,7 +296,7 @@ int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, Inc
         RC(smp_eval(level, S->J, S->theta_p, S->phi_cp));
         if (zeta >= 0.0) RC(smp_eval(level + 1, S->J, S->theta_p, S->phi_fp));
         CK(pcn_accept_launch(S->J, K, S->beta, beta_p, zeta, ev, opts.seed, S->theta, S->theta_p, S->phi_c,
-                             S->phi_cp, S->phi_f, S->phi_fp, S->n_acc, stream));
+                             S->phi_cp, S->phi_f, S->phi_fp, S->n_acc, rwm ? 1 : 0, stream));
         S->mcmc_event += 1;
     }
     unsigned long long acc = 0;

@@ -77,6 +77,17 @@ __device__ __forceinline__ Lv<Real> level_ptrs(Real* arena) {
     }
 }
 
+// load vector at node n from a table: FP64 values, or (hi, lo) float pairs with hi + lo = b
+__device__ __forceinline__ void load_rhs(const void* t, int n, double& hi, double& lo) {
+    hi = static_cast<const double*>(t)[n];
+    lo = 0.0;
+}
+__device__ __forceinline__ void load_rhs(const void* t, int n, float& hi, float& lo) {
+    const float2 v = static_cast<const float2*>(t)[n];
+    hi = v.x;
+    lo = v.y;
+}
+
 // 1 / x rounded to nearest (the same value as the IEEE division 1 / x)
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
@@ -563,14 +574,20 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     auto RH = [&](int q) -> Real& { return ref[(2 * NPT + q) * T + tid]; };
     auto RL = [&](int q) -> Real& { return ref[(3 * NPT + q) * T + tid]; };
 #pragma unroll
-    for (int q = 0; q < NPT; ++q) {
+    for (int q = 0; q < NPT; ++q) {   // r = b - A 0: the load vector (h^2 at every node for f = 1)
         XH(q) = XL(q) = RL(q) = Real(0);
         RH(q) = ((slot[q] >> 27) & 1) ? h2 : Real(0);
+        if (a.rhs && ((slot[q] >> 27) & 1)) {
+            Real hi, lo;
+            load_rhs(a.rhs, slot[q] & 0x1fff, hi, lo);
+            RH(q) = hi;
+            RL(q) = lo;
+        }
     }
     // inner CG state of this thread's nodes: residual r, correction d, preconditioned residual z
     // and search direction p (p is also published in shared memory for the stencil)
     Real r[NPT], d[NPT], z[NPT], pv[NPT];
-    const Real bnorm2 = Real(NI) * h2 * h2;
+    const Real bnorm2 = a.rhs ? Real(a.bnorm2) : Real(NI) * h2 * h2;
     const Real stop_outer = Real(a.rtol * a.rtol) * bnorm2;
     const Real rtol_in2 = Real(a.rtol_in * a.rtol_in);
     int parity = 0;
@@ -857,12 +874,19 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
     Real* dinv = sarena + arena_size(64);
     dense_setup<Real, direct_level<Real>(64), T>(level_ptrs<Real, 64, direct_level<Real>(64)>(sarena), dinv);
     const Real h2 = Real(1) / (Real(N) * Real(N));
-    for (int i = tid; i < NI; i += T) {
+    for (int i = tid; i < NI; i += T) {   // r = b: the load vector (h^2 at every node for f = 1)
         XH[i] = XL[i] = RL[i] = Real(0);
         RH[i] = h2;
+        if (a.rhs) {
+            const int jj = i / M + 1, ii = i - (jj - 1) * M + 1;
+            Real hi, lo;
+            load_rhs(a.rhs, jj * S + ii, hi, lo);
+            RH[i] = hi;
+            RL[i] = lo;
+        }
     }
     __syncthreads();
-    const Real bnorm2 = Real(NI) * h2 * h2;
+    const Real bnorm2 = a.rhs ? Real(a.bnorm2) : Real(NI) * h2 * h2;
     const Real stop_outer = Real(a.rtol * a.rtol) * bnorm2;
     const Real rtol_in2 = Real(a.rtol_in * a.rtol_in);
     int parity = 0, total_it = 0;

@@ -22,6 +22,8 @@ struct Level {
     uint16_t* psi_split = nullptr;   // mixed path: BF16 three-way split of Psi^T, [2N^2][kl_split_width(K)]
     std::vector<double> lambda;  // KL eigenvalues
     std::vector<double> psi_host;
+    void* rhs = nullptr;         // load vector (FemArgs::rhs), null for f = 1
+    double bnorm2 = 0.0;
 };
 
 struct Handle {

@@ -15,6 +15,13 @@ namespace mls2mc {
 void kl_eig_1d(double corr_len, int n_modes, std::vector<double>& lam, std::vector<double>& omega);
 void kl_table(int N, double corr_len, double variance, int K, std::vector<double>& psi,
               std::vector<double>& lambda);
+// Matern (smoothness 3/2) KL table by the Nystrom method (matern_host.cpp); K <= matern_max_terms()
+int matern_max_terms();
+void matern_kl_table(int N, double corr_len, double variance, int K, std::vector<double>& psi,
+                     std::vector<double>& lambda);
+// load vector of the nine-source term of Example 5.1 at the nodes of level N (padded row layout
+// below, zero at Dirichlet nodes and padding); bnorm2 = sum of squares over the interior nodes
+void nine_source_load(int N, std::vector<double>& b, double& bnorm2);
 // Nodes of a level with NL cells per side are stored row by row with row stride NL + 2 (one
 // padding word per row, never read): with an even stride, nodes of one red-black colour in two
 // adjacent rows fall on shared-memory banks of opposite parity.
@@ -47,6 +54,9 @@ struct FemArgs {
     double rtol_in;         // relative reduction of each inner CG pass
     int max_outer;          // refinement passes
     int max_inner;          // inner CG iterations per pass
+    const void* rhs;        // load vector at the nodes (padded row layout): double (FP64) or float2
+                            // (MIXED: hi, lo with hi + lo = the FP64 value); null: f = 1 (b = h^2)
+    double bnorm2;          // sum of squares of the load vector over the interior nodes (with rhs)
 };
 // Returns cudaSuccess or the launch error.
 // T = threads per particle (one of fem_block_sizes; <= 0: the first, the default)

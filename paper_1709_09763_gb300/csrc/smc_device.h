@@ -63,10 +63,12 @@ cudaError_t lu_increment_launch(const double* phi_c, const double* phi_f, int n,
 cudaError_t cv_lu_launch(const double* phi_c, const double* phi_f, int n, double beta, double* out, cudaStream_t st);
 // zeta < 0: tempering target beta * Phi_c; else bridging target beta ((1 - zeta) Phi_c + zeta Phi_f)
 // beta_p (device, or null): read beta there instead (the tempering parameter the increment search
-// left on the device, so the host need not wait for it)
+// left on the device, so the host need not wait for it); rwm: random-walk proposal, whose
+// acceptance includes the prior ratio of N(0, I)
 cudaError_t pcn_accept_launch(int n, int K, double beta, const double* beta_p, double zeta, uint32_t event,
                               uint64_t seed, double* theta, const double* theta_p, double* phi_c, const double* phi_cp,
-                              double* phi_f, const double* phi_fp, unsigned long long* n_acc, cudaStream_t st);
+                              double* phi_f, const double* phi_fp, unsigned long long* n_acc, int rwm,
+                              cudaStream_t st);
 cudaError_t da_stage1_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, const double* ps_c,
                              const double* ps_f, const double* psp_c, const double* psp_f, const double* theta_p,
                              int* pass, int* surv_idx, int* n_surv, double* theta_s, cudaStream_t st);

@@ -568,7 +568,7 @@ __device__ __forceinline__ double target_potential(double beta, double zeta, dou
 __global__ void pcn_accept_kernel(int n, int K, double beta, const double* beta_p, double zeta, uint32_t event,
                                   uint64_t seed, double* theta, const double* theta_p, double* phi_c,
                                   const double* phi_cp, double* phi_f, const double* phi_fp,
-                                  unsigned long long* n_acc) {
+                                  unsigned long long* n_acc, int rwm) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (beta_p) beta = *beta_p;
     bool ok = false;
@@ -577,7 +577,17 @@ __global__ void pcn_accept_kernel(int n, int K, double beta, const double* beta_
         const double U = 1.0 - u53(x.x, x.y);
         const double t_old = target_potential(beta, zeta, phi_c[j], zeta < 0.0 ? 0.0 : phi_f[j]);
         const double t_new = target_potential(beta, zeta, phi_cp[j], zeta < 0.0 ? 0.0 : phi_fp[j]);
-        ok = log(U) < -(t_new - t_old);
+        double log_prior = 0.0;   // random walk: log mu0(theta') - log mu0(theta), mu0 = N(0, I)
+        if (rwm) {
+            double sn = 0.0, so = 0.0;
+            for (int k = 0; k < K; ++k) {
+                const double a = theta_p[(size_t)j * K + k], b = theta[(size_t)j * K + k];
+                sn += a * a;
+                so += b * b;
+            }
+            log_prior = -0.5 * (sn - so);
+        }
+        ok = log(U) < -(t_new - t_old) + log_prior;
         if (ok) {
             for (int k = 0; k < K; ++k) theta[(size_t)j * K + k] = theta_p[(size_t)j * K + k];
             phi_c[j] = phi_cp[j];
@@ -795,11 +805,12 @@ cudaError_t cv_lu_launch(const double* phi_c, const double* phi_f, int n, double
 
 cudaError_t pcn_accept_launch(int n, int K, double beta, const double* beta_p, double zeta, uint32_t event,
                               uint64_t seed, double* theta, const double* theta_p, double* phi_c, const double* phi_cp,
-                              double* phi_f, const double* phi_fp, unsigned long long* n_acc, cudaStream_t st) {
+                              double* phi_f, const double* phi_fp, unsigned long long* n_acc, int rwm,
+                              cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     // 64-thread blocks: the FP64 work (log U, target potentials) spread over many SMs
     pcn_accept_kernel<<<grid_for(n, 64), 64, 0, st>>>(n, K, beta, beta_p, zeta, event, seed, theta, theta_p, phi_c,
-                                                      phi_cp, phi_f, phi_fp, n_acc);
+                                                      phi_cp, phi_f, phi_fp, n_acc, rwm);
     count_launches(1);
     return cudaGetLastError();
 }

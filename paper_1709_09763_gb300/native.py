@@ -22,6 +22,15 @@ SMC_FP64 = 0
 SMC_MIXED = 1
 SMC_FWD_FEM = 0
 SMC_FWD_LINEAR = 1
+SMC_COV_SEP_EXP = 0
+SMC_COV_MATERN = 1
+SMC_SRC_ONE = 0
+SMC_SRC_NINE = 1
+SMC_PROP_PCN = 0
+SMC_PROP_RWM = 1
+_COV = {"sep_exp": SMC_COV_SEP_EXP, "matern": SMC_COV_MATERN}
+_SRC = {"one": SMC_SRC_ONE, "nine": SMC_SRC_NINE}
+_PROP = {"pcn": SMC_PROP_PCN, "rwm": SMC_PROP_RWM}
 SMC_NOALLOC_MAX_PARTICLES = 65536
 
 ERROR_NAMES = {0: "SMC_OK", -1: "SMC_EINVAL", -2: "SMC_ENOMEM", -3: "SMC_ECUDA", -4: "SMC_ENOCONV",
@@ -35,7 +44,8 @@ class ProblemDesc(ctypes.Structure):
     _fields_ = [("n_levels", ctypes.c_int), ("inv_h", _ip), ("K", ctypes.c_int),
                 ("corr_len", ctypes.c_double), ("variance", ctypes.c_double),
                 ("n_obs", ctypes.c_int), ("obs_xy", _dp), ("y", _dp), ("sigma", ctypes.c_double),
-                ("forward_kind", ctypes.c_int), ("linear_A", _dp)]
+                ("forward_kind", ctypes.c_int), ("linear_A", _dp), ("cov_kind", ctypes.c_int),
+                ("source_kind", ctypes.c_int)]
 
 
 class SamplerOpts(ctypes.Structure):
@@ -44,7 +54,7 @@ class SamplerOpts(ctypes.Structure):
                 ("s_pcn", ctypes.c_double), ("precision", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("max_iter", ctypes.c_int), ("rtol", ctypes.c_double), ("surrogate", ctypes.c_int),
                 ("surrogate_train_steps", ctypes.c_int), ("surrogate_batch", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("proposal", ctypes.c_int)]
 
 
 class StageInfo(ctypes.Structure):
@@ -211,7 +221,7 @@ class Handle:
     def __init__(self, inv_h, K, obs_xy, y, sigma, corr_len=0.1, variance=1.0, J=0, J_tilde=100,
                  n_mcmc=5, tau_star=1.0, tau_lu=None, eps=1e-6, s_pcn=0.2, precision=SMC_FP64, seed=0,
                  max_iter=100, rtol=0.0, stream=None, linear_A=None, surrogate=0, surrogate_train_steps=0,
-                 surrogate_batch=0):
+                 surrogate_batch=0, cov="sep_exp", source="one", proposal="pcn"):
         lib = load()
         self._lib = lib
         self._inv_h = np.ascontiguousarray(inv_h, dtype=np.int32)
@@ -220,11 +230,12 @@ class Handle:
         self._A = None if linear_A is None else np.ascontiguousarray(linear_A, dtype=np.float64)
         d = ProblemDesc(len(self._inv_h), self._inv_h.ctypes.data_as(_ip), int(K), float(corr_len),
                         float(variance), self._obs.shape[0], _dptr(self._obs), _dptr(self._y), float(sigma),
-                        SMC_FWD_LINEAR if self._A is not None else SMC_FWD_FEM, _dptr(self._A))
+                        SMC_FWD_LINEAR if self._A is not None else SMC_FWD_FEM, _dptr(self._A), _COV[cov],
+                        _SRC[source])
         o = SamplerOpts(int(J), int(J_tilde), int(n_mcmc), float(tau_star),
                         float(tau_star if tau_lu is None else tau_lu), float(eps), float(s_pcn), int(precision),
                         int(seed), int(max_iter), float(rtol), int(surrogate), int(surrogate_train_steps),
-                        int(surrogate_batch), stream)
+                        int(surrogate_batch), stream, _PROP[proposal])
         h = ctypes.c_void_p()
         rc = lib.smc_init(ctypes.byref(d), ctypes.byref(o), ctypes.byref(h))
         self._h = h

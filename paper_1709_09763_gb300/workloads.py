@@ -31,7 +31,11 @@ class Workload:
     seed_noise: int = 2
     seed_sampler: int = 3
     precision: str = "fp64"   # "fp64" or "mixed"
-    noise_frac: float = 0.01  # sigma = noise_frac * max |p_data|
+    noise_frac: float = 0.01  # sigma = noise_frac * max |p_data| (unless sigma_abs is set)
+    sigma_abs: float = 0.0    # > 0: the noise standard deviation itself
+    cov: str = "sep_exp"      # prior covariance: "sep_exp" (separable exponential) or "matern" (nu = 3/2)
+    source: str = "one"       # source term: "one" (f = 1) or "nine" (the nine sources of Example 5.1)
+    proposal: str = "pcn"     # Markov kernel: "pcn" or "rwm" (random walk, step s_pcn)
 
     @property
     def n_obs(self):
@@ -55,6 +59,16 @@ WORKLOADS = {
     "large_mixed_h16_256": Workload("large_mixed_h16_256", (16, 32, 64, 128, 256), 1024, 128, 0.05,
                                     12, 16384, 10, seed_true=31, seed_noise=32, seed_sampler=33,
                                     precision="mixed"),
+    # the paper's Example 5.1 (Sec. 5): 5 levels h = 1/8 .. 1/128, Matern prior (lc = 0.65, nu = 3/2)
+    # with N_sto = 10, nine smoothed point sources, 25 observations, Gamma = 0.07^2 I, one
+    # random-walk step (proposal covariance 2.38^2 / N_sto I) per update, J = 2500, tau* = 1
+    "example_5_1": Workload("example_5_1", (8, 16, 32, 64, 128), 256, 10, 0.65, 5, 2500, 1,
+                            s_pcn=2.38 / 10 ** 0.5, seed_true=41, seed_noise=42, seed_sampler=43,
+                            precision="mixed", sigma_abs=0.07, cov="matern", source="nine", proposal="rwm"),
+    # Example 5.2: the same problem and data draw with Gamma = 0.035^2 I
+    "example_5_2": Workload("example_5_2", (8, 16, 32, 64, 128), 256, 10, 0.65, 5, 2500, 1,
+                            s_pcn=2.38 / 10 ** 0.5, seed_true=41, seed_noise=42, seed_sampler=53,
+                            precision="mixed", sigma_abs=0.035, cov="matern", source="nine", proposal="rwm"),
 }
 
 
