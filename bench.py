@@ -446,6 +446,13 @@ def main():
             wk, dk = wl.WORKLOADS[name], load_data(name)
             res = {"workload": name, "levels_inv_h": list(wk.inv_h), "K": wk.K, "J": wk.J, "sigma": dk["sigma"],
                    "tau_star": wk.tau_star, "proposal": wk.proposal}
+            # Eq. RelErr: weighted l1 distance of the posterior mean to theta_true, weights sqrt(lambda_k)
+            hk = native.Handle([wk.inv_h[0]], wk.K, wl.obs_grid(wk.obs_per_side), dk["y"], dk["sigma"],
+                               corr_len=wk.corr_len, precision=native.SMC_MIXED, cov=wk.cov, source=wk.source)
+            sq = np.sqrt(hk.kl_table(0, wk.inv_h[0])[1])
+            hk.close()
+            th_true = np.array(dk["theta_true"])
+            rel_err = lambda m: float(np.sum(sq * np.abs(np.asarray(m) - th_true)) / np.sum(sq * np.abs(th_true)))
             for label, inv_h in (("mls2mc", tuple(wk.inv_h)), ("smc_finest", (wk.inv_h[-1],))):
                 runs = [one_run(wk, dk, inv_h, 0, wk.seed_sampler + 1000 * rank + 17 * r) for r in range(R)]
                 L = len(inv_h)
@@ -456,7 +463,7 @@ def main():
                               "cost_finest_solves_mean": float(np.mean(cost)),
                               "updates": [x["updates"] for x in runs],
                               "log_evidence": [x["log_evidence"] for x in runs],
-                              "posterior_mean_first3": np.mean([x["mean"][:3] for x in runs], axis=0).tolist()}
+                              "rel_err_posterior_mean": [rel_err(x["mean"]) for x in runs]}
             res["speedup_mls2mc_vs_smc"] = res["smc_finest"]["seconds_median"] / res["mls2mc"]["seconds_median"]
             res["cost_ratio_smc_over_mls2mc"] = (res["smc_finest"]["cost_finest_solves_mean"] /
                                                  res["mls2mc"]["cost_finest_solves_mean"])

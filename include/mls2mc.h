@@ -103,6 +103,10 @@ typedef struct {
     void* stream;              /* cudaStream_t used for all work, or NULL for the default stream */
     int proposal;              /* SMC_PROP_PCN (0, the default) or SMC_PROP_RWM (step s = s_pcn; not with
                                   the surrogate screen) */
+    double tau_min;            /* > 0: update scheme u' of Sec. 4.5 (Eq. eq_updatescheme_final_Lmax):
+                                  at beta = 1 the level update is assessed by cv^LU on the first
+                                  J_tilde particles and the run stops on the current level when it is
+                                  below tau_min; 0: scheme u (every level is reached) */
 } smc_sampler_opts;
 
 typedef struct smc_handle smc_handle;
@@ -213,7 +217,8 @@ typedef struct {
  * are then unspecified. */
 int smc_step(smc_handle* h, smc_stage_info* info);
 
-/* Steps until beta = 1 on the finest level, or max_updates steps (<= 0: no cap). */
+/* Steps until beta = 1 on the finest level (under the scheme u', opts.tau_min > 0: on the level
+ * where the run stopped, which smc_state reports), or max_updates steps (<= 0: no cap). */
 int smc_run(smc_handle* h, int max_updates, smc_stage_info* last);
 
 /* Sampler state: current level (0-based), beta, log of the evidence estimate (Sec. 5.1.3),

@@ -110,7 +110,7 @@ class Sampler:
     """
 
     def __init__(self, evaluate, n_levels, K, J, J_tilde=100, n_mcmc=5, tau_star=1.0,
-                 tau_lu=None, eps=1e-6, s_pcn=0.2, seed=0, theta0=None, proposal="pcn"):
+                 tau_lu=None, eps=1e-6, s_pcn=0.2, seed=0, theta0=None, proposal="pcn", tau_min=0.0):
         self.evaluate_raw = evaluate
         self.L = n_levels
         self.K = K
@@ -124,6 +124,8 @@ class Sampler:
         if proposal not in ("pcn", "rwm"):
             raise ValueError("proposal must be 'pcn' or 'rwm'")
         self.proposal = proposal
+        self.tau_min = tau_min         # > 0: the scheme u' of Sec. 4.5 (adaptive maximum level)
+        self.terminated = False
         self.seed = seed
         self.evals = np.zeros(n_levels, dtype=np.int64)
         self.level = 0
@@ -145,7 +147,7 @@ class Sampler:
 
     @property
     def done(self):
-        return self.beta >= 1.0 and self.level == self.L - 1
+        return self.beta >= 1.0 and (self.level == self.L - 1 or self.terminated)
 
     # -- importance sampling + resampling ---------------------------------------------------
     def _reweight_resample(self, a, dmax):
@@ -234,15 +236,28 @@ class Sampler:
         return nb
 
     def step(self):
-        """One update of Eq. eq_updatescheme_final: an ITU, or a whole LU with its bridging steps."""
+        """One update of Eq. eq_updatescheme_final (or eq_updatescheme_final_Lmax when tau_min > 0):
+        an ITU, or a whole LU with its bridging steps; None when the sampler stops."""
         if self.done:
             return None
         l = self.level
         if l == self.L - 1:
             self._itu()
         elif self.beta >= 1.0:
-            # beta = 1: an ITU is impossible, so the level is raised
-            self._lu(np.empty(0))
+            # beta = 1: an ITU is impossible, so the level is raised. Under u' (Sec. 4.5) the
+            # information gain of that level update is assessed first by cv^LU on the first J~
+            # particles: below tau_min the sampler stops on this level (no update is recorded).
+            if self.tau_min > 0.0:
+                jt = self.J_tilde
+                head = self.evaluate(l + 1, self.theta[:jt])
+                d = head - self.phi[:jt]
+                cv_lu = cv(np.exp(-self.beta * (d - d.min())))
+                if cv_lu < self.tau_min:
+                    self.terminated = True
+                    return None
+                self._lu(head)
+            else:
+                self._lu(np.empty(0))
         elif self.prev_lu:
             self._itu()
         else:

@@ -45,6 +45,7 @@ struct Sampler {
     int level = 0;
     double beta = 0.0, log_z = 0.0;
     bool prev_lu = true;
+    bool terminated = false;   // scheme u': stopped on a level below the finest
     long long stage = 0, mcmc_event = 0;
     long long evals[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     std::vector<smc_stage_info> path;
@@ -458,6 +459,7 @@ int Handle::sampler_restart() {
     S->beta = 0.0;
     S->log_z = 0.0;
     S->prev_lu = true;
+    S->terminated = false;
     S->stage = 0;
     S->mcmc_event = 0;
     for (auto& v : S->evals) v = 0;
@@ -467,7 +469,7 @@ int Handle::sampler_restart() {
 }
 
 bool Handle::sampler_done() const {
-    return smp && smp->started && smp->beta >= 1.0 && smp->level == (int)levels.size() - 1;
+    return smp && smp->started && smp->beta >= 1.0 && (smp->level == (int)levels.size() - 1 || smp->terminated);
 }
 
 int Handle::step(smc_stage_info* info) {
@@ -481,14 +483,24 @@ int Handle::step(smc_stage_info* info) {
     if (sampler_done()) return SMC_OK;
     const int L = (int)levels.size();
     if (S->level == L - 1) return itu(-1.0, info);
-    if (S->beta >= 1.0) return lu(0, info);       // beta = 1: only the level can be raised
-    if (S->prev_lu) return itu(-1.0, info);
+    // beta = 1: only the level can be raised. Under the scheme u' of Sec. 4.5 (tau_min > 0) the
+    // level update is first assessed by cv^LU on the first J~ particles, and the sampler stops on
+    // this level when it is below tau_min (no update is recorded).
+    if (S->beta >= 1.0 && !(opts.tau_min > 0.0)) return lu(0, info);
+    if (S->beta < 1.0 && S->prev_lu) return itu(-1.0, info);
     const int jt = std::min(opts.J_tilde, S->J);
     RC(smp_eval(S->level + 1, jt, S->theta, S->phi_f));
     CK(cv_lu_launch(S->phi_c, S->phi_f, jt, S->beta, S->scal, stream));
     double cv_lu = 0.0;
     CK(cudaMemcpyAsync(&cv_lu, S->scal, 8, cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
+    if (S->beta >= 1.0) {
+        if (cv_lu < opts.tau_min) {
+            S->terminated = true;
+            return SMC_OK;   // info->status stays 1: nothing was done
+        }
+        return lu(jt, info);
+    }
     if (cv_lu < opts.tau_lu) return itu(cv_lu, info);
     return lu(jt, info);
 }

@@ -495,8 +495,10 @@ __host__ __device__ constexpr int solve_smem_reals(int N, int T) {
 // ---- the kernel ----------------------------------------------------------------------
 // the whole solve of particle p of a.n, by one thread block (all threads call it)
 // CP: compact hierarchy (mixed path, kappa from the synthesis) with the refinement state at
-// ref_ext (device memory) instead of shared memory
-template <typename Real, int N, int T, bool CP = false>
+// ref_ext (device memory) instead of shared memory. RHS: the load vector may come from a table
+// (a.rhs); false compiles the f = 1 path alone (the compact kernels are instantiated both ways:
+// at 64 registers a thread the table read's code costs them 20 % of their speed)
+template <typename Real, int N, int T, bool CP = false, bool RHS = true>
 __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Real* arena, double (*red_buf)[64],
                                                Real* theta_s, Real* ref_ext = nullptr) {
     constexpr int S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
@@ -577,7 +579,7 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     for (int q = 0; q < NPT; ++q) {   // r = b - A 0: the load vector (h^2 at every node for f = 1)
         XH(q) = XL(q) = RL(q) = Real(0);
         RH(q) = ((slot[q] >> 27) & 1) ? h2 : Real(0);
-        if (a.rhs && ((slot[q] >> 27) & 1)) {
+        if (RHS && a.rhs && ((slot[q] >> 27) & 1)) {
             Real hi, lo;
             load_rhs(a.rhs, slot[q] & 0x1fff, hi, lo);
             RH(q) = hi;
@@ -587,7 +589,7 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     // inner CG state of this thread's nodes: residual r, correction d, preconditioned residual z
     // and search direction p (p is also published in shared memory for the stencil)
     Real r[NPT], d[NPT], z[NPT], pv[NPT];
-    const Real bnorm2 = a.rhs ? Real(a.bnorm2) : Real(NI) * h2 * h2;
+    const Real bnorm2 = (RHS && a.rhs) ? Real(a.bnorm2) : Real(NI) * h2 * h2;
     const Real stop_outer = Real(a.rtol * a.rtol) * bnorm2;
     const Real rtol_in2 = Real(a.rtol_in * a.rtol_in);
     int parity = 0;
@@ -1115,7 +1117,7 @@ fem_eval_kernel(FemArgs a) {
 
 // compact form (mixed, kappa from the synthesis): MINB blocks per SM, persistent over the
 // particles; each block keeps its refinement state in its own slice of ref_scratch (L2-resident)
-template <int N, int T, int MINB>
+template <int N, int T, int MINB, bool RHS>
 __global__ void __launch_bounds__(T, MINB) fem_eval_compact(FemArgs a, float* ref_scratch, int* counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_buf[2][64];
@@ -1127,7 +1129,7 @@ __global__ void __launch_bounds__(T, MINB) fem_eval_compact(FemArgs a, float* re
         const int item = item_s;
         __syncthreads();
         if (item >= a.n) break;
-        solve_particle<float, N, T, true>(a, item, reinterpret_cast<float*>(smem_raw), red_buf, nullptr, ref);
+        solve_particle<float, N, T, true, RHS>(a, item, reinterpret_cast<float*>(smem_raw), red_buf, nullptr, ref);
         __syncthreads();
     }
 }
@@ -1227,15 +1229,21 @@ constexpr size_t compact_smem() {
     return sizeof(float) * (size_t)(arena_size_cp(N) + dense_reals<float>(N));
 }
 
-template <int N, int T>
-cudaError_t launch_compact(const FemArgs& a, float* ref_scratch, int blocks, int* counter, cudaStream_t st) {
+template <int N, int T, bool RHS>
+cudaError_t launch_compact_t(const FemArgs& a, float* ref_scratch, int blocks, int* counter, cudaStream_t st) {
     constexpr int MINB = compact_min_blocks(N, T);
-    cudaError_t e = cudaFuncSetAttribute(fem_eval_compact<N, T, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)compact_smem<N>());
+    cudaError_t e = cudaFuncSetAttribute(fem_eval_compact<N, T, MINB, RHS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)compact_smem<N>());
     if (e != cudaSuccess) return e;
-    fem_eval_compact<N, T, MINB><<<blocks, T, compact_smem<N>(), st>>>(a, ref_scratch, counter);
+    fem_eval_compact<N, T, MINB, RHS><<<blocks, T, compact_smem<N>(), st>>>(a, ref_scratch, counter);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <int N, int T>
+cudaError_t launch_compact(const FemArgs& a, float* ref_scratch, int blocks, int* counter, cudaStream_t st) {
+    return a.rhs ? launch_compact_t<N, T, true>(a, ref_scratch, blocks, counter, st)
+                 : launch_compact_t<N, T, false>(a, ref_scratch, blocks, counter, st);
 }
 
 template <int N, int T>
@@ -1244,9 +1252,11 @@ int compact_resident_blocks() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(fem_eval_compact<N, T, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // the two instantiations share the launch bounds and the shared-memory size
+    cudaFuncSetAttribute(fem_eval_compact<N, T, MINB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)compact_smem<N>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_compact<N, T, MINB>, T, compact_smem<N>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fem_eval_compact<N, T, MINB, false>, T,
+                                                  compact_smem<N>());
     return sms * std::max(1, per_sm);
 }
 

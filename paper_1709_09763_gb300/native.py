@@ -54,7 +54,7 @@ class SamplerOpts(ctypes.Structure):
                 ("s_pcn", ctypes.c_double), ("precision", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("max_iter", ctypes.c_int), ("rtol", ctypes.c_double), ("surrogate", ctypes.c_int),
                 ("surrogate_train_steps", ctypes.c_int), ("surrogate_batch", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("proposal", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("proposal", ctypes.c_int), ("tau_min", ctypes.c_double)]
 
 
 class StageInfo(ctypes.Structure):
@@ -221,7 +221,7 @@ class Handle:
     def __init__(self, inv_h, K, obs_xy, y, sigma, corr_len=0.1, variance=1.0, J=0, J_tilde=100,
                  n_mcmc=5, tau_star=1.0, tau_lu=None, eps=1e-6, s_pcn=0.2, precision=SMC_FP64, seed=0,
                  max_iter=100, rtol=0.0, stream=None, linear_A=None, surrogate=0, surrogate_train_steps=0,
-                 surrogate_batch=0, cov="sep_exp", source="one", proposal="pcn"):
+                 surrogate_batch=0, cov="sep_exp", source="one", proposal="pcn", tau_min=0.0):
         lib = load()
         self._lib = lib
         self._inv_h = np.ascontiguousarray(inv_h, dtype=np.int32)
@@ -235,7 +235,7 @@ class Handle:
         o = SamplerOpts(int(J), int(J_tilde), int(n_mcmc), float(tau_star),
                         float(tau_star if tau_lu is None else tau_lu), float(eps), float(s_pcn), int(precision),
                         int(seed), int(max_iter), float(rtol), int(surrogate), int(surrogate_train_steps),
-                        int(surrogate_batch), stream, _PROP[proposal])
+                        int(surrogate_batch), stream, _PROP[proposal], float(tau_min))
         h = ctypes.c_void_p()
         rc = lib.smc_init(ctypes.byref(d), ctypes.byref(o), ctypes.byref(h))
         self._h = h

@@ -214,3 +214,27 @@ def test_tempering_update_small_and_large_populations(J):
     assert info["log_z_inc"] == pytest.approx(o.log_z, rel=1e-12, abs=1e-14)
     assert np.allclose(th, o.theta, rtol=1e-10, atol=1e-12)
     assert np.allclose(phi, o.phi, rtol=1e-10)
+
+
+def test_adaptive_maximum_level_scheme_same_path_as_oracle():
+    """Scheme u' (opts.tau_min > 0, Sec. 4.5): levels 2 and 3 differ by 1e-9 of the operator, so
+    cv^LU at beta = 1 on level 2 is below tau_min and the run stops there: the same updates,
+    evaluation counts (the J~ pre-evaluations on level 3 included) and particles as the oracle."""
+    As0, y, s = _linear(K=3, n=6, sigma=0.2, seed=3)
+    A = As0[0]
+    B = np.random.default_rng(9).normal(0, 1, A.shape)
+    As = np.stack([A + 0.3 * B, A, A + 1e-9 * B])
+    J = 2000
+    kw = dict(J_tilde=100, n_mcmc=6, s_pcn=0.4, seed=21)
+    h = _handle_linear(As, y, s, J=J, tau_min=1e-3, **kw)
+    h.run()
+    o = smc.Sampler(lambda l, th: potential(th @ As[l].T, y, s), 3, 3, J, tau_min=1e-3, **kw).run()
+    assert o.terminated and o.level == 1
+    _compare_paths(h.path(), o.path, 1e-9)
+    st = h.state()
+    assert st["level"] == 1 and st["beta"] == 1.0
+    assert st["evals"][:3] == list(o.evals)
+    th, _ = h.particles()
+    assert np.allclose(th, o.theta, rtol=1e-8, atol=1e-9)
+    info = h.step()
+    assert info["status"] == 1 and h.state()["n_updates"] == st["n_updates"]

@@ -157,3 +157,27 @@ def test_mls2mc_linear_gaussian_levels_and_cost_identity():
         prev_level = p['level']
     assert np.array_equal(expect, s.evals), (expect, s.evals)
     assert s.level == 2 and s.beta == 1.0
+
+
+def test_adaptive_maximum_level_scheme_stops_when_levels_agree():
+    """Scheme u' (Sec. 4.5): at beta = 1 the level update is skipped, and the sampler stops, when
+    cv^LU on the first J~ particles is below tau_min. Levels 2 and 3 of the hierarchy below differ
+    by 1e-9 of the operator, so the run stops on level 2 and its posterior is that of level 2 (the
+    closed form); with tau_min = 0 the same run goes on to level 3."""
+    A, y, sigma = _linear_problem(K=3, n=6, sigma=0.2, seed=3)
+    B = np.random.default_rng(9).normal(0, 1, A.shape)
+    As = [A + 0.3 * B, A, A + 1e-9 * B]
+    J, jt = 2000, 100
+    ev = lambda l, th: potential(th @ As[l].T, y, sigma)
+    s = smc.Sampler(ev, 3, 3, J, J_tilde=jt, n_mcmc=6, s_pcn=0.4, seed=21, tau_min=1e-3).run()
+    assert s.done and s.terminated and s.level == 1 and s.beta == 1.0
+    n_pre = 1 + sum(1 for p in s.path if p['level'] == 1 and 'cv_lu' in p)
+    assert s.evals[2] == n_pre * jt                   # only J~ pre-evaluations on level 3
+    m_ex, C_ex = gaussian.posterior(As[1], y, sigma)
+    m, v = s.moments()
+    assert np.all(np.abs(m - m_ex) < 12 * np.sqrt(np.diag(C_ex) / J))
+    full = smc.Sampler(ev, 3, 3, J, J_tilde=jt, n_mcmc=6, s_pcn=0.4, seed=21).run()
+    assert full.level == 2 and not full.terminated
+    # both schemes take the same updates until beta first reaches 1 on level 2
+    n = len(s.path)
+    assert [(p['kind'], p['level']) for p in s.path] == [(p['kind'], p['level']) for p in full.path[:n]]
