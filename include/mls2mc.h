@@ -151,7 +151,8 @@ int smc_set_timing(smc_handle* h, int enable);
  * block size (threads per particle) on n_tune prior draws and keep the fastest for the process
  * (shared by all handles of the same 1/h and precision). chosen [n_levels] receives the block
  * sizes, best_ms [n_levels] the time per launch (either may be NULL). smc_set_block_size forces a
- * block size for a level (T = 0 restores the default); T must be one of the compiled sizes. A
+ * block size for a level (T = 0 restores the default: the compact form on 1/32 and 1/64 of the
+ * mixed path, else the first compiled size); T must be one of the compiled sizes. A
  * negative size -T selects the compact form with T threads per particle (mixed precision: -512 at
  * 1/h = 64, -256 at 1/h = 32): several particles per SM, the fine level in five arrays
  * and each coarse level in four, the refinement state in device memory (same results as the size

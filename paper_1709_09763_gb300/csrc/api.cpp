@@ -206,7 +206,8 @@ int Handle::eval_device(int level, int n, const double* theta, double* G, double
             if (e != cudaSuccess) return cuda_fail(e, "forward-solve launch");
             return SMC_OK;
         }
-        const int T = tuned_block(L.N, precision);
+        int T = tuned_block(L.N, precision);
+        if (T == 0) T = fem_default_block(L.N, precision);
         if (T < 0) {   // compact form: persistent blocks with their refinement state in device memory
             const int blocks = fem_compact_blocks(L.N, -T);
             if (blocks <= 0) return fail(SMC_EINVAL, "no compact form with %d threads at 1/h = %d", -T, L.N);

@@ -579,11 +579,20 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     for (int q = 0; q < NPT; ++q) {   // r = b - A 0: the load vector (h^2 at every node for f = 1)
         XH(q) = XL(q) = RL(q) = Real(0);
         RH(q) = ((slot[q] >> 27) & 1) ? h2 : Real(0);
-        if (RHS && a.rhs && ((slot[q] >> 27) & 1)) {
-            Real hi, lo;
-            load_rhs(a.rhs, slot[q] & 0x1fff, hi, lo);
-            RH(q) = hi;
-            RL(q) = lo;
+    }
+    if (RHS && a.rhs) {
+        // the load vector, read in a rolled loop of its own (node indices recomputed, no register
+        // array touched), which leaves the register allocation of the solve as it is for f = 1
+#pragma unroll 1
+        for (int q = 0; q < NPT; ++q) {
+            const bool red = q < NPH;
+            int ii, jj;
+            if (colour_node<N>(tid + T * (red ? q : q - NPH), red ? 0 : 1, ii, jj)) {
+                Real hi, lo;
+                load_rhs(a.rhs, jj * S + ii, hi, lo);
+                RH(q) = hi;
+                RL(q) = lo;
+            }
         }
     }
     // inner CG state of this thread's nodes: residual r, correction d, preconditioned residual z
@@ -1364,12 +1373,20 @@ bool fem_level_supported(int N, int precision) {
     return N == 4 || N == 8 || N == 16 || N == 32;
 }
 
+// the block size used when none was chosen: the compact form where it is compiled (it is
+// faster at J = 4000 on 1/32 and 1/64, and bit-identical to the size -T), else the first size
+int fem_default_block(int N, int precision) {
+    if (precision == SMC_MIXED && (N == 32 || N == 64)) return N == 64 ? -512 : -256;
+    const std::vector<int> s = fem_block_sizes(N, precision);
+    return s.empty() ? 0 : s[0];
+}
+
 // block sizes compiled for each level (threads per particle); the autotuner picks one
 std::vector<int> fem_block_sizes(int N, int precision) {
     if (precision == SMC_MIXED) {
         switch (N) {
             case 4: return {32};
-            case 8: return {64, 32};
+            case 8: return {32, 64};
             case 16: return {128, 64};
             case 32: return {256, 512, -256};   // -256: compact form, four blocks per SM
             case 64: return {512, 1024, -512};  // -512: compact form, two blocks per SM

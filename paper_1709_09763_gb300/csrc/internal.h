@@ -62,6 +62,8 @@ struct FemArgs {
 // T = threads per particle (one of fem_block_sizes; <= 0: the first, the default)
 cudaError_t fem_eval_launch(const FemArgs& a, cudaStream_t stream, int T = 0);
 std::vector<int> fem_block_sizes(int N, int precision);
+// the size used when none is set (negative: a compact form)
+int fem_default_block(int N, int precision);
 // large levels (1/h = 128, 256; mixed precision, kappa from the synthesis): hierarchy in global
 // scratch, blocks x fem_global_slice(N) floats; *counter (device) is reset by the launch
 size_t fem_global_slice(int N);
