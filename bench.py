@@ -272,6 +272,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-run", action="store_true", help="skip the seconds-to-posterior sampler run")
+    ap.add_argument("--autotune", action="store_true", help="let the library's autotuner pick the block sizes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -303,7 +304,10 @@ def main():
                       J_tilde=w.J_tilde, n_mcmc=1, s_pcn=w.s_pcn, tau_star=w.tau_star,
                       precision=native.SMC_MIXED, seed=w.seed_sampler + 1000 * rank, stream=stream.cuda_stream)
     theta0 = wl.particles(J, w.K, 1000 + rank)
-    tuned, _ = h.autotune(J)            # block size per level, chosen by the library's autotuner
+    if args.autotune:                   # block size per level, chosen by the library's autotuner
+        tuned, _ = h.autotune(J)
+    else:                               # the library's defaults (its fastest forms at this J)
+        tuned = [h.block_size(l) for l in range(L)]
     h.set_particles(theta0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
     n_mcmc_step = 1

@@ -159,6 +159,8 @@ int smc_set_timing(smc_handle* h, int enable);
  * T, bit for bit). */
 int smc_autotune(smc_handle* h, int n_tune, int* chosen, float* best_ms);
 int smc_set_block_size(smc_handle* h, int level, int T);
+/* The block size the solves of `level` run with (set, tuned or the default) into *T. */
+int smc_block_size(smc_handle* h, int level, int* T);
 
 /* Number of CUDA kernels this library has launched in the process so far (all handles). */
 long long smc_kernel_launches(void);

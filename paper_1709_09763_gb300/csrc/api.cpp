@@ -402,6 +402,17 @@ int smc_set_block_size(smc_handle* hh, int level, int T) {
     return SMC_OK;
 }
 
+int smc_block_size(smc_handle* hh, int level, int* T) {
+    if (!hh || !T) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (level < 0 || level >= (int)h->levels.size() || h->forward_kind != SMC_FWD_FEM)
+        return h->fail(SMC_EINVAL, "level out of range");
+    const int N = h->levels[level].N;
+    const int t = tuned_block(N, h->precision);
+    *T = t != 0 ? t : fem_default_block(N, h->precision);
+    return SMC_OK;
+}
+
 int smc_autotune(smc_handle* hh, int n_tune, int* chosen, float* best_ms) {
     if (!hh || n_tune < 1) return SMC_EINVAL;
     Handle* h = reinterpret_cast<Handle*>(hh);

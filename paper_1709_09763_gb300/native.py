@@ -97,6 +97,7 @@ SIGNATURES = {
     "smc_kernel_launches": (ctypes.c_longlong, []),
     "smc_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip, ctypes.c_void_p]),
     "smc_set_block_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "smc_block_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip]),
     "smc_get_timing": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "smc_tempering_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(StageInfo)]),
@@ -330,6 +331,12 @@ class Handle:
 
     def set_block_size(self, level, T):
         self._check(self._lib.smc_set_block_size(self._h, int(level), int(T)))
+
+    def block_size(self, level):
+        """Threads per particle the solves of `level` run with (negative: a compact form)."""
+        T = ctypes.c_int()
+        self._check(self._lib.smc_block_size(self._h, int(level), ctypes.byref(T)))
+        return T.value
 
     def set_timing(self, enable=True):
         self._check(self._lib.smc_set_timing(self._h, int(bool(enable))))

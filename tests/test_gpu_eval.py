@@ -145,16 +145,19 @@ def test_every_block_size_and_autotuner(prec):
     levels = [8, 16, 32, 64] if prec == native.SMC_MIXED else [8, 16, 32]
     tol = 1e-6 if prec == native.SMC_MIXED else 1e-10
     h = native.Handle(levels, w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, precision=prec)
-    sizes = {8: [64, 32], 16: [128, 64], 32: [256, 512, -256], 64: [512, 1024, -512]} if prec == native.SMC_MIXED else \
+    sizes = {8: [32, 64], 16: [128, 64], 32: [256, 512, -256], 64: [512, 1024, -512]} if prec == native.SMC_MIXED else \
         {8: [64], 16: [128, 256], 32: [256, 512]}
     theta = wl.particles(9, w.K, 31)
     for l, N in enumerate(levels):
         Gr, _ = _oracle(N, w, theta, obs, np.array(d["y"]), d["sigma"])
         for T in sizes[N]:
             h.set_block_size(l, T)
+            assert h.block_size(l) == T
             G, _ = h.eval_likelihood(l, theta)
             assert _rel(G, Gr).max() < tol, (N, T)
         h.set_block_size(l, 0)
+        default = {32: -256, 64: -512}.get(N, sizes[N][0]) if prec == native.SMC_MIXED else sizes[N][0]
+        assert h.block_size(l) == default, (N, h.block_size(l))
     with pytest.raises(native.SmcError):
         h.set_block_size(0, 96)
     with pytest.raises(native.SmcError):   # no compact form at 1/8, none with 128 threads at 1/32
