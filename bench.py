@@ -60,6 +60,22 @@ def algorithmic_flops_per_eval(N, K, iters, passes, synthesis=False):
     return iters * per_iter + passes * 100.0 * n + synth + 10.0 * (N + 1) ** 2
 
 
+def algorithmic_smem_bytes_per_eval(N, iters, passes):
+    """Shared-memory bytes one evaluation on level 1/h = N moves, counted from the solve's algorithm
+    (4-byte words; the block reductions' broadcast reads are not counted).
+
+    Per fine node and CG iteration: a black node loads 9 words (4 weights, 4 neighbours, its inverse
+    diagonal) and stores 1 in the black pre-sweep, loads 13 (the same plus 4 coarse values) and
+    stores 1 in the post-sweep with the prolongation, stores p once and loads 8 in A p; a red node
+    loads 8 and stores 1 for its residual, loads 9 in the red post-sweep, stores p, loads 8 in A p,
+    loads 1 and stores 1 for the next red pre-sweep: 31 words on average. The coarse levels add
+    about 26 words per coarse node (a quarter of the fine nodes per level): 8.7 more per fine node.
+    Per refinement pass: 18 words per node (d published, A d in edge form, x and r pairs). Set-up:
+    16 words per node (kappa staging, coefficients, coarsening)."""
+    n = (N - 1) ** 2
+    return 4.0 * n * (iters * (31.0 + 8.7) + passes * 18.0 + 16.0)
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -494,6 +510,8 @@ def main():
         traffic = per_particle * J if per_particle is not None else None
         flops = algorithmic_flops_per_eval(w.inv_h[-1], w.K, mean_it, 2.0) * J
         achieved = flops / (launch_ms * 1e-3) / 1e12
+        smem_tbs = algorithmic_smem_bytes_per_eval(w.inv_h[-1], mean_it, 2.0) * J / (launch_ms * 1e-3) / 1e12
+        smem_peak = 152 * 128 * sm_mhz * 1e6 / 1e12           # TB/s, one 128-byte wavefront per SM cycle
         total_evals = evals_per_step * world
         line = {
             "metric": "likelihood evals/s per mesh level", "value": job_throughput(evals_per_step, world, ms),
@@ -518,6 +536,12 @@ def main():
                          "launches": kern_n[kl], "mean_cg_iters": mean_it,
                          "peak_source": f"FP32 FMA issue rate: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "
                                         f"(sm_max_mhz {src})"},
+            # the bound that holds the solve: the shared-memory pipe (the FP32 issue roofline above
+            # is the contract's "alu" figure; the solve runs on chip, far from both HBM and ALU)
+            "roofline_smem": {"kernel": solve_kernel_name(w.inv_h[-1], tuned[-1]), "bound": "smem",
+                              "achieved": smem_tbs, "peak": smem_peak, "unit": "TB/s",
+                              "frac": smem_tbs / smem_peak,
+                              "peak_source": f"152 SMs x 128 B per cycle x {sm_mhz:.0f} MHz"},
             "e2e": {"value": job_throughput(e2e_evals, world, e2e), "unit": "evals/s",
                     "h2d_bytes_per_step": J * w.K * 8, "d2h_bytes_per_step": J * (w.K + 1) * 8},
             "gpu_launches": int(launches),
