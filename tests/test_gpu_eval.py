@@ -249,3 +249,20 @@ def test_compact_form_equals_shared_memory_form(inv_h, T):
         out[B] = (Phi.cpu().numpy(), it.cpu().numpy())
     h.set_block_size(0, 0)
     assert np.array_equal(out[T][0], out[-T][0]) and np.array_equal(out[T][1], out[-T][1])
+
+
+@pytest.mark.parametrize("prec", [native.SMC_MIXED, native.SMC_FP64])
+def test_maximum_terms_and_observations(prec):
+    """The largest problem the descriptor admits per particle: K = 256 KL terms and 1024
+    observations (a 32 x 32 interpolated grid) on 1/h = 16, against the oracle."""
+    K, N = 256, 16
+    obs = wl.obs_grid(32)
+    assert obs.shape[0] == 1024
+    theta = wl.particles(3, K, 404) * 0.3
+    y = np.zeros(1024)
+    h = native.Handle([N], K, obs, y, 1.0, corr_len=0.1, precision=prec)
+    G, _ = h.eval_likelihood(0, theta)
+    lv = ofwd.Level(N, 0.1, 1.0, K, obs)
+    Gr = lv.G_batch(theta)
+    tol = 1e-6 if prec == native.SMC_MIXED else 1e-10
+    assert _rel(G, Gr).max() < tol

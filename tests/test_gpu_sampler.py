@@ -238,3 +238,16 @@ def test_adaptive_maximum_level_scheme_same_path_as_oracle():
     assert np.allclose(th, o.theta, rtol=1e-8, atol=1e-9)
     info = h.step()
     assert info["status"] == 1 and h.state()["n_updates"] == st["n_updates"]
+
+
+def test_increment_search_reports_numerical_singularity():
+    """Degenerate weights (Sec. 4.3): when every potential is +inf no increment exists and the
+    search reports SMC_ESINGULAR instead of a step."""
+    As, y, s = _linear()
+    h = _handle_linear(As, y, s, J=64)
+    with pytest.raises(native.SmcError) as ei:
+        h.next_increment(np.full(64, np.inf), 1.0)
+    assert ei.value.code == native.SMC_ESINGULAR
+    # the handle stays usable
+    d, _, _ = h.next_increment(np.linspace(0.0, 1.0, 64), 1.0)
+    assert d == 1.0
