@@ -101,8 +101,8 @@ typedef struct {
     int surrogate_train_steps; /* Adam steps of the first training round of a level (<= 0: 25; later rounds 1/4) */
     int surrogate_batch;       /* training minibatch, at most the pairs held (<= 0: 8192) */
     void* stream;              /* cudaStream_t used for all work, or NULL for the default stream */
-    int proposal;              /* SMC_PROP_PCN (0, the default) or SMC_PROP_RWM (step s = s_pcn; not with
-                                  the surrogate screen) */
+    int proposal;              /* SMC_PROP_PCN (0, the default) or SMC_PROP_RWM (step s = s_pcn); with the
+                                  surrogate screen the prior ratio enters stage 1 */
     double tau_min;            /* > 0: update scheme u' of Sec. 4.5 (Eq. eq_updatescheme_final_Lmax):
                                   at beta = 1 the level update is assessed by cv^LU on the first
                                   J_tilde particles and the run stops on the current level when it is

@@ -313,7 +313,8 @@ int Handle::mcmc_da(int level, double zeta, double& rate) {
     Sampler* S = smp;
     const int J = S->J;
     const bool br = zeta >= 0.0;
-    const double s = opts.s_pcn, c0 = std::sqrt(1.0 - s * s);
+    const bool rwm = opts.proposal == SMC_PROP_RWM;
+    const double s = opts.s_pcn, c0 = rwm ? 1.0 : std::sqrt(1.0 - s * s);
     CK(cudaMemsetAsync(S->n_acc, 0, 8, stream));
     RC(mlp_predict(level, J, S->theta, nullptr, S->ps_c));
     if (br) RC(mlp_predict(level + 1, J, S->theta, nullptr, S->ps_f));
@@ -323,7 +324,8 @@ int Handle::mcmc_da(int level, double zeta, double& rate) {
         CK(normals_launch(S->theta_p, J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
         RC(mlp_predict(level, J, S->theta_p, nullptr, S->psp_c));
         if (br) RC(mlp_predict(level + 1, J, S->theta_p, nullptr, S->psp_f));
-        CK(da_stage1_launch(J, K, S->beta, zeta, ev, opts.seed, S->ps_c, S->ps_f, S->psp_c, S->psp_f, S->theta_p,
+        CK(da_stage1_launch(J, K, S->beta, zeta, ev, opts.seed, S->ps_c, S->ps_f, S->psp_c, S->psp_f, S->theta,
+                            S->theta_p, rwm ? 1 : 0,
                             S->da_pass, S->surv_idx, S->n_surv, S->theta_s, stream));
         int ns = 0;
         CK(cudaMemcpyAsync(&ns, S->n_surv, 4, cudaMemcpyDeviceToHost, stream));

@@ -70,8 +70,9 @@ cudaError_t pcn_accept_launch(int n, int K, double beta, const double* beta_p, d
                               double* phi_f, const double* phi_fp, unsigned long long* n_acc, int rwm,
                               cudaStream_t st);
 cudaError_t da_stage1_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, const double* ps_c,
-                             const double* ps_f, const double* psp_c, const double* psp_f, const double* theta_p,
-                             int* pass, int* surv_idx, int* n_surv, double* theta_s, cudaStream_t st);
+                             const double* ps_f, const double* psp_c, const double* psp_f, const double* theta,
+                             const double* theta_p, int rwm, int* pass, int* surv_idx, int* n_surv, double* theta_s,
+                             cudaStream_t st);
 cudaError_t da_stage2_launch(int ns, int K, double beta, double zeta, uint32_t event, uint64_t seed, const int* surv_idx,
                              const double* theta_s, const double* phi_cs, const double* phi_fs, double* theta,
                              double* phi_c, double* phi_f, double* ps_c, double* ps_f, const double* psp_c,

@@ -602,9 +602,11 @@ __global__ void pcn_accept_kernel(int n, int K, double beta, const double* beta_
 // stage 1 on the surrogate potentials: pass with probability min(1, exp(-(t~(theta') - t~(theta))));
 // the survivors are then compacted in particle order (deterministic: the exact solves, and the
 // training pairs they add to the surrogate's set, come in the same order on every run)
-__global__ void da_stage1_kernel(int n, double beta, double zeta, uint32_t event, uint64_t seed,
+// (random walk, rwm != 0: the prior ratio of N(0, I) enters stage 1; stage 2 divides the exact
+// target ratio by the surrogate one, in which the prior ratio cancels)
+__global__ void da_stage1_kernel(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed,
                                  const double* ps_c, const double* ps_f, const double* psp_c, const double* psp_f,
-                                 int* pass) {
+                                 const double* theta, const double* theta_p, int rwm, int* pass) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const uint4 x = philox(make_uint4(0u, (uint32_t)j, event, (uint32_t)kPurposeDaU), seed);
@@ -612,7 +614,17 @@ __global__ void da_stage1_kernel(int n, double beta, double zeta, uint32_t event
     const bool br = zeta >= 0.0;
     const double t_old = target_potential(beta, zeta, ps_c[j], br ? ps_f[j] : 0.0);
     const double t_new = target_potential(beta, zeta, psp_c[j], br ? psp_f[j] : 0.0);
-    pass[j] = log(U) < -(t_new - t_old);
+    double log_prior = 0.0;
+    if (rwm) {
+        double sn = 0.0, so = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double a = theta_p[(size_t)j * K + k], b = theta[(size_t)j * K + k];
+            sn += a * a;
+            so += b * b;
+        }
+        log_prior = -0.5 * (sn - so);
+    }
+    pass[j] = log(U) < -(t_new - t_old) + log_prior;
 }
 
 // surv_idx = the indices j with pass[j] set, increasing; *n_surv = their number (one block of
@@ -816,10 +828,12 @@ cudaError_t pcn_accept_launch(int n, int K, double beta, const double* beta_p, d
 }
 
 cudaError_t da_stage1_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, const double* ps_c,
-                             const double* ps_f, const double* psp_c, const double* psp_f, const double* theta_p,
-                             int* pass, int* surv_idx, int* n_surv, double* theta_s, cudaStream_t st) {
+                             const double* ps_f, const double* psp_c, const double* psp_f, const double* theta,
+                             const double* theta_p, int rwm, int* pass, int* surv_idx, int* n_surv, double* theta_s,
+                             cudaStream_t st) {
     if (n <= 0) return cudaMemsetAsync(n_surv, 0, sizeof(int), st);
-    da_stage1_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, beta, zeta, event, seed, ps_c, ps_f, psp_c, psp_f, pass);
+    da_stage1_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, K, beta, zeta, event, seed, ps_c, ps_f, psp_c, psp_f, theta,
+                                                       theta_p, rwm, pass);
     compact_kernel<<<1, 1024, 0, st>>>(pass, n, surv_idx, n_surv);
     gather_rows_kernel<<<grid_for((long long)n * K, 256), 256, 0, st>>>(surv_idx, n_surv, n, K, theta_p, theta_s);
     count_launches(3);

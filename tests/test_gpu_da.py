@@ -30,9 +30,10 @@ def _problem():
     return K, obs, y, sigma
 
 
-def _run(surrogate, seed, K, obs, y, sigma):
-    h = native.Handle([8, 16, 32], K, obs, y, sigma, corr_len=0.3, J=1500, J_tilde=100, n_mcmc=5, s_pcn=0.3,
-                      precision=native.SMC_MIXED, seed=seed, surrogate=surrogate, surrogate_train_steps=150)
+def _run(surrogate, seed, K, obs, y, sigma, proposal="pcn"):
+    h = native.Handle([8, 16, 32], K, obs, y, sigma, corr_len=0.3, J=1500, J_tilde=100, n_mcmc=5,
+                      s_pcn=0.3 if proposal == "pcn" else 2.38 / np.sqrt(K), precision=native.SMC_MIXED, seed=seed,
+                      surrogate=surrogate, surrogate_train_steps=150, proposal=proposal)
     h.run()
     m, v, lz = h.posterior_moments()
     path = h.path()
@@ -41,11 +42,13 @@ def _run(surrogate, seed, K, obs, y, sigma):
     return m, v, lz, path, st
 
 
-def test_delayed_acceptance_same_posterior_fewer_solves():
+@pytest.mark.parametrize("proposal", ["pcn", "rwm"])
+def test_delayed_acceptance_same_posterior_fewer_solves(proposal):
+    """With the pCN kernel, and with the random walk (whose prior ratio enters stage 1)."""
     K, obs, y, sigma = _problem()
     R = 8
-    plain = [_run(0, 100 + r, K, obs, y, sigma) for r in range(R)]
-    da = [_run(2, 100 + r, K, obs, y, sigma) for r in range(R)]
+    plain = [_run(0, 100 + r, K, obs, y, sigma, proposal) for r in range(R)]
+    da = [_run(2, 100 + r, K, obs, y, sigma, proposal) for r in range(R)]
     for idx in (0, 1):   # means, variances
         a = np.array([p[idx] for p in plain])
         b = np.array([d[idx] for d in da])

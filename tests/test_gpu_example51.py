@@ -114,10 +114,6 @@ def test_example_5_1_rwm_sampler_matches_oracle_path():
     assert 0.05 < np.mean([g["accept_rate"] for g in gp]) < 0.9
 
 
-def test_rwm_with_surrogate_is_rejected():
-    with pytest.raises(native.SmcError):
-        _handle([8], native.SMC_MIXED, J=16, proposal="rwm", surrogate=1)
-
 
 def test_mls2mc_and_single_level_smc_agree_on_example_5_1():
     """Both samplers target the posterior of the finest level: MLS^2MC on 1/8, 1/16, 1/32 and
