@@ -1,33 +1,40 @@
 // Batched likelihood evaluation G_l(theta), Phi_l(theta) on one mesh level.
 //
 // Path (Sec. 2.1, Sec. 5): theta -> u = theta . Psi on every triangle (Eq. truncKL)
-// -> kappa = exp(u) -> P1 FEM solve of -div(kappa grad p) = 1, p = 0 on the
+// -> kappa = exp(u) -> P1 FEM solve of -div(kappa grad p) = f, p = 0 on the
 // boundary -> observations p(d_n) -> Phi = 1/2 sum ((y - G)/sigma)^2 (Eq. phi).
 //
 // Design: one thread block owns one particle and keeps its whole problem on chip.
 // For P1 elements on the uniform mesh whose cells are split by the (i,j)-(i+1,j+1)
 // diagonal the stiffness matrix is a 5-point stencil: edge (i,j)-(i+1,j) has
 // weight (kappa_lower(i,j) + kappa_upper(i,j-1))/2, edge (i,j)-(i,j+1) has weight
-// (kappa_lower(i-1,j) + kappa_upper(i,j))/2, diagonal-edge couplings vanish, and
-// the load of f = 1 is h^2 at every interior node. The linear system is solved
-// matrix-free by multigrid-preconditioned CG:
+// (kappa_lower(i-1,j) + kappa_upper(i,j))/2, and diagonal-edge couplings vanish. The
+// load of f = 1 is h^2 at every interior node; any other f comes as a load-vector table
+// (the nine sources of Example 5.1). The linear system is solved matrix-free by
+// multigrid-preconditioned CG:
 //  * hierarchy N, N/2, ..., 2 cells per side; the coarse mesh is nested, the
 //    prolongation is P1 interpolation and restriction its transpose, and the
 //    coarse operator is the same stencil built from the mean kappa of the four
 //    fine triangles inside each coarse triangle -- for piecewise-constant kappa
 //    this equals the Galerkin product P^T A P exactly;
 //  * symmetric V(1,1) cycle with red-black Gauss-Seidel (red-black before the
-//    coarse correction, black-red after), exact solve on the single coarsest node;
+//    coarse correction, black-red after), fused so that each level needs five barriers;
+//    the coarsest level is solved exactly (the 9 x 9 inverse at 1/4 on the FP32 path,
+//    the single node at 1/2 otherwise);
 //  * SMC_MIXED: the field, stencil, multigrid and CG run in FP32; each pass ends
-//    with an FP64 update of the residual r <- r - A d, computed in edge form
-//    sum_e a_e (d_i - d_j) from the FP32 edge weights (so its diagonal is their
-//    exact sum), and an FP64 accumulation x <- x + d, until the FP64 relative
-//    residual reaches rtol (mixed-precision iterative refinement);
+//    with the update of the residual r <- r - A d in double-float arithmetic, in edge
+//    form sum_e a_e (d_i - d_j) from the FP32 edge weights (so its diagonal is their
+//    exact sum), and x <- x + d, until the relative residual reaches rtol
+//    (mixed-precision iterative refinement, no FP64 instruction in the solve);
 //    SMC_FP64: the same algorithm in FP64 throughout.
-// Shared memory holds, per level, the edge weights aE, aN, the diagonal D and the
+// Shared memory holds, per level, the edge weights aE, aN, the inverse diagonal and the
 // vectors e (multigrid correction), res (residual) and rhs (fine level: the CG
-// direction p). The fine-level CG vectors r, d and the FP64 x, r live in
-// registers: every fine node belongs to one thread for the whole solve.
+// direction p). The fine-level CG vectors r, d, z, p of a thread's nodes live in
+// registers (every fine node belongs to one thread for the whole solve); the
+// refinement state x, r (double-float pairs) lives in shared memory, or in a per-block
+// slice of device memory in the compact forms (two or four blocks per SM, coarse levels
+// without residual and inverse-diagonal arrays). Levels 1/128 and 1/256 keep their two
+// finest levels in device memory (fem_eval_global).
 #include <cuda_runtime.h>
 
 #include <cmath>
