@@ -1,7 +1,8 @@
 // Host controller of the MLS^2MC sampler (Sec. 4): the update scheme of Eq. eq_updatescheme_final
-// with the cv^LU predictor on the first J~ particles (Sec. 4.4). All per-particle work is queued on
-// the device (likelihood, increment search, resampling, pCN); the host reads back a few scalars
-// per update (the chosen increment, log mean weight, cv, accept count).
+// with the cv^LU predictor on the first J~ particles (Sec. 4.4), or the scheme u' of Eq.
+// eq_updatescheme_final_Lmax (Sec. 4.5) when opts.tau_min > 0. All per-particle work is queued on
+// the device (likelihood, increment search, resampling, pCN or random-walk moves); the host reads
+// back a few scalars per update (the chosen increment, log mean weight, cv, accept count).
 //
 // Order of operations and random draws (Philox counter layout) are the library's convention:
 //   prior particles              event 0, purpose 1 (normals)
@@ -11,7 +12,9 @@
 // delta took the whole remaining step) and runs n_mcmc pCN steps for exp(-beta Phi_l) mu0. An LU
 // evaluates Phi_{l+1} on all particles (reusing the J~ predictor evaluations), then bridges
 // zeta = 0 -> 1 with weights exp(-beta dzeta (Phi_{l+1} - Phi_l)), resampling and pCN steps for
-// exp(-beta((1 - zeta) Phi_l + zeta Phi_{l+1})) mu0 that solve both levels per proposal.
+// exp(-beta((1 - zeta) Phi_l + zeta Phi_{l+1})) mu0 that solve both levels per proposal. The
+// Markov kernel is pCN, or the random walk of Sec. 5 (opts.proposal; the same draws, theta' =
+// theta + s xi, with the prior ratio in the acceptance).
 #include <cuda_runtime.h>
 
 #include <cmath>

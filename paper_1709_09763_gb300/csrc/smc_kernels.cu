@@ -1,5 +1,6 @@
 // Sampler kernels, all FP64: linear test forward model, Philox draws, adaptive increment
-// search (cv target), evidence increment, systematic resampling, pCN propose/accept.
+// search (cv target), evidence increment, systematic resampling, pCN / random-walk propose and
+// accept, the two stages of delayed acceptance.
 //
 // Sources: cv and ESS of the incremental weights (Sec. 3.4, Eq. EQ:ESS:SMC_Update, population
 // moments); the next inverse temperature / bridging temperature minimises (cv - tau*)^2 over
