@@ -526,7 +526,12 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "per_level": {str(N): {"evals_per_s": 2 * J * world / (lm * 1e-3), "update_ms": lm,
                                    "solve_launch_ms": kern_ms[l] / max(kern_n[l], 1),
-                                   "solve_evals_per_s": J / (kern_ms[l] / max(kern_n[l], 1) * 1e-3)}
+                                   "solve_evals_per_s": J / (kern_ms[l] / max(kern_n[l], 1) * 1e-3),
+                                   "solve_kernel": solve_kernel_name(N, tuned[l]),
+                                   # shared-memory roofline of the level's solve (mean CG iterations
+                                   # of the finest level stand in for every level: 10-12 measured)
+                                   "smem_frac": algorithmic_smem_bytes_per_eval(N, mean_it, 2.0) * J /
+                                   (kern_ms[l] / max(kern_n[l], 1) * 1e-3) / 1e12 / smem_peak}
                           for l, (N, lm) in enumerate(zip(w.inv_h, lvl_ms))},
             "roofline": {"kernel": solve_kernel_name(w.inv_h[-1], tuned[-1]), "bound": "alu",
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
