@@ -145,6 +145,25 @@ def solve(N, kappa, f=None, A=None):
     return p
 
 
+def solve_flow_cell(N, kappa, A=None):
+    """Nodal P1 solution of the flow cell of Example 5.3 (Sec. 5): -div(kappa grad p) = 0 with
+    p = 0 on x = 0, p = 1 on x = 1 and no flow (homogeneous Neumann) on y = 0 and y = 1. The
+    unknowns are the nodes with 0 < x < 1, boundary rows included; the Dirichlet values enter the
+    right-hand side as -A_UD p_D."""
+    if A is None:
+        A = assemble(N, kappa)
+    nodes = np.arange((N + 1) ** 2)
+    i = nodes % (N + 1)
+    U = nodes[(i > 0) & (i < N)]
+    D = nodes[(i == 0) | (i == N)]
+    pD = np.where(i[D] == N, 1.0, 0.0)
+    A = A.tocsr()
+    p = np.zeros((N + 1) ** 2)
+    p[D] = pD
+    p[U] = spla.spsolve(A[U][:, U].tocsc(), -(A[U][:, D] @ pD))
+    return p
+
+
 def observation_operator(N, obs_xy):
     """Sparse (n_obs, (N+1)^2) matrix of P1 interpolation weights at the points obs_xy.
 

@@ -20,10 +20,16 @@ class Level:
     """One discretisation level: mesh N = 1/h, KL table and observation operator.
 
     cov: "sep_exp" (separable exponential, analytic KL) or "matern" (nu = 3/2, Nystrom KL);
-    f: source term f(x, y), None for f = 1."""
+    f: source term f(x, y), None for f = 1; bc: "dirichlet" (p = 0 on the boundary) or
+    "flow_cell" (Example 5.3: p = 0 / 1 on x = 0 / 1, no flow on y = 0, 1, f = 0); m0: the prior
+    mean of the field (Eq. truncKL)."""
 
-    def __init__(self, N, corr_len, variance, K, obs_xy, f=None, cov="sep_exp"):
+    def __init__(self, N, corr_len, variance, K, obs_xy, f=None, cov="sep_exp", bc="dirichlet", m0=0.0):
         self.N = N
+        if bc not in ("dirichlet", "flow_cell"):
+            raise ValueError("bc must be 'dirichlet' or 'flow_cell'")
+        self.bc = bc
+        self.m0 = m0
         if cov == "sep_exp":
             self.psi = kl.kl_table(N, corr_len, variance, K)
         elif cov == "matern":
@@ -35,9 +41,11 @@ class Level:
 
     def field(self, theta):
         """u on every triangle for one particle (Eq. truncKL)."""
-        return np.asarray(theta, dtype=np.float64) @ self.psi
+        return self.m0 + np.asarray(theta, dtype=np.float64) @ self.psi
 
     def solution(self, theta):
+        if self.bc == "flow_cell":
+            return fem.solve_flow_cell(self.N, np.exp(self.field(theta)))
         return fem.solve(self.N, np.exp(self.field(theta)), self.f)
 
     def G(self, theta):

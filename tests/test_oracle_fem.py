@@ -135,3 +135,56 @@ def test_observation_operator():
     O = fem.observation_operator(16, q)
     assert np.allclose(O @ lin, 0.3 + 1.7 * q[:, 0] - 0.4 * q[:, 1], atol=1e-14)
     assert np.allclose(O.sum(axis=1), 1.0)
+
+
+def _column_kappa(N, k):
+    """kappa constant in each column of cells (both triangles of cell (i, j) take k[i])."""
+    kap = np.empty(2 * N * N)
+    for j in range(N):
+        for i in range(N):
+            kap[2 * (j * N + i)] = kap[2 * (j * N + i) + 1] = k[i]
+    return kap
+
+
+def test_flow_cell_linear_solution_for_constant_kappa():
+    """Example 5.3's boundary conditions with kappa = c: p(x, y) = x at every node (P1 reproduces
+    the exact linear solution)."""
+    N = 16
+    p = fem.solve_flow_cell(N, np.full(2 * N * N, 3.7))
+    x = np.tile(np.arange(N + 1) / N, N + 1)
+    assert np.max(np.abs(p - x)) < 1e-12
+
+
+def test_flow_cell_series_conductances():
+    """kappa constant in each column of cells: the flow is one-dimensional and the nodal pressure
+    is the series-resistance formula p(x_i) = sum_{m<i} 1/k_m / sum_m 1/k_m on every row, the
+    boundary rows (half conductances) included."""
+    N = 16
+    k = np.exp(np.random.default_rng(3).normal(0, 1, N))
+    p = fem.solve_flow_cell(N, _column_kappa(N, k)).reshape(N + 1, N + 1)
+    r = np.concatenate([[0.0], np.cumsum(1.0 / k)]) / np.sum(1.0 / k)
+    assert np.max(np.abs(p - r[None, :])) < 1e-12
+
+
+def test_flow_cell_half_turn_and_maximum_principle():
+    """For kappa invariant under the half turn (x, y) -> (1-x, 1-y), which maps the mesh and swaps
+    the two Dirichlet sides, p(1-x, 1-y) = 1 - p(x, y); for any kappa 0 <= p <= 1."""
+    N = 16
+    rng = np.random.default_rng(8)
+    kap = np.exp(rng.normal(0, 1, 2 * N * N))
+    kap = 0.5 * (kap + kap[::-1])            # element e <-> 2N^2 - 1 - e is the half turn
+    p = fem.solve_flow_cell(N, kap).reshape(N + 1, N + 1)
+    assert np.max(np.abs(p[::-1, ::-1] - (1.0 - p))) < 1e-12
+    q = fem.solve_flow_cell(N, np.exp(rng.normal(0, 1.5, 2 * N * N)))
+    assert q.min() >= -1e-14 and q.max() <= 1 + 1e-14
+
+
+def test_flow_cell_prior_mean_scales_out():
+    """f = 0 and Dirichlet data: kappa -> c kappa leaves p unchanged, so the prior mean m0 = 2 of
+    Example 5.3 does not change G (checked through the forward map with and without m0)."""
+    from oracle import forward
+    obs = np.array([[0.25, 0.5], [0.5, 0.125], [0.875, 0.75]])
+    th = np.random.default_rng(1).normal(0, 1, 4)
+    a = forward.Level(16, 0.3, 1.0, 4, obs, bc="flow_cell").G(th)
+    b = forward.Level(16, 0.3, 1.0, 4, obs, bc="flow_cell", m0=2.0).G(th)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-14) and np.all((a > 0) & (a < 1))
