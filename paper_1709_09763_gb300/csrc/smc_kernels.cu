@@ -454,11 +454,12 @@ __global__ void __launch_bounds__(kRsThreads) resample_gather_kernel(
     if (tid == 0) ok_s = grid_barrier(bar, err, nb, generation);
     __syncthreads();
     if (!ok_s) return;
-    for (long long t = (long long)blockIdx.x * kRsThreads + tid; t < (long long)n * K; t += (long long)nb * kRsThreads) {
-        const int i = (int)(t / K), k = (int)(t - (long long)i * K);
+    // gather: one warp per particle row (coalesced over k), rows spread over every warp of the grid
+    const int n_warps = (int)nb * (kRsThreads / 32);
+    for (int i = (int)blockIdx.x * (kRsThreads / 32) + wid; i < n; i += n_warps) {
         const int src = __ldcg(&anc[i]);
-        th_out[t] = th_in[(size_t)src * K + k];
-        if (k == 0) {
+        for (int k = lane; k < K; k += 32) th_out[(size_t)i * K + k] = th_in[(size_t)src * K + k];
+        if (lane == 0) {
             if (p0_in) p0_out[i] = p0_in[src];
             if (p1_in) p1_out[i] = p1_in[src];
         }
@@ -790,7 +791,9 @@ cudaError_t resample_gather_launch(const double* a, int n, const IncState* state
                                    const double* p1_in, double* p1_out, double* cdf, int* anc, IncWork& w,
                                    cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    const int nb = std::min(kIncMaxBlocks, std::max(1, (n + kRsThreads - 1) / kRsThreads));
+    // one block per 32 particles (up to kIncMaxBlocks): the searches and the row gather are
+    // latency-bound, so they want many warps in flight
+    const int nb = std::min(kIncMaxBlocks, std::max(1, (n + 31) / 32));
     cudaError_t e = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     double* btot = w.partials;   // the search is finished: its scratch is free
