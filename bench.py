@@ -412,11 +412,11 @@ def main():
     # delayed-acceptance pCN screened by the surrogate, R seeds each, outside the timed region
     run = None
     if not args.no_run:
-        def one_run(wk, dk, inv_h, surrogate, seed):
+        def one_run(wk, dk, inv_h, surrogate, seed, precision=native.SMC_MIXED):
             ob = wl.obs_grid(wk.obs_per_side)
             hr = native.Handle(inv_h, wk.K, ob, dk["y"], dk["sigma"], corr_len=wk.corr_len, variance=wk.variance,
                                J=wk.J, J_tilde=wk.J_tilde, n_mcmc=wk.n_mcmc, s_pcn=wk.s_pcn,
-                               tau_star=wk.tau_star, precision=native.SMC_MIXED, seed=seed,
+                               tau_star=wk.tau_star, precision=precision, seed=seed,
                                stream=stream.cuda_stream, surrogate=surrogate, cov=wk.cov, source=wk.source,
                                proposal=wk.proposal)
             torch.cuda.synchronize(dev)
@@ -488,6 +488,17 @@ def main():
             res["cost_ratio_smc_over_mls2mc"] = (res["smc_finest"]["cost_finest_solves_mean"] /
                                                  res["mls2mc"]["cost_finest_solves_mean"])
             return res
+        # single-level SMC on the FP64 path (h = 1/16, K = 16, J = 1000, 5 pCN steps)
+        wf, dfp = wl.WORKLOADS["smc_fp64_h16"], load_data("smc_fp64_h16")
+        fr = [one_run(wf, dfp, tuple(wf.inv_h), 0, wf.seed_sampler + 17 * r, native.SMC_FP64) for r in range(3)]
+        run["smc_fp64_h16"] = {"workload": wf.name, "levels_inv_h": list(wf.inv_h), "K": wf.K, "J": wf.J,
+                               "n_mcmc": wf.n_mcmc, "precision": "fp64",
+                               "seconds_median": float(np.median([x["seconds"] for x in fr])),
+                               "seconds": [x["seconds"] for x in fr],
+                               "solves_mean": float(np.mean([x["solves_per_level"][0] for x in fr])),
+                               "solves_per_s": float(np.mean([x["solves_per_level"][0] / x["seconds"] for x in fr])),
+                               "updates": [x["updates"] for x in fr],
+                               "log_evidence": [x["log_evidence"] for x in fr]}
         run["paper_example_5_1"] = paper_example("example_5_1")
         run["paper_example_5_2"] = paper_example("example_5_2")
 
