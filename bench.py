@@ -406,7 +406,9 @@ def main():
         torch.cuda.synchronize(dev)
         e2e_ms.append(e0.elapsed_time(e1))
     e2e = float(np.mean(e2e_ms))
-    e2e_evals = evals_per_step + J          # smc_set_particles evaluates Phi on the coarsest level
+    # the step's evaluations only: smc_set_particles also evaluates Phi on the coarsest level (J cheap
+    # solves), which the timed region includes but the count leaves out
+    e2e_evals = evals_per_step
 
     # seconds to posterior: full MLS^2MC runs (n_mcmc = 5) of the workload from the prior, plain pCN and
     # delayed-acceptance pCN screened by the surrogate, R seeds each, outside the timed region
