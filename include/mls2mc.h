@@ -61,6 +61,12 @@ extern "C" {
 #define SMC_SRC_NINE    1  /* the nine smoothed point sources of Example 5.1: products of 1-D Gaussian
                               densities N(x1; 0.25 n, 0.001) N(x2; 0.25 m, 0.001), n, m = 1..3; load
                               vector by the edge-midpoint rule on every triangle */
+/* boundary conditions of the PDE */
+#define SMC_BC_DIRICHLET 0 /* p = 0 on the whole boundary (Examples 5.1, 5.2) */
+#define SMC_BC_FLOW_CELL 1 /* the flow cell of Example 5.3: p = 0 on x = 0, p = 1 on x = 1, no flow on
+                              y = 0 and y = 1, f = 0 (source_kind must be SMC_SRC_ONE and is ignored);
+                              levels 1/8 .. 1/64 (FP64: .. 1/32); the pressure does not depend on a
+                              uniform scale of kappa, so a prior mean m0 of the field has no effect */
 /* Markov kernel of the sampler */
 #define SMC_PROP_PCN    0  /* theta' = sqrt(1 - s^2) theta + s xi */
 #define SMC_PROP_RWM    1  /* theta' = theta + s xi (random walk of Sec. 5; s^2 = 2.38^2 / K there),
@@ -81,6 +87,7 @@ typedef struct {
     const double* linear_A;    /* SMC_FWD_LINEAR only: [n_levels][n_obs][K] */
     int cov_kind;              /* SMC_COV_SEP_EXP (0, the default) or SMC_COV_MATERN */
     int source_kind;           /* SMC_SRC_ONE (0, the default) or SMC_SRC_NINE */
+    int bc_kind;               /* SMC_BC_DIRICHLET (0, the default) or SMC_BC_FLOW_CELL */
 } smc_problem_desc;
 
 typedef struct {

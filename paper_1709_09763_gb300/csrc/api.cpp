@@ -158,6 +158,7 @@ FemArgs Handle::fem_args(int level, int n, const double* theta, double* G, doubl
     a.max_inner = max_iter;
     a.rhs = L.rhs;
     a.bnorm2 = L.bnorm2;
+    a.flow_cell = flow_cell;
     return a;
 }
 
@@ -208,6 +209,7 @@ int Handle::eval_device(int level, int n, const double* theta, double* G, double
         }
         int T = tuned_block(L.N, precision);
         if (T == 0) T = fem_default_block(L.N, precision);
+        if (flow_cell) T = 0;   // the flow cell has one (one-block) form per level
         if (T < 0) {   // compact form: persistent blocks with their refinement state in device memory
             const int blocks = fem_compact_blocks(L.N, -T);
             if (blocks <= 0) return fail(SMC_EINVAL, "no compact form with %d threads at 1/h = %d", -T, L.N);
@@ -283,6 +285,15 @@ int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** 
             return bail(h->fail(SMC_EINVAL, "the Matern KL keeps at most %d terms", matern_max_terms()));
         if (P->source_kind != SMC_SRC_ONE && P->source_kind != SMC_SRC_NINE)
             return bail(h->fail(SMC_EINVAL, "unknown source_kind"));
+        if (P->bc_kind != SMC_BC_DIRICHLET && P->bc_kind != SMC_BC_FLOW_CELL)
+            return bail(h->fail(SMC_EINVAL, "unknown bc_kind"));
+        if (P->bc_kind == SMC_BC_FLOW_CELL) {
+            if (P->source_kind != SMC_SRC_ONE) return bail(h->fail(SMC_EINVAL, "the flow cell has f = 0"));
+            const int top = O->precision == SMC_MIXED ? 64 : 32;
+            for (int l = 0; l < P->n_levels; ++l)
+                if (P->inv_h[l] < 8 || P->inv_h[l] > top)
+                    return bail(h->fail(SMC_EINVAL, "flow cell: 1/h must be in [8, %d] at this precision", top));
+        }
         for (int l = 0; l < P->n_levels; ++l) {
             if (!fem_level_supported(P->inv_h[l], O->precision))
                 return bail(h->fail(SMC_EINVAL, "level %d: 1/h = %d not supported at this precision", l, P->inv_h[l]));
@@ -298,6 +309,7 @@ int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** 
     h->n_obs = P->n_obs;
     h->sigma = P->sigma;
     h->forward_kind = P->forward_kind;
+    h->flow_cell = P->forward_kind == SMC_FWD_FEM && P->bc_kind == SMC_BC_FLOW_CELL ? 1 : 0;
     h->precision = O->precision;
     h->opts = *O;
     h->stream = (cudaStream_t)O->stream;
@@ -415,6 +427,13 @@ int smc_autotune(smc_handle* hh, int n_tune, int* chosen, float* best_ms) {
     if (!hh || n_tune < 1) return SMC_EINVAL;
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (h->forward_kind != SMC_FWD_FEM) return SMC_OK;
+    if (h->flow_cell) {   // one form per level: nothing to choose, and nothing to impose on other handles
+        for (int l = 0; l < (int)h->levels.size(); ++l) {
+            if (chosen) chosen[l] = 0;
+            if (best_ms) best_ms[l] = 0.f;
+        }
+        return SMC_OK;
+    }
     int rc = h->ensure_scratch(n_tune);
     if (rc != SMC_OK) return rc;
     cudaStream_t st = h->stream;

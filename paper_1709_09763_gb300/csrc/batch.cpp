@@ -99,7 +99,9 @@ int smc_batch_create(int n, smc_handle* const* handles, smc_batch** out) {
     Batch* b = new Batch();
     for (int i = 0; i < n; ++i) {
         Handle* h = reinterpret_cast<Handle*>(handles[i]);
-        if (!h || h->forward_kind != SMC_FWD_FEM || std::find(b->h.begin(), b->h.end(), h) != b->h.end()) {
+        // the persistent multi-problem forms solve the Dirichlet problem only
+        if (!h || h->forward_kind != SMC_FWD_FEM || h->flow_cell ||
+            std::find(b->h.begin(), b->h.end(), h) != b->h.end()) {
             delete b;
             return SMC_EINVAL;
         }

@@ -49,10 +49,18 @@ namespace mls2mc {
 namespace {
 
 __host__ __device__ constexpr int padded(int n) { return (n + 3) & ~3; }
-__host__ __device__ constexpr int lvl_size(int NL) { return padded((NL + 1) * fem_row_stride(NL)); }
+// FC (the flow cell of Example 5.3): the rows j = 0 and j = NL are unknowns, so every array of a
+// level gets a zero ghost row below and above (NL + 3 rows, the array pointer on row 0)
+__host__ __device__ constexpr int lvl_size(int NL, bool FC = false) {
+    return padded((NL + (FC ? 3 : 1)) * fem_row_stride(NL));
+}
 // element offset of level NL inside the shared arena of a hierarchy with top level N
-__host__ __device__ constexpr int lvl_offset(int N, int NL) { return N == NL ? 0 : 6 * lvl_size(N) + lvl_offset(N / 2, NL); }
-__host__ __device__ constexpr int arena_size(int N) { return N < 2 ? 0 : 6 * lvl_size(N) + arena_size(N / 2); }
+__host__ __device__ constexpr int lvl_offset(int N, int NL, bool FC = false) {
+    return N == NL ? 0 : 6 * lvl_size(N, FC) + lvl_offset(N / 2, NL, FC);
+}
+__host__ __device__ constexpr int arena_size(int N, bool FC = false) {
+    return N < 2 ? 0 : 6 * lvl_size(N, FC) + arena_size(N / 2, FC);
+}
 
 template <typename Real>
 struct Lv {
@@ -69,8 +77,13 @@ __host__ __device__ constexpr int coarse_offset_cp(int NL, int NC) {
 }
 __host__ __device__ constexpr int arena_size_cp(int N) { return 5 * lvl_size(N) + coarse_size_cp(N / 2); }
 
-template <typename Real, int N, int NL, bool CP = false>
+template <typename Real, int N, int NL, bool CP = false, bool FC = false>
 __device__ __forceinline__ Lv<Real> level_ptrs(Real* arena) {
+    if constexpr (FC) {   // ghost row -1 first: each pointer is one row stride into its array
+        constexpr int z = lvl_size(NL, true);
+        Real* b = arena + lvl_offset(N, NL, true) + fem_row_stride(NL);
+        return Lv<Real>{b, b + z, b + 2 * z, b + 3 * z, b + 4 * z, b + 5 * z};
+    }
     constexpr int z = lvl_size(NL);
     if constexpr (!CP) {
         Real* b = arena + lvl_offset(N, NL);
@@ -168,14 +181,17 @@ __device__ __forceinline__ void df_add(Real& ah, Real& al, Real bh, Real bl) {
 // same positions of row 2R + 2. With the even row stride the two rows' nodes of one colour lie on
 // banks of opposite parity, so for NL >= 32 a warp's 32 accesses hit 32 distinct banks. All
 // divisions are by powers of two. Returns false for idle positions.
-template <int NL>
+// FC: rows 0 .. NL are unknowns (pairs 2R, 2R + 1), colour_positions<NL, true> positions.
+template <int NL, bool FC = false>
+__host__ __device__ constexpr int colour_positions() { return FC ? (NL / 2 + 1) * NL : NL * NL / 2; }
+template <int NL, bool FC = false>
 __device__ __forceinline__ bool colour_node(int k, int col, int& i, int& j) {
     constexpr int G = NL / 2 < 16 ? NL / 2 : 16;
     const int blk = k / (2 * G), l = k - blk * 2 * G;
     const int R = blk / (NL / 2 / G), sg = blk - R * (NL / 2 / G);
-    j = 2 * R + 1 + l / G;
+    j = 2 * R + (FC ? 0 : 1) + l / G;
     i = (((j & 1) ^ col) ? 1 : 2) + 2 * (sg * G + l % G);
-    return k < NL * NL / 2 && j <= NL - 1 && i <= NL - 1;
+    return k < colour_positions<NL, FC>() && j <= (FC ? NL : NL - 1) && i <= NL - 1;
 }
 
 // ---- coarse-level multigrid pieces (rhs in shared memory) --------------------------------
@@ -188,12 +204,12 @@ __device__ __forceinline__ bool colour_node(int k, int col, int& i, int& j) {
 //  - Gauss-Seidel overwrites a node from its neighbours alone, so the coarse correction added to
 //    the black nodes and the red nodes' pre-sweep values are never read: the black post-sweep
 //    reads its red neighbours as e + P e_c directly.
-template <typename Real, int NL, int T>
+template <typename Real, int NL, int T, bool FC = false>
 __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
     constexpr int S = fem_row_stride(NL);
-    for (int k = threadIdx.x; k < NL * NL / 2; k += T) {
+    for (int k = threadIdx.x; k < colour_positions<NL, FC>(); k += T) {
         int i, j;
-        if (!colour_node<NL>(k, color, i, j)) continue;
+        if (!colour_node<NL, FC>(k, color, i, j)) continue;
         const int n = j * S + i;
         L.e[n] = (L.rhs[n] + offsum<Real, S>(L.aE, L.aN, L.e, n)) * inv_diag<Real, S>(L, n);
     }
@@ -206,11 +222,12 @@ __device__ __forceinline__ void smooth_color(const Lv<Real>& L, int color) {
 //
 // The coarse level's red pre-sweep from zero (e = rhs / D at red nodes) is folded in: it needs
 // nothing but the node's own rhs.
-template <typename Real, int NC, int T>
+template <typename Real, int NC, int T, bool FC = false>
 __device__ __forceinline__ void restrict_red(const Lv<Real>& F, const Lv<Real>& C) {
     constexpr int MC = NC - 1, SC = fem_row_stride(NC), SF = fem_row_stride(2 * NC);
-    for (int idx = threadIdx.x; idx < MC * MC; idx += T) {
-        const int J = idx / MC + 1, I = idx - (J - 1) * MC + 1;
+    constexpr int ROWS = FC ? NC + 1 : MC, ROW0 = FC ? 0 : 1;   // coarse rows with unknowns
+    for (int idx = threadIdx.x; idx < MC * ROWS; idx += T) {
+        const int J = idx / MC + ROW0, I = idx - (J - ROW0) * MC + 1;
         const int f = (2 * J) * SF + 2 * I, c = J * SC + I;
         const Real v = offsum<Real, SF>(F.aE, F.aN, F.e, f) +
                        Real(0.5) * (offsum<Real, SF>(F.aE, F.aN, F.e, f + SF + 1) +
@@ -222,11 +239,12 @@ __device__ __forceinline__ void restrict_red(const Lv<Real>& F, const Lv<Real>& 
 
 // the same restriction from red residuals stored in res (fine level of the on-chip solve, where
 // each thread computes the residuals of its own red nodes first)
-template <typename Real, int NC, int T>
+template <typename Real, int NC, int T, bool FC = false>
 __device__ __forceinline__ void restrict_gather(const Real* res, const Lv<Real>& C) {
     constexpr int MC = NC - 1, SC = fem_row_stride(NC), SF = fem_row_stride(2 * NC);
-    for (int idx = threadIdx.x; idx < MC * MC; idx += T) {
-        const int J = idx / MC + 1, I = idx - (J - 1) * MC + 1;
+    constexpr int ROWS = FC ? NC + 1 : MC, ROW0 = FC ? 0 : 1;
+    for (int idx = threadIdx.x; idx < MC * ROWS; idx += T) {
+        const int J = idx / MC + ROW0, I = idx - (J - ROW0) * MC + 1;
         const int f = (2 * J) * SF + 2 * I, c = J * SC + I;
         const Real v = res[f] + Real(0.5) * (res[f + SF + 1] + res[f - SF - 1]);
         C.rhs[c] = v;
@@ -236,10 +254,21 @@ __device__ __forceinline__ void restrict_gather(const Real* res, const Lv<Real>&
 
 // zero the boundary rings of e, res, rhs on every level from NL down (interior values are always
 // written before they are read; the rings must read as zero)
-template <typename Real, int N, int NL, int T, bool CP = false>
+template <typename Real, int N, int NL, int T, bool CP = false, bool FC = false>
 __device__ __forceinline__ void zero_rings(Real* arena) {
     constexpr int S = fem_row_stride(NL);
-    const Lv<Real> L = level_ptrs<Real, N, NL, CP>(arena);
+    const Lv<Real> L = level_ptrs<Real, N, NL, CP, FC>(arena);
+    if constexpr (FC) {
+        // ghost rows -1 and NL + 1 (whole rows), and the Dirichlet columns 0 and NL and the padding
+        // column NL + 1 of rows 0 .. NL; rows 0 and NL are unknowns here
+        for (int k = threadIdx.x; k < 2 * S + 3 * (NL + 1); k += T) {
+            const int n = k < S ? k - S : k < 2 * S ? (NL + 1) * S + (k - S)
+                        : ((k - 2 * S) / 3) * S + ((k - 2 * S) % 3 == 0 ? 0 : (k - 2 * S) % 3 == 1 ? NL : NL + 1);
+            L.e[n] = L.rhs[n] = L.res[n] = Real(0);
+        }
+        if constexpr (NL > 4) zero_rings<Real, N, NL / 2, T, false, true>(arena);
+        return;
+    }
     for (int k = threadIdx.x; k < 4 * NL; k += T) {   // rows 0 and NL, then columns 0 and NL
         const int n = k <= NL ? k : k <= 2 * NL + 1 ? NL * S + (k - NL - 1)
                                                      : (1 + ((k - 2 * NL - 2) >> 1)) * S + (((k - 2 * NL - 2) & 1) ? NL : 0);
@@ -266,12 +295,12 @@ __device__ __forceinline__ Real offsum_prolong(const Real* aE, const Real* aN, c
 }
 
 // black post-sweep with the coarse correction of level NL / 2 folded in
-template <typename Real, int NL, int T>
+template <typename Real, int NL, int T, bool FC = false>
 __device__ __forceinline__ void black_prolong(const Lv<Real>& L, const Real* ec) {
     constexpr int S = fem_row_stride(NL), SC = fem_row_stride(NL / 2);
-    for (int k = threadIdx.x; k < NL * NL / 2; k += T) {
+    for (int k = threadIdx.x; k < colour_positions<NL, FC>(); k += T) {
         int i, j;
-        if (!colour_node<NL>(k, 1, i, j)) continue;
+        if (!colour_node<NL, FC>(k, 1, i, j)) continue;
         const int n = j * S + i;
         const int c0 = (j >> 1) * SC + (i >> 1);
         L.e[n] = (L.rhs[n] + offsum_prolong<Real, S, SC>(L.aE, L.aN, L.e, ec, n, c0, (j & 1) == 0)) *
@@ -287,15 +316,19 @@ __device__ __forceinline__ void black_prolong(const Lv<Real>& L, const Real* ec)
 // higher, m = 49, lowers the iteration count by about 8 % but its m^3 setup costs more than that.)
 // The FP64 path keeps the full cycle: its Gauss-Jordan setup would run on the FP64 pipe, which
 // on this part costs more than the cycles it saves.
-template <typename Real>
+// The flow cell (FC) always stops at 1/4 (15 unknowns: rows 0 .. 4 of columns 1 .. 3), on both
+// paths: its coarsest levels would need the boundary rows in the single-node solve.
+template <typename Real, bool FC = false>
 __host__ __device__ constexpr int direct_level(int N) {
-    return sizeof(Real) == 8 ? 0 : (N >= 16 ? 4 : 0);
+    return FC ? (N >= 8 ? 4 : 0) : sizeof(Real) == 8 ? 0 : (N >= 16 ? 4 : 0);
 }
-template <typename Real>
+// unknowns of the dense level NL: (NL - 1)^2, or (NL - 1)(NL + 1) for the flow cell
+__host__ __device__ constexpr int dense_unknowns(int NL, bool FC) { return (NL - 1) * (FC ? NL + 1 : NL - 1); }
+template <typename Real, bool FC = false>
 __host__ __device__ constexpr int dense_reals(int N) {
-    return direct_level<Real>(N) ? padded((direct_level<Real>(N) - 1) * (direct_level<Real>(N) - 1) *
-                                          ((direct_level<Real>(N) - 1) * (direct_level<Real>(N) - 1) + 4))
-                                 : 0;
+    return direct_level<Real, FC>(N) ? padded(dense_unknowns(direct_level<Real, FC>(N), FC) *
+                                              (dense_unknowns(direct_level<Real, FC>(N), FC) + 4))
+                                     : 0;
 }
 
 // Ainv [m][m] := A^{-1} by in-place Gauss-Jordan elimination without pivoting (A is symmetric
@@ -303,14 +336,14 @@ __host__ __device__ constexpr int dense_reals(int N) {
 // pivot into 1 / a_kk and every other entry into a_uv - a_uk a_kv / a_kk; the old row and column
 // k are read from a buffer that step k - 1 filled, so one barrier per step suffices.
 // Ainv is followed by that buffer: [2][row | column], 4m Reals.
-template <typename Real, int NL, int T>
+template <typename Real, int NL, int T, bool FC = false>
 __device__ void dense_setup(const Lv<Real>& L, Real* Ainv) {
-    constexpr int MM = NL - 1, m = MM * MM, S = fem_row_stride(NL);
+    constexpr int MM = NL - 1, m = dense_unknowns(NL, FC), S = fem_row_stride(NL), ROW0 = FC ? 0 : 1;
     Real* buf = Ainv + m * m;
     for (int idx = threadIdx.x; idx < m * m; idx += T) {
         const int u = idx / m, v = idx - u * m;
         const int ui = u % MM, uj = u / MM, vi = v % MM, vj = v / MM;
-        const int n = (uj + 1) * S + ui + 1;
+        const int n = (uj + ROW0) * S + ui + 1;
         Real val = 0;
         if (u == v) val = L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S];
         else if (uj == vj && vi == ui + 1) val = -L.aE[n];
@@ -343,19 +376,19 @@ __device__ void dense_setup(const Lv<Real>& L, Real* Ainv) {
 }
 
 // L.e = Ainv L.rhs on the interior nodes: 8 lanes per row, reduced by warp shuffles
-template <typename Real, int NL, int T>
+template <typename Real, int NL, int T, bool FC = false>
 __device__ __forceinline__ void dense_solve(const Lv<Real>& L, const Real* Ainv) {
-    constexpr int MM = NL - 1, m = MM * MM, S = fem_row_stride(NL);
+    constexpr int MM = NL - 1, m = dense_unknowns(NL, FC), S = fem_row_stride(NL), ROW0 = FC ? 0 : 1;
     constexpr int W = (m * 8 + 31) / 32 * 32;   // whole warps: every lane takes part in the shuffles
     for (int w = threadIdx.x; w < W; w += T) {
         const int u = w >> 3, part = w & 7;
         Real acc = 0;
         if (u < m)
-            for (int v = part; v < m; v += 8) acc = fma(Ainv[u * m + v], L.rhs[(v / MM + 1) * S + v % MM + 1], acc);
+            for (int v = part; v < m; v += 8) acc = fma(Ainv[u * m + v], L.rhs[(v / MM + ROW0) * S + v % MM + 1], acc);
         acc += __shfl_xor_sync(0xffffffffu, acc, 4);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        if (part == 0 && u < m) L.e[(u / MM + 1) * S + u % MM + 1] = acc;
+        if (part == 0 && u < m) L.e[(u / MM + ROW0) * S + u % MM + 1] = acc;
     }
 }
 
@@ -369,31 +402,31 @@ __device__ __forceinline__ void phase_sync() {
 // V(1,1) cycle on a coarse level: reads L.rhs, writes L.e. Levels with at most 4 cells per side
 // (<= 9 unknowns) run inside warp 0 only (T = 32, warp barriers); the caller's next block
 // barrier publishes the result.
-template <typename Real, int N, int NL, int T, bool WARP = false, bool CP = false>
+template <typename Real, int N, int NL, int T, bool WARP = false, bool CP = false, bool FC = false>
 __device__ void vcycle_coarse(Real* arena, const Real* dinv) {
-    if constexpr (NL == direct_level<Real>(N)) {
-        dense_solve<Real, NL, T>(level_ptrs<Real, N, NL, CP>(arena), dinv);
+    if constexpr (NL == direct_level<Real, FC>(N)) {
+        dense_solve<Real, NL, T, FC>(level_ptrs<Real, N, NL, CP, FC>(arena), dinv);
         phase_sync<WARP>();
     } else if constexpr (!WARP && NL <= 4) {
-        if (threadIdx.x < 32) vcycle_coarse<Real, N, NL, 32, true, CP>(arena, dinv);
+        if (threadIdx.x < 32) vcycle_coarse<Real, N, NL, 32, true, CP, FC>(arena, dinv);
         __syncthreads();
         return;
     } else {
-        Lv<Real> L = level_ptrs<Real, N, NL, CP>(arena);
+        Lv<Real> L = level_ptrs<Real, N, NL, CP, FC>(arena);
         if constexpr (NL == 2) {
             constexpr int n11 = fem_row_stride(2) + 1;           // single interior node (1,1)
             if (threadIdx.x == 0) L.e[n11] = L.rhs[n11] * inv_diag<Real, fem_row_stride(2)>(L, n11);
             phase_sync<WARP>();
         } else {
-            Lv<Real> C = level_ptrs<Real, N, NL / 2, CP>(arena);
-            smooth_color<Real, NL, T>(L, 1);   // red pre-sweep done by the restriction above
+            Lv<Real> C = level_ptrs<Real, N, NL / 2, CP, FC>(arena);
+            smooth_color<Real, NL, T, FC>(L, 1);   // red pre-sweep done by the restriction above
             phase_sync<WARP>();
-            restrict_red<Real, NL / 2, T>(L, C);
+            restrict_red<Real, NL / 2, T, FC>(L, C);
             phase_sync<WARP>();
-            vcycle_coarse<Real, N, NL / 2, T, WARP, CP>(arena, dinv);
-            black_prolong<Real, NL, T>(L, C.e);
+            vcycle_coarse<Real, N, NL / 2, T, WARP, CP, FC>(arena, dinv);
+            black_prolong<Real, NL, T, FC>(L, C.e);
             phase_sync<WARP>();
-            smooth_color<Real, NL, T>(L, 0);
+            smooth_color<Real, NL, T, FC>(L, 0);
             phase_sync<WARP>();
         }
     }
@@ -424,13 +457,13 @@ __device__ __forceinline__ void build_coeffs(const Lv<Real>& L, const Real* kap)
     }
 }
 
-template <typename Real, int NL, int T>
+template <typename Real, int NL, int T, bool FC = false>
 __device__ __forceinline__ void build_diag(const Lv<Real>& L) {
     constexpr int S = fem_row_stride(NL);
     for (int n = threadIdx.x; n < (NL + 1) * S; n += T) {
         const int j = n / S, i = n - j * S;
-        Real d = 0;
-        if (i > 0 && j > 0 && i < NL && j < NL) d = L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S];
+        Real d = 0;   // the flow cell's boundary rows read the zero ghost rows for their missing edges
+        if (i > 0 && i < NL && (FC || (j > 0 && j < NL))) d = L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S];
         L.iD[n] = (d == Real(0)) ? Real(1) : recip(d);   // boundary entries are never used
     }
 }
@@ -451,20 +484,20 @@ __device__ __forceinline__ void coarsen_kappa(const Real* kf, Real* kc) {
 
 // builds coefficients of level NL from kappa at kin, coarser kappa into the other half
 // of the staging area, then recurses
-template <typename Real, int N, int NL, int T>
+template <typename Real, int N, int NL, int T, bool FC = false>
 __device__ void setup_levels(Real* arena, Real* stage, bool ping) {
-    Lv<Real> L = level_ptrs<Real, N, NL>(arena);
+    Lv<Real> L = level_ptrs<Real, N, NL, false, FC>(arena);
     Real* kin = ping ? stage : stage + 2 * N * N;
     build_coeffs<Real, NL, T>(L, kin);
     if constexpr (NL > 2) {
         Real* kout = ping ? stage + 2 * N * N : stage;
         coarsen_kappa<Real, NL / 2, T>(kin, kout);
         __syncthreads();
-        build_diag<Real, NL, T>(L);
-        setup_levels<Real, N, NL / 2, T>(arena, stage, !ping);
+        build_diag<Real, NL, T, FC>(L);
+        setup_levels<Real, N, NL / 2, T, FC>(arena, stage, !ping);
     } else {
         __syncthreads();
-        build_diag<Real, NL, T>(L);
+        build_diag<Real, NL, T, FC>(L);
         __syncthreads();
     }
 }
@@ -484,19 +517,34 @@ __device__ void setup_levels_cp(Real* arena, Real* kin, Real* kout) {
     }
 }
 
+// flow cell: the ghost rows -1 and NL + 1 of the coefficient arrays on every level down to 1/4
+// (the boundary rows' stencils read aN there); set before the coefficients are built
+template <typename Real, int N, int NL, int T>
+__device__ __forceinline__ void zero_ghost_weights(Real* arena) {
+    constexpr int S = fem_row_stride(NL);
+    const Lv<Real> L = level_ptrs<Real, N, NL, false, true>(arena);
+    for (int k = threadIdx.x; k < 2 * S; k += T) {
+        const int n = k < S ? k - S : (NL + 1) * S + (k - S);
+        L.aE[n] = L.aN[n] = L.iD[n] = Real(0);
+    }
+    if constexpr (NL > 4) zero_ghost_weights<Real, N, NL / 2, T>(arena);
+}
+
 template <typename Real, int N>
 struct Fine {
     static constexpr int M = N - 1, S = fem_row_stride(N), NI = M * M;
 };
 
 // fine-level slots per thread (half red, half black) of the on-chip solve
-__host__ __device__ constexpr int fine_slots(int N, int T) { return 2 * ((N * N / 2 + T - 1) / T); }
+__host__ __device__ constexpr int fine_slots(int N, int T, bool FC = false) {
+    return 2 * (((FC ? (N / 2 + 1) * N : N * N / 2) + T - 1) / T);
+}
 // dynamic shared memory of the on-chip solve, in Reals: the level arena, then the refinement
 // state (x and r, each a hi/lo pair) of every thread's slots, then the dense inverse of the
 // coarsest level kept
-template <typename Real>
+template <typename Real, bool FC = false>
 __host__ __device__ constexpr int solve_smem_reals(int N, int T) {
-    return arena_size(N) + 4 * fine_slots(N, T) * T + dense_reals<Real>(N);
+    return arena_size(N, FC) + 4 * fine_slots(N, T, FC) * T + dense_reals<Real, FC>(N);
 }
 
 // ---- the kernel ----------------------------------------------------------------------
@@ -505,18 +553,19 @@ __host__ __device__ constexpr int solve_smem_reals(int N, int T) {
 // ref_ext (device memory) instead of shared memory. RHS: the load vector may come from a table
 // (a.rhs); false compiles the f = 1 path alone (the compact kernels are instantiated both ways:
 // at 64 registers a thread the table read's code costs them 20 % of their speed)
-template <typename Real, int N, int T, bool CP = false, bool RHS = true>
+template <typename Real, int N, int T, bool CP = false, bool RHS = true, bool FC = false>
 __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Real* arena, double (*red_buf)[64],
                                                Real* theta_s, Real* ref_ext = nullptr) {
     constexpr int S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
-    constexpr int NPT = fine_slots(N, T);              // slots per thread (colour_node positions)
+    constexpr int NPT = fine_slots(N, T, FC);          // slots per thread (colour_node positions)
     constexpr int NPH = NPT / 2;                       // per colour
     constexpr int E = 2 * N * N;
     const int tid = threadIdx.x;
 
-    Lv<Real> F = level_ptrs<Real, N, N, CP>(arena);
+    Lv<Real> F = level_ptrs<Real, N, N, CP, FC>(arena);
     Real* stage = F.e;     // e, res, p of the fine level are contiguous: 3*lvl_size(N) >= 2.5 N^2
                            // (compact: e and p, 2*lvl_size(N) >= 2 N^2)
+    if constexpr (FC) zero_ghost_weights<Real, N, N, T>(arena);   // read by the boundary rows
 
     // 1) kappa = exp(u) on every fine triangle: read from the tensor-core synthesis, or
     //    u = theta . Psi computed here (FP64 path)
@@ -545,13 +594,14 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
         setup_levels_cp<Real, N, N / 2, T>(arena, F.iD, stage);
         build_diag<Real, N, T>(F);
     } else {
-        setup_levels<Real, N, N, T>(arena, stage, true);
+        setup_levels<Real, N, N, T, FC>(arena, stage, true);
     }
-    zero_rings<Real, N, N, T, CP>(arena);
+    zero_rings<Real, N, N, T, CP, FC>(arena);
     __syncthreads();
-    Real* dinv = CP ? arena + arena_size_cp(N) : arena + arena_size(N) + 4 * NPT * T;
-    if constexpr (direct_level<Real>(N) != 0)
-        dense_setup<Real, direct_level<Real>(N), T>(level_ptrs<Real, N, direct_level<Real>(N), CP>(arena), dinv);
+    Real* dinv = CP ? arena + arena_size_cp(N) : arena + arena_size(N, FC) + 4 * NPT * T;
+    if constexpr (direct_level<Real, FC>(N) != 0)
+        dense_setup<Real, direct_level<Real, FC>(N), T, FC>(
+            level_ptrs<Real, N, direct_level<Real, FC>(N), CP, FC>(arena), dinv);
 
     // fine nodes owned by this thread, one packed int each: bits 0-12 node index n, 13-23 the
     // coarse node c under it ((j/2) SC + i/2), 24-25 (i & 1) + 2 (j & 1), 26 red, 27 valid.
@@ -564,7 +614,7 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
         const bool red = q < NPH;
         const int k = tid + T * (red ? q : q - NPH);
         int ii, jj;
-        const int v = colour_node<N>(k, red ? 0 : 1, ii, jj);
+        const int v = colour_node<N, FC>(k, red ? 0 : 1, ii, jj);
         if (!v) ii = jj = 1;
         const int n0 = jj * S + ii;
         const int c = (jj >> 1) * SC + (ii >> 1);
@@ -577,7 +627,7 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     // numbers on the mixed path so that no FP64 instruction runs in the solve. They are touched
     // once per refinement pass, so they live in shared memory after the arena ([4][NPT][T]:
     // x hi, x lo, r hi, r lo), conflict-free per slot.
-    Real* ref = CP ? ref_ext : arena + arena_size(N);
+    Real* ref = CP ? ref_ext : arena + arena_size(N, FC);
     auto XH = [&](int q) -> Real& { return ref[(0 * NPT + q) * T + tid]; };
     auto XL = [&](int q) -> Real& { return ref[(1 * NPT + q) * T + tid]; };
     auto RH = [&](int q) -> Real& { return ref[(2 * NPT + q) * T + tid]; };
@@ -587,7 +637,19 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
         XH(q) = XL(q) = RL(q) = Real(0);
         RH(q) = ((slot[q] >> 27) & 1) ? h2 : Real(0);
     }
-    if (RHS && a.rhs) {
+    Real bflow = 0;   // flow cell: sum of b^2
+    if constexpr (FC) {
+        // f = 0 and p = 1 on x = 1: b = -A_UD p_D is the edge weight to the Dirichlet node (N, j)
+        // at the nodes of column N - 1, zero elsewhere
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+            const int n = slot[q] & 0x1fff;
+            const bool last = ((slot[q] >> 27) & 1) && n % S == N - 1;
+            RH(q) = last ? F.aE[n] : Real(0);
+            bflow += RH(q) * RH(q);
+        }
+        block_sum<T>(bflow, red_buf[1]);
+    } else if (RHS && a.rhs) {
         // the load vector, read in a rolled loop of its own (node indices recomputed, no register
         // array touched), which leaves the register allocation of the solve as it is for f = 1
 #pragma unroll 1
@@ -605,13 +667,13 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     // inner CG state of this thread's nodes: residual r, correction d, preconditioned residual z
     // and search direction p (p is also published in shared memory for the stencil)
     Real r[NPT], d[NPT], z[NPT], pv[NPT];
-    const Real bnorm2 = (RHS && a.rhs) ? Real(a.bnorm2) : Real(NI) * h2 * h2;
+    const Real bnorm2 = FC ? bflow : (RHS && a.rhs) ? Real(a.bnorm2) : Real(NI) * h2 * h2;
     const Real stop_outer = Real(a.rtol * a.rtol) * bnorm2;
     const Real rtol_in2 = Real(a.rtol_in * a.rtol_in);
     int parity = 0;
     int total_it = 0;
     bool converged = false;
-    Lv<Real> C1 = level_ptrs<Real, N, N / 2, CP>(arena);
+    Lv<Real> C1 = level_ptrs<Real, N, N / 2, CP, FC>(arena);
     Real* P = F.rhs;   // fine-level CG direction (the fine rhs is r, held in registers)
 
     for (int pass = 0; pass < a.max_outer && !converged; ++pass) {
@@ -652,9 +714,9 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
                     F.res[n] = offsum<Real, S>(F.aE, F.aN, F.e, n);
                 }
             __syncthreads();
-            restrict_gather<Real, N / 2, T>(F.res, C1);
+            restrict_gather<Real, N / 2, T, FC>(F.res, C1);
             __syncthreads();
-            vcycle_coarse<Real, N, N / 2, T, false, CP>(arena, dinv);
+            vcycle_coarse<Real, N, N / 2, T, false, CP, FC>(arena, dinv);
 #pragma unroll
             for (int q = NPH; q < NPT; ++q) {
                 z[q] = Real(0);
@@ -771,11 +833,20 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     // so that FP64 arithmetic runs only at the observed nodes); the boundary ring reads as zero
     using Node = typename std::conditional<sizeof(Real) == 8, double, float2>::type;
     Node* xs = reinterpret_cast<Node*>(F.e);   // e and res: 2*lvl_size(N) Real >= (N+1) S Nodes
-    for (int k = tid; k < 4 * N; k += T) {   // rows 0 and N (N + 1 nodes each), then columns 0 and N
-        const int n = k <= N ? k : k <= 2 * N + 1 ? N * S + (k - N - 1)
-                                                 : (1 + ((k - 2 * N - 2) >> 1)) * S + (((k - 2 * N - 2) & 1) ? N : 0);
-        if constexpr (sizeof(Real) == 8) xs[n] = 0.0;
-        else xs[n] = make_float2(0.f, 0.f);
+    if constexpr (FC) {   // the Dirichlet columns: p = 0 on x = 0, p = 1 on x = 1
+        for (int k = tid; k < 2 * (N + 1); k += T) {
+            const int n = (k >> 1) * S + ((k & 1) ? N : 0);
+            const Real v = (k & 1) ? Real(1) : Real(0);
+            if constexpr (sizeof(Real) == 8) xs[n] = v;
+            else xs[n] = make_float2(v, 0.f);
+        }
+    } else {
+        for (int k = tid; k < 4 * N; k += T) {   // rows 0 and N (N + 1 nodes each), then columns 0 and N
+            const int n = k <= N ? k : k <= 2 * N + 1 ? N * S + (k - N - 1)
+                                                     : (1 + ((k - 2 * N - 2) >> 1)) * S + (((k - 2 * N - 2) & 1) ? N : 0);
+            if constexpr (sizeof(Real) == 8) xs[n] = 0.0;
+            else xs[n] = make_float2(0.f, 0.f);
+        }
     }
 #pragma unroll
     for (int q = 0; q < NPT; ++q)
@@ -1131,6 +1202,19 @@ fem_eval_kernel(FemArgs a) {
     solve_particle<Real, N, T>(a, blockIdx.x, reinterpret_cast<Real*>(smem_raw), red_buf, theta_s);
 }
 
+// flow cell of Example 5.3 (FemArgs::flow_cell): the same solve with Neumann rows and the lifted
+// Dirichlet data
+template <typename Real, int N, int T>
+__global__ void __launch_bounds__(T, (solve_min_blocks<Real, N, T>()))
+fem_eval_kernel_fc(FemArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red_buf[2][64];
+    __shared__ Real theta_s[256];
+    if ((int)blockIdx.x >= a.n) return;
+    solve_particle<Real, N, T, false, false, true>(a, blockIdx.x, reinterpret_cast<Real*>(smem_raw), red_buf,
+                                                   theta_s);
+}
+
 // compact form (mixed, kappa from the synthesis): MINB blocks per SM, persistent over the
 // particles; each block keeps its refinement state in its own slice of ref_scratch (L2-resident)
 template <int N, int T, int MINB, bool RHS>
@@ -1188,6 +1272,17 @@ template <typename Real, int N, int T>
 cudaError_t launch_one(const FemArgs& a, cudaStream_t st) {
     const size_t smem = sizeof(Real) * (size_t)solve_smem_reals<Real>(N, T);
     auto kern = fem_eval_kernel<Real, N, T>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    kern<<<a.n, T, smem, st>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename Real, int N, int T>
+cudaError_t launch_one_fc(const FemArgs& a, cudaStream_t st) {
+    const size_t smem = sizeof(Real) * (size_t)solve_smem_reals<Real, true>(N, T);
+    auto kern = fem_eval_kernel_fc<Real, N, T>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     kern<<<a.n, T, smem, st>>>(a);
@@ -1413,6 +1508,23 @@ std::vector<int> fem_block_sizes(int N, int precision) {
 
 cudaError_t fem_eval_launch(const FemArgs& a, cudaStream_t st, int T) {
     if (a.n <= 0) return cudaSuccess;
+    if (a.flow_cell) {   // one block size per level (1/64: 448 threads keep it within shared memory)
+        if (a.precision == SMC_MIXED) {
+            switch (a.N) {
+                case 8: return launch_one_fc<float, 8, 32>(a, st);
+                case 16: return launch_one_fc<float, 16, 128>(a, st);
+                case 32: return launch_one_fc<float, 32, 256>(a, st);
+                case 64: return launch_one_fc<float, 64, 448>(a, st);
+            }
+        } else {
+            switch (a.N) {
+                case 8: return launch_one_fc<double, 8, 64>(a, st);
+                case 16: return launch_one_fc<double, 16, 128>(a, st);
+                case 32: return launch_one_fc<double, 32, 256>(a, st);
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
     if (T <= 0) T = fem_block_sizes(a.N, a.precision).at(0);
     if (a.precision == SMC_MIXED) {
         switch (a.N * 10000 + T) {

@@ -28,6 +28,7 @@ struct Level {
 
 struct Handle {
     int K = 0, n_obs = 0, forward_kind = SMC_FWD_FEM, precision = SMC_FP64;
+    int flow_cell = 0;           // SMC_BC_FLOW_CELL
     double sigma = 1.0, rtol = 1e-13;
     int max_iter = 100;
     smc_sampler_opts opts{};

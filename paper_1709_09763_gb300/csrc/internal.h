@@ -57,6 +57,8 @@ struct FemArgs {
     const void* rhs;        // load vector at the nodes (padded row layout): double (FP64) or float2
                             // (MIXED: hi, lo with hi + lo = the FP64 value); null: f = 1 (b = h^2)
     double bnorm2;          // sum of squares of the load vector over the interior nodes (with rhs)
+    int flow_cell;          // 1: the flow cell of Example 5.3 (p = 0 / 1 on x = 0 / 1, no flow on
+                            // y = 0, 1, f = 0; levels 1/8 .. 1/64, FP64 to 1/32, one-block form)
 };
 // Returns cudaSuccess or the launch error.
 // T = threads per particle (one of fem_block_sizes; <= 0: the first, the default)

@@ -31,6 +31,9 @@ SMC_PROP_RWM = 1
 _COV = {"sep_exp": SMC_COV_SEP_EXP, "matern": SMC_COV_MATERN}
 _SRC = {"one": SMC_SRC_ONE, "nine": SMC_SRC_NINE}
 _PROP = {"pcn": SMC_PROP_PCN, "rwm": SMC_PROP_RWM}
+SMC_BC_DIRICHLET = 0
+SMC_BC_FLOW_CELL = 1
+_BC = {"dirichlet": SMC_BC_DIRICHLET, "flow_cell": SMC_BC_FLOW_CELL}
 SMC_NOALLOC_MAX_PARTICLES = 65536
 
 ERROR_NAMES = {0: "SMC_OK", -1: "SMC_EINVAL", -2: "SMC_ENOMEM", -3: "SMC_ECUDA", -4: "SMC_ENOCONV",
@@ -45,7 +48,7 @@ class ProblemDesc(ctypes.Structure):
                 ("corr_len", ctypes.c_double), ("variance", ctypes.c_double),
                 ("n_obs", ctypes.c_int), ("obs_xy", _dp), ("y", _dp), ("sigma", ctypes.c_double),
                 ("forward_kind", ctypes.c_int), ("linear_A", _dp), ("cov_kind", ctypes.c_int),
-                ("source_kind", ctypes.c_int)]
+                ("source_kind", ctypes.c_int), ("bc_kind", ctypes.c_int)]
 
 
 class SamplerOpts(ctypes.Structure):
@@ -222,7 +225,7 @@ class Handle:
     def __init__(self, inv_h, K, obs_xy, y, sigma, corr_len=0.1, variance=1.0, J=0, J_tilde=100,
                  n_mcmc=5, tau_star=1.0, tau_lu=None, eps=1e-6, s_pcn=0.2, precision=SMC_FP64, seed=0,
                  max_iter=100, rtol=0.0, stream=None, linear_A=None, surrogate=0, surrogate_train_steps=0,
-                 surrogate_batch=0, cov="sep_exp", source="one", proposal="pcn", tau_min=0.0):
+                 surrogate_batch=0, cov="sep_exp", source="one", proposal="pcn", tau_min=0.0, bc="dirichlet"):
         lib = load()
         self._lib = lib
         self._inv_h = np.ascontiguousarray(inv_h, dtype=np.int32)
@@ -232,7 +235,7 @@ class Handle:
         d = ProblemDesc(len(self._inv_h), self._inv_h.ctypes.data_as(_ip), int(K), float(corr_len),
                         float(variance), self._obs.shape[0], _dptr(self._obs), _dptr(self._y), float(sigma),
                         SMC_FWD_LINEAR if self._A is not None else SMC_FWD_FEM, _dptr(self._A), _COV[cov],
-                        _SRC[source])
+                        _SRC[source], _BC[bc])
         o = SamplerOpts(int(J), int(J_tilde), int(n_mcmc), float(tau_star),
                         float(tau_star if tau_lu is None else tau_lu), float(eps), float(s_pcn), int(precision),
                         int(seed), int(max_iter), float(rtol), int(surrogate), int(surrogate_train_steps),

@@ -42,7 +42,9 @@ def test_invalid_descriptors_rejected_without_gpu(lib):
     bad = [dict(inv_h=[16], K=0), dict(inv_h=[16], K=300), dict(inv_h=[12], K=4),
            dict(inv_h=[16, 8], K=4), dict(inv_h=[16], K=4, sigma=0.0),
            dict(inv_h=[16], K=4, obs_xy=np.array([[1.5, 0.5]])),
-           dict(inv_h=[16], K=65, cov="matern")]                       # Matern KL keeps <= 64 terms
+           dict(inv_h=[16], K=65, cov="matern"),                       # Matern KL keeps <= 64 terms
+           dict(inv_h=[16, 128], K=4, bc="flow_cell"),                 # flow cell: levels up to 1/64
+           dict(inv_h=[16], K=4, bc="flow_cell", source="nine")]       # flow cell: f = 0
     for kw in bad:
         args = dict(obs_xy=obs, y=y, sigma=1.0)
         args.update(kw)
