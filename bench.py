@@ -420,7 +420,7 @@ def main():
                                J=wk.J, J_tilde=wk.J_tilde, n_mcmc=wk.n_mcmc, s_pcn=wk.s_pcn,
                                tau_star=wk.tau_star, precision=precision, seed=seed,
                                stream=stream.cuda_stream, surrogate=surrogate, cov=wk.cov, source=wk.source,
-                               proposal=wk.proposal)
+                               proposal=wk.proposal, bc=wk.bc, tau_min=wk.tau_min)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             hr.run()
@@ -432,6 +432,7 @@ def main():
             hr.close()
             rates = [p["da_stage1_rate"] for p in path if p["da_stage1_rate"] >= 0]
             return {"seconds": secs, "updates": st["n_updates"], "solves_per_level": st["evals"][:len(inv_h)],
+                    "final_level": st["level"],
                     "log_evidence": lz, "mean": m, "var": v,
                     "stage1_pass_rate": float(np.mean(rates)) if rates else None}
 
@@ -462,9 +463,10 @@ def main():
                "mls2mc_surrogate_workload": compare(wda, dda, tuple(wda.inv_h))}
 
         def paper_example(name, R=3):
-            """Examples 5.1/5.2 (Matern prior, nine sources, one random-walk step per update):
-            MLS^2MC on 1/8..1/128 against single-level SMC on 1/128, R seeded runs each; cost in
-            the paper's unit sum_l evals_l 4^(l - L) (one finest-level solve = 1)."""
+            """The paper's examples (Matern prior, one random-walk step per update; 5.1/5.2: nine
+            sources, 5.3: the flow cell under the scheme u'): MLS^2MC on the hierarchy against
+            single-level SMC on its finest level, R seeded runs each; cost in the paper's unit
+            sum_l evals_l 4^(l - L) (one finest-level solve = 1)."""
             wk, dk = wl.WORKLOADS[name], load_data(name)
             res = {"workload": name, "levels_inv_h": list(wk.inv_h), "K": wk.K, "J": wk.J, "sigma": dk["sigma"],
                    "tau_star": wk.tau_star, "proposal": wk.proposal}
@@ -485,7 +487,8 @@ def main():
                               "cost_finest_solves_mean": float(np.mean(cost)),
                               "updates": [x["updates"] for x in runs],
                               "log_evidence": [x["log_evidence"] for x in runs],
-                              "rel_err_posterior_mean": [rel_err(x["mean"]) for x in runs]}
+                              "rel_err_posterior_mean": [rel_err(x["mean"]) for x in runs],
+                              "final_level_inv_h": [inv_h[x["final_level"]] for x in runs]}
             res["speedup_mls2mc_vs_smc"] = res["smc_finest"]["seconds_median"] / res["mls2mc"]["seconds_median"]
             res["cost_ratio_smc_over_mls2mc"] = (res["smc_finest"]["cost_finest_solves_mean"] /
                                                  res["mls2mc"]["cost_finest_solves_mean"])
@@ -503,6 +506,8 @@ def main():
                                "log_evidence": [x["log_evidence"] for x in fr]}
         run["paper_example_5_1"] = paper_example("example_5_1")
         run["paper_example_5_2"] = paper_example("example_5_2")
+        # Example 5.3, the flow cell, at reduced size (levels 1/16 .. 1/64, 64 KL terms), scheme u'
+        run["paper_example_5_3"] = paper_example("example_5_3")
 
     batched = None if args.no_run else batched_measurement(native, wl, torch, dev)
     # many small problems: each per-problem launch fills a fraction of the GPU

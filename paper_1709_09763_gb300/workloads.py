@@ -36,6 +36,8 @@ class Workload:
     cov: str = "sep_exp"      # prior covariance: "sep_exp" (separable exponential) or "matern" (nu = 3/2)
     source: str = "one"       # source term: "one" (f = 1) or "nine" (the nine sources of Example 5.1)
     proposal: str = "pcn"     # Markov kernel: "pcn" or "rwm" (random walk, step s_pcn)
+    bc: str = "dirichlet"     # boundary conditions: "dirichlet" or "flow_cell" (Example 5.3)
+    tau_min: float = 0.0      # > 0: the update scheme u' (adaptive maximum level)
 
     @property
     def n_obs(self):
@@ -69,6 +71,14 @@ WORKLOADS = {
     "example_5_2": Workload("example_5_2", (8, 16, 32, 64, 128), 256, 10, 0.65, 5, 2500, 1,
                             s_pcn=2.38 / 10 ** 0.5, seed_true=41, seed_noise=42, seed_sampler=53,
                             precision="mixed", sigma_abs=0.035, cov="matern", source="nine", proposal="rwm"),
+    # the paper's Example 5.3 (flow cell) at reduced size: levels 1/16 .. 1/64 (the paper: to 1/256),
+    # Matern prior lc = 0.1 with 64 terms (the paper: 320, m0 = 2, which f = 0 makes irrelevant),
+    # 49 observations, Gamma = 0.045^2 I, one random-walk step per update, scheme u' with
+    # tau_min = 0.001, J = 1000
+    "example_5_3": Workload("example_5_3", (16, 32, 64), 128, 64, 0.1, 7, 1000, 1,
+                            s_pcn=2.38 / 64 ** 0.5, seed_true=71, seed_noise=72, seed_sampler=73,
+                            precision="mixed", sigma_abs=0.045, cov="matern", proposal="rwm",
+                            bc="flow_cell", tau_min=0.001),
 }
 
 

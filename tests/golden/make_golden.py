@@ -30,7 +30,10 @@ def make(w):
     else:
         psi = kl.kl_table(N, w.corr_len, w.variance, w.K)
     f = fem.nine_sources if w.source == "nine" else None
-    p = fem.solve(N, np.exp(th @ psi), f)
+    if w.bc == "flow_cell":
+        p = fem.solve_flow_cell(N, np.exp(th @ psi))
+    else:
+        p = fem.solve(N, np.exp(th @ psi), f)
     obs = wl.obs_grid(w.obs_per_side)
     G = fem.observation_operator(N, obs) @ p
     sigma = w.sigma_abs if w.sigma_abs > 0 else w.noise_frac * np.abs(p).max()
