@@ -65,7 +65,7 @@ extern "C" {
 #define SMC_BC_DIRICHLET 0 /* p = 0 on the whole boundary (Examples 5.1, 5.2) */
 #define SMC_BC_FLOW_CELL 1 /* the flow cell of Example 5.3: p = 0 on x = 0, p = 1 on x = 1, no flow on
                               y = 0 and y = 1, f = 0 (source_kind must be SMC_SRC_ONE and is ignored);
-                              levels 1/8 .. 1/64 (FP64: .. 1/32); the pressure does not depend on a
+                              levels 1/8 .. 1/256 (FP64: .. 1/32); the pressure does not depend on a
                               uniform scale of kappa, so a prior mean m0 of the field has no effect */
 /* Markov kernel of the sampler */
 #define SMC_PROP_PCN    0  /* theta' = sqrt(1 - s^2) theta + s xi */

@@ -182,7 +182,7 @@ int Handle::eval_device(int level, int n, const double* theta, double* G, double
         if (L.N >= 128) {
             // large level: hierarchy in global memory, persistent blocks
             const int blocks = fem_global_blocks(L.N);
-            const size_t need = (size_t)blocks * fem_global_slice(L.N);
+            const size_t need = (size_t)blocks * fem_global_slice(L.N, flow_cell != 0);
             if (need > big_cap) {
                 cudaFree(big_scratch);
                 big_scratch = nullptr;
@@ -289,7 +289,7 @@ int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** 
             return bail(h->fail(SMC_EINVAL, "unknown bc_kind"));
         if (P->bc_kind == SMC_BC_FLOW_CELL) {
             if (P->source_kind != SMC_SRC_ONE) return bail(h->fail(SMC_EINVAL, "the flow cell has f = 0"));
-            const int top = O->precision == SMC_MIXED ? 64 : 32;
+            const int top = O->precision == SMC_MIXED ? 256 : 32;
             for (int l = 0; l < P->n_levels; ++l)
                 if (P->inv_h[l] < 8 || P->inv_h[l] > top)
                     return bail(h->fail(SMC_EINVAL, "flow cell: 1/h must be in [8, %d] at this precision", top));

@@ -879,27 +879,27 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
 
 // Two-arena hierarchy of the large levels: levels with 1/h >= 128 live in device memory (the
 // arena of a top level N), levels 1/h <= 64 in shared memory (the arena of a top level 64).
-template <typename Real, int N, int NL>
+template <typename Real, int N, int NL, bool FC = false>
 __device__ __forceinline__ Lv<Real> ptrs2(Real* garena, Real* sarena) {
-    if constexpr (NL > 64) return level_ptrs<Real, N, NL>(garena);
-    else return level_ptrs<Real, 64, NL>(sarena);
+    if constexpr (NL > 64) return level_ptrs<Real, N, NL, false, FC>(garena);
+    else return level_ptrs<Real, 64, NL, false, FC>(sarena);
 }
 
-template <typename Real, int N, int NL, int T>
+template <typename Real, int N, int NL, int T, bool FC = false>
 __device__ void vcycle2(Real* garena, Real* sarena, const Real* dinv) {
     if constexpr (NL <= 64) {
-        vcycle_coarse<Real, 64, NL, T>(sarena, dinv);
+        vcycle_coarse<Real, 64, NL, T, false, false, FC>(sarena, dinv);
     } else {
-        Lv<Real> L = ptrs2<Real, N, NL>(garena, sarena);
-        Lv<Real> C = ptrs2<Real, N, NL / 2>(garena, sarena);
-        smooth_color<Real, NL, T>(L, 1);   // red pre-sweep done by the restriction above
+        Lv<Real> L = ptrs2<Real, N, NL, FC>(garena, sarena);
+        Lv<Real> C = ptrs2<Real, N, NL / 2, FC>(garena, sarena);
+        smooth_color<Real, NL, T, FC>(L, 1);   // red pre-sweep done by the restriction above
         __syncthreads();
-        restrict_red<Real, NL / 2, T>(L, C);
+        restrict_red<Real, NL / 2, T, FC>(L, C);
         __syncthreads();
-        vcycle2<Real, N, NL / 2, T>(garena, sarena, dinv);
-        black_prolong<Real, NL, T>(L, C.e);
+        vcycle2<Real, N, NL / 2, T, FC>(garena, sarena, dinv);
+        black_prolong<Real, NL, T, FC>(L, C.e);
         __syncthreads();
-        smooth_color<Real, NL, T>(L, 0);
+        smooth_color<Real, NL, T, FC>(L, 0);
         __syncthreads();
     }
 }
@@ -908,19 +908,25 @@ __device__ void vcycle2(Real* garena, Real* sarena, const Real* dinv) {
 // device memory (L2-resident for 1/128), the levels 1/h <= 64 in shared memory, and the fine-level
 // CG and refinement vectors as arrays indexed by interior node (too many nodes per thread for
 // registers). vec: 7 arrays of NI entries after the level arena: r, d, x_hi, x_lo, r_hi, r_lo, q.
-template <typename Real, int N, int T>
+// FC: the flow cell (rows 0 .. N unknowns, ghost rows, the lifted Dirichlet data).
+template <typename Real, int N, int T, bool FC = false>
 __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p, Real* arena, Real* sarena,
                                                    double (*red_buf)[64]) {
-    constexpr int M = Fine<Real, N>::M, S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
+    constexpr int M = Fine<Real, N>::M, S = Fine<Real, N>::S;
+    constexpr int ROW0 = FC ? 0 : 1, NI = M * (FC ? N + 1 : M);   // first unknown row, unknowns
     constexpr int E = 2 * N * N;
     constexpr int SC = fem_row_stride(N / 2);
     const int tid = threadIdx.x;
-    Lv<Real> F = level_ptrs<Real, N, N>(arena);
-    Real* vec = arena + arena_size(N);
+    Lv<Real> F = level_ptrs<Real, N, N, false, FC>(arena);
+    Real* vec = arena + arena_size(N, FC);
     Real *R = vec, *Dv = vec + NI, *XH = vec + 2 * NI, *XL = vec + 3 * NI, *RH = vec + 4 * NI, *RL = vec + 5 * NI,
          *QV = vec + 6 * NI;
     Real* stage = F.e;
 
+    if constexpr (FC) {   // ghost rows of the coefficient arrays, read by the boundary rows
+        zero_ghost_weights<Real, N, N, T>(arena);
+        zero_ghost_weights<Real, 64, 64, T>(sarena);
+    }
     const float* kp = a.kappa + (size_t)p * E;
     for (int e = tid; e < E; e += T) stage[e] = (Real)kp[e];
     __syncthreads();
@@ -931,58 +937,65 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
         build_coeffs<Real, N, T>(F, stage);
         coarsen_kappa<Real, N / 2, T>(stage, k1);
         __syncthreads();
-        build_diag<Real, N, T>(F);
+        build_diag<Real, N, T, FC>(F);
         Real* k64 = k1;
         if constexpr (N == 256) {
-            Lv<Real> L1 = level_ptrs<Real, N, 128>(arena);
+            Lv<Real> L1 = level_ptrs<Real, N, 128, false, FC>(arena);
             build_coeffs<Real, 128, T>(L1, k1);
             coarsen_kappa<Real, 64, T>(k1, stage);
             __syncthreads();
-            build_diag<Real, 128, T>(L1);
+            build_diag<Real, 128, T, FC>(L1);
             k64 = stage;
         }
-        setup_levels<Real, 64, 64, T>(sarena, k64, true);
+        setup_levels<Real, 64, 64, T, FC>(sarena, k64, true);
     }
     {
         int off = 0;
 #pragma unroll
         for (int NL = N; NL >= 128; NL >>= 1) {
-            const int z = lvl_size(NL);
+            const int z = lvl_size(NL, FC);
             for (int q = tid; q < 3 * z; q += T) arena[off + 3 * z + q] = Real(0);
             off += 6 * z;
         }
         off = 0;
 #pragma unroll
         for (int NL = 64; NL >= 2; NL >>= 1) {
-            const int z = lvl_size(NL);
+            const int z = lvl_size(NL, FC);
             for (int q = tid; q < 3 * z; q += T) sarena[off + 3 * z + q] = Real(0);
             off += 6 * z;
         }
     }
     __syncthreads();
-    Real* dinv = sarena + arena_size(64);
-    dense_setup<Real, direct_level<Real>(64), T>(level_ptrs<Real, 64, direct_level<Real>(64)>(sarena), dinv);
+    Real* dinv = sarena + arena_size(64, FC);
+    dense_setup<Real, direct_level<Real, FC>(64), T, FC>(
+        level_ptrs<Real, 64, direct_level<Real, FC>(64), false, FC>(sarena), dinv);
     const Real h2 = Real(1) / (Real(N) * Real(N));
+    Real bflow = 0;   // flow cell: sum of b^2
     for (int i = tid; i < NI; i += T) {   // r = b: the load vector (h^2 at every node for f = 1)
         XH[i] = XL[i] = RL[i] = Real(0);
         RH[i] = h2;
-        if (a.rhs) {
-            const int jj = i / M + 1, ii = i - (jj - 1) * M + 1;
+        if constexpr (FC) {   // b = the edge weight to the Dirichlet node (N, j) in column N - 1
+            const int jj = i / M, ii = i - jj * M + 1;
+            RH[i] = ii == N - 1 ? F.aE[jj * S + ii] : Real(0);
+            bflow += RH[i] * RH[i];
+        } else if (a.rhs) {
+            const int jj = i / M + ROW0, ii = i - (jj - ROW0) * M + 1;
             Real hi, lo;
             load_rhs(a.rhs, jj * S + ii, hi, lo);
             RH[i] = hi;
             RL[i] = lo;
         }
     }
+    if constexpr (FC) block_sum<T>(bflow, red_buf[1]);
     __syncthreads();
-    const Real bnorm2 = a.rhs ? Real(a.bnorm2) : Real(NI) * h2 * h2;
+    const Real bnorm2 = FC ? bflow : a.rhs ? Real(a.bnorm2) : Real(NI) * h2 * h2;
     const Real stop_outer = Real(a.rtol * a.rtol) * bnorm2;
     const Real rtol_in2 = Real(a.rtol_in * a.rtol_in);
     int parity = 0, total_it = 0;
     bool converged = false;
-    Lv<Real> C1 = ptrs2<Real, N, N / 2>(arena, sarena);
+    Lv<Real> C1 = ptrs2<Real, N, N / 2, FC>(arena, sarena);
     Real* P = F.rhs;
-#define NODE_OF(i) const int jj = (i) / M + 1, ii = (i) - (jj - 1) * M + 1, n = jj * S + ii
+#define NODE_OF(i) const int jj = (i) / M + ROW0, ii = (i) - (jj - ROW0) * M + 1, n = jj * S + ii
     // colour sweeps run over colour_node positions (every lane busy), the vector updates over the
     // interior index (coalesced); the red pre-sweep from zero is written where R is updated
     for (int pass = 0; pass < a.max_outer && !converged; ++pass) {
@@ -1000,38 +1013,38 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
         const Real stop2 = rtol_in2 * rr0;
         Real rz = 0;
         for (int it = 0; it < a.max_inner; ++it) {
-            for (int k = tid; k < N * N / 2; k += T) {   // black pre-sweep
+            for (int k = tid; k < colour_positions<N, FC>(); k += T) {   // black pre-sweep
                 int ii, jj;
-                if (!colour_node<N>(k, 1, ii, jj)) continue;
-                const int n = jj * S + ii, i = (jj - 1) * M + ii - 1;
+                if (!colour_node<N, FC>(k, 1, ii, jj)) continue;
+                const int n = jj * S + ii, i = (jj - ROW0) * M + ii - 1;
                 F.e[n] = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
             }
             __syncthreads();
-            for (int k = tid; k < N * N / 2; k += T) {   // red residuals
+            for (int k = tid; k < colour_positions<N, FC>(); k += T) {   // red residuals
                 int ii, jj;
-                if (!colour_node<N>(k, 0, ii, jj)) continue;
+                if (!colour_node<N, FC>(k, 0, ii, jj)) continue;
                 const int n = jj * S + ii;
                 F.res[n] = offsum<Real, S>(F.aE, F.aN, F.e, n);
             }
             __syncthreads();
-            restrict_gather<Real, N / 2, T>(F.res, C1);
+            restrict_gather<Real, N / 2, T, FC>(F.res, C1);
             __syncthreads();
-            vcycle2<Real, N, N / 2, T>(arena, sarena, dinv);
+            vcycle2<Real, N, N / 2, T, FC>(arena, sarena, dinv);
             Real rz_new = 0;
-            for (int k = tid; k < N * N / 2; k += T) {   // black post-sweep with the prolongation
+            for (int k = tid; k < colour_positions<N, FC>(); k += T) {   // black post-sweep with the prolongation
                 int ii, jj;
-                if (!colour_node<N>(k, 1, ii, jj)) continue;
-                const int n = jj * S + ii, i = (jj - 1) * M + ii - 1;
+                if (!colour_node<N, FC>(k, 1, ii, jj)) continue;
+                const int n = jj * S + ii, i = (jj - ROW0) * M + ii - 1;
                 const int c = (jj >> 1) * SC + (ii >> 1);
                 const Real z = (R[i] + offsum_prolong<Real, S, SC>(F.aE, F.aN, F.e, C1.e, n, c, (jj & 1) == 0)) * F.iD[n];
                 F.e[n] = z;
                 rz_new += R[i] * z;
             }
             __syncthreads();
-            for (int k = tid; k < N * N / 2; k += T) {   // red post-sweep
+            for (int k = tid; k < colour_positions<N, FC>(); k += T) {   // red post-sweep
                 int ii, jj;
-                if (!colour_node<N>(k, 0, ii, jj)) continue;
-                const int n = jj * S + ii, i = (jj - 1) * M + ii - 1;
+                if (!colour_node<N, FC>(k, 0, ii, jj)) continue;
+                const int n = jj * S + ii, i = (jj - ROW0) * M + ii - 1;
                 const Real z = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
                 F.e[n] = z;
                 rz_new += R[i] * z;
@@ -1108,8 +1121,9 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
     if (tid < 32) {   // the observed nodes straight from the interior arrays; one warp reduces
         auto val = [&](int n) -> double {
             const int j = n / S, i = n - j * S;
-            if (i < 1 || i > M || j < 1 || j > M) return 0.0;
-            const int k = (j - 1) * M + (i - 1);
+            if (FC && i == N) return 1.0;   // the flow cell's Dirichlet datum on x = 1
+            if (i < 1 || i > M || j < ROW0 || j > (FC ? N : M)) return 0.0;
+            const int k = (j - ROW0) * M + (i - 1);
             return (double)XH[k] + (double)XL[k];
         };
         double misfit = 0.0;
@@ -1130,7 +1144,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
 }
 
 // large levels: persistent blocks, each with its own arena slice of `scratch`
-template <int N, int T>
+template <int N, int T, bool FC = false>
 __global__ void __launch_bounds__(T, 1) fem_eval_global(FemArgs a, float* scratch, size_t slice, int* counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_buf[2][64];
@@ -1143,7 +1157,7 @@ __global__ void __launch_bounds__(T, 1) fem_eval_global(FemArgs a, float* scratc
         const int item = item_s;
         __syncthreads();
         if (item >= a.n) break;
-        solve_particle_mem<float, N, T>(a, item, arena, sarena, red_buf);
+        solve_particle_mem<float, N, T, FC>(a, item, arena, sarena, red_buf);
         __syncthreads();
     }
 }
@@ -1308,12 +1322,13 @@ cudaError_t launch_persistent(const FemArgs* groups, const int* offsets, const i
     return cudaGetLastError();
 }
 
-template <int N, int T>
+template <int N, int T, bool FC = false>
 cudaError_t launch_global(const FemArgs& a, float* scratch, size_t slice, int blocks, int* counter, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)(arena_size(64) + dense_reals<float>(64));
-    cudaError_t e = cudaFuncSetAttribute(fem_eval_global<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sizeof(float) * (size_t)(arena_size(64, FC) + dense_reals<float, FC>(64));
+    cudaError_t e =
+        cudaFuncSetAttribute(fem_eval_global<N, T, FC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fem_eval_global<N, T><<<blocks, T, smem, st>>>(a, scratch, slice, counter);
+    fem_eval_global<N, T, FC><<<blocks, T, smem, st>>>(a, scratch, slice, counter);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1399,9 +1414,9 @@ cudaError_t fem_eval_compact_launch(const FemArgs& a, int T, float* ref_scratch,
     return cudaErrorInvalidValue;
 }
 
-size_t fem_global_slice(int N) {
-    const int NI = (N - 1) * (N - 1);
-    const size_t floats = (size_t)arena_size(N) + 7 * (size_t)NI;
+size_t fem_global_slice(int N, bool FC) {
+    const int NI = (N - 1) * (FC ? N + 1 : N - 1);
+    const size_t floats = (size_t)arena_size(N, FC) + 7 * (size_t)NI;
     return (floats + 63) / 64 * 64;   // floats per block, 256-byte aligned slices
 }
 
@@ -1422,10 +1437,15 @@ int fem_global_blocks(int N) {
 
 cudaError_t fem_eval_global_launch(const FemArgs& a, float* scratch, int blocks, int* counter, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    const size_t slice = fem_global_slice(a.N);
+    const size_t slice = fem_global_slice(a.N, a.flow_cell != 0);
     const int grid = std::max(1, std::min(a.n, blocks));
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
+    if (a.flow_cell) {
+        if (a.N == 128) return launch_global<128, 1024, true>(a, scratch, slice, grid, counter, st);
+        if (a.N == 256) return launch_global<256, 1024, true>(a, scratch, slice, grid, counter, st);
+        return cudaErrorInvalidValue;
+    }
     if (a.N == 128) return launch_global<128, 1024>(a, scratch, slice, grid, counter, st);
     if (a.N == 256) return launch_global<256, 1024>(a, scratch, slice, grid, counter, st);
     return cudaErrorInvalidValue;

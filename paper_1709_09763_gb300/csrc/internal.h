@@ -58,7 +58,8 @@ struct FemArgs {
                             // (MIXED: hi, lo with hi + lo = the FP64 value); null: f = 1 (b = h^2)
     double bnorm2;          // sum of squares of the load vector over the interior nodes (with rhs)
     int flow_cell;          // 1: the flow cell of Example 5.3 (p = 0 / 1 on x = 0 / 1, no flow on
-                            // y = 0, 1, f = 0; levels 1/8 .. 1/64, FP64 to 1/32, one-block form)
+                            // y = 0, 1, f = 0; levels 1/8 .. 1/256, FP64 to 1/32; no compact or
+                            // batched form)
 };
 // Returns cudaSuccess or the launch error.
 // T = threads per particle (one of fem_block_sizes; <= 0: the first, the default)
@@ -68,7 +69,7 @@ std::vector<int> fem_block_sizes(int N, int precision);
 int fem_default_block(int N, int precision);
 // large levels (1/h = 128, 256; mixed precision, kappa from the synthesis): hierarchy in global
 // scratch, blocks x fem_global_slice(N) floats; *counter (device) is reset by the launch
-size_t fem_global_slice(int N);
+size_t fem_global_slice(int N, bool FC = false);   // FC: the flow cell's layout
 int fem_global_blocks(int N);
 cudaError_t fem_eval_global_launch(const FemArgs& a, float* scratch, int blocks, int* counter, cudaStream_t st);
 // large levels of many problems (groups, offsets, item_group as for fem_eval_persistent_launch;

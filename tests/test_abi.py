@@ -43,7 +43,7 @@ def test_invalid_descriptors_rejected_without_gpu(lib):
            dict(inv_h=[16, 8], K=4), dict(inv_h=[16], K=4, sigma=0.0),
            dict(inv_h=[16], K=4, obs_xy=np.array([[1.5, 0.5]])),
            dict(inv_h=[16], K=65, cov="matern"),                       # Matern KL keeps <= 64 terms
-           dict(inv_h=[16, 128], K=4, bc="flow_cell"),                 # flow cell: levels up to 1/64
+           dict(inv_h=[16, 64], K=4, bc="flow_cell", precision=native.SMC_FP64),   # FP64 flow cell to 1/32
            dict(inv_h=[16], K=4, bc="flow_cell", source="nine")]       # flow cell: f = 0
     for kw in bad:
         args = dict(obs_xy=obs, y=y, sigma=1.0)

@@ -39,6 +39,22 @@ def test_flow_cell_constant_field_gives_the_linear_pressure(prec):
         assert np.max(np.abs(G - obs[:, 0][None, :])) < tol, levels[l]
 
 
+@pytest.mark.parametrize("N,n", [(128, 4), (256, 2)])
+def test_flow_cell_large_levels(N, n):
+    """1/128 and 1/256 (fine levels in device memory): parity with the oracle and p = x for
+    kappa = 1."""
+    obs = wl.obs_grid(7)
+    y = np.full(49, 0.5)
+    h = native.Handle([N], K, obs, y, 0.045, corr_len=LC, precision=native.SMC_MIXED, cov="matern",
+                      bc="flow_cell")
+    G0, _ = h.eval_likelihood(0, np.zeros((1, K)))
+    assert np.max(np.abs(G0 - obs[:, 0][None, :])) < 1e-6
+    theta = wl.particles(n, K, 534)
+    G, Phi = h.eval_likelihood(0, theta)
+    Gr = ofwd.Level(N, LC, 1.0, K, obs, cov="matern", bc="flow_cell").G_batch(theta)
+    assert _rel(G, Gr).max() < 1e-6
+
+
 @pytest.mark.parametrize("prec", [native.SMC_MIXED, native.SMC_FP64])
 def test_flow_cell_likelihood_parity(prec):
     obs = wl.obs_grid(7)
