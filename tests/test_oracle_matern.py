@@ -1,8 +1,9 @@
 """Pins of the oracle's Matern KL (Nystrom), the nine-source term and the random-walk kernel of
 Sec. 5 against facts that do not come from the oracle's own code: the Bessel-function definition
-of the Matern covariance, the variance fraction the paper states for Example 5.1, the integral
-eigen-relation under an independent (finer) quadrature, the symmetry group of the square, the
-mass of the sources, and the invariance of the prior under a Metropolis kernel."""
+of the Matern covariance, the variance fractions the paper states for Examples 5.1 and 5.3, brute
+force on the full Nystrom matrix, the integral eigen-relation under an independent (finer)
+quadrature, the symmetry group of the square, the mass of the sources, and the invariance of the
+prior under a Metropolis kernel."""
 import math
 
 import numpy as np
@@ -153,3 +154,69 @@ def test_rwm_single_level_smc_linear_gaussian():
     assert np.all(np.abs(m - m_ex) < 12 * np.sqrt(np.diag(C_ex) / J)), (m, m_ex)
     assert np.allclose(v, np.diag(C_ex), rtol=0.15)
     assert s.log_z == pytest.approx(gaussian.log_evidence(A, y, 0.5), abs=0.15)
+
+
+def _expand(pair, M):
+    """The quarter-grid vector of a pair on the full M x M grid, by its reflection parities."""
+    _, sx, sy, u = pair
+    m = M // 2
+    q = u.reshape(m, m)
+    full = np.empty((M, M))
+    for ix in range(M):
+        for iy in range(M):
+            a, b, s = ix, iy, 1.0
+            if a >= m:
+                a, s = M - 1 - a, s * sx
+            if b >= m:
+                b, s = M - 1 - b, s * sy
+            full[ix, iy] = s * q[a, b]
+    return full.ravel()
+
+
+def test_320_terms_carry_the_variance_fraction_of_example_5_3():
+    """Example 5.3: with lc = 0.1, nu = 3/2 and variance 1 the 320 leading KL terms carry 95 % of
+    the variance (64 x 64 Nystrom grid), and they are the 320 largest eigenvalues of the full
+    4096 x 4096 Nystrom matrix, solved without the symmetry reduction (brute force)."""
+    from scipy.linalg import eigh
+    M, K = 64, 320
+    assert matern.nystrom_cells(K) == M and matern.nystrom_cells(64) == 32
+    top = matern.eigenvalues(0.1, 1.0, K)
+    assert 0.945 < top.sum() < 0.955
+    c = (np.arange(M) + 0.5) / M
+    X, Y = np.meshgrid(c, c, indexing="ij")
+    X, Y = X.ravel(), Y.ravel()
+    W = matern.matern_cov(np.hypot(X[:, None] - X[None, :], Y[:, None] - Y[None, :]), 0.1, 1.0) / (M * M)
+    assert abs(np.trace(W) - 1.0) < 1e-12
+    lam = eigh(W, eigvals_only=True, subset_by_index=[M * M - K, M * M - 1])[::-1]
+    assert np.allclose(top, lam, rtol=0, atol=1e-14)
+
+
+def test_320_pairs_are_orthonormal_eigenpairs_of_the_full_nystrom_matrix():
+    """W C u = lambda u and sum_q w u_k u_l = delta_kl on the full 64 x 64 grid for every one of
+    the 320 pairs at lc = 0.1, each vector expanded from its quarter grid by its parities; the
+    (+,+) and (-,-) vectors are even or odd under x <-> y, the (-,+) ones mirror a (+,-) one."""
+    M, K = 64, 320
+    pairs = matern.kl_pairs(0.1, 1.0, K)
+    c = (np.arange(M) + 0.5) / M
+    X, Y = np.meshgrid(c, c, indexing="ij")
+    X, Y = X.ravel(), Y.ravel()
+    W = matern.matern_cov(np.hypot(X[:, None] - X[None, :], Y[:, None] - Y[None, :]), 0.1, 1.0) / (M * M)
+    U = np.stack([_expand(p, M) for p in pairs], axis=1)
+    lam = np.array([p[0] for p in pairs])
+    assert np.abs(W @ U - U * lam).max() < 1e-13
+    assert np.allclose(U.T @ U / (M * M), np.eye(K), atol=1e-11)
+    assert np.all(np.diff(lam) <= 1e-9 * lam[:-1])
+    m = M // 2
+    for p in pairs:
+        q = p[3].reshape(m, m)
+        if p[1] == p[2]:
+            assert np.allclose(q.T, q, atol=1e-13) or np.allclose(q.T, -q, atol=1e-13)
+
+
+def test_field_equals_the_table_contraction():
+    """u = theta . Psi at every centroid, whether through the table or folded per sector."""
+    th = np.random.default_rng(9).standard_normal(80)
+    psi = matern.kl_table(8, 0.1, 1.0, 80)
+    assert np.allclose(matern.field(8, th, 0.1, 1.0, 80), th @ psi, rtol=0, atol=1e-12)
+    sub = np.array([0, 5, 77, 127])
+    assert np.allclose(matern.kl_table_at(8, sub, 0.1, 1.0, 80), psi[:, sub], rtol=0, atol=1e-15)
