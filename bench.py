@@ -289,6 +289,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-run", action="store_true", help="skip the seconds-to-posterior sampler run")
     ap.add_argument("--autotune", action="store_true", help="let the library's autotuner pick the block sizes")
+    ap.add_argument("--example-5-3-full", action="store_true",
+                    help="also run Example 5.3 at the paper's size (1/16 .. 1/256, 320 KL terms)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -508,6 +510,8 @@ def main():
         run["paper_example_5_2"] = paper_example("example_5_2")
         # Example 5.3, the flow cell, at reduced size (levels 1/16 .. 1/64, 64 KL terms), scheme u'
         run["paper_example_5_3"] = paper_example("example_5_3")
+        if args.example_5_3_full:   # the paper's size: 1/16 .. 1/256, 320 KL terms
+            run["paper_example_5_3_full"] = paper_example("example_5_3_full")
 
     batched = None if args.no_run else batched_measurement(native, wl, torch, dev)
     # many small problems: each per-problem launch fills a fraction of the GPU

@@ -76,7 +76,8 @@ typedef struct {
     int n_levels;              /* N_L >= 1 */
     const int* inv_h;          /* [n_levels] 1/h_l, coarse to fine; powers of two in [4, 32] (FP64),
                                   [4, 256] (mixed; 128 and 256 keep their fine levels in device memory) */
-    int K;                     /* KL terms N_sto, 1 <= K <= 256 */
+    int K;                     /* KL terms N_sto: 1 <= K <= 256, or <= 512 with the FEM forward map at
+                                  SMC_MIXED (Example 5.3 keeps 320); Matern: K <= 512 */
     double corr_len;           /* correlation length of the separable exponential covariance */
     double variance;           /* prior field variance */
     int n_obs;                 /* observations, 1 <= n_obs <= 1024 */
@@ -148,6 +149,15 @@ int smc_eval_likelihood_device(smc_handle* h, int level, int n, const double* th
  * e = 2*(j*N + i) + t, t = 0 lower / 1 upper half of cell (i, j)) to host memory,
  * and the K eigenvalues lambda_k (Eq. truncKL). Either pointer may be NULL. */
 int smc_kl_table(const smc_handle* h, int level, double* psi, double* lambda);
+/* The same table computed on the host without a handle or a GPU (Eq. truncKL; Sec. 5 for the
+ * Matern prior): cov_kind SMC_COV_SEP_EXP or SMC_COV_MATERN, 1 <= N <= 256 cells per side,
+ * K terms (Matern: K <= 512; the Nystrom grid has 32 x 32 cells up to 64 terms and 64 x 64
+ * beyond). psi: host [K][2 N^2] in the triangle order above, lambda: host [K]; either may be
+ * NULL. The Matern eigen-decomposition is computed once per process for each (corr_len,
+ * variance, grid) and reused by every later call and handle. SMC_EINVAL on invalid arguments
+ * or an eigen-solve that did not converge, SMC_ENOMEM if the host table cannot be allocated. */
+int smc_kl_table_host(int cov_kind, int N, double corr_len, double variance, int K, double* psi,
+                      double* lambda);
 
 /* Opt-in timing (no counterpart in the paper; for measurement): when enabled, every forward-solve
  * launch is bracketed by CUDA events on its stream. smc_get_timing waits for the recorded

@@ -174,20 +174,24 @@ def eigenfunction(pair, x, y, corr_len, variance, nu=1.5):
 
 def _extend(pairs, x, y, coef, corr_len, variance, nu):
     """sum over pairs of coef[k, :] times the Nystrom sums sum_q w C(x, q) u_k(q), per point:
-    returns (rows of coef) x (points). The folded kernel of each sector is formed once per
-    chunk of points and applied to all pairs of that sector."""
+    returns (rows of coef) x (points). Per chunk of points the kernel is evaluated once at q and
+    its three mirror images, folded per sector and applied to all pairs of that sector."""
     M = _cells_of(pairs[0][3])
     qx, qy = quarter_grid(M)
-    out = np.zeros((coef.shape[0], np.size(x)))
-    for a in range(0, np.size(x), 2048):
-        b = min(np.size(x), a + 2048)
-        for sx, sy in SECTORS:
-            ks = [k for k, p in enumerate(pairs) if (p[1], p[2]) == (sx, sy)]
+    x, y = np.ravel(x), np.ravel(y)
+    by_sector = {s: [k for k, p in enumerate(pairs) if (p[1], p[2]) == s] for s in SECTORS}
+    out = np.zeros((coef.shape[0], x.size))
+    for a in range(0, x.size, 2048):
+        b = min(x.size, a + 2048)
+        px, py = x[a:b, None], y[a:b, None]
+        c = [matern_cov(np.hypot(px - ax[None, :], py - ay[None, :]), corr_len, variance, nu)
+             for ax, ay in ((qx, qy), (1.0 - qx, qy), (qx, 1.0 - qy), (1.0 - qx, 1.0 - qy))]
+        for (sx, sy), ks in by_sector.items():
             if not ks:
                 continue
-            F = _folded(x[a:b], y[a:b], qx, qy, sx, sy, corr_len, variance, nu) / (M * M)
+            F = (c[0] + sx * c[1] + sy * c[2] + sx * sy * c[3]) / (M * M)
             U = np.stack([pairs[k][3] for k in ks], axis=1)        # Q x (pairs of the sector)
-            out[:, a:b] += (coef[:, ks] @ (F @ U).T)
+            out[:, a:b] += coef[:, ks] @ (F @ U).T
     return out
 
 

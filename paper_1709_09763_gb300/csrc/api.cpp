@@ -265,7 +265,10 @@ int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** 
         return code;
     };
     if (P->n_levels < 1 || P->n_levels > 8 || !P->inv_h) return bail(h->fail(SMC_EINVAL, "n_levels must be in [1, 8]"));
-    if (P->K < 1 || P->K > 256) return bail(h->fail(SMC_EINVAL, "K must be in [1, 256]"));
+    // the FP64 solve forms u = theta . Psi itself with theta staged in a 256-entry shared array;
+    // the mixed path takes kappa from the synthesis GEMM, which has no limit of its own
+    const int k_max = P->forward_kind == SMC_FWD_FEM && O->precision == SMC_MIXED ? 512 : 256;
+    if (P->K < 1 || P->K > k_max) return bail(h->fail(SMC_EINVAL, "K must be in [1, %d] here", k_max));
     if (P->n_obs < 1 || P->n_obs > 1024 || !P->obs_xy || !P->y)
         return bail(h->fail(SMC_EINVAL, "n_obs must be in [1, 1024] with obs_xy and y given"));
     if (!(P->sigma > 0.0)) return bail(h->fail(SMC_EINVAL, "sigma must be positive"));
@@ -323,8 +326,12 @@ int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** 
         if (P->forward_kind == SMC_FWD_FEM) {
             L.N = P->inv_h[l];
             std::vector<double> psi, lam;
-            if (P->cov_kind == SMC_COV_MATERN) matern_kl_table(L.N, P->corr_len, P->variance, P->K, psi, lam);
-            else kl_table(L.N, P->corr_len, P->variance, P->K, psi, lam);
+            if (P->cov_kind == SMC_COV_MATERN) {
+                if (!matern_kl_table(L.N, P->corr_len, P->variance, P->K, psi, lam))
+                    return bail(h->fail(SMC_EINVAL, "Matern KL: the eigen-solve did not converge"));
+            } else {
+                kl_table(L.N, P->corr_len, P->variance, P->K, psi, lam);
+            }
             std::vector<float> psi32(psi.begin(), psi.end());
             std::vector<int> idx;
             std::vector<double> wts;
@@ -384,6 +391,25 @@ int smc_sizes(const smc_handle* hh, int* K, int* n_obs, int* n_levels, int* J) {
     if (n_obs) *n_obs = h->n_obs;
     if (n_levels) *n_levels = (int)h->levels.size();
     if (J) *J = h->opts.J;
+    return SMC_OK;
+}
+
+int smc_kl_table_host(int cov_kind, int N, double corr_len, double variance, int K, double* psi, double* lambda) {
+    if (N < 1 || N > 256 || K < 1 || !(corr_len > 0.0) || !(variance > 0.0)) return SMC_EINVAL;
+    if (cov_kind != SMC_COV_SEP_EXP && cov_kind != SMC_COV_MATERN) return SMC_EINVAL;
+    if (cov_kind == SMC_COV_MATERN && K > matern_max_terms()) return SMC_EINVAL;
+    std::vector<double> p, lam;
+    try {
+        if (cov_kind == SMC_COV_MATERN) {
+            if (!matern_kl_table(N, corr_len, variance, K, p, lam)) return SMC_EINVAL;
+        } else {
+            kl_table(N, corr_len, variance, K, p, lam);
+        }
+    } catch (const std::bad_alloc&) {
+        return SMC_ENOMEM;
+    }
+    if (psi) std::copy(p.begin(), p.end(), psi);
+    if (lambda) std::copy(lam.begin(), lam.end(), lambda);
     return SMC_OK;
 }
 

@@ -15,9 +15,13 @@ namespace mls2mc {
 void kl_eig_1d(double corr_len, int n_modes, std::vector<double>& lam, std::vector<double>& omega);
 void kl_table(int N, double corr_len, double variance, int K, std::vector<double>& psi,
               std::vector<double>& lambda);
+// eigen-decomposition of a symmetric n x n matrix a (row-major, destroyed) (sym_eigen.cpp):
+// eigenvalues to w (unordered), eigenvector i to row i of vt; false if the QR iteration stalls
+bool symmetric_eigen(int n, std::vector<double>& a, std::vector<double>& w, std::vector<double>& vt);
 // Matern (smoothness 3/2) KL table by the Nystrom method (matern_host.cpp); K <= matern_max_terms()
+// (false if the eigen-solve failed)
 int matern_max_terms();
-void matern_kl_table(int N, double corr_len, double variance, int K, std::vector<double>& psi,
+bool matern_kl_table(int N, double corr_len, double variance, int K, std::vector<double>& psi,
                      std::vector<double>& lambda);
 // load vector of the nine-source term of Example 5.1 at the nodes of level N (padded row layout
 // below, zero at Dirichlet nodes and padding); bnorm2 = sum of squares over the interior nodes

@@ -87,6 +87,8 @@ SIGNATURES = {
                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                   ctypes.c_void_p]),
     "smc_kl_table": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, _dp]),
+    "smc_kl_table_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         _dp, _dp]),
     "smc_sizes": (ctypes.c_int, [ctypes.c_void_p, _ip, _ip, _ip, _ip]),
     "smc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(StageInfo)]),
     "smc_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(StageInfo)]),
@@ -171,6 +173,17 @@ def gemm_bf16(A, B):
     if rc != SMC_OK:
         raise SmcError(rc, "smc_gemm_bf16")
     return C
+
+
+def kl_table_host(cov, N, corr_len, variance, K):
+    """KL table Psi [K][2 N^2] and eigenvalues [K] computed on the host (no handle, no GPU)."""
+    lib = load()
+    psi = np.empty((K, 2 * N * N))
+    lam = np.empty(K)
+    rc = lib.smc_kl_table_host(_COV[cov], N, corr_len, variance, K, _dptr(psi), _dptr(lam))
+    if rc != SMC_OK:
+        raise SmcError(rc, "smc_kl_table_host")
+    return psi, lam
 
 
 class Batch:

@@ -79,6 +79,13 @@ WORKLOADS = {
                             s_pcn=2.38 / 64 ** 0.5, seed_true=71, seed_noise=72, seed_sampler=73,
                             precision="mixed", sigma_abs=0.045, cov="matern", proposal="rwm",
                             bc="flow_cell", tau_min=0.001),
+    # Example 5.3 at the paper's size: levels 1/16 .. 1/256, Matern prior lc = 0.1 with
+    # N_sto = 320 terms, 49 observations, Gamma = 0.045^2 I, one random-walk step (covariance
+    # 2.38^2 / 320 I) per update, scheme u' with tau_min = 0.001, J = 1000
+    "example_5_3_full": Workload("example_5_3_full", (16, 32, 64, 128, 256), 512, 320, 0.1, 7, 1000, 1,
+                                 s_pcn=2.38 / 320 ** 0.5, seed_true=81, seed_noise=82, seed_sampler=83,
+                                 precision="mixed", sigma_abs=0.045, cov="matern", proposal="rwm",
+                                 bc="flow_cell", tau_min=0.001),
 }
 
 

@@ -26,14 +26,14 @@ def make(w):
     N = w.inv_h_data
     th = wl.theta_true(w)
     if w.cov == "matern":
-        psi = matern.kl_table(N, w.corr_len, w.variance, w.K)
+        u = matern.field(N, th, w.corr_len, w.variance, w.K)
     else:
-        psi = kl.kl_table(N, w.corr_len, w.variance, w.K)
+        u = th @ kl.kl_table(N, w.corr_len, w.variance, w.K)
     f = fem.nine_sources if w.source == "nine" else None
     if w.bc == "flow_cell":
-        p = fem.solve_flow_cell(N, np.exp(th @ psi))
+        p = fem.solve_flow_cell(N, np.exp(u))
     else:
-        p = fem.solve(N, np.exp(th @ psi), f)
+        p = fem.solve(N, np.exp(u), f)
     obs = wl.obs_grid(w.obs_per_side)
     G = fem.observation_operator(N, obs) @ p
     sigma = w.sigma_abs if w.sigma_abs > 0 else w.noise_frac * np.abs(p).max()
