@@ -80,6 +80,7 @@ Handle::~Handle() {
     }
     cudaFree(synth_kappa_buf);
     cudaFree(synth_theta_buf);
+    cudaFree(synth_part_buf);
     cudaFree(synth_err);
     cudaFree(big_scratch);
     cudaFree(cp_scratch);

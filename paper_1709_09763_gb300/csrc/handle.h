@@ -19,7 +19,8 @@ struct Level {
     int* obs_idx = nullptr;      // [n_obs][3]
     double* obs_w = nullptr;     // [n_obs][3]
     double* linA = nullptr;      // linear forward model [n_obs][K]
-    uint16_t* psi_split = nullptr;   // mixed path: BF16 three-way split of Psi^T, [2N^2][kl_split_width(K)]
+    uint16_t* psi_split = nullptr;   // mixed path: BF16 three-way split of Psi^T, [2N^2][kl_split_width(K)],
+                                     // or per group of 64 terms such a block when K > 256 (kl_split_table)
     std::vector<double> lambda;  // KL eigenvalues
     std::vector<double> psi_host;
     void* rhs = nullptr;         // load vector (FemArgs::rhs), null for f = 1
@@ -59,6 +60,8 @@ struct Handle {
     float* synth_kappa_buf = nullptr;
     uint16_t* synth_theta_buf = nullptr;
     size_t synth_kappa_cap = 0, synth_theta_cap = 0;
+    float* synth_part_buf = nullptr;   // K > 256: FP32 partial fields of the term groups [groups][n][E]
+    size_t synth_part_cap = 0;
     int* synth_err = nullptr;
     int synth_kappa(int level, int n, const double* theta, cudaStream_t st);
 
@@ -123,6 +126,8 @@ struct Handle {
 };
 
 int kl_split_width(int K);
+int kl_groups(int K);        // term groups the synthesis accumulates separately (1 up to K = 256)
+int kl_split_total(int K);   // summed split widths of the groups
 std::vector<uint16_t> kl_split_table(const std::vector<double>& psi, int K, int E);
 
 // G = A theta and Phi for the linear test forward model (smc_kernels.cu)

@@ -1,7 +1,7 @@
 """Example 5.3 at the paper's size on the GPU path against the FP64 oracle: the 320-term Matern KL
-(64 x 64 Nystrom grid) on 1/16 .. 1/256, the synthesis GEMM with K = 320 (a contraction 1920
-wide after the three-way split), G parity of the flow cell on every level, and a short MLS^2MC run
-under the scheme u' with the random-walk kernel."""
+(64 x 64 Nystrom grid) on 1/16 .. 1/256, the synthesis of 320 terms (five tensor-core
+contractions of 64 terms each, their partial fields summed in FP64), G parity of the flow cell on
+every level, and a short MLS^2MC run under the scheme u' with the random-walk kernel."""
 import json
 import math
 import os
