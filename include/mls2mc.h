@@ -53,9 +53,10 @@ extern "C" {
 #define SMC_COV_SEP_EXP 0  /* variance exp(-|x1-x1'|/lc - |x2-x2'|/lc); analytic KL pairs */
 #define SMC_COV_MATERN  1  /* Matern, smoothness 3/2: variance (1 + z) exp(-z), z = sqrt(6) |x - x'| / lc
                               (Minasny & McBratney 2005); KL by the Nystrom method on the midpoint
-                              rule of a 32 x 32 cell grid, eigenvectors of definite parity under
-                              x -> 1-x and y -> 1-y (the library documentation gives the order and
-                              sign rules); K <= 64 */
+                              rule of a 32 x 32 cell grid (64 x 64 beyond 64 terms), eigenvectors
+                              of definite parity under x -> 1-x and y -> 1-y, and under x <-> y
+                              where that maps the parity sector onto itself (the library
+                              documentation gives the order and sign rules); K <= 512 */
 /* source term f of the PDE */
 #define SMC_SRC_ONE     0  /* f = 1 */
 #define SMC_SRC_NINE    1  /* the nine smoothed point sources of Example 5.1: products of 1-D Gaussian

@@ -72,7 +72,8 @@ WORKLOADS = {
                             s_pcn=2.38 / 10 ** 0.5, seed_true=41, seed_noise=42, seed_sampler=53,
                             precision="mixed", sigma_abs=0.035, cov="matern", source="nine", proposal="rwm"),
     # the paper's Example 5.3 (flow cell) at reduced size: levels 1/16 .. 1/64 (the paper: to 1/256),
-    # Matern prior lc = 0.1 with 64 terms (the paper: 320, m0 = 2, which f = 0 makes irrelevant),
+    # Matern prior lc = 0.1 with 64 terms (the paper: 320, see example_5_3_full; its m0 = 2 is
+    # irrelevant since f = 0),
     # 49 observations, Gamma = 0.045^2 I, one random-walk step per update, scheme u' with
     # tau_min = 0.001, J = 1000
     "example_5_3": Workload("example_5_3", (16, 32, 64), 128, 64, 0.1, 7, 1000, 1,
