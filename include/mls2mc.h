@@ -152,7 +152,7 @@ int smc_eval_likelihood_device(smc_handle* h, int level, int n, const double* th
 int smc_kl_table(const smc_handle* h, int level, double* psi, double* lambda);
 /* The same table computed on the host without a handle or a GPU (Eq. truncKL; Sec. 5 for the
  * Matern prior): cov_kind SMC_COV_SEP_EXP or SMC_COV_MATERN, 1 <= N <= 256 cells per side,
- * K terms (Matern: K <= 512; the Nystrom grid has 32 x 32 cells up to 64 terms and 64 x 64
+ * 1 <= K <= 512 terms (the Matern Nystrom grid has 32 x 32 cells up to 64 terms and 64 x 64
  * beyond). psi: host [K][2 N^2] in the triangle order above, lambda: host [K]; either may be
  * NULL. The Matern eigen-decomposition is computed once per process for each (corr_len,
  * variance, grid) and reused by every later call and handle. SMC_EINVAL on invalid arguments

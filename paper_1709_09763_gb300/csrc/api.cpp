@@ -396,7 +396,7 @@ int smc_sizes(const smc_handle* hh, int* K, int* n_obs, int* n_levels, int* J) {
 }
 
 int smc_kl_table_host(int cov_kind, int N, double corr_len, double variance, int K, double* psi, double* lambda) {
-    if (N < 1 || N > 256 || K < 1 || !(corr_len > 0.0) || !(variance > 0.0)) return SMC_EINVAL;
+    if (N < 1 || N > 256 || K < 1 || K > 512 || !(corr_len > 0.0) || !(variance > 0.0)) return SMC_EINVAL;
     if (cov_kind != SMC_COV_SEP_EXP && cov_kind != SMC_COV_MATERN) return SMC_EINVAL;
     if (cov_kind == SMC_COV_MATERN && K > matern_max_terms()) return SMC_EINVAL;
     std::vector<double> p, lam;

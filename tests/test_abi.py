@@ -84,7 +84,7 @@ def test_host_sep_exp_table_and_invalid_arguments(lib):
     psi, lam = native.kl_table_host("sep_exp", 16, 0.3, 1.0, 16)
     assert np.abs(psi - kl.kl_table(16, 0.3, 1.0, 16)).max() < 1e-13
     for args in (("matern", 16, 0.1, 1.0, 513), ("matern", 0, 0.1, 1.0, 4), ("matern", 16, 0.0, 1.0, 4),
-                 ("sep_exp", 16, 0.3, -1.0, 4), ("matern", 512, 0.1, 1.0, 4)):
+                 ("sep_exp", 16, 0.3, -1.0, 4), ("matern", 512, 0.1, 1.0, 4), ("sep_exp", 8, 0.3, 1.0, 513)):
         with pytest.raises(native.SmcError) as ei:
             native.kl_table_host(*args)
         assert ei.value.code == native.SMC_EINVAL, args
