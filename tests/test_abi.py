@@ -59,7 +59,7 @@ def test_invalid_descriptors_rejected_without_gpu(lib):
     assert ei.value.code == native.SMC_EINVAL
 
 
-@pytest.mark.parametrize("N,lc,K", [(8, 0.65, 10), (32, 0.65, 10), (16, 0.1, 64), (16, 0.1, 320)])
+@pytest.mark.parametrize("N,lc,K", [(8, 0.65, 10), (32, 0.65, 10), (16, 0.1, 64), (16, 0.1, 65), (16, 0.1, 320)])
 def test_host_matern_table_equals_oracle(lib, N, lc, K):
     """The library's Nystrom KL (its own eigen-solver and symmetry reduction) against the oracle's
     (LAPACK on the same sub-problems): every table entry and eigenvalue, up to rounding."""
