@@ -324,10 +324,13 @@ int smc_systematic_resample(smc_handle* h, int n, const double* w, double U, int
  * DEVICE arrays, the work is queued on `stream` (a cudaStream_t, NULL = default stream) without
  * waiting, and no handle is needed. Its scratch (one double per particle) is a fixed device array
  * of SMC_NOALLOC_MAX_PARTICLES entries (512 KiB) that every GPU loading the library holds until the
- * process exits; n beyond that maximum returns SMC_EINVAL. It calls no cudaMalloc or cudaFree. The
- * first call on a device looks up the array's device address (make that first call before any
- * stream capture). All calls share the array: calls that overlap on the GPU race on it, so the
- * caller must serialise them. Returns SMC_EINVAL for bad arguments, SMC_ECUDA if the launch fails. */
+ * process exits; n beyond that maximum returns SMC_EINVAL. It calls no cudaMalloc or cudaFree.
+ * Every call looks up the array's device address in the current context (nothing is cached, so a
+ * device reset or another current context is safe). The first call on a device may load the
+ * library's device code: make it before any stream capture (a first call on a capturing stream
+ * returns SMC_EINVAL). All calls share the array: calls that overlap on the GPU race on it, so the
+ * caller must serialise them. Returns SMC_EINVAL for bad arguments (n < 1, n too large, U outside
+ * [0, 1) or NaN, NULL arrays), SMC_ECUDA if the look-up or the launch fails. */
 #define SMC_NOALLOC_MAX_PARTICLES 65536
 int smc_systematic_resample_noalloc(const double* w, int n, double U, int* anc, void* stream);
 

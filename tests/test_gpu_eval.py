@@ -133,7 +133,9 @@ def test_full_size_sampled_parity():
     idx = np.array([0, 1, 777, 2048, 3998, 3999])
     Gr, Phir = _oracle(64, w, theta[idx], wl.obs_grid(7), np.array(d["y"]), d["sigma"])
     assert _rel(G.cpu().numpy()[idx], Gr).max() < 1e-6
-    assert np.all(np.isfinite(Phi.cpu().numpy()))
+    Phi = Phi.cpu().numpy()
+    assert np.all(np.isfinite(Phi))
+    assert _phi_ok(Phi[idx], Phir, Gr, d["sigma"], 1e-6)
 
 
 @pytest.mark.parametrize("prec", [native.SMC_MIXED, native.SMC_FP64])

@@ -61,3 +61,39 @@ def test_adam_first_step_and_convergence():
     for _ in range(3000):
         opt.step(w, [A.T @ (A @ w[0] - c)])
     assert np.allclose(w[0], np.linalg.lstsq(A, c, rcond=None)[0], atol=1e-3)
+
+
+def test_bf16_round_against_hand_values_and_torch():
+    """The storage model's rounding: 8 significant bits, nearest, ties to even, checked on
+    hand-computed values and against torch's float32 -> bfloat16 conversion (a library routine)."""
+    torch = pytest.importorskip("torch")
+    e = 2.0 ** -8
+    cases = {1.0: 1.0, 1.0 + e: 1.0, 1.0 + 3 * e: 1.0 + 4 * e, 1.0 + 1.5 * e: 1.0 + 2 * e,
+             -(1.0 + 3 * e): -(1.0 + 4 * e), 3.0: 3.0, 0.0: 0.0, 2.0 ** -130: 2.0 ** -130}
+    for x, want in cases.items():
+        assert mlp.bf16_round(np.array([x]))[0] == want
+    x = np.random.default_rng(3).normal(0, 1, 20000) * np.exp(np.random.default_rng(4).normal(0, 8, 20000))
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16_round(x), ref)
+
+
+def test_storage_model_rounds_only_stored_values():
+    """With store = bf16_round every hidden activation is a BF16 value, the pre-activations are
+    the exact affine maps of the stored inputs, and the gradients stay within the first-order
+    effect of relative perturbations of 2^-9 per stored value (a few per cent for a four-layer net)."""
+    rng = np.random.default_rng(5)
+    sizes = [6, 16, 16, 16, 4]
+    W, b = mlp.init_params(sizes, 2)
+    x = rng.normal(0, 1, (32, 6))
+    t = rng.normal(0, 1, (32, 4))
+    out, (acts, pres) = mlp.forward(W, b, x, mlp.bf16_round)
+    for l in range(1, len(W)):
+        assert np.array_equal(mlp.bf16_round(acts[l]), acts[l])
+        assert np.allclose(pres[l], acts[l] @ W[l].T + b[l], rtol=0, atol=0)
+    l0, gW0, gb0 = mlp.loss_and_grads(W, b, x, t)
+    l1, gW1, gb1 = mlp.loss_and_grads(W, b, x, t, mlp.bf16_round)
+    assert abs(l1 - l0) < 2e-2 * l0
+    for a, r in zip(gW1 + gb1, gW0 + gb0):
+        assert np.linalg.norm(a - r) < 5e-2 * np.linalg.norm(r)
+    # rounding the stored values is not the identity (the model is active)
+    assert not np.array_equal(gW1[0], gW0[0])

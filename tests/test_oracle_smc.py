@@ -88,6 +88,28 @@ def test_philox_uniform_and_normal_statistics():
     assert np.array_equal(philox.normals(3, 5, 0, 2, 7), philox.normals(3, 6, 0, 2, 7)[:, :5])
 
 
+def test_philox_known_answer_vectors():
+    """Philox4x32-10 against the generator's published known-answer vectors (Salmon, Moraes, Dror
+    and Shaw, SC 2011; the test vectors distributed with the authors' Random123 library, rounds = 10:
+    counter words c0..c3, key words k0, k1, output words in the same order). A wrong multiplier,
+    Weyl constant, round count or word order fails at least one of the three."""
+    kat = [
+        ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
+         (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+        ((0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff), (0xffffffff, 0xffffffff),
+         (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+        ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+         (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+    ]
+    for ctr, (k0, k1), want in kat:
+        got = philox.philox4x32_10(*ctr, k0 | (k1 << 32))
+        assert tuple(int(w) for w in got) == want
+    # the vectorised form gives the same words element by element
+    c = np.array([kat[0][0][0], kat[1][0][0]], dtype=np.uint64)
+    x0 = philox.philox4x32_10(c, c, c, c, 0)[0]
+    assert int(x0[0]) == 0x6627e8d5
+
+
 def test_pcn_preserves_prior_with_zero_potential():
     """Phi == 0: every proposal is accepted and N(0, I) is invariant under the pCN map."""
     K, J = 4, 20000
