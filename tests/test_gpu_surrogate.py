@@ -4,8 +4,10 @@ Weights are set identically on both sides (the oracle uses the BF16-rounded valu
 hidden activations and back-propagated errors in BF16 between layers; the oracle runs the same
 storage model (oracle.mlp.bf16_round at every place the kernels store BF16) in FP64. What remains is
 the FP32 accumulation of the tensor cores and the rare BF16 rounding that falls the other way
-because an FP32 value differs from the FP64 one near a rounding boundary. Bound: per-tensor relative
-Frobenius error <= 1e-2 and cosine >= 0.9999 for gradients, 1e-2 for outputs.
+because an FP32 value differs from the FP64 one near a rounding boundary (measured on the GB300:
+outputs 2.1e-4, gradients 3e-5 .. 4.2e-4 relative Frobenius). Bound: per-tensor relative Frobenius
+error <= 2e-3 and cosine >= 0.99999 for gradients, 2e-3 for outputs (the 1e-2 per tensor that a
+BF16 network warrants, with room to spare).
 """
 import numpy as np
 import pytest
@@ -76,7 +78,7 @@ def test_forward_matches_oracle():
     z, _ = omlp.forward(W, b, xr, omlp.bf16_round)
     Gref = mu[:NOBS].astype(np.float64) + sd[:NOBS] * z
     print(f"surrogate forward rel err {_rel(G, Gref):.3e}")
-    assert _rel(G, Gref) < 1e-2
+    assert _rel(G, Gref) < 2e-3
     assert np.max(np.abs((G - Gref) / sd[:NOBS])) < 0.1 * np.max(np.abs(z))
 
 
@@ -92,16 +94,16 @@ def test_gradients_match_oracle():
     xr = native.bf16_value(native.bf16_bits(theta)).astype(np.float64)
     tz = (G - mu[:NOBS]) / sd[:NOBS]
     lref, rW, rb = omlp.loss_and_grads(W, b, xr, tz, omlp.bf16_round)
-    assert loss == pytest.approx(lref, rel=1e-2)
+    assert loss == pytest.approx(lref, rel=2e-3)
     gW0, gW4, gb4 = gW[0][:, :K], gW[4][:NOBS, :], gb[4][:NOBS]
     pairs = [(gW0, rW[0]), (gW[1], rW[1]), (gW[2], rW[2]), (gW[3], rW[3]), (gW4, rW[4]),
              (gb[0], rb[0]), (gb[3], rb[3]), (gb4, rb[4])]
     errs = [_rel(a, r) for a, r in pairs]
     print("surrogate gradient rel errs " + " ".join(f"{e:.2e}" for e in errs))
     for a, r in pairs:
-        assert _rel(a, r) < 1e-2
+        assert _rel(a, r) < 2e-3
         cos = np.sum(a * r) / (np.linalg.norm(a) * np.linalg.norm(r))
-        assert cos > 0.9999
+        assert cos > 0.99999
     # padding receives no gradient
     assert np.all(gW[0][:, K:] == 0) and np.all(gW[4][NOBS:, :] == 0)
 
