@@ -15,6 +15,7 @@ out every step). Multi-GPU: independent replicas per rank (no data-path collecti
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 """
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -456,7 +457,7 @@ def main():
     # delayed-acceptance pCN screened by the surrogate, R seeds each, outside the timed region
     run = None
     if not args.no_run:
-        def one_run(wk, dk, inv_h, surrogate, seed, precision=native.SMC_MIXED):
+        def one_run(wk, dk, inv_h, surrogate, seed, precision=native.SMC_MIXED, marginals=False):
             ob = wl.obs_grid(wk.obs_per_side)
             hr = native.Handle(inv_h, wk.K, ob, dk["y"], dk["sigma"], corr_len=wk.corr_len, variance=wk.variance,
                                J=wk.J, J_tilde=wk.J_tilde, n_mcmc=wk.n_mcmc, s_pcn=wk.s_pcn,
@@ -471,12 +472,18 @@ def main():
             st = hr.state()
             path = hr.path()
             m, v, lz = hr.posterior_moments()
+            extra = {}
+            if marginals:
+                # the leading three coefficients' particles (KS distances) and Phi of the posterior
+                # mean on the finest level (Eq. RelMisfit), outside the timed region
+                extra["marginals"] = hr.particles()[0][:, :3].copy()
+                extra["phi_at_mean"] = float(hr.eval_likelihood(len(inv_h) - 1, np.asarray(m)[None, :])[1][0])
             hr.close()
             rates = [p["da_stage1_rate"] for p in path if p["da_stage1_rate"] >= 0]
             return {"seconds": secs, "updates": st["n_updates"], "solves_per_level": st["evals"][:len(inv_h)],
                     "final_level": st["level"],
                     "log_evidence": lz, "mean": m, "var": v,
-                    "stage1_pass_rate": float(np.mean(rates)) if rates else None}
+                    "stage1_pass_rate": float(np.mean(rates)) if rates else None, **extra}
 
         def fp64_solve_roofline(wk, dk, reps=5):
             """The FP64 solve of the single-level workload against the FP64 FMA issue peak: J
@@ -538,36 +545,75 @@ def main():
         run = {"mls2mc": compare(w, d, tuple(w.inv_h)), "smc_finest": compare(w, d, (w.inv_h[-1],), R=6),
                "mls2mc_surrogate_workload": compare(wda, dda, tuple(wda.inv_h))}
 
-        def paper_example(name, R=3):
+        def paper_example(name, R=3, J_sweep=()):
             """The paper's examples (Matern prior, one random-walk step per update; 5.1/5.2: nine
             sources, 5.3: the flow cell under the scheme u'): MLS^2MC on the hierarchy against
             single-level SMC on its finest level, R seeded runs each; cost in the paper's unit
-            sum_l evals_l 4^(l - L) (one finest-level solve = 1)."""
+            sum_l evals_l 4^(l - L) (one finest-level solve = 1). Accuracy as in Sec. 5.1: RelErr
+            and RelMisfit of each run's posterior mean, KS distances of the theta_1..theta_3
+            marginals between the runs of the two samplers and within single-level SMC (the base
+            scatter), RelErrEvid against the geometric mean of the single-level SMC evidences.
+            J_sweep: the same comparison (R // 2 runs each) at smaller J, for cost against accuracy."""
+            from paper_1709_09763_gb300 import metrics
             wk, dk = wl.WORKLOADS[name], load_data(name)
             res = {"workload": name, "levels_inv_h": list(wk.inv_h), "K": wk.K, "J": wk.J, "sigma": dk["sigma"],
-                   "tau_star": wk.tau_star, "proposal": wk.proposal}
-            # Eq. RelErr: weighted l1 distance of the posterior mean to theta_true, weights sqrt(lambda_k)
+                   "tau_star": wk.tau_star, "proposal": wk.proposal, "replicates": R}
             hk = native.Handle([wk.inv_h[0]], wk.K, wl.obs_grid(wk.obs_per_side), dk["y"], dk["sigma"],
                                corr_len=wk.corr_len, precision=native.SMC_MIXED, cov=wk.cov, source=wk.source)
-            sq = np.sqrt(hk.kl_table(0, wk.inv_h[0])[1])
+            lam = hk.kl_table(0, wk.inv_h[0])[1]
             hk.close()
             th_true = np.array(dk["theta_true"])
-            rel_err = lambda m: float(np.sum(sq * np.abs(np.asarray(m) - th_true)) / np.sum(sq * np.abs(th_true)))
-            for label, inv_h in (("mls2mc", tuple(wk.inv_h)), ("smc_finest", (wk.inv_h[-1],))):
-                runs = [one_run(wk, dk, inv_h, 0, wk.seed_sampler + 1000 * rank + 17 * r) for r in range(R)]
+
+            def arm(wj, inv_h, n):
+                runs = [one_run(wj, dk, inv_h, 0, wj.seed_sampler + 1000 * rank + 17 * r, marginals=True)
+                        for r in range(n)]
                 L = len(inv_h)
                 cost = [float(sum(e * 4.0 ** (l - (L - 1)) for l, e in enumerate(x["solves_per_level"]))) for x in runs]
-                res[label] = {"seconds_median": float(np.median([x["seconds"] for x in runs])),
+                return runs, {"seconds_median": float(np.median([x["seconds"] for x in runs])),
                               "seconds": [x["seconds"] for x in runs],
                               "solves_per_level_mean": np.mean([x["solves_per_level"] for x in runs], axis=0).tolist(),
                               "cost_finest_solves_mean": float(np.mean(cost)),
                               "updates": [x["updates"] for x in runs],
                               "log_evidence": [x["log_evidence"] for x in runs],
-                              "rel_err_posterior_mean": [rel_err(x["mean"]) for x in runs],
+                              "rel_err_posterior_mean": [metrics.rel_err(x["mean"], th_true, lam) for x in runs],
+                              "rel_misfit_posterior_mean": [metrics.rel_misfit(x["phi_at_mean"], dk["y"], dk["sigma"])
+                                                            for x in runs],
                               "final_level_inv_h": [inv_h[x["final_level"]] for x in runs]}
+
+            def accuracy(ml_runs, sl_runs):
+                ref = metrics.log_z_ref([x["log_evidence"] for x in sl_runs])
+                ks_ml, ks_ml_sd, n_ml = metrics.pairwise_ks([x["marginals"] for x in ml_runs],
+                                                             [x["marginals"] for x in sl_runs])
+                ks_sl, ks_sl_sd, n_sl = metrics.pairwise_ks([x["marginals"] for x in sl_runs])
+                ree = lambda rs: metrics.rel_err_evid([x["log_evidence"] for x in rs], ref)
+                return {"ks_mls2mc_vs_smc_mean": ks_ml.tolist(), "ks_mls2mc_vs_smc_sd": ks_ml_sd.tolist(),
+                        "ks_pairs": n_ml, "ks_smc_vs_smc_mean": ks_sl.tolist(), "ks_smc_vs_smc_sd": ks_sl_sd.tolist(),
+                        "log_z_ref": ref, "rel_err_evid_mls2mc_mean": float(np.mean(ree(ml_runs))),
+                        "rel_err_evid_smc_mean": float(np.mean(ree(sl_runs)))}
+
+            ml_runs, res["mls2mc"] = arm(wk, tuple(wk.inv_h), R)
+            sl_runs, res["smc_finest"] = arm(wk, (wk.inv_h[-1],), R)
             res["speedup_mls2mc_vs_smc"] = res["smc_finest"]["seconds_median"] / res["mls2mc"]["seconds_median"]
             res["cost_ratio_smc_over_mls2mc"] = (res["smc_finest"]["cost_finest_solves_mean"] /
                                                  res["mls2mc"]["cost_finest_solves_mean"])
+            if R >= 2:
+                res["accuracy"] = accuracy(ml_runs, sl_runs)
+            if J_sweep:
+                # cost against accuracy: finest-level solve equivalents and seconds vs RelErr per J
+                table = []
+                for J in J_sweep:
+                    wj = dataclasses.replace(wk, J=J)
+                    n = max(2, R // 2)
+                    mr, ms = arm(wj, tuple(wk.inv_h), n)
+                    sr, ss = arm(wj, (wk.inv_h[-1],), n)
+                    for label, st in (("mls2mc", ms), ("smc_finest", ss)):
+                        table.append({"J": J, "sampler": label, "runs": n,
+                                      "cost_finest_solves": st["cost_finest_solves_mean"],
+                                      "seconds_median": st["seconds_median"],
+                                      "rel_err_mean": float(np.mean(st["rel_err_posterior_mean"])),
+                                      "rel_err_sd": float(np.std(st["rel_err_posterior_mean"])),
+                                      "rel_misfit_mean": float(np.mean(st["rel_misfit_posterior_mean"]))})
+                res["cost_vs_accuracy"] = table
             return res
         # single-level SMC on the FP64 path (h = 1/16, K = 16, J = 1000, 5 pCN steps)
         wf, dfp = wl.WORKLOADS["smc_fp64_h16"], load_data("smc_fp64_h16")
@@ -581,8 +627,8 @@ def main():
                                "updates": [x["updates"] for x in fr],
                                "log_evidence": [x["log_evidence"] for x in fr],
                                "roofline": fp64_solve_roofline(wf, dfp)}
-        run["paper_example_5_1"] = paper_example("example_5_1")
-        run["paper_example_5_2"] = paper_example("example_5_2")
+        run["paper_example_5_1"] = paper_example("example_5_1", R=12, J_sweep=(625, 1250))
+        run["paper_example_5_2"] = paper_example("example_5_2", R=12, J_sweep=(625, 1250))
         # Example 5.3, the flow cell, at reduced size (levels 1/16 .. 1/64, 64 KL terms), scheme u'
         run["paper_example_5_3"] = paper_example("example_5_3")
         if args.example_5_3_full:   # the paper's size: 1/16 .. 1/256, 320 KL terms

@@ -111,13 +111,23 @@ __device__ __forceinline__ void load_rhs(const void* t, int n, float& hi, float&
 // 1 / x rounded to nearest (the same value as the IEEE division 1 / x)
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+// The smoother's inverse diagonals on the coarse levels: the approximate reciprocal of the special
+// function unit (one instruction, relative error below 2^-22) on the FP32 path. They only shape the
+// multigrid preconditioner -- the CG operator and the refinement residual use the edge weights --
+// and the preconditioner stays symmetric because every sweep uses the same value at a node.
+__device__ __forceinline__ float recip_coarse(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double recip_coarse(double x) { return __drcp_rn(x); }
 
 // inverse stencil diagonal at interior node n: stored, or formed from the four edge weights
 // (the same expression and order as where it is stored)
 template <typename Real, int S>
 __device__ __forceinline__ Real inv_diag(const Lv<Real>& L, int n) {
     if (L.iD) return L.iD[n];
-    return recip(L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S]);
+    return recip_coarse(L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S]);
 }
 
 // sum of a_nb * v_nb over the four stencil neighbours of padded node n (row stride S)
@@ -334,7 +344,8 @@ __host__ __device__ constexpr int dense_reals(int N) {
 // Ainv [m][m] := A^{-1} by in-place Gauss-Jordan elimination without pivoting (A is symmetric
 // positive definite). Step k turns row k into row k / a_kk, column k into -column k / a_kk, the
 // pivot into 1 / a_kk and every other entry into a_uv - a_uk a_kv / a_kk; the old row and column
-// k are read from a buffer that step k - 1 filled, so one barrier per step suffices.
+// k are read from a buffer that step k - 1 filled, so one barrier per step suffices (a warp
+// barrier when one warp runs it, T = 32).
 // Ainv is followed by that buffer: [2][row | column], 4m Reals.
 template <typename Real, int NL, int T, bool FC = false>
 __device__ void dense_setup(const Lv<Real>& L, Real* Ainv) {
@@ -354,7 +365,7 @@ __device__ void dense_setup(const Lv<Real>& L, Real* Ainv) {
         if (u == 0) buf[v] = val;
         if (v == 0) buf[m + u] = val;
     }
-    __syncthreads();
+    if constexpr (T == 32) __syncwarp(); else __syncthreads();
     for (int k = 0; k < m; ++k) {
         const Real* rowk = buf + (k & 1) * 2 * m;
         const Real* colk = rowk + m;
@@ -371,7 +382,7 @@ __device__ void dense_setup(const Lv<Real>& L, Real* Ainv) {
             if (u == k + 1) rown[v] = val;
             if (v == k + 1) coln[u] = val;
         }
-        __syncthreads();
+        if constexpr (T == 32) __syncwarp(); else __syncthreads();
     }
 }
 
@@ -457,14 +468,14 @@ __device__ __forceinline__ void build_coeffs(const Lv<Real>& L, const Real* kap)
     }
 }
 
-template <typename Real, int NL, int T, bool FC = false>
+template <typename Real, int NL, int T, bool FC = false, bool COARSE = false>
 __device__ __forceinline__ void build_diag(const Lv<Real>& L) {
     constexpr int S = fem_row_stride(NL);
     for (int n = threadIdx.x; n < (NL + 1) * S; n += T) {
         const int j = n / S, i = n - j * S;
         Real d = 0;   // the flow cell's boundary rows read the zero ghost rows for their missing edges
         if (i > 0 && i < NL && (FC || (j > 0 && j < NL))) d = L.aE[n] + L.aE[n - 1] + L.aN[n] + L.aN[n - S];
-        L.iD[n] = (d == Real(0)) ? Real(1) : recip(d);   // boundary entries are never used
+        L.iD[n] = (d == Real(0)) ? Real(1) : COARSE ? recip_coarse(d) : recip(d);   // boundary entries are never used
     }
 }
 
@@ -493,11 +504,11 @@ __device__ void setup_levels(Real* arena, Real* stage, bool ping) {
         Real* kout = ping ? stage + 2 * N * N : stage;
         coarsen_kappa<Real, NL / 2, T>(kin, kout);
         __syncthreads();
-        build_diag<Real, NL, T, FC>(L);
+        build_diag<Real, NL, T, FC, (NL < N)>(L);
         setup_levels<Real, N, NL / 2, T, FC>(arena, stage, !ping);
     } else {
         __syncthreads();
-        build_diag<Real, NL, T, FC>(L);
+        build_diag<Real, NL, T, FC, (NL < N)>(L);
         __syncthreads();
     }
 }
@@ -599,9 +610,19 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     zero_rings<Real, N, N, T, CP, FC>(arena);
     __syncthreads();
     Real* dinv = CP ? arena + arena_size_cp(N) : arena + arena_size(N, FC) + 4 * NPT * T;
-    if constexpr (direct_level<Real, FC>(N) != 0)
-        dense_setup<Real, direct_level<Real, FC>(N), T, FC>(
-            level_ptrs<Real, N, direct_level<Real, FC>(N), CP, FC>(arena), dinv);
+    if constexpr (direct_level<Real, FC>(N) != 0) {
+        if constexpr (CP) {
+            // compact forms: one warp runs the pivot steps while the SM's other blocks keep it busy
+            // (with one block per SM the block-wide form is faster)
+            if (tid < 32)
+                dense_setup<Real, direct_level<Real, FC>(N), 32, FC>(
+                    level_ptrs<Real, N, direct_level<Real, FC>(N), CP, FC>(arena), dinv);
+            __syncthreads();
+        } else {
+            dense_setup<Real, direct_level<Real, FC>(N), T, FC>(
+                level_ptrs<Real, N, direct_level<Real, FC>(N), CP, FC>(arena), dinv);
+        }
+    }
 
     // fine nodes owned by this thread, one packed int each: bits 0-12 node index n, 13-23 the
     // coarse node c under it ((j/2) SC + i/2), 24-25 (i & 1) + 2 (j & 1), 26 red, 27 valid.
