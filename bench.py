@@ -3,9 +3,10 @@
 Workload: the MLS^2MC configuration of 4 levels h = 1/8, 1/16, 1/32, 1/64, K = 32 KL
 terms (correlation length 0.1), 49 observations on the 7 x 7 grid, J = 4000 particles,
 mixed precision (FP32 multigrid-PCG with extended-precision refinement). One step is
-one pass of the hot path over the particle batch: the likelihood G_l(theta), Phi_l(theta)
-of every particle on every level of the hierarchy (KL field, P1 solve, observation
-gather, Gaussian misfit).
+one pass of the hot path over the particle batch: on every level a tempering update and,
+below the finest level, a bridging step to the next level, each with 5 pCN sweeps -- the
+likelihood G_l(theta), Phi_l(theta) (KL field, P1 solve, observation gather, Gaussian
+misfit) of every particle and proposal, the adaptive increments, resampling and moves.
 
 value: likelihood evaluations per second over the whole job (all levels, all ranks),
 inputs resident in device memory, L2 flushed between steps. e2e: the same step through
@@ -321,6 +322,64 @@ def batched_measurement(native, wl, torch, dev, reps=5, n_problems=64, max_inv_h
             "speedup": ms_seq / ms_bat, "identical_potentials": same}
 
 
+def batched_sampler_measurement(native, wl, torch, dev, n_problems=64, max_inv_h=128, j_range=(500, 8000)):
+    """The batched workload's samplers to their posteriors: n_problems independent MLS^2MC problems of
+    uneven size (finest 1/h from {16, 32, 64, 128}, K from {16, 32, 64}, J log-uniform in j_range,
+    5 pCN steps, mixed precision; problem p's sampler seed 300 + p), each run alone with smc_run, one
+    after another, against all of them advanced together by the batched sampler (smc_batch_run: every
+    problem's next update in shared launches). Data as in batched_measurement. Wall seconds on the
+    host clock with the stream synchronised; whether every problem's path and particles agree."""
+    specs = wl.batched_uneven(n_problems=n_problems, max_inv_h=max_inv_h, j_range=j_range)
+    stream = torch.cuda.Stream(dev)
+    s = stream.cuda_stream
+    obs = wl.obs_grid(7)
+    kws = []
+    for p, sp in enumerate(specs):
+        h0 = native.Handle(sp["levels"], sp["K"], obs, np.zeros(49), 1.0, corr_len=sp["corr_len"],
+                           precision=native.SMC_MIXED, stream=s)
+        G, _ = h0.eval_likelihood(len(sp["levels"]) - 1, wl.standard_normals((1, sp["K"]), sp["seed_true"]))
+        h0.close()
+        sigma = 0.01 * float(np.abs(G).max())
+        y = G[0] + sigma * wl.standard_normals((49,), sp["seed_noise"])
+        kws.append(dict(inv_h=list(sp["levels"]), K=sp["K"], obs_xy=obs, y=y, sigma=sigma, corr_len=sp["corr_len"],
+                        J=sp["J"], n_mcmc=5, precision=native.SMC_MIXED, seed=300 + p, stream=s))
+
+    def make(kw):
+        kw = dict(kw)
+        return native.Handle(kw.pop("inv_h"), kw.pop("K"), kw.pop("obs_xy"), kw.pop("y"), kw.pop("sigma"), **kw)
+
+    seq = [make(kw) for kw in kws]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for h in seq:
+        h.run()
+    stream.synchronize()
+    t_seq = time.perf_counter() - t0
+    bat = [make(kw) for kw in kws]
+    b = native.Batch(bat)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    steps = b.run()
+    stream.synchronize()
+    t_bat = time.perf_counter() - t0
+    same_particles = [bool(np.array_equal(x.particles()[0], z.particles()[0])) for x, z in zip(seq, bat)]
+    same_state = [x.state() == z.state() for x, z in zip(seq, bat)]
+    same_path = [x.path() == z.path() for x, z in zip(seq, bat)]
+    same = all(same_particles) and all(same_state) and all(same_path)
+    updates = sum(h.state()["n_updates"] for h in bat)
+    b.close()
+    for h in seq + bat:
+        h.close()
+    by_size = {}
+    for sp in specs:
+        by_size[str(sp["levels"][-1])] = by_size.get(str(sp["levels"][-1]), 0) + 1
+    return {"problems": len(specs), "particles": int(sum(sp["J"] for sp in specs)), "problems_by_finest_inv_h": by_size,
+            "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat, "batched_steps": steps,
+            "updates": updates, "identical_paths_and_particles": bool(same),
+            "problems_with_identical": {"particles": int(sum(same_particles)), "state": int(sum(same_state)),
+                                        "path": int(sum(same_path))}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -369,14 +428,21 @@ def main():
         tuned = [h.block_size(l) for l in range(L)]
     h.set_particles(theta0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
-    n_mcmc_step = 1
-    evals_per_step = L * J * (1 + n_mcmc_step)
+    # one step: on every level a tempering update (Phi of all particles, adaptive increment,
+    # resampling, n_mcmc pCN sweeps) and, below the finest level, a bridging step to the next level
+    # (Phi on both levels, adaptive zeta increment, resampling, n_mcmc pCN sweeps solving both levels
+    # per proposal, Sec. 4.1): the sampler's two update kinds with the workload's 5 pCN steps
+    n_mcmc_step = w.n_mcmc
+    evals_level = [J * (1 + n_mcmc_step) + (2 * J * (1 + n_mcmc_step) if l < L - 1 else 0) for l in range(L)]
+    evals_per_step = int(sum(evals_level))
 
     def step(ev=None):
         for l in range(L):
             if ev is not None:
                 ev[l][0].record(stream)
             h.tempering_update(l, 0.0, n_mcmc_step)
+            if l < L - 1:
+                h.bridging_update(l, 1.0, 0.0, n_mcmc_step)
             if ev is not None:
                 ev[l][1].record(stream)
 
@@ -457,13 +523,15 @@ def main():
     # delayed-acceptance pCN screened by the surrogate, R seeds each, outside the timed region
     run = None
     if not args.no_run:
-        def one_run(wk, dk, inv_h, surrogate, seed, precision=native.SMC_MIXED, marginals=False):
+        def one_run(wk, dk, inv_h, surrogate, seed, precision=native.SMC_MIXED, marginals=False, breakdown=False):
             ob = wl.obs_grid(wk.obs_per_side)
             hr = native.Handle(inv_h, wk.K, ob, dk["y"], dk["sigma"], corr_len=wk.corr_len, variance=wk.variance,
                                J=wk.J, J_tilde=wk.J_tilde, n_mcmc=wk.n_mcmc, s_pcn=wk.s_pcn,
                                tau_star=wk.tau_star, precision=precision, seed=seed,
                                stream=stream.cuda_stream, surrogate=surrogate, cov=wk.cov, source=wk.source,
                                proposal=wk.proposal, bc=wk.bc, tau_min=wk.tau_min)
+            if breakdown:
+                hr.set_timing(True)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             hr.run()
@@ -473,10 +541,22 @@ def main():
             path = hr.path()
             m, v, lz = hr.posterior_moments()
             extra = {}
+            if breakdown:
+                # device time by part of the run (events on the handle's stream; a separate run from
+                # the timed ones): forward solves per level, surrogate training and inference,
+                # screening, increments and resampling, Markov moves, the gate's calibration
+                sms, scnt = hr.get_timing()
+                extra["breakdown_ms"] = {"solves_per_level": sms[:len(inv_h)].tolist(),
+                                         "solve_launches_per_level": scnt[:len(inv_h)], **hr.get_phase_timing()}
+                extra["breakdown_ms"]["wall_ms"] = secs * 1e3
+                hr.set_timing(False)
             if marginals:
                 # the leading three coefficients' particles (KS distances) and Phi of the posterior
                 # mean on the finest level (Eq. RelMisfit), outside the timed region
-                extra["marginals"] = hr.particles()[0][:, :3].copy()
+                th_all = hr.particles()[0]
+                extra["marginals"] = th_all[:, :3].copy()
+                extra["unique_particles"] = int(np.unique(th_all, axis=0).shape[0])
+                extra["accept_mean"] = float(np.mean([p["accept_rate"] for p in path])) if path else None
                 extra["phi_at_mean"] = float(hr.eval_likelihood(len(inv_h) - 1, np.asarray(m)[None, :])[1][0])
             hr.close()
             rates = [p["da_stage1_rate"] for p in path if p["da_stage1_rate"] >= 0]
@@ -519,7 +599,7 @@ def main():
                     "peak_source": "FP64 FMA issue: 152 SMs x 2 FMA per clock x 2 flops x sm_max_mhz "
                                    "(the 1.25 TFLOP/s FP64 figure of this part)"}
 
-        def compare(wk, dk, inv_h, R=3):
+        def compare(wk, dk, inv_h, R=3, breakdown=False):
             res = {}
             for name, sur in (("plain", 0), ("surrogate", 1)):
                 runs = [one_run(wk, dk, inv_h, sur, wk.seed_sampler + 1000 * rank + 17 * r) for r in range(R)]
@@ -530,6 +610,9 @@ def main():
                              "log_evidence": [x["log_evidence"] for x in runs],
                              "stage1_pass_rate": runs[0]["stage1_pass_rate"],
                              "_means": np.array([x["mean"] for x in runs])}
+                if breakdown:
+                    res[name]["breakdown_ms"] = one_run(wk, dk, inv_h, sur, wk.seed_sampler + 1000 * rank,
+                                                        breakdown=True)["breakdown_ms"]
             a, b = res["plain"].pop("_means"), res["surrogate"].pop("_means")
             se = np.sqrt(a.var(axis=0, ddof=1) / R + b.var(axis=0, ddof=1) / R)
             z = np.abs(a.mean(0) - b.mean(0)) / np.where(se > 0, se, np.inf)
@@ -543,7 +626,7 @@ def main():
         wda = wl.WORKLOADS["da_mixed_h8_128"]
         dda = load_data(wda.name)
         run = {"mls2mc": compare(w, d, tuple(w.inv_h)), "smc_finest": compare(w, d, (w.inv_h[-1],), R=6),
-               "mls2mc_surrogate_workload": compare(wda, dda, tuple(wda.inv_h))}
+               "mls2mc_surrogate_workload": compare(wda, dda, tuple(wda.inv_h), breakdown=True)}
 
         def paper_example(name, R=3, J_sweep=()):
             """The paper's examples (Matern prior, one random-walk step per update; 5.1/5.2: nine
@@ -578,7 +661,9 @@ def main():
                               "rel_err_posterior_mean": [metrics.rel_err(x["mean"], th_true, lam) for x in runs],
                               "rel_misfit_posterior_mean": [metrics.rel_misfit(x["phi_at_mean"], dk["y"], dk["sigma"])
                                                             for x in runs],
-                              "final_level_inv_h": [inv_h[x["final_level"]] for x in runs]}
+                              "final_level_inv_h": [inv_h[x["final_level"]] for x in runs],
+                              "unique_particles_median": float(np.median([x["unique_particles"] for x in runs])),
+                              "accept_rate_mean": float(np.mean([x["accept_mean"] for x in runs]))}
 
             def accuracy(ml_runs, sl_runs):
                 ref = metrics.log_z_ref([x["log_evidence"] for x in sl_runs])
@@ -635,6 +720,7 @@ def main():
             run["paper_example_5_3_full"] = paper_example("example_5_3_full")
 
     batched = None if args.no_run else batched_measurement(native, wl, torch, dev)
+    batched_run = None if args.no_run else batched_sampler_measurement(native, wl, torch, dev)
     # many small problems: each per-problem launch fills a fraction of the GPU
     batched_small = None if args.no_run else batched_measurement(native, wl, torch, dev, n_problems=256,
                                                                  max_inv_h=64, j_range=(16, 256))
@@ -662,12 +748,15 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "levels_inv_h": list(w.inv_h), "K": w.K, "n_obs": n_obs, "J": J,
-                       "precision": "mixed", "step": "per level: Phi on all particles, adaptive increment, "
-                       "systematic resampling, 1 pCN sweep (propose, solve, accept)",
+                       "precision": "mixed", "step": "per level: a tempering update (Phi on all particles, "
+                       "adaptive increment, systematic resampling, 5 pCN sweeps) and, below the finest level, a "
+                       "bridging step to the next level (Phi on both levels, adaptive zeta increment, "
+                       "resampling, 5 pCN sweeps solving both levels per proposal)",
                        "evals_per_step": evals_per_step, "l2": "flushed between steps (256 MB write)",
                        "threads_per_particle": dict(zip([str(N) for N in w.inv_h], tuned)),
                        "parallelism": f"replicas x{world}"},
-            "per_level": {str(N): {"evals_per_s": 2 * J * world / (lm * 1e-3), "update_ms": lm,
+            "per_level": {str(N): {"evals_per_s": evals_level[l] * world / (lm * 1e-3), "update_ms": lm,
+                                   "evals": evals_level[l],
                                    "solve_launch_ms": kern_ms[l] / max(kern_n[l], 1),
                                    "solve_evals_per_s": J / (kern_ms[l] / max(kern_n[l], 1) * 1e-3),
                                    "solve_kernel": solve_kernel_name(N, tuned[l]),
@@ -701,6 +790,8 @@ def main():
             line["batched_uneven"] = batched
         if batched_small is not None:
             line["batched_small_problems"] = batched_small
+        if batched_run is not None:
+            line["batched_sampler_to_posterior"] = batched_run
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

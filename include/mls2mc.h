@@ -180,6 +180,15 @@ int smc_set_block_size(smc_handle* h, int level, int T);
 /* The block size the solves of `level` run with (set, tuned or the default) into *T. */
 int smc_block_size(smc_handle* h, int level, int* T);
 
+/* Phase timing (no counterpart in the paper; for measurement): with smc_set_timing enabled, the parts
+ * of the sampler's updates that are not forward solves are bracketed by CUDA events on the handle's
+ * stream. ms8 [8] (may be NULL) receives the summed device milliseconds since the last call, by
+ * phase: 0 surrogate training, 1 surrogate inference (stage-1 forward passes), 2 stage-1 screening
+ * and survivor compaction, 3 increments and resampling (Sec. 3.4, Sec. 2.4), 4 Markov-move
+ * proposals and acceptances, 5 the screening gate's calibration, 6-7 unused. The forward solves
+ * themselves are in smc_get_timing. Waits for the recorded events. */
+int smc_get_phase_timing(smc_handle* h, double* ms8);
+
 /* Number of CUDA kernels this library has launched in the process so far (all handles). */
 long long smc_kernel_launches(void);
 int smc_get_timing(smc_handle* h, double* ms_per_level, long long* launches_per_level);
@@ -271,6 +280,48 @@ int smc_set_particles(smc_handle* h, const double* theta);
  * Without the surrogate the host does not wait for the increment search: its failures
  * (SMC_ESINGULAR, SMC_ETIMEOUT) are reported when the update ends, the particles then unspecified. */
 int smc_tempering_update(smc_handle* h, int level, double beta0, int n_mcmc, smc_stage_info* info);
+
+/* One bridging step between `level` and level + 1 (0 <= level < n_levels - 1) at inverse temperature
+ * beta (0 < beta <= 1), from bridging temperature zeta0 in [0, 1) (Sec. 4.1): evaluate Phi_level and
+ * Phi_level+1 on all particles, choose dzeta in [min(eps, 1 - zeta0), 1 - zeta0] for the weights
+ * exp(-beta dzeta (Phi_level+1 - Phi_level)) (Eq. Eq_cv_opt), resample systematically, and run n_mcmc
+ * pCN steps for exp(-beta ((1 - zeta) Phi_level + zeta Phi_level+1)) mu0 with zeta = zeta0 + dzeta
+ * (1 when the whole remaining step was taken), each proposal solved on both levels. The particles
+ * change; the update-scheme state of smc_step does not. The building block of a level update
+ * (smc_step runs these from zeta0 = 0 until zeta = 1). info (may be NULL): type 1, level + 1, beta,
+ * the new zeta, dzeta, cv, log mean weight, accept rate. Waits for the increment search. */
+int smc_bridging_update(smc_handle* h, int level, double beta, double zeta0, int n_mcmc, smc_stage_info* info);
+
+/* ---- many problems' samplers advanced together ------------------------------------------------
+ * smc_init_batch builds n_problems handles (smc_init of problems[p] with opts[p]) and a batch that
+ * owns them (smc_batch_destroy destroys them); smc_batch_handle returns problem p's handle (owned
+ * by the batch; NULL for a bad index) for smc_state, smc_path, smc_posterior_moments and
+ * smc_get_particles. smc_batch_create also makes a batch that a sampler can step, from handles the
+ * caller keeps.
+ *
+ * smc_batch_step performs, for every problem not yet finished, its next importance-sampling update
+ * under the update scheme of Eq. eq_updatescheme_final (Sec. 4.4, or the scheme u' of Sec. 4.5 when
+ * its opts.tau_min > 0): an ITU, or one bridging step of a level update (Sec. 4.1), with the cv^LU
+ * predictor on the first J~ particles where the scheme asks for it. The work of all problems runs
+ * phase by phase in shared launches: the likelihoods in one persistent launch per level size, the
+ * adaptive increments (Sec. 3.4, Eq. Eq_cv_opt) in one cooperative launch, the resampling with its
+ * gather (Sec. 2.4) in another, each pCN step's proposals and acceptances in one launch each. Each
+ * problem's path and particles equal those that smc_step on its own handle produces, bit for bit
+ * (an LU that smc_step performs in one call takes one batched step per bridging step). The first
+ * step of a problem draws its prior particles (as smc_step does). infos (may be NULL): [n_problems]
+ * records of this step's update per problem, status 1 where the problem had nothing left to do.
+ * Requirements: FEM problems with Dirichlet boundary conditions, the plain sampler (opts.surrogate
+ * = 0), one stream shared by all handles (SMC_EINVAL otherwise). On a failure of some problem the
+ * step still completes the others' updates and returns the first error (smc_batch_last_error names
+ * the problem). Queues work on the handles' stream and waits for it (once at the end, and once after
+ * the predictors when some problem needs one).
+ * smc_batch_run steps until every problem is finished (beta = 1 on its finest level, or stopped by
+ * the scheme u'), or max_steps steps (<= 0: no cap); *steps (may be NULL) receives the steps taken. */
+int smc_init_batch(int n_problems, const smc_problem_desc* problems, const smc_sampler_opts* opts,
+                   smc_batch** out);
+smc_handle* smc_batch_handle(smc_batch* b, int p);
+int smc_batch_step(smc_batch* b, smc_stage_info* infos);
+int smc_batch_run(smc_batch* b, int max_steps, int* steps);
 
 /* ---- surrogate network (no counterpart in the paper) ------------------------------------------
  * Per level, a network theta -> G_l(theta): K inputs, 4 hidden layers of 256 with the exact GELU

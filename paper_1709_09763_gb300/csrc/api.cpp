@@ -87,9 +87,14 @@ Handle::~Handle() {
     cudaFree(big_counter);
     cudaFree(d_y);
     free_sampler();
-    for (auto& t : timed) {
-        cudaEventDestroy(t.start);
-        cudaEventDestroy(t.stop);
+    for (auto* v : {&timed, &timed_phase})
+        for (auto& t : *v) {
+            cudaEventDestroy(t.start);
+            cudaEventDestroy(t.stop);
+        }
+    for (auto& d : da_ev) {
+        if (d.a) cudaEventDestroy(d.a);
+        if (d.b) cudaEventDestroy(d.b);
     }
     for (auto ev : event_pool) cudaEventDestroy(ev);
     for (auto& m : mlps) m.release();
@@ -528,6 +533,25 @@ int smc_get_timing(smc_handle* hh, double* ms_per_level, long long* launches_per
         if (ms_per_level) ms_per_level[l] = ms[l];
         if (launches_per_level) launches_per_level[l] = cnt[l];
     }
+    return SMC_OK;
+}
+
+int smc_get_phase_timing(smc_handle* hh, double* ms8) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    std::vector<double> ms(8, 0.0);
+    for (auto& t : h->timed_phase) {
+        cudaError_t e = cudaEventSynchronize(t.stop);
+        float v = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&v, t.start, t.stop);
+        if (e != cudaSuccess) return h->cuda_fail(e, "read phase timing");
+        if (t.level >= 0 && t.level < 8) ms[t.level] += v;
+        h->event_pool.push_back(t.start);
+        h->event_pool.push_back(t.stop);
+    }
+    h->timed_phase.clear();
+    if (ms8)
+        for (int i = 0; i < 8; ++i) ms8[i] = ms[i];
     return SMC_OK;
 }
 

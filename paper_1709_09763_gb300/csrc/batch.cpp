@@ -15,49 +15,10 @@
 #include <string>
 #include <vector>
 
+#include "batch.h"
 #include "handle.h"
 
 namespace mls2mc {
-
-struct Batch {
-    std::vector<Handle*> h;
-    struct Group {
-        int N = 0, precision = 0, T = 0, total = 0;
-        std::vector<FemArgs> args;
-        std::vector<int> offsets;
-        FemArgs* d_args = nullptr;
-        int* d_offsets = nullptr;
-        int* d_item_group = nullptr;   // group of each work item
-    };
-    std::vector<Group> groups;
-    int* d_counters = nullptr;
-    float* big_scratch = nullptr;    // per-block slices for the groups of large levels (1/h >= 128)
-    int big_blocks = 0;
-    std::vector<long long> signature;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    long long graph_kernels = 0;
-    std::string last_error;
-
-    void free_groups() {
-        for (auto& g : groups) {
-            cudaFree(g.d_args);
-            cudaFree(g.d_offsets);
-            cudaFree(g.d_item_group);
-        }
-        groups.clear();
-        cudaFree(d_counters);
-        d_counters = nullptr;
-        cudaFree(big_scratch);
-        big_scratch = nullptr;
-        big_blocks = 0;
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
-        exec = nullptr;
-        graph = nullptr;
-    }
-    ~Batch() { free_groups(); }
-};
 
 long long launch_count();
 

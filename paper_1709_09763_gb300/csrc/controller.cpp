@@ -20,39 +20,16 @@
 #include <cmath>
 #include <cstddef>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "handle.h"
+#include "sampler.h"
 #include "smc_device.h"
 
 namespace mls2mc {
-
-struct Sampler {
-    int J = 0, K = 0;
-    double *theta = nullptr, *theta_p = nullptr, *theta_t = nullptr;
-    double *phi_c = nullptr, *phi_f = nullptr, *phi_cp = nullptr, *phi_fp = nullptr;
-    double *phi_t0 = nullptr, *phi_t1 = nullptr;
-    double *a = nullptr, *cdf = nullptr, *scal = nullptr, *mom = nullptr;
-    int *anc = nullptr, *iters = nullptr;
-    unsigned long long* n_acc = nullptr;
-    IncWork inc;
-    // delayed acceptance: surrogate potentials of current particles (s) and proposals (sp),
-    // compacted survivors of stage 1, observations of exact solves (training pairs)
-    double *G_buf = nullptr, *ps_c = nullptr, *ps_f = nullptr, *psp_c = nullptr, *psp_f = nullptr;
-    double *theta_s = nullptr, *phi_cs = nullptr, *phi_fs = nullptr;
-    int *surv_idx = nullptr, *n_surv = nullptr, *da_pass = nullptr;
-    long long pairs_new[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    long long da_proposals = 0, da_pass1 = 0;
-    // host-side state
-    bool started = false;
-    int level = 0;
-    double beta = 0.0, log_z = 0.0;
-    bool prev_lu = true;
-    bool terminated = false;   // scheme u': stopped on a level below the finest
-    long long stage = 0, mcmc_event = 0;
-    long long evals[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    std::vector<smc_stage_info> path;
-};
 
 int Handle::alloc_sampler() {
     const int J = opts.J;
@@ -120,6 +97,28 @@ void Handle::free_sampler() {
         if (_r != SMC_OK) return _r;    \
     } while (0)
 
+// Opt-in phase timing (smc_set_timing): CUDA events on the handle's stream around the parts of an
+// update that are not forward solves (those are timed per level by eval_device); the phases of
+// smc_get_phase_timing.
+enum Phase { kPhTrain = 0, kPhInfer = 1, kPhScreen = 2, kPhReweight = 3, kPhMove = 4, kPhGate = 5 };
+struct PhaseTimer {
+    Handle* h;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseTimer(Handle* h_, int ph) : h(h_), phase(ph) {
+        if (h->timing) {
+            a = h->take_event();
+            cudaEventRecord(a, h->stream);
+        }
+    }
+    ~PhaseTimer() {
+        if (!a) return;
+        cudaEvent_t b = h->take_event();
+        cudaEventRecord(b, h->stream);
+        h->timed_phase.push_back({phase, a, b});
+    }
+};
+
 // exact likelihood of n particles on one level, counted; with the surrogate enabled the
 // observations are kept as training pairs (theta, G_l(theta)) of that level's network
 int Handle::smp_eval(int level, int n, const double* theta, double* phi) {
@@ -127,7 +126,22 @@ int Handle::smp_eval(int level, int n, const double* theta, double* phi) {
     // no pairs for a level whose screening gate has been measured and said no
     const bool collect = opts.surrogate && forward_kind == SMC_FWD_FEM &&
                          !(level < (int)da_gate.size() && da_gate[level] < 0);
+    // the screening gate's solve time: events around the first evaluation of at least half the
+    // particles on a level whose gate is still open
+    const bool gate_open = opts.surrogate == 1 && forward_kind == SMC_FWD_FEM && 2 * n >= smp->J &&
+                           !(level < (int)da_gate.size() && da_gate[level] != 0) &&
+                           !(level < (int)da_ev.size() && da_ev[level].n > 0);
+    if (gate_open) {
+        if ((int)da_ev.size() < (int)levels.size()) da_ev.resize(levels.size());
+        da_ev[level].a = take_event();
+        da_ev[level].b = take_event();
+        cudaEventRecord(da_ev[level].a, stream);
+    }
     RC(eval_device(level, n, theta, collect ? smp->G_buf : nullptr, phi, smp->iters, stream));
+    if (gate_open) {
+        cudaEventRecord(da_ev[level].b, stream);
+        da_ev[level].n = n;
+    }
     smp->evals[level] += n;
     if (collect) {
         RC(mlp_add_pairs(level, n, theta, smp->G_buf));
@@ -170,6 +184,62 @@ int Handle::read_counters(unsigned long long* acc, IncState* pending) {
 // (the screen adds a forward pass, a compaction and a host read per pCN step).
 constexpr double kDaCostRatio = 8.0;
 
+namespace {
+// a surrogate forward pass of J particles has the same shapes on every level (K -> 4 x 256 -> n_obs):
+// its device time is measured once per process for each (K, n_obs, J)
+std::mutex g_pred_mu;
+std::map<std::tuple<int, int, int>, float> g_pred_ms;
+}  // namespace
+
+// device time of an exact solve of J particles on `level`: from the sampler's own first evaluation
+// of (most of) its particles there (events recorded by smp_eval), else measured now
+float Handle::da_solve_ms(int level) {
+    Sampler* S = smp;
+    if (level < (int)da_ev.size() && da_ev[level].n > 0) {
+        float t = 0.f;
+        const DaSolveEvents& d = da_ev[level];
+        if (cudaEventSynchronize(d.b) == cudaSuccess && cudaEventElapsedTime(&t, d.a, d.b) == cudaSuccess)
+            return t * (float)S->J / (float)d.n;
+    }
+    cudaEvent_t a = take_event(), b = take_event();
+    cudaEventRecord(a, stream);
+    const int rc = eval_device(level, S->J, S->theta, nullptr, S->phi_t1, S->iters, stream);
+    cudaEventRecord(b, stream);
+    float t = 0.f;
+    if (rc != SMC_OK || cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess)
+        t = -1.f;
+    event_pool.push_back(a);
+    event_pool.push_back(b);
+    return t;
+}
+
+float Handle::da_predict_ms(int level) {
+    Sampler* S = smp;
+    const auto key = std::make_tuple(K, n_obs, S->J);
+    {
+        std::lock_guard<std::mutex> lock(g_pred_mu);
+        auto it = g_pred_ms.find(key);
+        if (it != g_pred_ms.end()) return it->second;
+    }
+    if (mlp_setup(level) != SMC_OK) return -1.f;
+    // untimed pass first: buffers allocated on first use must not fall inside the measurement
+    if (mlp_predict(level, S->J, S->theta, nullptr, S->phi_t0) != SMC_OK) return -1.f;
+    cudaEvent_t a = take_event(), b = take_event();
+    cudaEventRecord(a, stream);
+    const int rc = mlp_predict(level, S->J, S->theta, nullptr, S->phi_t0);
+    cudaEventRecord(b, stream);
+    float t = 0.f;
+    if (rc != SMC_OK || cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess)
+        t = -1.f;
+    event_pool.push_back(a);
+    event_pool.push_back(b);
+    if (t > 0.f) {
+        std::lock_guard<std::mutex> lock(g_pred_mu);
+        g_pred_ms[key] = t;
+    }
+    return t;
+}
+
 bool Handle::da_worth(int level) {
     if ((int)da_gate.size() < (int)levels.size()) {
         da_gate.assign(levels.size(), 0);
@@ -181,28 +251,12 @@ bool Handle::da_worth(int level) {
         da_gate[level] = 1;
         return true;
     }
-    Sampler* S = smp;
-    if (mlp_setup(level) != SMC_OK) return false;
-    // untimed pass first: buffers allocated on first use must not fall inside the measurement
-    if (mlp_predict(level, S->J, S->theta, nullptr, S->phi_t0) != SMC_OK) return false;
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return false;
-    cudaEvent_t a = take_event(), b = take_event(), c = take_event();
-    cudaEventRecord(a, stream);
-    int rc = mlp_predict(level, S->J, S->theta, nullptr, S->phi_t0);
-    cudaEventRecord(b, stream);
-    if (rc == SMC_OK) rc = eval_device(level, S->J, S->theta, nullptr, S->phi_t1, S->iters, stream);
-    cudaEventRecord(c, stream);
-    float t_pred = 0.f, t_solve = 0.f;
-    if (cudaEventSynchronize(c) == cudaSuccess) {
-        cudaEventElapsedTime(&t_pred, a, b);
-        cudaEventElapsedTime(&t_solve, b, c);
-    }
-    event_pool.push_back(a);
-    event_pool.push_back(b);
-    event_pool.push_back(c);
-    da_t_solve[level] = t_solve;
-    da_t_pred[level] = t_pred;
-    da_gate[level] = (rc == SMC_OK && t_solve > kDaCostRatio * t_pred) ? 1 : -1;
+    PhaseTimer pt(this, kPhGate);
+    const float t_solve = da_solve_ms(level);
+    const float t_pred = t_solve > 0.f ? da_predict_ms(level) : -1.f;
+    da_t_solve[level] = std::max(t_solve, 0.f);
+    da_t_pred[level] = std::max(t_pred, 0.f);
+    da_gate[level] = (t_solve > 0.f && t_pred > 0.f && t_solve > kDaCostRatio * t_pred) ? 1 : -1;
     return da_gate[level] > 0;
 }
 
@@ -219,6 +273,7 @@ int Handle::maybe_train(int level) {
     const int steps = M.t == 0 ? base : std::max(1, base / 4);
     const int batch = std::min(opts.surrogate_batch > 0 ? opts.surrogate_batch : 8192, M.count);
     double loss = 0.0;
+    PhaseTimer pt(this, kPhTrain);
     RC(mlp_train(level, steps, batch, &loss));
     smp->pairs_new[level] = 0;
     return SMC_OK;
@@ -266,6 +321,7 @@ int Handle::increment(const double* a, int n, double dmax, double base, IncState
 // increment, evidence factor (when waited for), resampling and gather
 int Handle::reweight_resample(const double* a, double dmax, double base, bool carry_fine, IncState& st, bool wait) {
     Sampler* S = smp;
+    PhaseTimer pt(this, kPhReweight);
     RC(increment(a, S->J, dmax, base, st, wait));
     if (wait) S->log_z += st.log_mean_w;
     CK(resample_gather_launch(a, S->J, S->inc.state, (uint32_t)S->stage, opts.seed, K, S->theta, S->theta_t,
@@ -296,9 +352,13 @@ int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, Inc
     CK(cudaMemsetAsync(S->n_acc, 0, 8, stream));
     for (int m = 0; m < opts.n_mcmc; ++m) {
         const uint32_t ev = (uint32_t)S->mcmc_event;
-        CK(normals_launch(S->theta_p, S->J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
+        {
+            PhaseTimer pt(this, kPhMove);
+            CK(normals_launch(S->theta_p, S->J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
+        }
         RC(smp_eval(level, S->J, S->theta_p, S->phi_cp));
         if (zeta >= 0.0) RC(smp_eval(level + 1, S->J, S->theta_p, S->phi_fp));
+        PhaseTimer pt(this, kPhMove);
         CK(pcn_accept_launch(S->J, K, S->beta, beta_p, zeta, ev, opts.seed, S->theta, S->theta_p, S->phi_c,
                              S->phi_cp, S->phi_f, S->phi_fp, S->n_acc, rwm ? 1 : 0, stream));
         S->mcmc_event += 1;
@@ -319,24 +379,37 @@ int Handle::mcmc_da(int level, double zeta, double& rate) {
     const bool rwm = opts.proposal == SMC_PROP_RWM;
     const double s = opts.s_pcn, c0 = rwm ? 1.0 : std::sqrt(1.0 - s * s);
     CK(cudaMemsetAsync(S->n_acc, 0, 8, stream));
-    RC(mlp_predict(level, J, S->theta, nullptr, S->ps_c));
-    if (br) RC(mlp_predict(level + 1, J, S->theta, nullptr, S->ps_f));
+    {
+        PhaseTimer pt(this, kPhInfer);
+        RC(mlp_predict(level, J, S->theta, nullptr, S->ps_c));
+        if (br) RC(mlp_predict(level + 1, J, S->theta, nullptr, S->ps_f));
+    }
     long long passed = 0;
     for (int m = 0; m < opts.n_mcmc; ++m) {
         const uint32_t ev = (uint32_t)S->mcmc_event;
-        CK(normals_launch(S->theta_p, J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
-        RC(mlp_predict(level, J, S->theta_p, nullptr, S->psp_c));
-        if (br) RC(mlp_predict(level + 1, J, S->theta_p, nullptr, S->psp_f));
-        CK(da_stage1_launch(J, K, S->beta, zeta, ev, opts.seed, S->ps_c, S->ps_f, S->psp_c, S->psp_f, S->theta,
-                            S->theta_p, rwm ? 1 : 0,
-                            S->da_pass, S->surv_idx, S->n_surv, S->theta_s, stream));
+        {
+            PhaseTimer pt(this, kPhMove);
+            CK(normals_launch(S->theta_p, J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
+        }
+        {
+            PhaseTimer pt(this, kPhInfer);
+            RC(mlp_predict(level, J, S->theta_p, nullptr, S->psp_c));
+            if (br) RC(mlp_predict(level + 1, J, S->theta_p, nullptr, S->psp_f));
+        }
         int ns = 0;
-        CK(cudaMemcpyAsync(&ns, S->n_surv, 4, cudaMemcpyDeviceToHost, stream));
+        {
+            PhaseTimer pt(this, kPhScreen);
+            CK(da_stage1_launch(J, K, S->beta, zeta, ev, opts.seed, S->ps_c, S->ps_f, S->psp_c, S->psp_f, S->theta,
+                                S->theta_p, rwm ? 1 : 0,
+                                S->da_pass, S->surv_idx, S->n_surv, S->theta_s, stream));
+            CK(cudaMemcpyAsync(&ns, S->n_surv, 4, cudaMemcpyDeviceToHost, stream));
+        }
         CK(cudaStreamSynchronize(stream));
         passed += ns;
         if (ns > 0) {
             RC(smp_eval(level, ns, S->theta_s, S->phi_cs));
             if (br) RC(smp_eval(level + 1, ns, S->theta_s, S->phi_fs));
+            PhaseTimer pt(this, kPhMove);
             CK(da_stage2_launch(ns, K, S->beta, zeta, ev, opts.seed, S->surv_idx, S->theta_s, S->phi_cs, S->phi_fs,
                                 S->theta, S->phi_c, S->phi_f, S->ps_c, S->ps_f, S->psp_c, S->psp_f, S->n_acc,
                                 stream));
@@ -404,6 +477,49 @@ int Handle::tempering_update(int level, double beta0, int n_mcmc, smc_stage_info
         info->cv_lu = -1.0;
         info->log_z_inc = st.log_mean_w;
         info->accept_rate = rate;
+        for (int l = 0; l < 8; ++l) info->evals_per_level[l] = S->evals[l];
+    }
+    S->stage += 1;
+    return SMC_OK;
+}
+
+// One bridging step between `level` and level + 1 at inverse temperature beta, from bridging
+// temperature zeta0 (Sec. 4.1): Phi_level and Phi_level+1 of every particle, the adaptive increment of
+// zeta for the weights exp(-beta dzeta (Phi_level+1 - Phi_level)) (Eq. Eq_cv_opt), resampling with both
+// potentials carried, and n_mcmc Markov steps for exp(-beta ((1 - zeta) Phi_level + zeta Phi_level+1))
+// mu0, each proposal solved on both levels. Like tempering_update it leaves the update scheme's
+// state (level, beta, evidence) unchanged.
+int Handle::bridging_update(int level, double beta, double zeta0, int n_mcmc, smc_stage_info* info) {
+    Sampler* S = smp;
+    RC(smp_eval(level, S->J, S->theta, S->phi_c));
+    RC(smp_eval(level + 1, S->J, S->theta, S->phi_f));
+    CK(lu_increment_launch(S->phi_c, S->phi_f, S->J, beta, S->a, stream));
+    IncState st;
+    const double log_z = S->log_z, beta_s = S->beta;
+    const int nm = opts.n_mcmc;
+    S->beta = beta;
+    int rc = reweight_resample(S->a, 1.0 - zeta0, zeta0, true, st, true);
+    double rate = 0.0;
+    if (rc == SMC_OK) {
+        opts.n_mcmc = n_mcmc;
+        rc = mcmc(level, st.next, rate);
+        opts.n_mcmc = nm;
+    }
+    S->beta = beta_s;
+    S->log_z = log_z;
+    if (rc != SMC_OK) return rc;
+    if (info) {
+        std::memset(info, 0, sizeof *info);
+        info->type = 1;
+        info->level = level + 1;
+        info->beta = beta;
+        info->zeta = st.next;
+        info->delta = st.delta;
+        info->cv = st.cv;
+        info->cv_lu = -1.0;
+        info->log_z_inc = st.log_mean_w;
+        info->accept_rate = rate;
+        info->n_bridge = 1;
         for (int l = 0; l < 8; ++l) info->evals_per_level[l] = S->evals[l];
     }
     S->stage += 1;
@@ -623,6 +739,21 @@ int smc_tempering_update(smc_handle* hh, int level, double beta0, int n_mcmc, sm
         if (rc != SMC_OK) return rc;
     }
     return h->tempering_update(level, beta0, n_mcmc, info);
+}
+
+int smc_bridging_update(smc_handle* hh, int level, double beta, double zeta0, int n_mcmc, smc_stage_info* info) {
+    if (!hh) return SMC_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->smp) return h->fail(SMC_EINVAL, "handle was created with J = 0");
+    if (level < 0 || level + 1 >= (int)h->levels.size())
+        return h->fail(SMC_EINVAL, "level %d has no finer level", level);
+    if (!(beta > 0.0 && beta <= 1.0) || !(zeta0 >= 0.0 && zeta0 < 1.0) || n_mcmc < 0)
+        return h->fail(SMC_EINVAL, "need 0 < beta <= 1, 0 <= zeta0 < 1, n_mcmc >= 0");
+    if (!h->smp->started) {
+        int rc = h->sampler_start();
+        if (rc != SMC_OK) return rc;
+    }
+    return h->bridging_update(level, beta, zeta0, n_mcmc, info);
 }
 
 // ---- kernel-level entry points -----------------------------------------------------------------

@@ -72,6 +72,7 @@ struct Handle {
         cudaEvent_t start, stop;
     };
     std::vector<TimedLaunch> timed;
+    std::vector<TimedLaunch> timed_phase;   // level = phase of smc_get_phase_timing
     std::vector<cudaEvent_t> event_pool;
     cudaEvent_t take_event();
 
@@ -114,10 +115,18 @@ struct Handle {
     bool da_worth(int level);
     std::vector<int> da_gate;   // per level: 0 unknown, 1 screen pays, -1 it does not
     std::vector<float> da_t_solve, da_t_pred;   // per level: the gate's measured device times (ms)
+    struct DaSolveEvents {
+        cudaEvent_t a = nullptr, b = nullptr;
+        int n = 0;   // particles the recorded evaluation solved (0: none recorded)
+    };
+    std::vector<DaSolveEvents> da_ev;   // per level: the sampler's first large evaluation, timed for the gate
+    float da_solve_ms(int level);
+    float da_predict_ms(int level);
     double last_da_rate = -1.0;
     void record(int type, double zeta, const struct IncState& st, double rate, double cv_lu, smc_stage_info* info);
     int itu(double cv_lu, smc_stage_info* info);
     int tempering_update(int level, double beta0, int n_mcmc, smc_stage_info* info);
+    int bridging_update(int level, double beta, double zeta0, int n_mcmc, smc_stage_info* info);
     int lu(int head, smc_stage_info* info);
     int sampler_start();
     int sampler_restart();

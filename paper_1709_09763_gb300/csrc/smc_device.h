@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <utility>
+#include <vector>
 
 namespace mls2mc {
 
@@ -78,6 +80,95 @@ cudaError_t da_stage2_launch(int ns, int K, double beta, double zeta, uint32_t e
                              double* phi_c, double* phi_f, double* ps_c, double* ps_f, const double* psp_c,
                              const double* psp_f, unsigned long long* n_acc, cudaStream_t st);
 cudaError_t count_bad_launch(const int* iters, int n, unsigned* bad, cudaStream_t st);
+
+// ---- many problems in one launch (the batched sampler) ------------------------------------------
+// Task tables travel as kernel parameters (__grid_constant__, at most kMaxTasks problems per launch;
+// the launchers split longer lists). Each problem gets the block count its single-problem launch
+// would use and its own barrier counter and scratch, so its results equal that launch's bit for bit.
+constexpr int kMaxTasks = 64;
+
+struct IncTask {
+    const double* a;
+    int n, max_iter;
+    double dmax, tau, eps, base, top;
+    IncWork w;
+};
+struct RsTask {
+    const double* a;
+    int n, K;
+    const IncState* state;
+    uint32_t event, pad;
+    uint64_t seed;
+    const double *th_in, *p0_in, *p1_in;
+    double *th_out, *p0_out, *p1_out, *cdf, *btot;
+    int* anc;
+    unsigned* bar;
+    int* err;
+};
+struct NormTask {
+    double* out;
+    const double* base;
+    uint64_t seed;
+    int J, K;
+    uint32_t event, purpose;
+    double c0, c1;
+};
+struct AccTask {
+    int n, K, rwm;
+    uint32_t event;
+    uint64_t seed;
+    double beta, zeta;
+    const double *beta_p, *zeta_p;   // read on the device instead, where given
+    double *theta, *phi_c, *phi_f;
+    const double *theta_p, *phi_cp, *phi_fp;
+    unsigned long long* n_acc;
+};
+struct LuTask {
+    const double *phi_c, *phi_f;
+    double* a;
+    int n;
+    double beta;
+};
+struct CvTask {
+    const double *phi_c, *phi_f;
+    double* out;
+    int n;
+    double beta;
+};
+struct BadTask {
+    const int* iters;
+    unsigned* bad;
+    int n;
+};
+template <typename Task>
+struct TaskList {
+    Task t[kMaxTasks];
+    int start[kMaxTasks + 1];   // first block of each task; start[count] = the grid
+    int count;
+};
+using IncTasks = TaskList<IncTask>;
+using RsTasks = TaskList<RsTask>;
+using NormTasks = TaskList<NormTask>;
+using AccTasks = TaskList<AccTask>;
+using LuTasks = TaskList<LuTask>;
+using CvTasks = TaskList<CvTask>;
+using BadTasks = TaskList<BadTask>;
+struct ZeroList {
+    unsigned* ptr[2 * kMaxTasks];
+    int words[2 * kMaxTasks];
+    int count;
+};
+
+int rs_blocks(int n);   // blocks of one problem's resampling launch
+cudaError_t inc_search_multi_launch(const std::vector<IncTask>& tasks, cudaStream_t st);
+cudaError_t resample_gather_multi_launch(const std::vector<RsTask>& tasks, cudaStream_t st);
+cudaError_t normals_multi_launch(const std::vector<NormTask>& tasks, cudaStream_t st);
+cudaError_t pcn_accept_multi_launch(const std::vector<AccTask>& tasks, cudaStream_t st);
+cudaError_t lu_increment_multi_launch(const std::vector<LuTask>& tasks, cudaStream_t st);
+cudaError_t cv_lu_multi_launch(const std::vector<CvTask>& tasks, cudaStream_t st);
+cudaError_t count_bad_multi_launch(const std::vector<BadTask>& tasks, cudaStream_t st);
+// words (unsigned) to zero: (pointer, count) pairs
+cudaError_t zero_words_launch(const std::vector<std::pair<unsigned*, int>>& list, cudaStream_t st);
 cudaError_t moments_launch(const double* theta, int n, int K, double* mean, double* var, cudaStream_t st);
 
 }  // namespace mls2mc

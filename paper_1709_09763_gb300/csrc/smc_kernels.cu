@@ -76,6 +76,21 @@ __device__ __forceinline__ void normal_pair(uint32_t b, uint32_t j, uint32_t eve
     z1 = r * sin(ang);
 }
 
+// the task (problem) of this block in a multi-problem launch: start[p] <= blockIdx.x < start[p + 1]
+__device__ __forceinline__ int task_of_block(const int* start, int count) {
+    __shared__ int p_s;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (start[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        p_s = lo;
+    }
+    __syncthreads();
+    return p_s;
+}
+
 __global__ void normals_kernel(double* out, int J, int K, uint32_t event, uint32_t purpose, uint64_t seed,
                                const double* base, double c0, double c1) {
     // out[j][k] = c0 * base[j][k] + c1 * xi[j][k]  (base == null: out = xi)
@@ -92,6 +107,26 @@ __global__ void normals_kernel(double* out, int J, int K, uint32_t event, uint32
     } else {
         out[o] = z0;
         if (2 * b + 1 < K) out[o + 1] = z1;
+    }
+}
+
+// many problems' proposals or draws (256-thread blocks, a contiguous block range per problem)
+__global__ void normals_multi_kernel(const __grid_constant__ NormTasks T) {
+    const int p = task_of_block(T.start, T.count);
+    const NormTask& k = T.t[p];
+    const int nb = (k.K + 1) / 2;
+    const long long t = (long long)(blockIdx.x - (unsigned)T.start[p]) * blockDim.x + threadIdx.x;
+    if (t >= (long long)k.J * nb) return;
+    const int j = (int)(t / nb), b = (int)(t - (long long)j * nb);
+    double z0, z1;
+    normal_pair((uint32_t)b, (uint32_t)j, k.event, k.purpose, k.seed, z0, z1);
+    const size_t o = (size_t)j * k.K + 2 * b;
+    if (k.base) {
+        k.out[o] = __dadd_rn(__dmul_rn(k.c0, k.base[o]), __dmul_rn(k.c1, z0));
+        if (2 * b + 1 < k.K) k.out[o + 1] = __dadd_rn(__dmul_rn(k.c0, k.base[o + 1]), __dmul_rn(k.c1, z1));
+    } else {
+        k.out[o] = z0;
+        if (2 * b + 1 < k.K) k.out[o + 1] = z1;
     }
 }
 
@@ -291,24 +326,26 @@ __device__ __forceinline__ void inc_block_sum(double (&v)[kIncSums], double* sh 
     }
 }
 
-__global__ void __launch_bounds__(kIncThreads) inc_search_kernel(const double* a, int n, double dmax, double tau,
-                                                                 double eps, int max_iter, double base, double top,
-                                                                 IncWork w) {
+// The search of one problem by the blocks bid = 0 .. nb - 1 that a launch gives it (the whole grid
+// of a single-problem launch, or a contiguous range of a multi-problem launch); the result depends
+// on n and nb only, not on the rest of the grid.
+__device__ __forceinline__ void inc_search_blocks(const double* a, int n, double dmax, double tau, double eps,
+                                                  int max_iter, double base, double top, const IncWork& w,
+                                                  const unsigned bid, const unsigned nb) {
     __shared__ double sh[kIncSums * 32];
     __shared__ IncState st;
     __shared__ int ok_s;
-    const unsigned nb = gridDim.x;
     const int lane = threadIdx.x & 31;
     unsigned generation = 0;
     // minimum of the potentials (the weights are formed relative to it)
     double m = INFINITY;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) m = fmin(m, a[j]);
+    for (int j = bid * blockDim.x + threadIdx.x; j < n; j += nb * blockDim.x) m = fmin(m, a[j]);
     for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
     if (lane == 0) sh[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int k = 1; k < kIncThreads / 32; ++k) m = fmin(m, sh[k]);
-        w.partials[blockIdx.x] = m;
+        w.partials[bid] = m;
         ok_s = grid_barrier(w.bar, w.err, nb, generation);
     }
     __syncthreads();
@@ -326,7 +363,7 @@ __global__ void __launch_bounds__(kIncThreads) inc_search_kernel(const double* a
         double v[kIncSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (st.phase == 0) {   // both ends of the interval
             const double xh = st.dmax, xl = st.dmin;
-            for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+            for (int j = bid * blockDim.x + threadIdx.x; j < n; j += nb * blockDim.x) {
                 const double at = a[j] - amin;
                 const double wh = exp(-xh * at), wl = exp(-xl * at);
                 v[0] += wh;
@@ -338,7 +375,7 @@ __global__ void __launch_bounds__(kIncThreads) inc_search_kernel(const double* a
             }
         } else {
             const double x = st.x;
-            for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+            for (int j = bid * blockDim.x + threadIdx.x; j < n; j += nb * blockDim.x) {
                 const double at = a[j] - amin;
                 const double wj = exp(-x * at);
                 const double w2 = wj * wj;
@@ -353,7 +390,7 @@ __global__ void __launch_bounds__(kIncThreads) inc_search_kernel(const double* a
         inc_block_sum(v, sh);
         if (threadIdx.x == 0) {
 #pragma unroll
-            for (int i = 0; i < kIncSums; ++i) part[blockIdx.x * kIncSums + i] = v[i];
+            for (int i = 0; i < kIncSums; ++i) part[bid * kIncSums + i] = v[i];
             ok_s = grid_barrier(w.bar, w.err, nb, generation);
         }
         __syncthreads();
@@ -370,8 +407,25 @@ __global__ void __launch_bounds__(kIncThreads) inc_search_kernel(const double* a
         }
         __syncthreads();
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *w.state = st;
+    if (bid == 0 && threadIdx.x == 0) *w.state = st;
 }
+
+__global__ void __launch_bounds__(kIncThreads) inc_search_kernel(const double* a, int n, double dmax, double tau,
+                                                                 double eps, int max_iter, double base, double top,
+                                                                 IncWork w) {
+    inc_search_blocks(a, n, dmax, tau, eps, max_iter, base, top, w, blockIdx.x, gridDim.x);
+}
+
+// many problems' searches in one cooperative launch: problem p takes inc_blocks(n_p) blocks and
+// its own barrier counter, so every problem's result is the single-problem launch's, bit for bit
+__global__ void __launch_bounds__(kIncThreads) inc_search_multi_kernel(const __grid_constant__ IncTasks T) {
+    const int p = task_of_block(T.start, T.count);
+    const IncTask& k = T.t[p];
+    inc_search_blocks(k.a, k.n, k.dmax, k.tau, k.eps, k.max_iter, k.base, k.top, k.w,
+                      blockIdx.x - (unsigned)T.start[p], (unsigned)(T.start[p + 1] - T.start[p]));
+}
+
+
 
 // ---- systematic resampling with the gather, one cooperative launch ------------------------------
 // The weights w_j = exp(-delta (a_j - amin)) of the increment just found, their normalised inclusive
@@ -381,18 +435,18 @@ __global__ void __launch_bounds__(kIncThreads) inc_search_kernel(const double* a
 // fixed order by every block). Deterministic for given n and grid.
 constexpr int kRsThreads = 128;
 
-__global__ void __launch_bounds__(kRsThreads) resample_gather_kernel(
+// the resampling of one problem by the blocks bid = 0 .. nb - 1 that a launch gives it
+__device__ __forceinline__ void resample_gather_blocks(
     const double* a, int n, const IncState* state, uint32_t event, uint64_t seed, int K, const double* th_in,
     double* th_out, const double* p0_in, double* p0_out, const double* p1_in, double* p1_out, double* cdf, int* anc,
-    double* btot, unsigned* bar, int* err) {
+    double* btot, unsigned* bar, int* err, const unsigned bid, const unsigned nb) {
     __shared__ double warp_tot[kRsThreads / 32];
     __shared__ double run_s, off_s, inv_s;
     __shared__ int ok_s;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const unsigned nb = gridDim.x;
     unsigned generation = 0;
     const int chunk = (n + (int)nb - 1) / (int)nb;
-    const int j0 = min(n, (int)blockIdx.x * chunk), j1 = min(n, j0 + chunk);
+    const int j0 = min(n, (int)bid * chunk), j1 = min(n, j0 + chunk);
     const double delta = state->delta, amin = state->amin;
     if (tid == 0) run_s = 0.0;
     __syncthreads();
@@ -414,7 +468,7 @@ __global__ void __launch_bounds__(kRsThreads) resample_gather_kernel(
         __syncthreads();
     }
     if (tid == 0) {
-        btot[blockIdx.x] = run_s;
+        btot[bid] = run_s;
         ok_s = grid_barrier(bar, err, nb, generation);
     }
     __syncthreads();
@@ -424,7 +478,7 @@ __global__ void __launch_bounds__(kRsThreads) resample_gather_kernel(
         for (unsigned k = lane; k < nb; k += 32) {
             const double v = __ldcg(&btot[k]);
             tot += v;
-            if (k < blockIdx.x) off += v;
+            if (k < bid) off += v;
         }
         for (int o = 16; o > 0; o >>= 1) {
             off += __shfl_xor_sync(0xffffffffu, off, o);
@@ -442,7 +496,7 @@ __global__ void __launch_bounds__(kRsThreads) resample_gather_kernel(
     if (!ok_s) return;
     const uint4 x = philox(make_uint4(0u, 0u, event, (uint32_t)kPurposeResample), seed);
     const double U = u53(x.x, x.y);
-    for (int i = blockIdx.x * kRsThreads + tid; i < n; i += nb * kRsThreads) {
+    for (int i = bid * kRsThreads + tid; i < n; i += nb * kRsThreads) {
         const double pos = (U + (double)i) / (double)n;
         int lo = 0, hi = n - 1;   // cdf[n-1] = 1 > pos always
         while (lo < hi) {
@@ -456,7 +510,7 @@ __global__ void __launch_bounds__(kRsThreads) resample_gather_kernel(
     if (!ok_s) return;
     // gather: one warp per particle row (coalesced over k), rows spread over every warp of the grid
     const int n_warps = (int)nb * (kRsThreads / 32);
-    for (int i = (int)blockIdx.x * (kRsThreads / 32) + wid; i < n; i += n_warps) {
+    for (int i = (int)bid * (kRsThreads / 32) + wid; i < n; i += n_warps) {
         const int src = __ldcg(&anc[i]);
         for (int k = lane; k < K; k += 32) th_out[(size_t)i * K + k] = th_in[(size_t)src * K + k];
         if (lane == 0) {
@@ -464,6 +518,24 @@ __global__ void __launch_bounds__(kRsThreads) resample_gather_kernel(
             if (p1_in) p1_out[i] = p1_in[src];
         }
     }
+}
+
+__global__ void __launch_bounds__(kRsThreads) resample_gather_kernel(
+    const double* a, int n, const IncState* state, uint32_t event, uint64_t seed, int K, const double* th_in,
+    double* th_out, const double* p0_in, double* p0_out, const double* p1_in, double* p1_out, double* cdf, int* anc,
+    double* btot, unsigned* bar, int* err) {
+    resample_gather_blocks(a, n, state, event, seed, K, th_in, th_out, p0_in, p0_out, p1_in, p1_out, cdf, anc, btot,
+                           bar, err, blockIdx.x, gridDim.x);
+}
+
+// many problems' resamplings in one cooperative launch (rs_blocks(n_p) blocks and a barrier counter
+// per problem: each result is the single-problem launch's, bit for bit)
+__global__ void __launch_bounds__(kRsThreads) resample_gather_multi_kernel(const __grid_constant__ RsTasks T) {
+    const int p = task_of_block(T.start, T.count);
+    const RsTask& k = T.t[p];
+    resample_gather_blocks(k.a, k.n, k.state, k.event, k.seed, k.K, k.th_in, k.th_out, k.p0_in, k.p0_out, k.p1_in,
+                           k.p1_out, k.cdf, k.anc, k.btot, k.bar, k.err, blockIdx.x - (unsigned)T.start[p],
+                           (unsigned)(T.start[p + 1] - T.start[p]));
 }
 
 // ---- systematic resampling -----------------------------------------------------------------
@@ -535,8 +607,15 @@ __global__ void lu_increment_kernel(const double* phi_c, const double* phi_f, in
     if (j < n) a[j] = beta * (phi_f[j] - phi_c[j]);
 }
 
+__global__ void lu_increment_multi_kernel(const __grid_constant__ LuTasks T) {
+    const int p = task_of_block(T.start, T.count);
+    const LuTask& k = T.t[p];
+    const int j = (int)(blockIdx.x - (unsigned)T.start[p]) * blockDim.x + threadIdx.x;
+    if (j < k.n) k.a[j] = k.beta * (k.phi_f[j] - k.phi_c[j]);
+}
+
 // cv of exp(-beta (d_j - min d)), d_j = phi_f[j] - phi_c[j], j < n (one block)
-__global__ void cv_lu_kernel(const double* phi_c, const double* phi_f, int n, double beta, double* out) {
+__device__ __forceinline__ void cv_lu_block(const double* phi_c, const double* phi_f, int n, double beta, double* out) {
     __shared__ double sh[2 * 32];
     __shared__ double smin[32];
     double m = INFINITY;
@@ -559,6 +638,16 @@ __global__ void cv_lu_kernel(const double* phi_c, const double* phi_f, int n, do
     }
 }
 
+__global__ void cv_lu_kernel(const double* phi_c, const double* phi_f, int n, double beta, double* out) {
+    cv_lu_block(phi_c, phi_f, n, beta, out);
+}
+
+// one block per problem, each the single-problem kernel's arithmetic
+__global__ void cv_lu_multi_kernel(const __grid_constant__ CvTasks T) {
+    const CvTask& k = T.t[blockIdx.x];
+    cv_lu_block(k.phi_c, k.phi_f, k.n, k.beta, k.out);
+}
+
 // ---- pCN acceptance ---------------------------------------------------------------------------
 // target potential beta * ((1 - zeta) Phi_c + zeta Phi_f) (zeta < 0: beta * Phi_c), with explicit
 // rounding so the comparison with log U is evaluated exactly as written
@@ -567,12 +656,10 @@ __device__ __forceinline__ double target_potential(double beta, double zeta, dou
     return __dmul_rn(beta, __dadd_rn(__dmul_rn(1.0 - zeta, pc), __dmul_rn(zeta, pf)));
 }
 
-__global__ void pcn_accept_kernel(int n, int K, double beta, const double* beta_p, double zeta, uint32_t event,
-                                  uint64_t seed, double* theta, const double* theta_p, double* phi_c,
-                                  const double* phi_cp, double* phi_f, const double* phi_fp,
-                                  unsigned long long* n_acc, int rwm) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (beta_p) beta = *beta_p;
+// the Metropolis decision of particle j (j >= n: none); true if the proposal was taken
+__device__ __forceinline__ bool pcn_accept_one(int j, int n, int K, double beta, double zeta, uint32_t event,
+                                               uint64_t seed, double* theta, const double* theta_p, double* phi_c,
+                                               const double* phi_cp, double* phi_f, const double* phi_fp, int rwm) {
     bool ok = false;
     if (j < n) {
         const uint4 x = philox(make_uint4(0u, (uint32_t)j, event, (uint32_t)kPurposePcnU), seed);
@@ -596,8 +683,32 @@ __global__ void pcn_accept_kernel(int n, int K, double beta, const double* beta_
             if (zeta >= 0.0) phi_f[j] = phi_fp[j];
         }
     }
+    return ok;
+}
+
+__global__ void pcn_accept_kernel(int n, int K, double beta, const double* beta_p, double zeta, uint32_t event,
+                                  uint64_t seed, double* theta, const double* theta_p, double* phi_c,
+                                  const double* phi_cp, double* phi_f, const double* phi_fp,
+                                  unsigned long long* n_acc, int rwm) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (beta_p) beta = *beta_p;
+    const bool ok = pcn_accept_one(j, n, K, beta, zeta, event, seed, theta, theta_p, phi_c, phi_cp, phi_f, phi_fp, rwm);
     const unsigned ballot = __ballot_sync(0xffffffffu, ok);
     if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(n_acc, (unsigned long long)__popc(ballot));
+}
+
+// many problems' acceptances (64-thread blocks, a contiguous block range per problem); beta and
+// zeta read from the device where a pointer is given (the value an increment search left there)
+__global__ void pcn_accept_multi_kernel(const __grid_constant__ AccTasks T) {
+    const int p = task_of_block(T.start, T.count);
+    const AccTask& k = T.t[p];
+    const int j = (int)(blockIdx.x - (unsigned)T.start[p]) * blockDim.x + threadIdx.x;
+    const double beta = k.beta_p ? *k.beta_p : k.beta;
+    const double zeta = k.zeta_p ? *k.zeta_p : k.zeta;
+    const bool ok = pcn_accept_one(j, k.n, k.K, beta, zeta, k.event, k.seed, k.theta, k.theta_p, k.phi_c, k.phi_cp,
+                                   k.phi_f, k.phi_fp, k.rwm);
+    const unsigned ballot = __ballot_sync(0xffffffffu, ok);
+    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(k.n_acc, (unsigned long long)__popc(ballot));
 }
 
 // ---- delayed acceptance (Christen & Fox 2005) ----------------------------------------------------
@@ -710,6 +821,21 @@ __global__ void count_bad_kernel(const int* iters, int n, unsigned* bad) {
     const bool b = i < n && iters[i] < 0;
     const unsigned ballot = __ballot_sync(0xffffffffu, b);
     if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(bad, (unsigned)__popc(ballot));
+}
+
+__global__ void count_bad_multi_kernel(const __grid_constant__ BadTasks T) {
+    const int p = task_of_block(T.start, T.count);
+    const BadTask& k = T.t[p];
+    const int i = (int)(blockIdx.x - (unsigned)T.start[p]) * blockDim.x + threadIdx.x;
+    const bool b = i < k.n && k.iters[i] < 0;
+    const unsigned ballot = __ballot_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(k.bad, (unsigned)__popc(ballot));
+}
+
+// zero words[i] words at ptr[i] (barrier counters, error flags, accept counters of many problems)
+__global__ void zero_words_kernel(const __grid_constant__ ZeroList Z) {
+    for (int i = threadIdx.x; i < Z.count; i += blockDim.x)
+        for (int w = 0; w < Z.words[i]; ++w) Z.ptr[i][w] = 0u;
 }
 
 // ---- posterior moments over equally weighted particles ----------------------------------------
@@ -860,6 +986,147 @@ cudaError_t count_bad_launch(const int* iters, int n, unsigned* bad, cudaStream_
     count_bad_kernel<<<grid_for(n, 256), 256, 0, st>>>(iters, n, bad);
     count_launches(1);
     return cudaGetLastError();
+}
+
+// ---- multi-problem launchers -------------------------------------------------------------------
+int rs_blocks(int n) { return std::min(kIncMaxBlocks, std::max(1, (n + 31) / 32)); }
+
+namespace {
+
+// co-resident blocks of a cooperative kernel on this device
+int coop_capacity(const void* kern, int threads) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    return std::max(1, sms * per_sm);
+}
+
+// split tasks into launches of at most kMaxTasks tasks and `cap` blocks (blocks_of(task) each) and
+// call launch(list) for each
+template <typename Task, typename BlocksOf, typename Launch>
+cudaError_t for_task_lists(const std::vector<Task>& tasks, int cap, BlocksOf blocks_of, Launch launch) {
+    size_t i = 0;
+    while (i < tasks.size()) {
+        TaskList<Task> L;
+        L.count = 0;
+        int blocks = 0;
+        while (i < tasks.size() && L.count < kMaxTasks) {
+            const int b = blocks_of(tasks[i]);
+            if (L.count > 0 && blocks + b > cap) break;
+            L.t[L.count] = tasks[i];
+            L.start[L.count] = blocks;
+            blocks += b;
+            ++L.count;
+            ++i;
+        }
+        L.start[L.count] = blocks;
+        if (blocks > 0) {
+            cudaError_t e = launch(L, blocks);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t zero_bars(const IncTasks& L, cudaStream_t st) {
+    std::vector<std::pair<unsigned*, int>> z;
+    for (int i = 0; i < L.count; ++i) z.push_back({L.t[i].w.bar, 2});
+    return zero_words_launch(z, st);
+}
+
+}  // namespace
+
+cudaError_t zero_words_launch(const std::vector<std::pair<unsigned*, int>>& list, cudaStream_t st) {
+    for (size_t i = 0; i < list.size(); i += 2 * kMaxTasks) {
+        ZeroList Z;
+        Z.count = 0;
+        for (size_t k = i; k < list.size() && Z.count < 2 * kMaxTasks; ++k) {
+            Z.ptr[Z.count] = list[k].first;
+            Z.words[Z.count] = list[k].second;
+            ++Z.count;
+        }
+        zero_words_kernel<<<1, 128, 0, st>>>(Z);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t inc_search_multi_launch(const std::vector<IncTask>& tasks, cudaStream_t st) {
+    static int cap = 0;
+    if (!cap) cap = coop_capacity((const void*)inc_search_multi_kernel, kIncThreads);
+    return for_task_lists(tasks, cap, [](const IncTask& t) { return inc_blocks(t.n); },
+                          [&](const IncTasks& L, int blocks) {
+                              cudaError_t e = zero_bars(L, st);
+                              if (e != cudaSuccess) return e;
+                              void* args[] = {(void*)&L};
+                              e = cudaLaunchCooperativeKernel((const void*)inc_search_multi_kernel, dim3(blocks),
+                                                              dim3(kIncThreads), args, 0, st);
+                              count_launches(1);
+                              return e;
+                          });
+}
+
+cudaError_t resample_gather_multi_launch(const std::vector<RsTask>& tasks, cudaStream_t st) {
+    static int cap = 0;
+    if (!cap) cap = coop_capacity((const void*)resample_gather_multi_kernel, kRsThreads);
+    return for_task_lists(tasks, cap, [](const RsTask& t) { return rs_blocks(t.n); },
+                          [&](const RsTasks& L, int blocks) {
+                              std::vector<std::pair<unsigned*, int>> z;
+                              for (int i = 0; i < L.count; ++i) z.push_back({L.t[i].bar, 2});
+                              cudaError_t e = zero_words_launch(z, st);
+                              if (e != cudaSuccess) return e;
+                              void* args[] = {(void*)&L};
+                              e = cudaLaunchCooperativeKernel((const void*)resample_gather_multi_kernel, dim3(blocks),
+                                                              dim3(kRsThreads), args, 0, st);
+                              count_launches(1);
+                              return e;
+                          });
+}
+
+cudaError_t normals_multi_launch(const std::vector<NormTask>& tasks, cudaStream_t st) {
+    return for_task_lists(tasks, 1 << 30, [](const NormTask& t) { return grid_for((long long)t.J * ((t.K + 1) / 2), 256); },
+                          [&](const NormTasks& L, int blocks) {
+                              normals_multi_kernel<<<blocks, 256, 0, st>>>(L);
+                              count_launches(1);
+                              return cudaGetLastError();
+                          });
+}
+
+cudaError_t pcn_accept_multi_launch(const std::vector<AccTask>& tasks, cudaStream_t st) {
+    return for_task_lists(tasks, 1 << 30, [](const AccTask& t) { return grid_for(t.n, 64); },
+                          [&](const AccTasks& L, int blocks) {
+                              pcn_accept_multi_kernel<<<blocks, 64, 0, st>>>(L);
+                              count_launches(1);
+                              return cudaGetLastError();
+                          });
+}
+
+cudaError_t lu_increment_multi_launch(const std::vector<LuTask>& tasks, cudaStream_t st) {
+    return for_task_lists(tasks, 1 << 30, [](const LuTask& t) { return grid_for(t.n, 256); },
+                          [&](const LuTasks& L, int blocks) {
+                              lu_increment_multi_kernel<<<blocks, 256, 0, st>>>(L);
+                              count_launches(1);
+                              return cudaGetLastError();
+                          });
+}
+
+cudaError_t cv_lu_multi_launch(const std::vector<CvTask>& tasks, cudaStream_t st) {
+    return for_task_lists(tasks, 1 << 30, [](const CvTask&) { return 1; },
+                          [&](const CvTasks& L, int blocks) {
+                              cv_lu_multi_kernel<<<blocks, 256, 0, st>>>(L);
+                              count_launches(1);
+                              return cudaGetLastError();
+                          });
+}
+
+cudaError_t count_bad_multi_launch(const std::vector<BadTask>& tasks, cudaStream_t st) {
+    return for_task_lists(tasks, 1 << 30, [](const BadTask& t) { return grid_for(t.n, 256); },
+                          [&](const BadTasks& L, int blocks) {
+                              count_bad_multi_kernel<<<blocks, 256, 0, st>>>(L);
+                              count_launches(1);
+                              return cudaGetLastError();
+                          });
 }
 
 cudaError_t moments_launch(const double* theta, int n, int K, double* mean, double* var, cudaStream_t st) {

@@ -104,8 +104,11 @@ SIGNATURES = {
     "smc_set_block_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "smc_block_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip]),
     "smc_get_timing": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "smc_get_phase_timing": (ctypes.c_int, [ctypes.c_void_p, _dp]),
     "smc_tempering_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(StageInfo)]),
+    "smc_bridging_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int, ctypes.POINTER(StageInfo)]),
     "smc_next_increment": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_double, _dp]),
     "smc_systematic_resample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_double, _ip]),
     "smc_philox_normals": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint,
@@ -126,6 +129,11 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.c_void_p, ctypes.c_int]),
     "smc_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "smc_init_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ProblemDesc), ctypes.POINTER(SamplerOpts),
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "smc_batch_handle": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int]),
+    "smc_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(StageInfo)]),
+    "smc_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip]),
     "smc_batch_destroy": (None, [ctypes.c_void_p]),
     "smc_gemm_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p]),
@@ -210,6 +218,24 @@ class Batch:
         if rc != SMC_OK:
             raise SmcError(rc, self._lib.smc_batch_last_error(self._b).decode())
 
+    # ---- the batched sampler (every problem's next update in shared launches) ---------------
+    def _check(self, rc, what):
+        if rc != SMC_OK:
+            raise SmcError(rc, f"{what}: {self._lib.smc_batch_last_error(self._b).decode()}")
+
+    def step(self):
+        """One importance-sampling update of every unfinished problem; returns their records."""
+        P = len(self.handles)
+        infos = (StageInfo * P)()
+        self._check(self._lib.smc_batch_step(self._b, infos), "smc_batch_step")
+        return [i.as_dict() for i in infos]
+
+    def run(self, max_steps=0):
+        """Steps until every problem is finished; returns the number of batched steps."""
+        n = ctypes.c_int()
+        self._check(self._lib.smc_batch_run(self._b, int(max_steps), ctypes.byref(n)), "smc_batch_run")
+        return n.value
+
     def close(self):
         if getattr(self, "_b", None) is not None and self._b.value:
             self._lib.smc_batch_destroy(self._b)
@@ -222,6 +248,29 @@ class Batch:
             pass
 
 
+def init_batch(problems):
+    """smc_init_batch: a batch that owns one handle per problem; `problems` is a list of keyword
+    dicts of Handle (inv_h, K, obs_xy, y, sigma and the options). The handles are available as
+    batch.handles (views, destroyed with the batch)."""
+    lib = load()
+    P = len(problems)
+    ds, os_, keep = (ProblemDesc * P)(), (SamplerOpts * P)(), []
+    for i, kw in enumerate(problems):
+        kw = dict(kw)
+        d, o, k = _desc_opts(kw.pop("inv_h"), kw.pop("K"), kw.pop("obs_xy"), kw.pop("y"), kw.pop("sigma"), **kw)
+        ds[i], os_[i] = d, o
+        keep.append(k)
+    out = ctypes.c_void_p()
+    rc = lib.smc_init_batch(P, ds, os_, ctypes.byref(out))
+    if rc != SMC_OK:
+        raise SmcError(rc, "smc_init_batch")
+    b = Batch.__new__(Batch)
+    b._lib = lib
+    b._b = out
+    b.handles = [Handle.borrowed(lib.smc_batch_handle(out, p), b) for p in range(P)]
+    return b
+
+
 class SmcError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
@@ -232,27 +281,31 @@ def _dptr(a):
     return a.ctypes.data_as(_dp) if a is not None else None
 
 
+def _desc_opts(inv_h, K, obs_xy, y, sigma, corr_len=0.1, variance=1.0, J=0, J_tilde=100, n_mcmc=5, tau_star=1.0,
+               tau_lu=None, eps=1e-6, s_pcn=0.2, precision=SMC_FP64, seed=0, max_iter=100, rtol=0.0, stream=None,
+               linear_A=None, surrogate=0, surrogate_train_steps=0, surrogate_batch=0, cov="sep_exp",
+               source="one", proposal="pcn", tau_min=0.0, bc="dirichlet"):
+    """smc_problem_desc and smc_sampler_opts of the keyword form, and the arrays they point to."""
+    inv_h = np.ascontiguousarray(inv_h, dtype=np.int32)
+    obs = np.ascontiguousarray(obs_xy, dtype=np.float64).reshape(-1, 2)
+    yy = np.ascontiguousarray(y, dtype=np.float64).ravel()
+    A = None if linear_A is None else np.ascontiguousarray(linear_A, dtype=np.float64)
+    d = ProblemDesc(len(inv_h), inv_h.ctypes.data_as(_ip), int(K), float(corr_len), float(variance), obs.shape[0],
+                    _dptr(obs), _dptr(yy), float(sigma), SMC_FWD_LINEAR if A is not None else SMC_FWD_FEM, _dptr(A),
+                    _COV[cov], _SRC[source], _BC[bc])
+    o = SamplerOpts(int(J), int(J_tilde), int(n_mcmc), float(tau_star), float(tau_star if tau_lu is None else tau_lu),
+                    float(eps), float(s_pcn), int(precision), int(seed), int(max_iter), float(rtol), int(surrogate),
+                    int(surrogate_train_steps), int(surrogate_batch), stream, _PROP[proposal], float(tau_min))
+    return d, o, (inv_h, obs, yy, A)
+
+
 class Handle:
     """Owns one smc_handle. Arrays passed in are kept alive for the call's duration only."""
 
-    def __init__(self, inv_h, K, obs_xy, y, sigma, corr_len=0.1, variance=1.0, J=0, J_tilde=100,
-                 n_mcmc=5, tau_star=1.0, tau_lu=None, eps=1e-6, s_pcn=0.2, precision=SMC_FP64, seed=0,
-                 max_iter=100, rtol=0.0, stream=None, linear_A=None, surrogate=0, surrogate_train_steps=0,
-                 surrogate_batch=0, cov="sep_exp", source="one", proposal="pcn", tau_min=0.0, bc="dirichlet"):
+    def __init__(self, inv_h, K, obs_xy, y, sigma, **kw):
         lib = load()
         self._lib = lib
-        self._inv_h = np.ascontiguousarray(inv_h, dtype=np.int32)
-        self._obs = np.ascontiguousarray(obs_xy, dtype=np.float64).reshape(-1, 2)
-        self._y = np.ascontiguousarray(y, dtype=np.float64).ravel()
-        self._A = None if linear_A is None else np.ascontiguousarray(linear_A, dtype=np.float64)
-        d = ProblemDesc(len(self._inv_h), self._inv_h.ctypes.data_as(_ip), int(K), float(corr_len),
-                        float(variance), self._obs.shape[0], _dptr(self._obs), _dptr(self._y), float(sigma),
-                        SMC_FWD_LINEAR if self._A is not None else SMC_FWD_FEM, _dptr(self._A), _COV[cov],
-                        _SRC[source], _BC[bc])
-        o = SamplerOpts(int(J), int(J_tilde), int(n_mcmc), float(tau_star),
-                        float(tau_star if tau_lu is None else tau_lu), float(eps), float(s_pcn), int(precision),
-                        int(seed), int(max_iter), float(rtol), int(surrogate), int(surrogate_train_steps),
-                        int(surrogate_batch), stream, _PROP[proposal], float(tau_min))
+        d, o, self._keep = _desc_opts(inv_h, K, obs_xy, y, sigma, **kw)
         h = ctypes.c_void_p()
         rc = lib.smc_init(ctypes.byref(d), ctypes.byref(o), ctypes.byref(h))
         self._h = h
@@ -264,7 +317,22 @@ class Handle:
         lib.smc_sizes(h, ctypes.byref(K_), ctypes.byref(n_obs), ctypes.byref(nl), ctypes.byref(J_))
         self.K, self.n_obs, self.n_levels, self.J = K_.value, n_obs.value, nl.value, J_.value
 
+    @classmethod
+    def borrowed(cls, ptr, owner):
+        """A view of a handle that `owner` (a Batch made by init_batch) owns and destroys."""
+        self = cls.__new__(cls)
+        self._lib = load()
+        self._h = ctypes.c_void_p(ptr)
+        self._owner = owner
+        K_, n_obs, nl, J_ = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._lib.smc_sizes(self._h, ctypes.byref(K_), ctypes.byref(n_obs), ctypes.byref(nl), ctypes.byref(J_))
+        self.K, self.n_obs, self.n_levels, self.J = K_.value, n_obs.value, nl.value, J_.value
+        return self
+
     def close(self):
+        if getattr(self, "_owner", None) is not None:   # borrowed: the batch destroys it
+            self._h = None
+            return
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.smc_destroy(self._h)
         self._h = None
@@ -363,10 +431,24 @@ class Handle:
         self._check(self._lib.smc_get_timing(self._h, _dptr(ms), cnt))
         return ms, list(cnt)
 
+    PHASES = ("surrogate_training", "surrogate_inference", "screening", "reweight_resample", "moves", "gate")
+
+    def get_phase_timing(self):
+        """Device milliseconds per phase since the last call (with set_timing(True))."""
+        ms = np.zeros(8)
+        self._check(self._lib.smc_get_phase_timing(self._h, _dptr(ms)))
+        return dict(zip(self.PHASES, ms[:len(self.PHASES)].tolist()))
+
     def tempering_update(self, level, beta0=0.0, n_mcmc=1):
         info = StageInfo()
         self._check(self._lib.smc_tempering_update(self._h, int(level), float(beta0), int(n_mcmc),
                                                    ctypes.byref(info)))
+        return info.as_dict()
+
+    def bridging_update(self, level, beta=1.0, zeta0=0.0, n_mcmc=1):
+        info = StageInfo()
+        self._check(self._lib.smc_bridging_update(self._h, int(level), float(beta), float(zeta0), int(n_mcmc),
+                                                  ctypes.byref(info)))
         return info.as_dict()
 
     # ---- kernel-level entry points ---------------------------------------------------------

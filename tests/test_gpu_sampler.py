@@ -251,3 +251,41 @@ def test_increment_search_reports_numerical_singularity():
     # the handle stays usable
     d, _, _ = h.next_increment(np.linspace(0.0, 1.0, 64), 1.0)
     assert d == 1.0
+
+
+def test_bridging_update_equals_oracle_bridging_step():
+    """smc_bridging_update (Sec. 4.1): Phi on both levels, the increment of zeta from zeta0 at the given
+    beta, resampling with both potentials, pCN steps on the bridged target -- the oracle's bridging
+    step with the same draws gives the same zeta, evidence factor, particles and potentials."""
+    As, y, s = _linear(K=4, n=6, sigma=0.3, seed=9, levels=2)
+    J, K = 1200, 4
+    kw = dict(n_mcmc=3, s_pcn=0.4, seed=91)
+    h = _handle_linear(As, y, s, J=J, **kw)
+    th0 = philox.normals(J, K, 0, philox.PURPOSE_PRIOR, 91)
+    h.set_particles(th0)
+    beta, zeta0 = 0.7, 0.2
+    info = h.bridging_update(0, beta, zeta0, 3)
+    ev = lambda l, th: potential(th @ As[l].T, y, s)
+    o = smc.Sampler(ev, 2, K, J, theta0=th0, **kw)
+    phi_c, phi_f = o.evaluate(0, o.theta), o.evaluate(1, o.theta)
+    delta, anc, cvw = o._reweight_resample(beta * (phi_f - phi_c), 1.0 - zeta0)
+    o.theta, phi_c, phi_f = o.theta[anc], phi_c[anc], phi_f[anc]
+    zeta = 1.0 if delta >= 1.0 - zeta0 else zeta0 + delta
+
+    def target(prop):
+        if prop is None:
+            return beta * ((1.0 - zeta) * phi_c + zeta * phi_f), [phi_c, phi_f]
+        pc, pf = o.evaluate(0, prop), o.evaluate(1, prop)
+        return beta * ((1.0 - zeta) * pc + zeta * pf), [pc, pf]
+    rate = o._mcmc(target)
+    assert info["kind"] == "LU" and info["level"] == 1
+    assert info["zeta"] == pytest.approx(zeta, rel=1e-12)
+    assert info["delta"] == pytest.approx(delta, rel=1e-12)
+    assert info["log_z_inc"] == pytest.approx(o.log_z, rel=1e-12)
+    assert info["accept_rate"] == pytest.approx(rate, abs=1e-12)
+    th, phi = h.particles()
+    assert np.allclose(th, o.theta, rtol=1e-10, atol=1e-12)
+    assert np.allclose(phi, phi_c, rtol=1e-10)
+    st = h.state()
+    assert st["beta"] == 0.0 and st["level"] == 0       # the update-scheme state is untouched
+    assert st["evals"][:2] == list(o.evals)               # both levels solved per proposal
