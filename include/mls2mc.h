@@ -116,6 +116,12 @@ typedef struct {
                                   at beta = 1 the level update is assessed by cv^LU on the first
                                   J_tilde particles and the run stops on the current level when it is
                                   below tau_min; 0: scheme u (every level is reached) */
+    double accept_target;      /* > 0: adapt the Markov kernel's step between updates: the first update
+                                  uses s_pcn, each later one s * exp(a - accept_target), a the previous
+                                  update's acceptance rate (clamped to [1e-4, 1] for pCN, [1e-4, 100]
+                                  for the random walk). The step of an update depends on earlier updates
+                                  only, so each update's kernel still leaves its target invariant. 0: the
+                                  step stays s_pcn (not in the paper; Sec. 5 fixes the step) */
 } smc_sampler_opts;
 
 typedef struct smc_handle smc_handle;
@@ -237,6 +243,9 @@ typedef struct {
     long long evals_per_level[8];
     int n_bridge;
     int status;            /* 1: the sampler had already reached beta = 1 on the finest level */
+    int n_unique;          /* distinct ancestors the update's resampling kept (of J) */
+    int pad;
+    double step;           /* the Markov kernel's step s the update's moves used */
 } smc_stage_info;
 
 /* One step of the update scheme u of Eq. eq_updatescheme_final (Sec. 4.4): an ITU, or a whole LU

@@ -110,7 +110,8 @@ class Sampler:
     """
 
     def __init__(self, evaluate, n_levels, K, J, J_tilde=100, n_mcmc=5, tau_star=1.0,
-                 tau_lu=None, eps=1e-6, s_pcn=0.2, seed=0, theta0=None, proposal="pcn", tau_min=0.0):
+                 tau_lu=None, eps=1e-6, s_pcn=0.2, seed=0, theta0=None, proposal="pcn", tau_min=0.0,
+                 accept_target=0.0):
         self.evaluate_raw = evaluate
         self.L = n_levels
         self.K = K
@@ -125,6 +126,13 @@ class Sampler:
             raise ValueError("proposal must be 'pcn' or 'rwm'")
         self.proposal = proposal
         self.tau_min = tau_min         # > 0: the scheme u' of Sec. 4.5 (adaptive maximum level)
+        # > 0: the Markov kernel's step adapts between updates, s <- s exp(a - accept_target) with a
+        # the last update's acceptance rate (clamped to [1e-4, 1] for pCN, [1e-4, 100] for the random
+        # walk); an update's step depends on finished updates only, so its kernel leaves its target
+        # invariant (the paper fixes the step)
+        self.accept_target = accept_target
+        self.step_size = s_pcn
+        self.last_unique = J
         self.terminated = False
         self.seed = seed
         self.evals = np.zeros(n_levels, dtype=np.int64)
@@ -155,6 +163,7 @@ class Sampler:
         self.log_z += log_mean_weight(a, delta)
         U = philox.uniform_scalar(self.stage, philox.PURPOSE_RESAMPLE, self.seed)
         anc = systematic_resample(-delta * a, U)
+        self.last_unique = int(np.unique(anc).size)
         w = np.exp(-delta * (a - a.min()))
         return delta, anc, cv(w)
 
@@ -163,15 +172,17 @@ class Sampler:
         evaluates the proposal."""
         acc = 0
         phi_t, caches = target(None)
+        s = self.step_size if self.accept_target > 0.0 else self.s
+        self.last_step = s
         for _ in range(self.n_mcmc):
             xi = philox.normals(self.J, self.K, self.mcmc_event, philox.PURPOSE_PCN_XI, self.seed)
             u = philox.uniforms_open(self.J, self.mcmc_event, philox.PURPOSE_PCN_U, self.seed)
             if self.proposal == "pcn":
-                prop = pcn_propose(self.theta, xi, self.s)
+                prop = pcn_propose(self.theta, xi, s)
                 phi_t_new, caches_new = target(prop)
                 ok = np.log(u) < -(phi_t_new - phi_t)
             else:   # random walk: the prior ratio enters the acceptance
-                prop = rwm_propose(self.theta, xi, self.s)
+                prop = rwm_propose(self.theta, xi, s)
                 phi_t_new, caches_new = target(prop)
                 ok = np.log(u) < -(phi_t_new - phi_t) + log_prior_ratio(prop, self.theta)
             self.theta[ok] = prop[ok]
@@ -180,7 +191,11 @@ class Sampler:
                 c[ok] = cn[ok]
             acc += int(ok.sum())
             self.mcmc_event += 1
-        return acc / (self.n_mcmc * self.J)
+        rate = acc / (self.n_mcmc * self.J) if self.n_mcmc > 0 else 0.0
+        if self.accept_target > 0.0:
+            hi = 100.0 if self.proposal == "rwm" else 1.0
+            self.step_size = min(hi, max(1e-4, self.step_size * math.exp(rate - self.accept_target)))
+        return rate
 
     # -- the two update types ----------------------------------------------------------------
     def _itu(self):
@@ -198,7 +213,7 @@ class Sampler:
             return beta * p, [p]
         rate = self._mcmc(target)
         self.path.append(dict(kind='ITU', level=l, beta=self.beta, zeta=None, delta=delta,
-                              cv=cvw, accept=rate))
+                              cv=cvw, accept=rate, n_unique=self.last_unique, step=self.last_step))
         self.stage += 1
         self.prev_lu = False
 
@@ -228,7 +243,7 @@ class Sampler:
             rate = self._mcmc(target)
             nb += 1
             self.path.append(dict(kind='LU', level=l + 1, beta=beta, zeta=zeta, delta=delta,
-                                  cv=cvw, accept=rate))
+                                  cv=cvw, accept=rate, n_unique=self.last_unique, step=self.last_step))
             self.stage += 1
         self.level = l + 1
         self.phi = phi_f

@@ -82,7 +82,7 @@ struct BatchSampler {
     // barrier error flag, the search state, the predictor's cv
     struct Back {
         unsigned long long acc;
-        unsigned bad, pad;
+        unsigned bad, distinct;
         int inc_err, pad2;
         double cv_lu;
         IncState st;
@@ -383,6 +383,7 @@ int batch_step(Batch* b, smc_stage_info* infos) {
         t.btot = s->inc.partials;
         t.bar = s->inc.bar;
         t.err = s->inc.err;
+        t.distinct = h->distinct_counter();
         rs.push_back(t);
     }
     if (e == cudaSuccess) e = resample_gather_multi_launch(rs, st);
@@ -411,7 +412,8 @@ int batch_step(Batch* b, smc_stage_info* infos) {
             if (m >= h->opts.n_mcmc) continue;
             Sampler* s = h->smp;
             const bool rwm = h->opts.proposal == SMC_PROP_RWM;
-            const double sp = h->opts.s_pcn, c0 = rwm ? 1.0 : std::sqrt(1.0 - sp * sp);
+            const double sp = h->mcmc_step(), c0 = rwm ? 1.0 : std::sqrt(1.0 - sp * sp);
+            h->last_step = sp;
             const uint32_t ev = (uint32_t)(s->mcmc_event + m);
             nt.push_back({s->theta_p, s->theta, h->opts.seed, s->J, h->K, ev, kPurposePcnXi, c0, sp});
             rc0.push_back({p, s->level, s->J, s->theta_p, s->phi_cp});
@@ -476,6 +478,9 @@ int batch_step(Batch* b, smc_stage_info* infos) {
             continue;
         }
         const double rate = h->opts.n_mcmc > 0 ? (double)r.acc / ((double)h->opts.n_mcmc * s->J) : 0.0;
+        h->last_distinct = r.distinct;
+        if (h->opts.n_mcmc <= 0) h->last_step = h->mcmc_step();
+        h->adapt_step(rate);
         smc_stage_info* info = infos ? &infos[p] : nullptr;
         if (act[p] == kItu) {
             s->beta = r.st.next;

@@ -17,6 +17,7 @@
 // theta + s xi, with the prior ratio in the acceptance).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -153,6 +154,17 @@ int Handle::smp_eval(int level, int n, const double* theta, double* phi) {
 }
 
 unsigned* Handle::bad_counter() { return reinterpret_cast<unsigned*>(reinterpret_cast<char*>(smp->n_acc) + 8); }
+unsigned* Handle::distinct_counter() { return reinterpret_cast<unsigned*>(reinterpret_cast<char*>(smp->n_acc) + 12); }
+
+// the Markov kernel's step for the coming moves, and its adaptation from their acceptance rate
+// (opts.accept_target > 0: s <- s exp(a - target), clamped; the next update's step depends only on
+// updates that are finished, so every update's kernel is fixed when it runs)
+double Handle::mcmc_step() const { return opts.accept_target > 0.0 ? smp->step : opts.s_pcn; }
+void Handle::adapt_step(double rate) {
+    if (!(opts.accept_target > 0.0)) return;
+    const double hi = opts.proposal == SMC_PROP_RWM ? 100.0 : 1.0;
+    smp->step = std::min(hi, std::max(1e-4, smp->step * std::exp(rate - opts.accept_target)));
+}
 
 // read the accept and non-convergence counters and the grid-barrier flag of the last increment
 // search and resampling, and (pending != null) the state of a search whose result the host has
@@ -170,6 +182,7 @@ int Handle::read_counters(unsigned long long* acc, IncState* pending) {
     unsigned bad;
     std::memcpy(&a, buf, 8);
     std::memcpy(&bad, buf + 8, 4);
+    std::memcpy(&last_distinct, buf + 12, 4);
     if (acc) *acc = a;
     if (bad) {
         CK(cudaMemsetAsync(bad_counter(), 0, 4, stream));
@@ -326,7 +339,7 @@ int Handle::reweight_resample(const double* a, double dmax, double base, bool ca
     if (wait) S->log_z += st.log_mean_w;
     CK(resample_gather_launch(a, S->J, S->inc.state, (uint32_t)S->stage, opts.seed, K, S->theta, S->theta_t,
                               S->phi_c, S->phi_t0, carry_fine ? S->phi_f : nullptr, S->phi_t1, S->cdf, S->anc,
-                              S->inc, stream));
+                              S->inc, distinct_counter(), stream));
     std::swap(S->theta, S->theta_t);
     std::swap(S->phi_c, S->phi_t0);
     if (carry_fine) std::swap(S->phi_f, S->phi_t1);
@@ -348,7 +361,8 @@ int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, Inc
     if (da_ready(level, zeta)) return mcmc_da(level, zeta, rate);
     Sampler* S = smp;
     const bool rwm = opts.proposal == SMC_PROP_RWM;
-    const double s = opts.s_pcn, c0 = rwm ? 1.0 : std::sqrt(1.0 - s * s);
+    const double s = mcmc_step(), c0 = rwm ? 1.0 : std::sqrt(1.0 - s * s);
+    last_step = s;
     CK(cudaMemsetAsync(S->n_acc, 0, 8, stream));
     for (int m = 0; m < opts.n_mcmc; ++m) {
         const uint32_t ev = (uint32_t)S->mcmc_event;
@@ -366,6 +380,7 @@ int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, Inc
     unsigned long long acc = 0;
     RC(read_counters(&acc, pending));
     rate = opts.n_mcmc > 0 ? (double)acc / ((double)opts.n_mcmc * S->J) : 0.0;
+    adapt_step(rate);
     return SMC_OK;
 }
 
@@ -377,7 +392,8 @@ int Handle::mcmc_da(int level, double zeta, double& rate) {
     const int J = S->J;
     const bool br = zeta >= 0.0;
     const bool rwm = opts.proposal == SMC_PROP_RWM;
-    const double s = opts.s_pcn, c0 = rwm ? 1.0 : std::sqrt(1.0 - s * s);
+    const double s = mcmc_step(), c0 = rwm ? 1.0 : std::sqrt(1.0 - s * s);
+    last_step = s;
     CK(cudaMemsetAsync(S->n_acc, 0, 8, stream));
     {
         PhaseTimer pt(this, kPhInfer);
@@ -420,6 +436,7 @@ int Handle::mcmc_da(int level, double zeta, double& rate) {
     RC(read_counters(&acc));
     const double props = (double)opts.n_mcmc * J;
     rate = props > 0 ? (double)acc / props : 0.0;
+    adapt_step(rate);
     S->da_proposals += (long long)props;
     S->da_pass1 += passed;
     last_da_rate = props > 0 ? (double)passed / props : 0.0;
@@ -439,6 +456,8 @@ void Handle::record(int type, double zeta, const IncState& st, double rate, doub
     r.cv_lu = cv_lu;
     r.log_z_inc = st.log_mean_w;
     r.accept_rate = rate;
+    r.n_unique = (int)last_distinct;
+    r.step = last_step;
     r.da_stage1_rate = last_da_rate;
     last_da_rate = -1.0;
     for (int l = 0; l < 8; ++l) r.evals_per_level[l] = S->evals[l];
@@ -453,7 +472,7 @@ int Handle::tempering_update(int level, double beta0, int n_mcmc, smc_stage_info
     Sampler* S = smp;
     RC(smp_eval(level, S->J, S->theta, S->phi_c));
     IncState st;
-    const double log_z = S->log_z, beta = S->beta;
+    const double log_z = S->log_z, beta = S->beta, step0 = S->step;
     const int nm = opts.n_mcmc;
     const bool wait = opts.surrogate != 0;
     S->beta = beta0;
@@ -465,9 +484,12 @@ int Handle::tempering_update(int level, double beta0, int n_mcmc, smc_stage_info
     opts.n_mcmc = nm;
     S->beta = beta;
     S->log_z = log_z;
+    S->step = step0;
     if (rc != SMC_OK) return rc;
     if (info) {
         std::memset(info, 0, sizeof *info);
+        info->n_unique = (int)last_distinct;
+        info->step = last_step;
         info->type = 0;
         info->level = level;
         info->beta = st.next;
@@ -495,7 +517,7 @@ int Handle::bridging_update(int level, double beta, double zeta0, int n_mcmc, sm
     RC(smp_eval(level + 1, S->J, S->theta, S->phi_f));
     CK(lu_increment_launch(S->phi_c, S->phi_f, S->J, beta, S->a, stream));
     IncState st;
-    const double log_z = S->log_z, beta_s = S->beta;
+    const double log_z = S->log_z, beta_s = S->beta, step0 = S->step;
     const int nm = opts.n_mcmc;
     S->beta = beta;
     int rc = reweight_resample(S->a, 1.0 - zeta0, zeta0, true, st, true);
@@ -507,9 +529,12 @@ int Handle::bridging_update(int level, double beta, double zeta0, int n_mcmc, sm
     }
     S->beta = beta_s;
     S->log_z = log_z;
+    S->step = step0;
     if (rc != SMC_OK) return rc;
     if (info) {
         std::memset(info, 0, sizeof *info);
+        info->n_unique = (int)last_distinct;
+        info->step = last_step;
         info->type = 1;
         info->level = level + 1;
         info->beta = beta;
@@ -583,6 +608,7 @@ int Handle::sampler_restart() {
     S->terminated = false;
     S->stage = 0;
     S->mcmc_event = 0;
+    S->step = opts.s_pcn;
     for (auto& v : S->evals) v = 0;
     S->path.clear();
     S->started = true;

@@ -103,6 +103,11 @@ struct Handle {
     int smp_eval(int level, int n, const double* theta, double* phi);
     int check_iters(int n);
     unsigned* bad_counter();
+    unsigned* distinct_counter();
+    double mcmc_step() const;
+    void adapt_step(double rate);
+    unsigned last_distinct = 0;   // distinct ancestors of the last resampling (read with the counters)
+    double last_step = 0.0;       // the Markov kernel's step of the last moves
     int read_counters(unsigned long long* acc, struct IncState* pending = nullptr);
     int check_increment(const struct IncState& st);
     const double* next_param_device() const;

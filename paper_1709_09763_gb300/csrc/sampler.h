@@ -32,6 +32,7 @@ struct Sampler {
     bool prev_lu = true;
     bool terminated = false;   // scheme u': stopped on a level below the finest
     long long stage = 0, mcmc_event = 0;
+    double step = 0.0;                 // the Markov kernel's step s for the next update
     long long evals[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     std::vector<smc_stage_info> path;
 };

@@ -55,11 +55,12 @@ cudaError_t resample_launch(const double* a, const double* w_in, int n, const In
                             uint32_t event, uint64_t seed, double* cdf, int* anc, cudaStream_t st);
 // weights of the increment in *state, systematic resampling (U from Philox (event, kPurposeResample))
 // and the gather of theta rows and up to two potential caches, in one cooperative launch; uses
-// w's barrier and scratch (w.err set if a grid barrier timed out)
+// w's barrier and scratch (w.err set if a grid barrier timed out); *distinct (if given) receives the
+// number of distinct ancestors
 cudaError_t resample_gather_launch(const double* a, int n, const IncState* state, uint32_t event, uint64_t seed,
                                    int K, const double* th_in, double* th_out, const double* p0_in, double* p0_out,
                                    const double* p1_in, double* p1_out, double* cdf, int* anc, IncWork& w,
-                                   cudaStream_t st);
+                                   unsigned* distinct, cudaStream_t st);
 cudaError_t lu_increment_launch(const double* phi_c, const double* phi_f, int n, double beta, double* a,
                                 cudaStream_t st);
 cudaError_t cv_lu_launch(const double* phi_c, const double* phi_f, int n, double beta, double* out, cudaStream_t st);
@@ -104,6 +105,7 @@ struct RsTask {
     int* anc;
     unsigned* bar;
     int* err;
+    unsigned* distinct;   // distinct ancestors (may be null)
 };
 struct NormTask {
     double* out;

@@ -435,14 +435,18 @@ __global__ void __launch_bounds__(kIncThreads) inc_search_multi_kernel(const __g
 // fixed order by every block). Deterministic for given n and grid.
 constexpr int kRsThreads = 128;
 
-// the resampling of one problem by the blocks bid = 0 .. nb - 1 that a launch gives it
+// the resampling of one problem by the blocks bid = 0 .. nb - 1 that a launch gives it; *distinct
+// (if given) receives the number of distinct ancestors
 __device__ __forceinline__ void resample_gather_blocks(
     const double* a, int n, const IncState* state, uint32_t event, uint64_t seed, int K, const double* th_in,
     double* th_out, const double* p0_in, double* p0_out, const double* p1_in, double* p1_out, double* cdf, int* anc,
-    double* btot, unsigned* bar, int* err, const unsigned bid, const unsigned nb) {
+    double* btot, unsigned* bar, int* err, unsigned* distinct, const unsigned bid, const unsigned nb) {
     __shared__ double warp_tot[kRsThreads / 32];
     __shared__ double run_s, off_s, inv_s;
     __shared__ int ok_s;
+    __shared__ unsigned distinct_s;
+    // zeroed before the first grid barrier, added to after the last one
+    if (distinct && bid == 0 && threadIdx.x == 0) *distinct = 0u;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     unsigned generation = 0;
     const int chunk = (n + (int)nb - 1) / (int)nb;
@@ -508,24 +512,34 @@ __device__ __forceinline__ void resample_gather_blocks(
     if (tid == 0) ok_s = grid_barrier(bar, err, nb, generation);
     __syncthreads();
     if (!ok_s) return;
-    // gather: one warp per particle row (coalesced over k), rows spread over every warp of the grid
+    // gather: one warp per particle row (coalesced over k), rows spread over every warp of the grid;
+    // a row starts a new ancestor when its index differs from the previous row's (sorted ancestors)
+    if (tid == 0) distinct_s = 0u;
+    __syncthreads();
     const int n_warps = (int)nb * (kRsThreads / 32);
+    unsigned fresh = 0u;
     for (int i = (int)bid * (kRsThreads / 32) + wid; i < n; i += n_warps) {
         const int src = __ldcg(&anc[i]);
         for (int k = lane; k < K; k += 32) th_out[(size_t)i * K + k] = th_in[(size_t)src * K + k];
         if (lane == 0) {
             if (p0_in) p0_out[i] = p0_in[src];
             if (p1_in) p1_out[i] = p1_in[src];
+            fresh += (i == 0 || __ldcg(&anc[i - 1]) != src) ? 1u : 0u;
         }
+    }
+    if (distinct) {
+        if (lane == 0 && fresh) atomicAdd(&distinct_s, fresh);
+        __syncthreads();
+        if (tid == 0 && distinct_s) atomicAdd(distinct, distinct_s);
     }
 }
 
 __global__ void __launch_bounds__(kRsThreads) resample_gather_kernel(
     const double* a, int n, const IncState* state, uint32_t event, uint64_t seed, int K, const double* th_in,
     double* th_out, const double* p0_in, double* p0_out, const double* p1_in, double* p1_out, double* cdf, int* anc,
-    double* btot, unsigned* bar, int* err) {
+    double* btot, unsigned* bar, int* err, unsigned* distinct) {
     resample_gather_blocks(a, n, state, event, seed, K, th_in, th_out, p0_in, p0_out, p1_in, p1_out, cdf, anc, btot,
-                           bar, err, blockIdx.x, gridDim.x);
+                           bar, err, distinct, blockIdx.x, gridDim.x);
 }
 
 // many problems' resamplings in one cooperative launch (rs_blocks(n_p) blocks and a barrier counter
@@ -534,7 +548,7 @@ __global__ void __launch_bounds__(kRsThreads) resample_gather_multi_kernel(const
     const int p = task_of_block(T.start, T.count);
     const RsTask& k = T.t[p];
     resample_gather_blocks(k.a, k.n, k.state, k.event, k.seed, k.K, k.th_in, k.th_out, k.p0_in, k.p0_out, k.p1_in,
-                           k.p1_out, k.cdf, k.anc, k.btot, k.bar, k.err, blockIdx.x - (unsigned)T.start[p],
+                           k.p1_out, k.cdf, k.anc, k.btot, k.bar, k.err, k.distinct, blockIdx.x - (unsigned)T.start[p],
                            (unsigned)(T.start[p + 1] - T.start[p]));
 }
 
@@ -915,7 +929,7 @@ cudaError_t resample_launch(const double* a, const double* w_in, int n, const In
 cudaError_t resample_gather_launch(const double* a, int n, const IncState* state, uint32_t event, uint64_t seed,
                                    int K, const double* th_in, double* th_out, const double* p0_in, double* p0_out,
                                    const double* p1_in, double* p1_out, double* cdf, int* anc, IncWork& w,
-                                   cudaStream_t st) {
+                                   unsigned* distinct, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     // one block per 32 particles (up to kIncMaxBlocks): the searches and the row gather are
     // latency-bound, so they want many warps in flight
@@ -925,7 +939,8 @@ cudaError_t resample_gather_launch(const double* a, int n, const IncState* state
     double* btot = w.partials;   // the search is finished: its scratch is free
     void* args[] = {(void*)&a,     (void*)&n,      (void*)&state,  (void*)&event, (void*)&seed, (void*)&K,
                     (void*)&th_in, (void*)&th_out, (void*)&p0_in,  (void*)&p0_out, (void*)&p1_in,
-                    (void*)&p1_out, (void*)&cdf,   (void*)&anc,    (void*)&btot,  (void*)&w.bar, (void*)&w.err};
+                    (void*)&p1_out, (void*)&cdf,   (void*)&anc,    (void*)&btot,  (void*)&w.bar, (void*)&w.err,
+                    (void*)&distinct};
     e = cudaLaunchCooperativeKernel((const void*)resample_gather_kernel, dim3(nb), dim3(kRsThreads), args, 0, st);
     count_launches(1);
     return e;

@@ -57,7 +57,8 @@ class SamplerOpts(ctypes.Structure):
                 ("s_pcn", ctypes.c_double), ("precision", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("max_iter", ctypes.c_int), ("rtol", ctypes.c_double), ("surrogate", ctypes.c_int),
                 ("surrogate_train_steps", ctypes.c_int), ("surrogate_batch", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("proposal", ctypes.c_int), ("tau_min", ctypes.c_double)]
+                ("stream", ctypes.c_void_p), ("proposal", ctypes.c_int), ("tau_min", ctypes.c_double),
+                ("accept_target", ctypes.c_double)]
 
 
 class StageInfo(ctypes.Structure):
@@ -65,10 +66,11 @@ class StageInfo(ctypes.Structure):
                 ("zeta", ctypes.c_double), ("delta", ctypes.c_double), ("cv", ctypes.c_double),
                 ("cv_lu", ctypes.c_double), ("log_z_inc", ctypes.c_double),
                 ("accept_rate", ctypes.c_double), ("da_stage1_rate", ctypes.c_double),
-                ("evals_per_level", ctypes.c_longlong * 8), ("n_bridge", ctypes.c_int), ("status", ctypes.c_int)]
+                ("evals_per_level", ctypes.c_longlong * 8), ("n_bridge", ctypes.c_int), ("status", ctypes.c_int),
+                ("n_unique", ctypes.c_int), ("pad", ctypes.c_int), ("step", ctypes.c_double)]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "evals_per_level"}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("evals_per_level", "pad")}
         d["evals_per_level"] = list(self.evals_per_level)
         d["kind"] = "ITU" if self.type == 0 else "LU"
         return d
@@ -284,7 +286,7 @@ def _dptr(a):
 def _desc_opts(inv_h, K, obs_xy, y, sigma, corr_len=0.1, variance=1.0, J=0, J_tilde=100, n_mcmc=5, tau_star=1.0,
                tau_lu=None, eps=1e-6, s_pcn=0.2, precision=SMC_FP64, seed=0, max_iter=100, rtol=0.0, stream=None,
                linear_A=None, surrogate=0, surrogate_train_steps=0, surrogate_batch=0, cov="sep_exp",
-               source="one", proposal="pcn", tau_min=0.0, bc="dirichlet"):
+               source="one", proposal="pcn", tau_min=0.0, bc="dirichlet", accept_target=0.0):
     """smc_problem_desc and smc_sampler_opts of the keyword form, and the arrays they point to."""
     inv_h = np.ascontiguousarray(inv_h, dtype=np.int32)
     obs = np.ascontiguousarray(obs_xy, dtype=np.float64).reshape(-1, 2)
@@ -295,7 +297,8 @@ def _desc_opts(inv_h, K, obs_xy, y, sigma, corr_len=0.1, variance=1.0, J=0, J_ti
                     _COV[cov], _SRC[source], _BC[bc])
     o = SamplerOpts(int(J), int(J_tilde), int(n_mcmc), float(tau_star), float(tau_star if tau_lu is None else tau_lu),
                     float(eps), float(s_pcn), int(precision), int(seed), int(max_iter), float(rtol), int(surrogate),
-                    int(surrogate_train_steps), int(surrogate_batch), stream, _PROP[proposal], float(tau_min))
+                    int(surrogate_train_steps), int(surrogate_batch), stream, _PROP[proposal], float(tau_min),
+                    float(accept_target))
     return d, o, (inv_h, obs, yy, A)
 
 

@@ -34,18 +34,20 @@ def _specs(prec):
         return [dict(levels=(4, 8, 16), K=8, lc=0.3, J=300, seed=11),
                 dict(levels=(8,), K=4, lc=0.3, J=200, seed=12),
                 dict(levels=(4, 8, 16, 32), K=12, lc=0.2, J=257, seed=13, proposal="rwm", s_pcn=0.5),
-                dict(levels=(8, 16), K=6, lc=0.3, J=150, seed=14, tau_min=0.3)]
+                dict(levels=(8, 16), K=6, lc=0.3, J=150, seed=14, tau_min=0.3),
+                dict(levels=(4, 8), K=5, lc=0.3, J=180, seed=15, accept_target=0.3)]
     return [dict(levels=(8, 16, 32), K=16, lc=0.2, J=400, seed=21),
             dict(levels=(16, 32, 64), K=32, lc=0.1, J=333, seed=22),
             dict(levels=(32,), K=8, lc=0.3, J=128, seed=23),
-            dict(levels=(8, 16, 32, 64), K=24, lc=0.1, J=512, seed=24)]
+            dict(levels=(8, 16, 32, 64), K=24, lc=0.1, J=512, seed=24, accept_target=0.25)]
 
 
 def _kwargs(sp, prec, stream):
     obs, y, sigma = _data(sp["levels"], sp["K"], sp["lc"], 100 + sp["seed"])
     return dict(inv_h=list(sp["levels"]), K=sp["K"], obs_xy=obs, y=y, sigma=sigma, corr_len=sp["lc"], J=sp["J"],
                 J_tilde=64, n_mcmc=3, precision=prec, seed=sp["seed"], stream=stream,
-                proposal=sp.get("proposal", "pcn"), s_pcn=sp.get("s_pcn", 0.2), tau_min=sp.get("tau_min", 0.0))
+                proposal=sp.get("proposal", "pcn"), s_pcn=sp.get("s_pcn", 0.2), tau_min=sp.get("tau_min", 0.0),
+                accept_target=sp.get("accept_target", 0.0))
 
 
 def _handle(kw):
@@ -58,7 +60,7 @@ def _same_run(hb, hs):
     assert len(pb) == len(ps)
     for a, c in zip(pb, ps):
         for k in ("type", "level", "beta", "zeta", "delta", "cv", "cv_lu", "log_z_inc", "accept_rate",
-                  "evals_per_level", "n_bridge"):
+                  "evals_per_level", "n_bridge", "n_unique", "step"):
             assert a[k] == c[k], (k, a[k], c[k])
     tb, fb = hb.particles()
     ts, fs = hs.particles()

@@ -289,3 +289,28 @@ def test_bridging_update_equals_oracle_bridging_step():
     st = h.state()
     assert st["beta"] == 0.0 and st["level"] == 0       # the update-scheme state is untouched
     assert st["evals"][:2] == list(o.evals)               # both levels solved per proposal
+
+
+def test_adaptive_step_and_distinct_ancestors_match_oracle():
+    """Two FEM levels on the FP64 path with the adaptive Markov-kernel step (accept_target = 0.3):
+    the same path, steps and distinct-ancestor counts per update as the oracle's sampler."""
+    K, J = 4, 300
+    obs = wl.obs_grid(3)
+    lv = [ofwd.Level(N, 0.3, 1.0, K, obs) for N in (8, 16)]
+    th_true = np.random.default_rng(3).standard_normal(K)
+    Gt = lv[1].G(th_true)
+    sigma = 0.02 * np.abs(Gt).max()
+    y = Gt + sigma * np.random.default_rng(4).standard_normal(obs.shape[0])
+    kw = dict(J_tilde=50, n_mcmc=2, s_pcn=0.6, seed=15, accept_target=0.3)
+    h = native.Handle([8, 16], K, obs, y, sigma, corr_len=0.3, J=J, precision=native.SMC_FP64, rtol=1e-13, **kw)
+    h.run()
+    ev = lambda l, th: potential(lv[l].G_batch(th), y, sigma)
+    o = smc.Sampler(ev, 2, K, J, **kw).run()
+    gp = h.path()
+    _compare_paths(gp, o.path, 1e-7)
+    for g, r in zip(gp, o.path):
+        assert g["n_unique"] == r["n_unique"]
+        assert g["step"] == pytest.approx(r["step"], rel=1e-10)
+    assert len({g["step"] for g in gp}) > 1
+    th, _ = h.particles()
+    assert np.allclose(th, o.theta, rtol=1e-7, atol=1e-8)

@@ -203,3 +203,47 @@ def test_adaptive_maximum_level_scheme_stops_when_levels_agree():
     # both schemes take the same updates until beta first reaches 1 on level 2
     n = len(s.path)
     assert [(p['kind'], p['level']) for p in s.path] == [(p['kind'], p['level']) for p in full.path[:n]]
+
+
+@pytest.mark.parametrize("proposal,s0", [("pcn", 0.05), ("rwm", 2.0)])
+def test_adaptive_step_keeps_the_posterior_and_moves_toward_the_target_rate(proposal, s0):
+    """With accept_target > 0 the step of each update is fixed before its moves (it depends on the
+    finished updates only), so every update's kernel still leaves its target invariant: the
+    linear-Gaussian posterior and evidence come out as in closed form, from a poor first step
+    either way, each step follows the rule, and a step far off moves toward the target rate."""
+    A, y, sigma = _linear_problem()
+    m_ex, C_ex = gaussian.posterior(A, y, sigma)
+    lz_ex = gaussian.log_evidence(A, y, sigma)
+    J = 4000
+    ev = lambda l, th: potential(th @ A.T, y, sigma)
+    s = smc.Sampler(ev, 1, 3, J, n_mcmc=10, s_pcn=s0, seed=13, proposal=proposal, accept_target=0.3).run()
+    m, v = s.moments()
+    se_m = np.sqrt(np.diag(C_ex) / J) * 3.0
+    assert np.all(np.abs(m - m_ex) < 4 * se_m), (m, m_ex)
+    assert np.allclose(v, np.diag(C_ex), rtol=0.15)
+    assert s.log_z == pytest.approx(lz_ex, abs=0.15)
+    steps = [p['step'] for p in s.path]
+    assert steps[0] == s0 and len(set(steps)) == len(steps)        # adapted between every update
+    # each step follows the rule from the previous update's acceptance
+    for a, b in zip(s.path[:-1], s.path[1:]):
+        hi = 100.0 if proposal == "rwm" else 1.0
+        assert b['step'] == min(hi, max(1e-4, a['step'] * math.exp(a['accept'] - 0.3)))
+    # from a step far off, it moves in the direction that brings the rate toward the target
+    assert (steps[-1] - steps[0]) * (s.path[0]['accept'] - 0.3) > 0
+
+
+def test_distinct_ancestors_recorded():
+    """n_unique of an update is the number of distinct ancestors its resampling kept: all J for a
+    first update with equal potentials, fewer once the weights differ."""
+    J = 500
+    s = smc.Sampler(lambda l, th: np.zeros(th.shape[0]), 1, 2, J, n_mcmc=1, seed=3)
+    s.step()
+    assert s.path[-1]['n_unique'] == J
+    A, y, sigma = _linear_problem()
+    ev = lambda l, th: potential(th @ A.T, y, sigma)
+    s = smc.Sampler(ev, 1, 3, J, n_mcmc=1, seed=3)
+    s.step()
+    U = philox.uniform_scalar(0, philox.PURPOSE_RESAMPLE, 3)
+    phi0 = ev(0, philox.normals(J, 3, 0, philox.PURPOSE_PRIOR, 3))
+    anc = smc.systematic_resample(-s.path[-1]['delta'] * phi0, U)
+    assert s.path[-1]['n_unique'] == np.unique(anc).size < J
