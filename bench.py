@@ -366,6 +366,16 @@ def batched_sampler_measurement(native, wl, torch, dev, n_problems=64, max_inv_h
     same_state = [x.state() == z.state() for x, z in zip(seq, bat)]
     same_path = [x.path() == z.path() for x, z in zip(seq, bat)]
     same = all(same_particles) and all(same_state) and all(same_path)
+    differ = []
+    for p, (x, z) in enumerate(zip(seq, bat)):
+        if same_particles[p] and same_state[p] and same_path[p]:
+            continue
+        px, pz = x.path(), z.path()
+        first = next((i for i, (a, c) in enumerate(zip(px, pz)) if a != c), min(len(px), len(pz)))
+        fields = sorted(k for k in px[first] if first < len(px) and first < len(pz) and px[first][k] != pz[first][k]) \
+            if first < min(len(px), len(pz)) else ["length"]
+        differ.append({"problem": p, "levels": specs[p]["levels"], "K": specs[p]["K"], "J": specs[p]["J"],
+                       "first_differing_update": first, "updates": [len(px), len(pz)], "fields": fields})
     updates = sum(h.state()["n_updates"] for h in bat)
     b.close()
     for h in seq + bat:
@@ -377,7 +387,7 @@ def batched_sampler_measurement(native, wl, torch, dev, n_problems=64, max_inv_h
             "sequential_s": t_seq, "batched_s": t_bat, "speedup": t_seq / t_bat, "batched_steps": steps,
             "updates": updates, "identical_paths_and_particles": bool(same),
             "problems_with_identical": {"particles": int(sum(same_particles)), "state": int(sum(same_state)),
-                                        "path": int(sum(same_path))}}
+                                        "path": int(sum(same_path))}, "differing": differ}
 
 
 def main():
@@ -389,6 +399,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-run", action="store_true", help="skip the seconds-to-posterior sampler run")
     ap.add_argument("--autotune", action="store_true", help="let the library's autotuner pick the block sizes")
+    ap.add_argument("--large", action="store_true",
+                    help="also run the large workload (1/16 .. 1/256, K = 128, J = 16384): the prescribed "
+                         "pCN step against the adaptive step, plain and screened, with per-update diagnostics")
     ap.add_argument("--example-5-3-full", action="store_true",
                     help="also run Example 5.3 at the paper's size (1/16 .. 1/256, 320 KL terms)")
     args = ap.parse_args()
@@ -523,13 +536,14 @@ def main():
     # delayed-acceptance pCN screened by the surrogate, R seeds each, outside the timed region
     run = None
     if not args.no_run:
-        def one_run(wk, dk, inv_h, surrogate, seed, precision=native.SMC_MIXED, marginals=False, breakdown=False):
+        def one_run(wk, dk, inv_h, surrogate, seed, precision=native.SMC_MIXED, marginals=False, breakdown=False,
+                    accept_target=0.0):
             ob = wl.obs_grid(wk.obs_per_side)
             hr = native.Handle(inv_h, wk.K, ob, dk["y"], dk["sigma"], corr_len=wk.corr_len, variance=wk.variance,
                                J=wk.J, J_tilde=wk.J_tilde, n_mcmc=wk.n_mcmc, s_pcn=wk.s_pcn,
                                tau_star=wk.tau_star, precision=precision, seed=seed,
                                stream=stream.cuda_stream, surrogate=surrogate, cov=wk.cov, source=wk.source,
-                               proposal=wk.proposal, bc=wk.bc, tau_min=wk.tau_min)
+                               proposal=wk.proposal, bc=wk.bc, tau_min=wk.tau_min, accept_target=accept_target)
             if breakdown:
                 hr.set_timing(True)
             torch.cuda.synchronize(dev)
@@ -599,10 +613,15 @@ def main():
                     "peak_source": "FP64 FMA issue: 152 SMs x 2 FMA per clock x 2 flops x sm_max_mhz "
                                    "(the 1.25 TFLOP/s FP64 figure of this part)"}
 
-        def compare(wk, dk, inv_h, R=3, breakdown=False):
+        def compare(wk, dk, inv_h, R=3, breakdown=False, accept_target=0.0):
+            """Plain and surrogate-screened MLS^2MC, R seeds each (the same seeds for both arms): wall
+            seconds to the posterior, the posterior means' agreement (largest |z| over the K
+            coordinates of the two arms' replicate means) and the speed-up of the medians with a 95 %
+            bootstrap interval (runs resampled within each arm, 2000 draws, fixed seed)."""
             res = {}
             for name, sur in (("plain", 0), ("surrogate", 1)):
-                runs = [one_run(wk, dk, inv_h, sur, wk.seed_sampler + 1000 * rank + 17 * r) for r in range(R)]
+                runs = [one_run(wk, dk, inv_h, sur, wk.seed_sampler + 1000 * rank + 17 * r,
+                                accept_target=accept_target) for r in range(R)]
                 res[name] = {"seconds_median": float(np.median([x["seconds"] for x in runs])),
                              "seconds": [x["seconds"] for x in runs],
                              "solves_per_level_mean": np.mean([x["solves_per_level"] for x in runs], axis=0).tolist(),
@@ -612,13 +631,18 @@ def main():
                              "_means": np.array([x["mean"] for x in runs])}
                 if breakdown:
                     res[name]["breakdown_ms"] = one_run(wk, dk, inv_h, sur, wk.seed_sampler + 1000 * rank,
-                                                        breakdown=True)["breakdown_ms"]
+                                                        breakdown=True, accept_target=accept_target)["breakdown_ms"]
             a, b = res["plain"].pop("_means"), res["surrogate"].pop("_means")
             se = np.sqrt(a.var(axis=0, ddof=1) / R + b.var(axis=0, ddof=1) / R)
             z = np.abs(a.mean(0) - b.mean(0)) / np.where(se > 0, se, np.inf)
+            tp, ts = np.array(res["plain"]["seconds"]), np.array(res["surrogate"]["seconds"])
+            rng_b = np.random.default_rng(12345)
+            boot = [np.median(rng_b.choice(tp, R)) / np.median(rng_b.choice(ts, R)) for _ in range(2000)]
             return {"workload": wk.name, "levels_inv_h": list(inv_h), "K": wk.K, "J": wk.J, "n_mcmc": wk.n_mcmc,
+                    "s_pcn": wk.s_pcn, "accept_target": accept_target,
                     "replicates": R, "plain": res["plain"], "surrogate": res["surrogate"],
                     "speedup_surrogate_vs_plain": res["plain"]["seconds_median"] / res["surrogate"]["seconds_median"],
+                    "speedup_ci95": [float(np.percentile(boot, 2.5)), float(np.percentile(boot, 97.5))],
                     "posterior_mean_diff_over_se_max": float(np.max(z))}
         # MLS^2MC on the workload's hierarchy, single-level SMC on its finest level (Example
         # example_SMC, the paper's reference sampler), and the surrogate workload (5 levels to 1/128,
@@ -626,7 +650,9 @@ def main():
         wda = wl.WORKLOADS["da_mixed_h8_128"]
         dda = load_data(wda.name)
         run = {"mls2mc": compare(w, d, tuple(w.inv_h)), "smc_finest": compare(w, d, (w.inv_h[-1],), R=6),
-               "mls2mc_surrogate_workload": compare(wda, dda, tuple(wda.inv_h), breakdown=True)}
+               "mls2mc_surrogate_workload": compare(wda, dda, tuple(wda.inv_h), R=8, breakdown=True),
+               "mls2mc_surrogate_workload_adaptive_step": compare(wda, dda, tuple(wda.inv_h), R=8, breakdown=True,
+                                                                  accept_target=0.25)}
 
         def paper_example(name, R=3, J_sweep=()):
             """The paper's examples (Matern prior, one random-walk step per update; 5.1/5.2: nine
@@ -700,6 +726,61 @@ def main():
                                       "rel_misfit_mean": float(np.mean(st["rel_misfit_posterior_mean"]))})
                 res["cost_vs_accuracy"] = table
             return res
+        def large_study(R=3):
+            """The large workload (5 levels 1/16 .. 1/256, K = 128, 144 interpolated observations, J =
+            16384, 10 pCN steps): the prescribed step s = 0.2 against the adaptive step (accept_target
+            0.25), plain and screened; per update the acceptance rate, the distinct ancestors its
+            resampling kept and the step; across replicates the spread of the posterior means and of
+            log Z, and the largest |z| between the arms' replicate means."""
+            wk, dk = wl.WORKLOADS["large_mixed_h16_256"], load_data("large_mixed_h16_256")
+            ob = wl.obs_grid(wk.obs_per_side)
+            out = {"workload": wk.name, "levels_inv_h": list(wk.inv_h), "K": wk.K, "J": wk.J, "n_mcmc": wk.n_mcmc,
+                   "replicates": R}
+            means = {}
+            for label, sur, target in (("prescribed_step", 0, 0.0), ("adaptive_step", 0, 0.25),
+                                       ("adaptive_step_screened", 1, 0.25)):
+                runs = []
+                for r in range(R):
+                    hr = native.Handle(list(wk.inv_h), wk.K, ob, dk["y"], dk["sigma"], corr_len=wk.corr_len,
+                                       J=wk.J, J_tilde=wk.J_tilde, n_mcmc=wk.n_mcmc, s_pcn=wk.s_pcn,
+                                       tau_star=wk.tau_star, precision=native.SMC_MIXED,
+                                       seed=wk.seed_sampler + 1000 * rank + 17 * r, stream=stream.cuda_stream,
+                                       surrogate=sur, accept_target=target)
+                    torch.cuda.synchronize(dev)
+                    t0 = time.perf_counter()
+                    hr.run()
+                    torch.cuda.synchronize(dev)
+                    secs = time.perf_counter() - t0
+                    path = hr.path()
+                    m, v, lz = hr.posterior_moments()
+                    st = hr.state()
+                    hr.close()
+                    runs.append({"seconds": secs, "updates": len(path), "log_z": lz, "mean": np.asarray(m),
+                                 "solves_per_level": st["evals"][:len(wk.inv_h)],
+                                 "accept": [round(p["accept_rate"], 4) for p in path],
+                                 "n_unique": [p["n_unique"] for p in path],
+                                 "step": [round(p["step"], 5) for p in path],
+                                 "kind_level": [f'{p["kind"]}{p["level"]}' for p in path]})
+                M = np.array([x["mean"] for x in runs])
+                means[label] = M
+                out[label] = {"seconds": [x["seconds"] for x in runs],
+                              "seconds_median": float(np.median([x["seconds"] for x in runs])),
+                              "updates": [x["updates"] for x in runs], "log_z": [x["log_z"] for x in runs],
+                              "solves_per_level_mean": np.mean([x["solves_per_level"] for x in runs], axis=0).tolist(),
+                              "replicate_sd_of_mean_max": float(M.std(axis=0, ddof=1).max()),
+                              "replicate_sd_of_mean_median": float(np.median(M.std(axis=0, ddof=1))),
+                              "log_z_sd": float(np.std([x["log_z"] for x in runs], ddof=1)),
+                              "first_run": {k: runs[0][k] for k in ("accept", "n_unique", "step", "kind_level")}}
+
+            def zmax(a, b):
+                se = np.sqrt(a.var(axis=0, ddof=1) / len(a) + b.var(axis=0, ddof=1) / len(b))
+                return float(np.max(np.abs(a.mean(0) - b.mean(0)) / np.where(se > 0, se, np.inf)))
+            out["z_max_adaptive_vs_prescribed"] = zmax(means["adaptive_step"], means["prescribed_step"])
+            out["z_max_screened_vs_plain_adaptive"] = zmax(means["adaptive_step_screened"], means["adaptive_step"])
+            out["speedup_screened_vs_plain_adaptive"] = (out["adaptive_step"]["seconds_median"] /
+                                                        out["adaptive_step_screened"]["seconds_median"])
+            return out
+
         # single-level SMC on the FP64 path (h = 1/16, K = 16, J = 1000, 5 pCN steps)
         wf, dfp = wl.WORKLOADS["smc_fp64_h16"], load_data("smc_fp64_h16")
         fr = [one_run(wf, dfp, tuple(wf.inv_h), 0, wf.seed_sampler + 17 * r, native.SMC_FP64) for r in range(3)]
@@ -718,9 +799,15 @@ def main():
         run["paper_example_5_3"] = paper_example("example_5_3")
         if args.example_5_3_full:   # the paper's size: 1/16 .. 1/256, 320 KL terms
             run["paper_example_5_3_full"] = paper_example("example_5_3_full")
+        if args.large:
+            run["large_workload"] = large_study()
 
     batched = None if args.no_run else batched_measurement(native, wl, torch, dev)
     batched_run = None if args.no_run else batched_sampler_measurement(native, wl, torch, dev)
+    # many small problems' samplers: each sequential run fills a fraction of the GPU
+    batched_run_small = None if args.no_run else batched_sampler_measurement(native, wl, torch, dev,
+                                                                             n_problems=256, max_inv_h=64,
+                                                                             j_range=(64, 512))
     # many small problems: each per-problem launch fills a fraction of the GPU
     batched_small = None if args.no_run else batched_measurement(native, wl, torch, dev, n_problems=256,
                                                                  max_inv_h=64, j_range=(16, 256))
@@ -792,6 +879,8 @@ def main():
             line["batched_small_problems"] = batched_small
         if batched_run is not None:
             line["batched_sampler_to_posterior"] = batched_run
+        if batched_run_small is not None:
+            line["batched_sampler_small_problems_to_posterior"] = batched_run_small
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -89,8 +89,16 @@ struct BatchSampler {
     };
     Back* back = nullptr;
     size_t back_cap = 0;
+    // the update phase of a step (increments, resampling, moves) as a CUDA graph: captured every step
+    // from the second on (kernel arguments change with the particle buffers and counters), the
+    // executable graph updated in place when the captured graph has the same shape
+    long long steps = 0;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_ok = true;
+    long long graph_updates = 0, graph_instantiations = 0;
 
     ~BatchSampler() {
+        if (exec) cudaGraphExecDestroy(exec);
         cudaFree(d_args);
         cudaFree(d_offsets);
         cudaFree(d_counters);
@@ -242,7 +250,25 @@ int batch_step(Batch* b, smc_stage_info* infos) {
         if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_offsets, sizeof(int) * kMaxTasks);
         if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_counters, sizeof(int) * kMaxTasks);
         if (e == cudaSuccess) e = cudaMallocHost((void**)&S->back, sizeof(BatchSampler::Back) * (size_t)P);
+        // the largest item table and large-level scratch a step can need, allocated now: the update
+        // phase is captured into a graph, where nothing may be allocated
+        size_t items = 0, big = 0;
+        for (Handle* h : b->h) {
+            items += (size_t)h->smp->J;
+            for (const Level& L : h->levels)
+                if (L.N >= 128) big = std::max(big, (size_t)fem_global_blocks(L.N) * fem_global_slice(L.N));
+            // the syntheses' buffers at their largest (J particles on the finest level): a buffer that
+            // grew inside a captured update would free memory that earlier captured launches use
+            if (h->precision == SMC_MIXED) {
+                const int rc = h->synth_reserve((int)h->levels.size() - 1, h->smp->J);
+                if (rc != SMC_OK) return bfail(b, rc, h->last_error);
+            }
+        }
+        if (e == cudaSuccess) e = cudaMalloc((void**)&S->d_item_group, sizeof(int) * std::max<size_t>(items, 1));
+        if (e == cudaSuccess && big) e = cudaMalloc((void**)&S->big_scratch, big * sizeof(float));
         if (e != cudaSuccess) return bfail(b, SMC_ENOMEM, "batched sampler tables");
+        S->item_cap = std::max<size_t>(items, 1);
+        S->big_cap = big;
         S->back_cap = (size_t)P;
     }
     BatchSampler* S = b->smp;
@@ -338,6 +364,53 @@ int batch_step(Batch* b, smc_stage_info* infos) {
     for (int p = 0; p < P; ++p)
         if (act[p] == kItu || act[p] == kBridge) live.push_back(p);
     if (live.empty()) return SMC_OK;
+    // capture the update phase (the first step runs eagerly: buffers that grow on first use, such as
+    // the syntheses', reach their size there); a capture that fails falls back to eager launches
+    const bool capture = S->graph_ok && S->steps > 0 && st != nullptr;
+    S->steps += 1;
+    if (capture && cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        S->graph_ok = false;
+        return bfail(b, SMC_ECUDA, "batched sampler: stream capture could not begin");
+    }
+    int phase_rc = SMC_OK;
+    auto end_capture = [&](bool launch) -> int {
+        if (!capture) return SMC_OK;
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (ce != cudaSuccess || !g || !launch) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            S->graph_ok = false;
+            return ce == cudaSuccess ? SMC_OK : bfail(b, SMC_ECUDA, std::string("batched sampler capture: ") +
+                                                                      cudaGetErrorString(ce));
+        }
+        if (S->exec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(S->exec, g, &info) == cudaSuccess) {
+                S->graph_updates += 1;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(S->exec);
+                S->exec = nullptr;
+            }
+        }
+        if (!S->exec) {
+            ce = cudaGraphInstantiate(&S->exec, g, 0);
+            if (ce != cudaSuccess) {
+                cudaGraphDestroy(g);
+                S->exec = nullptr;
+                S->graph_ok = false;
+                return bfail(b, SMC_ECUDA, std::string("batched sampler graph: ") + cudaGetErrorString(ce));
+            }
+            S->graph_instantiations += 1;
+        }
+        cudaGraphDestroy(g);
+        ce = cudaGraphLaunch(S->exec, st);
+        if (ce != cudaSuccess) return bfail(b, SMC_ECUDA, std::string("batched sampler graph launch: ") +
+                                                            cudaGetErrorString(ce));
+        return SMC_OK;
+    };
     std::vector<LuTask> lut;
     std::vector<IncTask> inc;
     for (int p : live) {
@@ -387,7 +460,10 @@ int batch_step(Batch* b, smc_stage_info* infos) {
         rs.push_back(t);
     }
     if (e == cudaSuccess) e = resample_gather_multi_launch(rs, st);
-    if (e != cudaSuccess) return bfail(b, SMC_ECUDA, std::string("batched resampling: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        end_capture(false);
+        return bfail(b, SMC_ECUDA, std::string("batched resampling: ") + cudaGetErrorString(e));
+    }
     for (int p : live) {
         Sampler* s = b->h[p]->smp;
         std::swap(s->theta, s->theta_t);
@@ -402,7 +478,10 @@ int batch_step(Batch* b, smc_stage_info* infos) {
         steps = std::max(steps, b->h[p]->opts.n_mcmc);
     }
     e = zero_words_launch(zero, st);
-    if (e != cudaSuccess) return bfail(b, SMC_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        end_capture(false);
+        return bfail(b, SMC_ECUDA, cudaGetErrorString(e));
+    }
     for (int m = 0; m < steps; ++m) {
         std::vector<NormTask> nt;
         std::vector<EvalReq> rc0, rc1;
@@ -440,13 +519,19 @@ int batch_step(Batch* b, smc_stage_info* infos) {
             at.push_back(a);
         }
         e = normals_multi_launch(nt, st);
-        if (e != cudaSuccess) return bfail(b, SMC_ECUDA, cudaGetErrorString(e));
-        int rc = multi_eval(b, rc0, st);
+        int rc = e == cudaSuccess ? multi_eval(b, rc0, st) : bfail(b, SMC_ECUDA, cudaGetErrorString(e));
         if (rc == SMC_OK && !rc1.empty()) rc = multi_eval(b, rc1, st);
-        if (rc != SMC_OK) return rc;
-        e = pcn_accept_multi_launch(at, st);
-        if (e != cudaSuccess) return bfail(b, SMC_ECUDA, cudaGetErrorString(e));
+        if (rc == SMC_OK) {
+            e = pcn_accept_multi_launch(at, st);
+            if (e != cudaSuccess) rc = bfail(b, SMC_ECUDA, cudaGetErrorString(e));
+        }
+        if (rc != SMC_OK) {
+            end_capture(false);
+            return rc;
+        }
     }
+    phase_rc = end_capture(true);
+    if (phase_rc != SMC_OK) return phase_rc;
     // read back every problem's counters and search state, one wait
     for (int p : live) {
         Sampler* s = b->h[p]->smp;

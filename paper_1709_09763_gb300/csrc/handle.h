@@ -64,6 +64,7 @@ struct Handle {
     size_t synth_part_cap = 0;
     int* synth_err = nullptr;
     int synth_kappa(int level, int n, const double* theta, cudaStream_t st);
+    int synth_reserve(int level, int n);
 
     // opt-in CUDA-event timing of forward-solve launches, per level
     bool timing = false;

@@ -149,21 +149,24 @@ std::vector<uint16_t> kl_split_table(const std::vector<double>& psi, int K, int 
     return out;
 }
 
-int Handle::synth_kappa(int level, int n, const double* theta, cudaStream_t st) {
+// grow the synthesis buffers to hold n particles on `level` (no launch); a no-op when they do
+int Handle::synth_reserve(int level, int n) {
     const Level& L = levels[level];
     const int E = 2 * L.N * L.N, Kt = kl_split_total(K), G = kl_groups(K);
     const size_t need_k = (size_t)n * E, need_t = (size_t)n * Kt;
     if (need_k > synth_kappa_cap || need_t > synth_theta_cap) {
+        // both buffers grow to at least their previous size: alternating shapes never shrink them
+        const size_t cap_k = std::max(need_k, synth_kappa_cap), cap_t = std::max(need_t, synth_theta_cap);
         cudaFree(synth_kappa_buf);
         cudaFree(synth_theta_buf);
         synth_kappa_buf = nullptr;
         synth_theta_buf = nullptr;
         synth_kappa_cap = synth_theta_cap = 0;
-        cudaError_t e = cudaMalloc((void**)&synth_kappa_buf, need_k * 4);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&synth_theta_buf, need_t * 2);
+        cudaError_t e = cudaMalloc((void**)&synth_kappa_buf, cap_k * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&synth_theta_buf, cap_t * 2);
         if (e != cudaSuccess) return fail(SMC_ENOMEM, "synthesis buffers for %d particles: %s", n, cudaGetErrorString(e));
-        synth_kappa_cap = need_k;
-        synth_theta_cap = need_t;
+        synth_kappa_cap = cap_k;
+        synth_theta_cap = cap_t;
     }
     const size_t need_p = G > 1 ? (size_t)G * n * E : 0;   // FP32 partials of the term groups
     if (need_p > synth_part_cap) {
@@ -179,6 +182,13 @@ int Handle::synth_kappa(int level, int n, const double* theta, cudaStream_t st) 
         if (e == cudaSuccess) e = cudaMemset(synth_err, 0, 4);
         if (e != cudaSuccess) return fail(SMC_ENOMEM, "synthesis flag");
     }
+    return SMC_OK;
+}
+
+int Handle::synth_kappa(int level, int n, const double* theta, cudaStream_t st) {
+    const Level& L = levels[level];
+    const int E = 2 * L.N * L.N, Kt = kl_split_total(K), G = kl_groups(K);
+    RC_CHECK(synth_reserve(level, n));
     if (G == 1) {
         const long long work = (long long)n * Kt;
         theta_split_kernel<<<(int)((work + 255) / 256), 256, 0, st>>>(
