@@ -495,6 +495,7 @@ __device__ __forceinline__ void resample_gather_blocks(
     }
     __syncthreads();
     for (int j = j0 + tid; j < j1; j += kRsThreads) cdf[j] = j == n - 1 ? 1.0 : (cdf[j] + off_s) * inv_s;
+    __syncthreads();   // every thread's entries written before thread 0 arrives at the grid barrier
     if (tid == 0) ok_s = grid_barrier(bar, err, nb, generation);
     __syncthreads();
     if (!ok_s) return;
@@ -509,6 +510,7 @@ __device__ __forceinline__ void resample_gather_blocks(
         }
         anc[i] = lo;
     }
+    __syncthreads();
     if (tid == 0) ok_s = grid_barrier(bar, err, nb, generation);
     __syncthreads();
     if (!ok_s) return;
