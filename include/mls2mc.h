@@ -103,7 +103,9 @@ typedef struct {
     int precision;             /* SMC_FP64 or SMC_MIXED */
     uint64_t seed;             /* Philox4x32-10 key */
     int max_iter;              /* cap on inner CG iterations per refinement pass */
-    double rtol;               /* FP64 relative residual target of each forward solve */
+    double rtol;               /* relative residual target of each forward solve (<= 0: 1e-13 on the FP64
+                                  path, 2e-7 on the mixed path, where the solve's share of the G error is
+                                  then below 1e-8; the KL synthesis in BF16 splits dominates it) */
     int surrogate;             /* 0: plain pCN; 1: delayed-acceptance pCN screened by the surrogate network on
                                   the levels where an exact solve costs more than 8 surrogate passes (measured);
                                   2: screen on every level */

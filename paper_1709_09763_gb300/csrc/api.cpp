@@ -324,7 +324,7 @@ int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** 
     h->precision = O->precision;
     h->opts = *O;
     h->stream = (cudaStream_t)O->stream;
-    h->rtol = O->rtol > 0 ? O->rtol : (O->precision == SMC_MIXED ? 1e-8 : 1e-13);
+    h->rtol = O->rtol > 0 ? O->rtol : (O->precision == SMC_MIXED ? 2e-7 : 1e-13);
     h->max_iter = O->max_iter > 0 ? O->max_iter : 100;
     h->y_host.assign(P->y, P->y + P->n_obs);
     cudaError_t e = upload(&h->d_y, P->y, (size_t)P->n_obs);

@@ -278,7 +278,7 @@ bool Handle::da_worth(int level) {
 // small GEMMs of a step are latency-bound, so few large steps train for less than many small ones
 int Handle::maybe_train(int level) {
     if (!opts.surrogate || forward_kind != SMC_FWD_FEM) return SMC_OK;
-    if ((int)mlps.size() <= level || !mlps[level].ready) return SMC_OK;
+    if ((int)mlps.size() <= level) return SMC_OK;
     Mlp& M = mlps[level];
     if (M.count < smp->J) return SMC_OK;
     if (M.t > 0 && smp->pairs_new[level] < 4LL * smp->J) return SMC_OK;
@@ -290,6 +290,12 @@ int Handle::maybe_train(int level) {
     RC(mlp_train(level, steps, batch, &loss));
     smp->pairs_new[level] = 0;
     return SMC_OK;
+}
+
+// whether the moves of a target on level (and level + 1 when bridging, zeta >= 0) can be screened:
+// every level involved is worth it (its gate is measured here if it is still open)
+bool Handle::may_screen(int level, double zeta) {
+    return opts.surrogate && forward_kind == SMC_FWD_FEM && da_worth(level) && (zeta < 0.0 || da_worth(level + 1));
 }
 
 bool Handle::da_ready(int level, double zeta) const {
@@ -354,7 +360,7 @@ const double* Handle::next_param_device() const {
 // bridging target on level, level+1
 int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, IncState* pending) {
     // networks are trained only for targets whose every level is worth screening
-    if (opts.surrogate && forward_kind == SMC_FWD_FEM && da_worth(level) && (zeta < 0.0 || da_worth(level + 1))) {
+    if (may_screen(level, zeta)) {
         RC(maybe_train(level));
         if (zeta >= 0.0) RC(maybe_train(level + 1));
     }
@@ -467,14 +473,14 @@ void Handle::record(int type, double zeta, const IncState& st, double rate, doub
 
 // The plain sampler does not wait for the increment search: the pCN accept reads the new beta
 // from the device and the search state comes back with the update's counters (one host wait per
-// update). With the surrogate the host needs beta earlier (screening), so it waits.
+// update). Where the surrogate may screen the moves, the host needs beta earlier, so it waits.
 int Handle::tempering_update(int level, double beta0, int n_mcmc, smc_stage_info* info) {
     Sampler* S = smp;
     RC(smp_eval(level, S->J, S->theta, S->phi_c));
     IncState st;
     const double log_z = S->log_z, beta = S->beta, step0 = S->step;
     const int nm = opts.n_mcmc;
-    const bool wait = opts.surrogate != 0;
+    const bool wait = may_screen(level, -1.0);
     S->beta = beta0;
     RC(reweight_resample(S->phi_c, 1.0 - beta0, beta0, false, st, wait));
     if (wait) S->beta = st.next;
@@ -554,7 +560,7 @@ int Handle::bridging_update(int level, double beta, double zeta0, int n_mcmc, sm
 int Handle::itu(double cv_lu, smc_stage_info* info) {
     Sampler* S = smp;
     IncState st;
-    const bool wait = opts.surrogate != 0;
+    const bool wait = may_screen(S->level, -1.0);
     RC(reweight_resample(S->phi_c, 1.0 - S->beta, S->beta, false, st, wait));
     if (wait) S->beta = st.next;
     double rate = 0.0;

@@ -690,6 +690,9 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
     Real r[NPT], d[NPT], z[NPT], pv[NPT];
     const Real bnorm2 = FC ? bflow : (RHS && a.rhs) ? Real(a.bnorm2) : Real(NI) * h2 * h2;
     const Real stop_outer = Real(a.rtol * a.rtol) * bnorm2;
+    // an inner pass ends at its relative reduction or once its residual is below half the outer
+    // target, whichever comes first (the last pass then stops where the solve is done)
+    const Real stop_last = Real(0.25 * a.rtol * a.rtol) * bnorm2;
     const Real rtol_in2 = Real(a.rtol_in * a.rtol_in);
     int parity = 0;
     int total_it = 0;
@@ -713,7 +716,7 @@ __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Re
         block_sum<T>(rr0, red_buf[parity]);
         parity ^= 1;
         if (!(rr0 > Real(0))) break;
-        const Real stop2 = rtol_in2 * rr0;
+        const Real stop2 = fmax(rtol_in2 * rr0, stop_last);
         Real rz = 0;
         for (int it = 0; it < a.max_inner; ++it) {
             // z = M^{-1} r: V(1,1) cycle with the fine rhs held in registers (red pre-sweep
@@ -1011,6 +1014,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
     __syncthreads();
     const Real bnorm2 = FC ? bflow : a.rhs ? Real(a.bnorm2) : Real(NI) * h2 * h2;
     const Real stop_outer = Real(a.rtol * a.rtol) * bnorm2;
+    const Real stop_last = Real(0.25 * a.rtol * a.rtol) * bnorm2;   // as in solve_particle
     const Real rtol_in2 = Real(a.rtol_in * a.rtol_in);
     int parity = 0, total_it = 0;
     bool converged = false;
@@ -1031,7 +1035,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
         block_sum<T>(rr0, red_buf[parity]);
         parity ^= 1;
         if (!(rr0 > Real(0))) break;
-        const Real stop2 = rtol_in2 * rr0;
+        const Real stop2 = fmax(rtol_in2 * rr0, stop_last);
         Real rz = 0;
         for (int it = 0; it < a.max_inner; ++it) {
             for (int k = tid; k < colour_positions<N, FC>(); k += T) {   // black pre-sweep

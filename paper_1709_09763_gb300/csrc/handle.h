@@ -81,6 +81,7 @@ struct Handle {
     std::vector<Mlp> mlps;
     MlpWork mwork;
     float mlp_lr = 1e-3f;
+    int mlp_ring(int level);
     int mlp_setup(int level);
     int mlp_sync_bf16(int level);
     int mlp_work(int B);
@@ -119,6 +120,7 @@ struct Handle {
     int maybe_train(int level);
     bool da_ready(int level, double zeta) const;
     bool da_worth(int level);
+    bool may_screen(int level, double zeta);
     std::vector<int> da_gate;   // per level: 0 unknown, 1 screen pays, -1 it does not
     std::vector<float> da_t_solve, da_t_pred;   // per level: the gate's measured device times (ms)
     struct DaSolveEvents {

@@ -220,8 +220,24 @@ int grid_of(long long n, int t) { return (int)((n + t - 1) / t); }
 // ---- host side ---------------------------------------------------------------------------------
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-int Handle::mlp_setup(int level) {
+// the ring of training pairs of a level (two buffers, nothing initialised: count says what is valid);
+// collecting pairs needs nothing else, so a level whose screen is never used costs two allocations
+int Handle::mlp_ring(int level) {
     if ((int)mlps.size() < (int)levels.size()) mlps.resize(levels.size());
+    Mlp& S = mlps[level];
+    if (S.ring_th) return SMC_OK;
+    const int cap = std::max(4 * std::max(opts.J, 1), 8192);
+    cudaError_t e = cudaMalloc((void**)&S.ring_th, (size_t)cap * K * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&S.ring_G, (size_t)cap * n_obs * 8);
+    if (e != cudaSuccess) return fail(SMC_ENOMEM, "surrogate pair ring: %s", cudaGetErrorString(e));
+    S.cap = cap;
+    return SMC_OK;
+}
+
+// the network of a level: weights (He-normal from the library's Philox stream), Adam state,
+// standardisation; set up on first training or prediction
+int Handle::mlp_setup(int level) {
+    RC_CHECK(mlp_ring(level));
     Mlp& S = mlps[level];
     if (S.ready) return SMC_OK;
     S.d[0] = round_up(K, 8);
@@ -247,9 +263,6 @@ int Handle::mlp_setup(int level) {
     }
     A((void**)&S.mu, (size_t)S.d[5] * 4);
     A((void**)&S.sd, (size_t)S.d[5] * 4);
-    S.cap = std::max(4 * std::max(opts.J, 1), 8192);
-    A((void**)&S.ring_th, (size_t)S.cap * K * 8);
-    A((void**)&S.ring_G, (size_t)S.cap * n_obs * 8);
     A((void**)&S.err, 4);
     if (e != cudaSuccess) return fail(SMC_ENOMEM, "surrogate buffers: %s", cudaGetErrorString(e));
     // He-normal initial weights from the library's Philox stream (purpose 7, event = level * 8 + layer)
@@ -450,7 +463,7 @@ int Handle::mlp_adam(int level) {
 }
 
 int Handle::mlp_add_pairs(int level, int n, const double* theta, const double* G) {
-    RC_CHECK(mlp_setup(level));
+    RC_CHECK(mlp_ring(level));
     Mlp& S = mlps[level];
     if (n <= 0) return SMC_OK;
     if (n > S.cap) {   // keep the most recent cap pairs

@@ -4,7 +4,9 @@ tests/golden/quad_k2_h16.json holds the exact posterior mean and variance of the
 problem on 1/h = 16 (oracle FEM, trapezoid grid, grid error ~1e-11). R seeded replicates of the
 mixed-precision MLS^2MC sampler (levels 1/8, 1/16), plain and with the surrogate screen forced on
 every level, must give replicate-averaged posterior means and variances within 3 Monte Carlo
-standard errors of it (the standard error estimated from the replicate spread)."""
+standard errors of it (the standard error estimated from the replicate spread). With R = 32 the
+deviation over its estimated standard error follows Student's t with 31 degrees of freedom: a
+correct sampler exceeds 3 in one of the four comparisons of a run with probability 2.1 %."""
 import json
 import os
 
@@ -26,7 +28,7 @@ def built():
 @pytest.mark.parametrize("surrogate", [0, 2])
 def test_sampler_matches_quadrature_within_3_se(surrogate):
     q = json.load(open(GOLD))
-    R = 16
+    R = 32
     means, vars_ = [], []
     for r in range(R):
         h = native.Handle([8, 16], 2, np.array(q["obs"]), q["y"], q["sigma"], corr_len=q["corr_len"], J=2000,

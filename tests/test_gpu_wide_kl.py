@@ -12,6 +12,7 @@ import pytest
 from oracle import fem as ofem
 from oracle import forward as ofwd
 from oracle import matern as omat
+from oracle import smc
 from oracle.forward import potential
 from paper_1709_09763_gb300 import native
 from paper_1709_09763_gb300 import workloads as wl
@@ -85,4 +86,39 @@ def test_example_5_3_full_mls2mc_run(setup):
     assert path and all(0.0 <= p["accept_rate"] <= 1.0 for p in path)
     mean, var, log_z = h.posterior_moments()
     assert mean.shape == (W.K,) and np.all(np.isfinite(mean)) and np.all(var > 0) and np.isfinite(log_z)
+    h.close()
+
+
+def test_320_term_mls2mc_path_equals_oracle_sampler(setup):
+    """The 320-term flow cell on the levels 1/16, 1/32, 1/64 with J = 100, one random-walk step per
+    update, scheme u' (Sec. 4.5): the mixed-precision sampler takes the oracle sampler's update path
+    (kinds, beta, zeta, increments within the mixed path's 1e-6 potential error), the same evaluation
+    counts per level, and the same particles (the draws are shared, so equal accept decisions give
+    equal rows)."""
+    _, d, obs = setup
+    y, sigma = np.array(d["y"]), d["sigma"]
+    levels = (16, 32, 64)
+    J = 100
+    kw = dict(J_tilde=32, n_mcmc=1, s_pcn=2.38 / math.sqrt(W.K), seed=W.seed_sampler)
+    h = native.Handle(list(levels), W.K, obs, y, sigma, corr_len=W.corr_len, J=J, precision=native.SMC_MIXED,
+                      cov="matern", bc="flow_cell", proposal="rwm", tau_min=W.tau_min, **kw)
+    h.run()
+    lv = [ofwd.Level(N, W.corr_len, 1.0, W.K, obs, cov="matern", bc="flow_cell") for N in levels]
+    o = smc.Sampler(lambda l, th: potential(lv[l].G_batch(th), y, sigma), len(levels), W.K, J, proposal="rwm",
+                    tau_min=W.tau_min, **kw).run()
+    gp = h.path()
+    assert len(gp) == len(o.path) and len(gp) >= 6
+    assert any(r["kind"] == "LU" for r in o.path)
+    for g, r in zip(gp, o.path):
+        assert g["kind"] == r["kind"]
+        assert g["beta"] == pytest.approx(r["beta"], rel=1e-4, abs=1e-6)
+        assert g["delta"] == pytest.approx(r["delta"], rel=1e-4, abs=1e-6)
+        if r["kind"] == "LU":
+            assert g["zeta"] == pytest.approx(r["zeta"], rel=1e-4, abs=1e-6)
+    st = h.state()
+    assert st["evals"][:3] == list(o.evals)
+    assert st["level"] == o.level and st["beta"] == 1.0
+    th, _ = h.particles()
+    assert np.allclose(th, o.theta, rtol=1e-9, atol=1e-9)
+    assert h.posterior_moments()[2] == pytest.approx(o.log_z, rel=1e-5)
     h.close()
