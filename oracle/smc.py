@@ -16,7 +16,9 @@ Pieces and where they come from:
                           (systematic) is not fixed by the paper
   Markov kernel           Sec. 5 uses one random-walk Metropolis step; here the
                           preconditioned Crank-Nicolson proposal the paper names as
-                          the better choice in high dimension (Cotter et al. 2013)
+                          the better choice in high dimension (Cotter et al. 2013),
+                          that random walk, and (not in the paper) a random walk
+                          whose covariance is the particle population's
   update scheme           Sec. 4.4, Eq. eq_updatescheme_final with the cv^LU
                           predictor on J~ particles (Sec. 4.4)
 """
@@ -96,6 +98,26 @@ def rwm_propose(theta, xi, s):
     return theta + s * xi
 
 
+def population_chol(theta, ridge=1e-4):
+    """Lower Cholesky factor L of the covariance-shaped random walk's proposal covariance (not in
+    the paper, whose random walk has covariance s^2 I): the covariance of the particle population,
+    C = (1/J) sum_j (theta_j - mean)(theta_j - mean)^T, plus ridge * (tr C / K + 1e-12) I, which
+    keeps it positive definite when the population spans fewer than K directions (the 1e-12, far
+    below any spread of a prior N(0, I) sample, covers a population of identical particles, whose C
+    is rounding noise). It is formed from the population before an update's moves, so every move of
+    the update uses the same symmetric proposal and leaves the update's target invariant."""
+    J, K = theta.shape
+    d = theta - theta.mean(axis=0)
+    C = d.T @ d / J
+    C = C + ridge * (np.trace(C) / K + 1e-12) * np.eye(K)
+    return np.linalg.cholesky(C)
+
+
+def rwm_cov_propose(theta, xi, s, L):
+    """theta' = theta + s L xi for every row (the covariance-shaped random walk)."""
+    return theta + s * (xi @ L.T)
+
+
 def log_prior_ratio(theta_new, theta):
     """log mu0(theta') - log mu0(theta) for mu0 = N(0, I), one value per row."""
     return -0.5 * (np.sum(theta_new * theta_new, axis=1) - np.sum(theta * theta, axis=1))
@@ -122,8 +144,8 @@ class Sampler:
         self.tau_lu = tau_star if tau_lu is None else tau_lu
         self.eps = eps
         self.s = s_pcn
-        if proposal not in ("pcn", "rwm"):
-            raise ValueError("proposal must be 'pcn' or 'rwm'")
+        if proposal not in ("pcn", "rwm", "rwm_cov"):
+            raise ValueError("proposal must be 'pcn', 'rwm' or 'rwm_cov'")
         self.proposal = proposal
         self.tau_min = tau_min         # > 0: the scheme u' of Sec. 4.5 (adaptive maximum level)
         # > 0: the Markov kernel's step adapts between updates, s <- s exp(a - accept_target) with a
@@ -174,6 +196,8 @@ class Sampler:
         phi_t, caches = target(None)
         s = self.step_size if self.accept_target > 0.0 else self.s
         self.last_step = s
+        # the covariance-shaped walk takes its covariance from the population before the moves
+        L = population_chol(self.theta) if self.proposal == "rwm_cov" else None
         for _ in range(self.n_mcmc):
             xi = philox.normals(self.J, self.K, self.mcmc_event, philox.PURPOSE_PCN_XI, self.seed)
             u = philox.uniforms_open(self.J, self.mcmc_event, philox.PURPOSE_PCN_U, self.seed)
@@ -181,8 +205,8 @@ class Sampler:
                 prop = pcn_propose(self.theta, xi, s)
                 phi_t_new, caches_new = target(prop)
                 ok = np.log(u) < -(phi_t_new - phi_t)
-            else:   # random walk: the prior ratio enters the acceptance
-                prop = rwm_propose(self.theta, xi, s)
+            else:   # random walks: the prior ratio enters the acceptance
+                prop = rwm_propose(self.theta, xi, s) if L is None else rwm_cov_propose(self.theta, xi, s, L)
                 phi_t_new, caches_new = target(prop)
                 ok = np.log(u) < -(phi_t_new - phi_t) + log_prior_ratio(prop, self.theta)
             self.theta[ok] = prop[ok]
@@ -193,7 +217,7 @@ class Sampler:
             self.mcmc_event += 1
         rate = acc / (self.n_mcmc * self.J) if self.n_mcmc > 0 else 0.0
         if self.accept_target > 0.0:
-            hi = 100.0 if self.proposal == "rwm" else 1.0
+            hi = 1.0 if self.proposal == "pcn" else 100.0
             self.step_size = min(hi, max(1e-4, self.step_size * math.exp(rate - self.accept_target)))
         return rate
 
