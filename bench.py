@@ -18,6 +18,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|refere
 import argparse
 import dataclasses
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -726,10 +727,11 @@ def main():
                                       "rel_misfit_mean": float(np.mean(st["rel_misfit_posterior_mean"]))})
                 res["cost_vs_accuracy"] = table
             return res
-        def large_study(R=3):
+        def large_study(R=4):
             """The large workload (5 levels 1/16 .. 1/256, K = 128, 144 interpolated observations, J =
-            16384, 10 pCN steps): the prescribed step s = 0.2 against the adaptive step (accept_target
-            0.25), plain and screened; per update the acceptance rate, the distinct ancestors its
+            16384, 10 Markov steps): pCN with the prescribed step s = 0.2 against pCN with the adaptive
+            step (accept_target 0.25) and the covariance-shaped random walk (first step 2.38 / sqrt(K),
+            adaptive), plain and screened; per update the acceptance rate, the distinct ancestors its
             resampling kept and the step; across replicates the spread of the posterior means and of
             log Z, and the largest |z| between the arms' replicate means."""
             wk, dk = wl.WORKLOADS["large_mixed_h16_256"], load_data("large_mixed_h16_256")
@@ -737,15 +739,19 @@ def main():
             out = {"workload": wk.name, "levels_inv_h": list(wk.inv_h), "K": wk.K, "J": wk.J, "n_mcmc": wk.n_mcmc,
                    "replicates": R}
             means = {}
-            for label, sur, target in (("prescribed_step", 0, 0.0), ("adaptive_step", 0, 0.25),
-                                       ("adaptive_step_screened", 1, 0.25)):
+            s_cov = 2.38 / math.sqrt(wk.K)
+            for label, sur, target, prop, s0 in (("prescribed_step", 0, 0.0, "pcn", wk.s_pcn),
+                                                 ("adaptive_step", 0, 0.25, "pcn", wk.s_pcn),
+                                                 ("adaptive_step_screened", 1, 0.25, "pcn", wk.s_pcn),
+                                                 ("covariance_walk", 0, 0.25, "rwm_cov", s_cov),
+                                                 ("covariance_walk_screened", 1, 0.25, "rwm_cov", s_cov)):
                 runs = []
                 for r in range(R):
                     hr = native.Handle(list(wk.inv_h), wk.K, ob, dk["y"], dk["sigma"], corr_len=wk.corr_len,
-                                       J=wk.J, J_tilde=wk.J_tilde, n_mcmc=wk.n_mcmc, s_pcn=wk.s_pcn,
+                                       J=wk.J, J_tilde=wk.J_tilde, n_mcmc=wk.n_mcmc, s_pcn=s0,
                                        tau_star=wk.tau_star, precision=native.SMC_MIXED,
                                        seed=wk.seed_sampler + 1000 * rank + 17 * r, stream=stream.cuda_stream,
-                                       surrogate=sur, accept_target=target)
+                                       surrogate=sur, accept_target=target, proposal=prop)
                     torch.cuda.synchronize(dev)
                     t0 = time.perf_counter()
                     hr.run()
@@ -775,10 +781,31 @@ def main():
             def zmax(a, b):
                 se = np.sqrt(a.var(axis=0, ddof=1) / len(a) + b.var(axis=0, ddof=1) / len(b))
                 return float(np.max(np.abs(a.mean(0) - b.mean(0)) / np.where(se > 0, se, np.inf)))
+
+            def welch(a, b, fwer=0.05):
+                """Largest Welch t over the K coordinates of two arms' replicate means, its coordinate's
+                degrees of freedom, and the critical value of a family-wise false-alarm rate fwer
+                (Bonferroni over K, two-sided) at those degrees of freedom."""
+                from scipy.stats import t as student_t
+                va, vb = a.var(axis=0, ddof=1) / len(a), b.var(axis=0, ddof=1) / len(b)
+                tv = np.abs(a.mean(0) - b.mean(0)) / np.sqrt(va + vb)
+                k = int(np.argmax(tv))
+                dof = (va[k] + vb[k]) ** 2 / (va[k] ** 2 / (len(a) - 1) + vb[k] ** 2 / (len(b) - 1))
+                crit = float(student_t.ppf(1.0 - fwer / (2 * a.shape[1]), dof))
+                return {"t_max": float(tv[k]), "dof": float(dof), "critical": crit, "agree": bool(tv[k] < crit)}
             out["z_max_adaptive_vs_prescribed"] = zmax(means["adaptive_step"], means["prescribed_step"])
             out["z_max_screened_vs_plain_adaptive"] = zmax(means["adaptive_step_screened"], means["adaptive_step"])
             out["speedup_screened_vs_plain_adaptive"] = (out["adaptive_step"]["seconds_median"] /
                                                         out["adaptive_step_screened"]["seconds_median"])
+            out["z_max_covariance_walk_screened_vs_plain"] = zmax(means["covariance_walk_screened"],
+                                                                  means["covariance_walk"])
+            out["z_max_covariance_walk_vs_adaptive_pcn"] = zmax(means["covariance_walk"], means["adaptive_step"])
+            out["speedup_covariance_walk_screened_vs_plain"] = (out["covariance_walk"]["seconds_median"] /
+                                                               out["covariance_walk_screened"]["seconds_median"])
+            out["welch_covariance_walk_screened_vs_plain"] = welch(means["covariance_walk_screened"],
+                                                                   means["covariance_walk"])
+            out["welch_adaptive_pcn_screened_vs_plain"] = welch(means["adaptive_step_screened"], means["adaptive_step"])
+            out["welch_covariance_walk_vs_adaptive_pcn"] = welch(means["covariance_walk"], means["adaptive_step"])
             return out
 
         # single-level SMC on the FP64 path (h = 1/16, K = 16, J = 1000, 5 pCN steps)

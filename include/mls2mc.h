@@ -72,6 +72,11 @@ extern "C" {
 #define SMC_PROP_PCN    0  /* theta' = sqrt(1 - s^2) theta + s xi */
 #define SMC_PROP_RWM    1  /* theta' = theta + s xi (random walk of Sec. 5; s^2 = 2.38^2 / K there),
                               accepted with the prior ratio N(0, I) included */
+#define SMC_PROP_RWM_COV 2 /* theta' = theta + s L xi, accepted as SMC_PROP_RWM: a random walk shaped by
+                              the particle population (not in the paper). Before each update's moves,
+                              L L^T = C + 1e-4 (tr C / K + 1e-12) I with C the covariance of the
+                              population (1/J normalisation); every move of the update uses the same L,
+                              so each leaves its target invariant. Not run by the batched sampler */
 
 typedef struct {
     int n_levels;              /* N_L >= 1 */
@@ -112,8 +117,9 @@ typedef struct {
     int surrogate_train_steps; /* Adam steps of the first training round of a level (<= 0: 25; later rounds 1/4) */
     int surrogate_batch;       /* training minibatch, at most the pairs held (<= 0: 8192) */
     void* stream;              /* cudaStream_t used for all work, or NULL for the default stream */
-    int proposal;              /* SMC_PROP_PCN (0, the default) or SMC_PROP_RWM (step s = s_pcn); with the
-                                  surrogate screen the prior ratio enters stage 1 */
+    int proposal;              /* SMC_PROP_PCN (0, the default), SMC_PROP_RWM or SMC_PROP_RWM_COV (step
+                                  s = s_pcn); with the surrogate screen the prior ratio of the random
+                                  walks enters stage 1 */
     double tau_min;            /* > 0: update scheme u' of Sec. 4.5 (Eq. eq_updatescheme_final_Lmax):
                                   at beta = 1 the level update is assessed by cv^LU on the first
                                   J_tilde particles and the run stops on the current level when it is

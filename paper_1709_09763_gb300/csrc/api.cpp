@@ -284,7 +284,8 @@ int smc_init(const smc_problem_desc* P, const smc_sampler_opts* O, smc_handle** 
         return bail(h->fail(SMC_EINVAL, "linear_A required for SMC_FWD_LINEAR"));
     if (O->precision != SMC_FP64 && O->precision != SMC_MIXED) return bail(h->fail(SMC_EINVAL, "unknown precision"));
     if (O->J < 0) return bail(h->fail(SMC_EINVAL, "J must be >= 0"));
-    if (O->proposal != SMC_PROP_PCN && O->proposal != SMC_PROP_RWM) return bail(h->fail(SMC_EINVAL, "unknown proposal"));
+    if (O->proposal != SMC_PROP_PCN && O->proposal != SMC_PROP_RWM && O->proposal != SMC_PROP_RWM_COV)
+        return bail(h->fail(SMC_EINVAL, "unknown proposal"));
     if (!(O->accept_target >= 0.0 && O->accept_target < 1.0))
         return bail(h->fail(SMC_EINVAL, "accept_target must be in [0, 1)"));
     if (P->forward_kind == SMC_FWD_FEM) {

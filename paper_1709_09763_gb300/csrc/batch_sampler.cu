@@ -235,9 +235,11 @@ int batch_step(Batch* b, smc_stage_info* infos) {
     for (int p = 0; p < P; ++p) {
         Handle* h = b->h[p];
         if (!h->smp) return bfail(b, SMC_EINVAL, "problem " + std::to_string(p) + ": handle created with J = 0");
-        if (h->forward_kind != SMC_FWD_FEM || h->flow_cell || h->opts.surrogate)
+        if (h->forward_kind != SMC_FWD_FEM || h->flow_cell || h->opts.surrogate ||
+            h->opts.proposal == SMC_PROP_RWM_COV)
             return bfail(b, SMC_EINVAL, "problem " + std::to_string(p) +
-                                            ": the batched sampler runs the plain sampler of the Dirichlet problem");
+                                            ": the batched sampler runs the plain sampler of the Dirichlet problem "
+                                            "(pCN or the random walk)");
         if (h->stream != st) return bfail(b, SMC_EINVAL, "all handles of a batched sampler must share one stream");
     }
     if (!b->smp) {

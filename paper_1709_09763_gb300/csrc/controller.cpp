@@ -67,6 +67,12 @@ int Handle::alloc_sampler() {
         A((void**)&smp->da_pass, (size_t)J * 4);
         A((void**)&smp->n_surv, 4);
     }
+    if (opts.proposal == SMC_PROP_RWM_COV) {
+        A((void**)&smp->cmean, (size_t)K * 8);
+        A((void**)&smp->cpart, pop_cov_partial_doubles(J, K) * 8);
+        A((void**)&smp->cov, (size_t)K * K * 8);
+        A((void**)&smp->chol, (size_t)K * K * 8);
+    }
     if (e == cudaSuccess) e = cudaMemset(smp->n_acc, 0, 16);
     if (e != cudaSuccess) return fail(SMC_ENOMEM, "sampler buffers for J = %d: %s", J, cudaGetErrorString(e));
     return SMC_OK;
@@ -81,7 +87,7 @@ void Handle::free_sampler() {
                     (void*)smp->inc.partials, (void*)smp->inc.bar, (void*)smp->G_buf, (void*)smp->ps_c, (void*)smp->ps_f,
                     (void*)smp->psp_c, (void*)smp->psp_f, (void*)smp->theta_s, (void*)smp->phi_cs,
                     (void*)smp->phi_fs, (void*)smp->surv_idx, (void*)smp->n_surv,
-                    (void*)smp->da_pass})
+                    (void*)smp->da_pass, (void*)smp->cmean, (void*)smp->cpart, (void*)smp->cov, (void*)smp->chol})
         cudaFree(p);
     delete smp;
     smp = nullptr;
@@ -162,7 +168,7 @@ unsigned* Handle::distinct_counter() { return reinterpret_cast<unsigned*>(reinte
 double Handle::mcmc_step() const { return opts.accept_target > 0.0 ? smp->step : opts.s_pcn; }
 void Handle::adapt_step(double rate) {
     if (!(opts.accept_target > 0.0)) return;
-    const double hi = opts.proposal == SMC_PROP_RWM ? 100.0 : 1.0;
+    const double hi = opts.proposal == SMC_PROP_PCN ? 1.0 : 100.0;
     smp->step = std::min(hi, std::max(1e-4, smp->step * std::exp(rate - opts.accept_target)));
 }
 
@@ -356,6 +362,49 @@ const double* Handle::next_param_device() const {
     return reinterpret_cast<const double*>(reinterpret_cast<const char*>(smp->inc.state) + offsetof(IncState, next));
 }
 
+// the proposals of one Markov step into theta_p: pCN sqrt(1 - s^2) theta + s xi, the random walk
+// theta + s xi, or the covariance-shaped walk theta + s L xi (xi from the library's Philox layout)
+int Handle::propose(uint32_t ev, double s) {
+    Sampler* S = smp;
+    if (opts.proposal == SMC_PROP_RWM_COV) {
+        CK(normals_launch(S->theta_p, S->J, K, ev, kPurposePcnXi, opts.seed, nullptr, 0.0, 0.0, stream));
+        CK(cov_step_launch(S->theta, S->theta_p, S->chol, S->J, K, s, stream));
+        return SMC_OK;
+    }
+    const double c0 = opts.proposal == SMC_PROP_RWM ? 1.0 : std::sqrt(1.0 - s * s);
+    CK(normals_launch(S->theta_p, S->J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
+    return SMC_OK;
+}
+
+// the covariance-shaped walk's factor L for the coming moves (not in the paper): L L^T = C +
+// 1e-4 (tr C / K + 1e-12) I with C the covariance of the population before the moves, computed on
+// the device (FP64, fixed summation order), factored on the host (Cholesky, FP64) and sent back
+int Handle::shape_factor() {
+    Sampler* S = smp;
+    CK(pop_cov_launch(S->theta, S->J, K, S->cmean, S->cpart, S->cov, stream));
+    std::vector<double> C((size_t)K * K), L((size_t)K * K, 0.0);
+    CK(cudaMemcpyAsync(C.data(), S->cov, C.size() * 8, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    double tr = 0.0;
+    for (int k = 0; k < K; ++k) tr += C[(size_t)k * K + k];
+    const double ridge = 1e-4 * (tr / K + 1e-12);
+    for (int k = 0; k < K; ++k) C[(size_t)k * K + k] += ridge;
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double v = C[(size_t)i * K + j];
+            for (int k = 0; k < j; ++k) v -= L[(size_t)i * K + k] * L[(size_t)j * K + k];
+            if (i == j) {
+                if (!(v > 0.0)) return fail(SMC_ESINGULAR, "population covariance is not positive definite");
+                L[(size_t)i * K + i] = std::sqrt(v);
+            } else {
+                L[(size_t)i * K + j] = v / L[(size_t)j * K + j];
+            }
+        }
+    CK(cudaMemcpyAsync(S->chol, L.data(), L.size() * 8, cudaMemcpyHostToDevice, stream));
+    CK(cudaStreamSynchronize(stream));   // L's host storage is released on return
+    return SMC_OK;
+}
+
 // n_mcmc pCN (or random-walk) Metropolis steps; zeta < 0: tempering target on `level`, else
 // bridging target on level, level+1
 int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, IncState* pending) {
@@ -366,15 +415,16 @@ int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, Inc
     }
     if (da_ready(level, zeta)) return mcmc_da(level, zeta, rate);
     Sampler* S = smp;
-    const bool rwm = opts.proposal == SMC_PROP_RWM;
-    const double s = mcmc_step(), c0 = rwm ? 1.0 : std::sqrt(1.0 - s * s);
+    const bool rwm = opts.proposal != SMC_PROP_PCN;
+    const double s = mcmc_step();
     last_step = s;
+    if (opts.proposal == SMC_PROP_RWM_COV) RC(shape_factor());
     CK(cudaMemsetAsync(S->n_acc, 0, 8, stream));
     for (int m = 0; m < opts.n_mcmc; ++m) {
         const uint32_t ev = (uint32_t)S->mcmc_event;
         {
             PhaseTimer pt(this, kPhMove);
-            CK(normals_launch(S->theta_p, S->J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
+            RC(propose(ev, s));
         }
         RC(smp_eval(level, S->J, S->theta_p, S->phi_cp));
         if (zeta >= 0.0) RC(smp_eval(level + 1, S->J, S->theta_p, S->phi_fp));
@@ -397,9 +447,10 @@ int Handle::mcmc_da(int level, double zeta, double& rate) {
     Sampler* S = smp;
     const int J = S->J;
     const bool br = zeta >= 0.0;
-    const bool rwm = opts.proposal == SMC_PROP_RWM;
-    const double s = mcmc_step(), c0 = rwm ? 1.0 : std::sqrt(1.0 - s * s);
+    const bool rwm = opts.proposal != SMC_PROP_PCN;
+    const double s = mcmc_step();
     last_step = s;
+    if (opts.proposal == SMC_PROP_RWM_COV) RC(shape_factor());
     CK(cudaMemsetAsync(S->n_acc, 0, 8, stream));
     {
         PhaseTimer pt(this, kPhInfer);
@@ -411,7 +462,7 @@ int Handle::mcmc_da(int level, double zeta, double& rate) {
         const uint32_t ev = (uint32_t)S->mcmc_event;
         {
             PhaseTimer pt(this, kPhMove);
-            CK(normals_launch(S->theta_p, J, K, ev, kPurposePcnXi, opts.seed, S->theta, c0, s, stream));
+            RC(propose(ev, s));
         }
         {
             PhaseTimer pt(this, kPhInfer);

@@ -121,6 +121,8 @@ struct Handle {
     bool da_ready(int level, double zeta) const;
     bool da_worth(int level);
     bool may_screen(int level, double zeta);
+    int propose(uint32_t ev, double s);
+    int shape_factor();
     std::vector<int> da_gate;   // per level: 0 unknown, 1 screen pays, -1 it does not
     std::vector<float> da_t_solve, da_t_pred;   // per level: the gate's measured device times (ms)
     struct DaSolveEvents {

@@ -23,6 +23,8 @@ struct Sampler {
     double *G_buf = nullptr, *ps_c = nullptr, *ps_f = nullptr, *psp_c = nullptr, *psp_f = nullptr;
     double *theta_s = nullptr, *phi_cs = nullptr, *phi_fs = nullptr;
     int *surv_idx = nullptr, *n_surv = nullptr, *da_pass = nullptr;
+    // covariance-shaped random walk: population mean, covariance partials, covariance, its factor
+    double *cmean = nullptr, *cpart = nullptr, *cov = nullptr, *chol = nullptr;
     long long pairs_new[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long da_proposals = 0, da_pass1 = 0;
     // host-side state

@@ -172,5 +172,10 @@ cudaError_t count_bad_multi_launch(const std::vector<BadTask>& tasks, cudaStream
 // words (unsigned) to zero: (pointer, count) pairs
 cudaError_t zero_words_launch(const std::vector<std::pair<unsigned*, int>>& list, cudaStream_t st);
 cudaError_t moments_launch(const double* theta, int n, int K, double* mean, double* var, cudaStream_t st);
+// covariance-shaped random walk: the population covariance (scratch: mean K doubles, partials
+// pop_cov_partial_doubles(n, K) doubles) and the step out = theta + s L out (out holds xi on entry)
+size_t pop_cov_partial_doubles(int n, int K);
+cudaError_t pop_cov_launch(const double* theta, int n, int K, double* mean, double* part, double* cov, cudaStream_t st);
+cudaError_t cov_step_launch(const double* theta, double* out, const double* L, int n, int K, double s, cudaStream_t st);
 
 }  // namespace mls2mc

@@ -874,6 +874,86 @@ __global__ void moments_kernel(const double* theta, int n, int K, double* mean, 
     }
 }
 
+// ---- covariance-shaped random walk (not in the paper) ----------------------------------------
+// The population mean (one block per coordinate, fixed-order block sum).
+__global__ void pop_mean_kernel(const double* theta, int n, int K, double* mean) {
+    __shared__ double sh[32];
+    const int k = blockIdx.x;
+    double m[1] = {0.0};
+    for (int j = threadIdx.x; j < n; j += blockDim.x) m[0] += theta[(size_t)j * K + k];
+    block_reduce_sum<1>(m, sh);
+    if (threadIdx.x == 0) mean[k] = m[0] / n;
+}
+
+// Partial sums of (theta_j - mean)(theta_j - mean)^T over chunks of kCovRows particles: block
+// (tile pair, chunk) sums its rows in order for a 16 x 16 tile (a-tile <= b-tile) of the upper
+// triangle into part[chunk][a][b].
+constexpr int kCovTile = 16, kCovRows = 1024;
+__global__ void __launch_bounds__(256) pop_cov_partial_kernel(const double* theta, int n, int K, const double* mean,
+                                                              double* part) {
+    __shared__ double ta[32][kCovTile + 1], tb[32][kCovTile + 1];
+    const int nt = (K + kCovTile - 1) / kCovTile;
+    int pair = blockIdx.x, ai = 0;   // pair index -> (ai, bi) with ai <= bi
+    while (pair >= nt - ai) {
+        pair -= nt - ai;
+        ++ai;
+    }
+    const int bi = ai + pair;
+    const int chunk = blockIdx.y;
+    const int j0 = chunk * kCovRows, j1 = min(n, j0 + kCovRows);
+    const int tx = threadIdx.x % kCovTile, ty = threadIdx.x / kCovTile;   // entry (a0 + ty, b0 + tx)
+    const int a0 = ai * kCovTile, b0 = bi * kCovTile;
+    double acc = 0.0;
+    for (int jb = j0; jb < j1; jb += 32) {
+        // stage 32 rows of both tiles' coordinates, centred
+        for (int q = threadIdx.x; q < 32 * kCovTile; q += 256) {
+            const int r = q / kCovTile, c = q % kCovTile, j = jb + r;
+            const int ka = a0 + c, kb = b0 + c;
+            ta[r][c] = (j < j1 && ka < K) ? theta[(size_t)j * K + ka] - mean[ka] : 0.0;
+            tb[r][c] = (j < j1 && kb < K) ? theta[(size_t)j * K + kb] - mean[kb] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) acc = fma(ta[r][ty], tb[r][tx], acc);
+        __syncthreads();
+    }
+    const int a = a0 + ty, b = b0 + tx;
+    if (a < K && b < K && a <= b) part[((size_t)chunk * K + a) * K + b] = acc;
+}
+
+// C[a][b] = C[b][a] = (sum of the chunks' partials in chunk order) / n, for a <= b
+__global__ void pop_cov_finish_kernel(const double* part, int chunks, int n, int K, double* cov) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)K * K) return;
+    const int a = (int)(t / K), b = (int)(t - (long long)a * K);
+    if (a > b) return;
+    double s = 0.0;
+    for (int c = 0; c < chunks; ++c) s += part[((size_t)c * K + a) * K + b];
+    s /= n;
+    cov[(size_t)a * K + b] = s;
+    cov[(size_t)b * K + a] = s;
+}
+
+// theta'_j = theta_j + s L xi_j, xi_j read from and theta'_j written to out (row j): one warp per
+// particle, the row of xi staged in shared memory, lane k sums L[k][m] xi[m] for m <= k in order
+constexpr int kStepWarps = 4;
+__global__ void __launch_bounds__(32 * kStepWarps) cov_step_kernel(const double* theta, double* out,
+                                                                   const double* L, int n, int K, double s) {
+    extern __shared__ double xs[];   // [kStepWarps][K]
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * kStepWarps + w;
+    if (j >= n) return;              // whole warps leave together
+    double* x = xs + (size_t)w * K;
+    for (int k = lane; k < K; k += 32) x[k] = out[(size_t)j * K + k];
+    __syncwarp();
+    for (int k = lane; k < K; k += 32) {
+        const double* Lk = L + (size_t)k * K;
+        double acc = 0.0;
+        for (int m = 0; m <= k; ++m) acc = fma(Lk[m], x[m], acc);
+        out[(size_t)j * K + k] = fma(s, acc, theta[(size_t)j * K + k]);
+    }
+}
+
 }  // namespace
 
 // ---- launch wrappers ----------------------------------------------------------------------------
@@ -1144,6 +1224,28 @@ cudaError_t count_bad_multi_launch(const std::vector<BadTask>& tasks, cudaStream
                               count_launches(1);
                               return cudaGetLastError();
                           });
+}
+
+// population covariance of theta (n x K) into cov (K x K, symmetric); mean (K) and part
+// (pop_cov_partial_doubles(n, K)) are scratch
+size_t pop_cov_partial_doubles(int n, int K) { return (size_t)((n + kCovRows - 1) / kCovRows) * K * K; }
+
+cudaError_t pop_cov_launch(const double* theta, int n, int K, double* mean, double* part, double* cov, cudaStream_t st) {
+    if (n <= 0 || K <= 0) return cudaSuccess;
+    pop_mean_kernel<<<K, 256, 0, st>>>(theta, n, K, mean);
+    const int nt = (K + kCovTile - 1) / kCovTile, chunks = (n + kCovRows - 1) / kCovRows;
+    pop_cov_partial_kernel<<<dim3(nt * (nt + 1) / 2, chunks), 256, 0, st>>>(theta, n, K, mean, part);
+    pop_cov_finish_kernel<<<grid_for((long long)K * K, 256), 256, 0, st>>>(part, chunks, n, K, cov);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+cudaError_t cov_step_launch(const double* theta, double* out, const double* L, int n, int K, double s, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = (size_t)kStepWarps * K * sizeof(double);
+    cov_step_kernel<<<(n + kStepWarps - 1) / kStepWarps, 32 * kStepWarps, smem, st>>>(theta, out, L, n, K, s);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t moments_launch(const double* theta, int n, int K, double* mean, double* var, cudaStream_t st) {

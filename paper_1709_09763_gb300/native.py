@@ -28,9 +28,10 @@ SMC_SRC_ONE = 0
 SMC_SRC_NINE = 1
 SMC_PROP_PCN = 0
 SMC_PROP_RWM = 1
+SMC_PROP_RWM_COV = 2
 _COV = {"sep_exp": SMC_COV_SEP_EXP, "matern": SMC_COV_MATERN}
 _SRC = {"one": SMC_SRC_ONE, "nine": SMC_SRC_NINE}
-_PROP = {"pcn": SMC_PROP_PCN, "rwm": SMC_PROP_RWM}
+_PROP = {"pcn": SMC_PROP_PCN, "rwm": SMC_PROP_RWM, "rwm_cov": SMC_PROP_RWM_COV}
 SMC_BC_DIRICHLET = 0
 SMC_BC_FLOW_CELL = 1
 _BC = {"dirichlet": SMC_BC_DIRICHLET, "flow_cell": SMC_BC_FLOW_CELL}

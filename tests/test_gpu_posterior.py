@@ -3,7 +3,7 @@
 tests/golden/quad_k2_h16.json holds the exact posterior mean and variance of the discretised
 problem on 1/h = 16 (oracle FEM, trapezoid grid, grid error ~1e-11). R seeded replicates of the
 mixed-precision MLS^2MC sampler (levels 1/8, 1/16), plain and with the surrogate screen forced on
-every level, must give replicate-averaged posterior means and variances within 3 Monte Carlo
+every level, with pCN and with the covariance-shaped random walk (step 2.38 / sqrt(2)), must give replicate-averaged posterior means and variances within 3 Monte Carlo
 standard errors of it (the standard error estimated from the replicate spread). With R = 32 the
 deviation over its estimated standard error follows Student's t with 31 degrees of freedom: a
 correct sampler exceeds 3 in one of the four comparisons of a run with probability 2.1 %."""
@@ -25,15 +25,16 @@ def built():
     build.build()
 
 
-@pytest.mark.parametrize("surrogate", [0, 2])
-def test_sampler_matches_quadrature_within_3_se(surrogate):
+@pytest.mark.parametrize("surrogate,proposal,step", [(0, "pcn", 0.3), (2, "pcn", 0.3), (0, "rwm_cov", 1.68),
+                                                     (2, "rwm_cov", 1.68)])
+def test_sampler_matches_quadrature_within_3_se(surrogate, proposal, step):
     q = json.load(open(GOLD))
     R = 32
     means, vars_ = [], []
     for r in range(R):
         h = native.Handle([8, 16], 2, np.array(q["obs"]), q["y"], q["sigma"], corr_len=q["corr_len"], J=2000,
-                          J_tilde=100, n_mcmc=5, s_pcn=0.3, precision=native.SMC_MIXED, seed=1000 + r,
-                          surrogate=surrogate)
+                          J_tilde=100, n_mcmc=5, s_pcn=step, precision=native.SMC_MIXED, seed=1000 + r,
+                          surrogate=surrogate, proposal=proposal)
         h.run()
         m, v, _ = h.posterior_moments()
         means.append(m)

@@ -314,3 +314,47 @@ def test_adaptive_step_and_distinct_ancestors_match_oracle():
     assert len({g["step"] for g in gp}) > 1
     th, _ = h.particles()
     assert np.allclose(th, o.theta, rtol=1e-7, atol=1e-8)
+
+
+@pytest.mark.parametrize("accept_target", [0.0, 0.3])
+def test_covariance_shaped_walk_matches_oracle_linear(accept_target):
+    """The covariance-shaped random walk (proposal "rwm_cov", not in the paper) on a three-level
+    linear hierarchy, K = 4: the population covariance, its factor and the shaped steps on the GPU
+    give the oracle's update path, steps, distinct-ancestor counts, particles and evidence."""
+    As, y, s = _linear(K=4, n=6, sigma=0.1, seed=12, levels=3)
+    J = 1500
+    kw = dict(J_tilde=100, n_mcmc=3, s_pcn=2.38 / 2.0, seed=31, proposal="rwm_cov", accept_target=accept_target)
+    h = _handle_linear(As, y, s, J=J, **kw)
+    h.run()
+    o = _oracle_linear(As, y, s, J, **kw)
+    gp = h.path()
+    _compare_paths(gp, o.path, 1e-9)
+    for g, r in zip(gp, o.path):
+        assert g["n_unique"] == r["n_unique"]
+        assert g["accept_rate"] == pytest.approx(r["accept"], abs=1e-12)
+        assert g["step"] == pytest.approx(r["step"], rel=1e-12)
+    th, _ = h.particles()
+    assert np.allclose(th, o.theta, rtol=1e-9, atol=1e-10)
+    assert h.posterior_moments()[2] == pytest.approx(o.log_z, rel=1e-10)
+    assert h.state()["evals"][:3] == list(o.evals)
+
+
+def test_covariance_shaped_walk_matches_oracle_fem():
+    """Two FEM levels (1/8, 1/16) on the FP64 path with the covariance-shaped walk: the oracle's
+    path and particles."""
+    K, J = 4, 300
+    obs = wl.obs_grid(3)
+    lv = [ofwd.Level(N, 0.3, 1.0, K, obs) for N in (8, 16)]
+    th_true = np.random.default_rng(7).standard_normal(K)
+    Gt = lv[1].G(th_true)
+    sigma = 0.02 * np.abs(Gt).max()
+    y = Gt + sigma * np.random.default_rng(8).standard_normal(obs.shape[0])
+    kw = dict(J_tilde=50, n_mcmc=2, s_pcn=1.0, seed=19, proposal="rwm_cov")
+    h = native.Handle([8, 16], K, obs, y, sigma, corr_len=0.3, J=J, precision=native.SMC_FP64, rtol=1e-13, **kw)
+    h.run()
+    ev = lambda l, th: potential(lv[l].G_batch(th), y, sigma)
+    o = smc.Sampler(ev, 2, K, J, **kw).run()
+    _compare_paths(h.path(), o.path, 1e-7)
+    th, _ = h.particles()
+    assert np.allclose(th, o.theta, rtol=1e-7, atol=1e-8)
+    assert h.state()["evals"][:2] == list(o.evals)
