@@ -653,7 +653,11 @@ def main():
         run = {"mls2mc": compare(w, d, tuple(w.inv_h)), "smc_finest": compare(w, d, (w.inv_h[-1],), R=6),
                "mls2mc_surrogate_workload": compare(wda, dda, tuple(wda.inv_h), R=8, breakdown=True),
                "mls2mc_surrogate_workload_adaptive_step": compare(wda, dda, tuple(wda.inv_h), R=8, breakdown=True,
-                                                                  accept_target=0.25)}
+                                                                  accept_target=0.25),
+               # the same workload with the covariance-shaped random walk (first step 2.38 / sqrt(K), adaptive)
+               "mls2mc_surrogate_workload_covariance_walk": compare(
+                   dataclasses.replace(wda, proposal="rwm_cov", s_pcn=2.38 / math.sqrt(wda.K)), dda,
+                   tuple(wda.inv_h), R=8, breakdown=True, accept_target=0.25)}
 
         def paper_example(name, R=3, J_sweep=()):
             """The paper's examples (Matern prior, one random-walk step per update; 5.1/5.2: nine

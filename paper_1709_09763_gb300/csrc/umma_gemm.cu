@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <atomic>
 #include <mutex>
 #include <unordered_map>
@@ -61,6 +62,21 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
             dst),
         "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
         : "memory");
+}
+
+// TMA store of a 32 x 32 FP32 box (128-byte swizzled rows in shared memory) at column x, row y of
+// the output; rows and columns beyond the tensor are not written. x is a multiple of 32 (128 bytes).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
+                 "r"(src), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until at most one committed store group still reads shared memory
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
 // shared-memory matrix descriptor, K-major operand with 128-byte swizzle: 8-row groups of
@@ -154,8 +170,8 @@ __device__ __forceinline__ void epilogue(const GemmEpi& e, int row, int col, flo
 
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(128, 3)
-umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
-                 int K, GemmEpi epi, int* err) {
+umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const __grid_constant__ CUtensorMap tmC, int M, int N, int K, GemmEpi epi, int* err) {
     constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
@@ -229,7 +245,40 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (done) {
         const uint32_t t_row = tmem + ((uint32_t)(32 * warp) << 16);
-        if (epi.kind == kEpiStoreF32 || epi.kind == kEpiExp) {
+        if (epi.tma_out) {
+            // FP32 output (exp applied, or stored as is) by TMA: each lane holds one row of a 32 x 32
+            // block, writes it as eight 16-byte chunks into a 128-byte swizzled staging row (chunk c
+            // of row r at c ^ (r & 7): a warp's chunk stores spread over all banks), and lane 0 stores
+            // the block with one bulk copy. Two staging buffers per warp in the free pipeline slots,
+            // so a block is written while the previous one is still being read.
+            const uint32_t stage0 = base + (uint32_t)warp * 8192u;
+            int buf = 0;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32, buf ^= 1) {
+                float v[32];
+                tmem_ld32(t_row + (uint32_t)c0, v);
+                if (epi.kind == kEpiExp) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = expf(v[i]);
+                }
+                const uint32_t sb = stage0 + (uint32_t)buf * 4096u;
+                if (lane == 0) bulk_wait_read1();   // the store issued from this buffer two blocks ago
+                __syncwarp();
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    st_shared_v4(sb + (uint32_t)lane * 128u + ((uint32_t)(c ^ (lane & 7)) << 4), v[4 * c],
+                                 v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                // boxes reaching past the output are clipped by the copy; boxes wholly past it are skipped
+                if (lane == 0 && n0 + c0 < N && m0 + 32 * warp < M) {
+                    tma_store_2d(&tmC, sb, n0 + c0, m0 + 32 * warp);
+                    bulk_commit();
+                }
+            }
+            if (lane == 0) bulk_wait_all();
+            __syncwarp();
+        } else if (epi.kind == kEpiStoreF32 || epi.kind == kEpiExp) {
             // 32 x 32 blocks staged through shared memory (the pipeline slots are free now): each
             // lane holds one row, then each store instruction writes 32 consecutive columns of one row
             float* stage = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw))) + warp * (32 * 33);
@@ -304,11 +353,27 @@ bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int
     return r == CUDA_SUCCESS;
 }
 
+// 2-D FP32 tensor map of an output: rows x cols (row stride ld elements), box 32 x 32, 128-byte
+// swizzle (the epilogue's staging layout)
+bool make_out_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    if (((uintptr_t)ptr & 15u) != 0 || (ld * 4) % 16 != 0) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // encoded maps of this thread, keyed by everything a map encodes (address, shape, stride, box):
 // a key fully determines its map, so entries never go stale
 struct MapKey {
     const void* ptr;
-    int rows, cols, ld, box_rows;
+    int rows, cols, ld, box_rows;   // box_rows < 0: an FP32 output map (make_out_map)
     bool operator==(const MapKey& o) const {
         return ptr == o.ptr && rows == o.rows && cols == o.cols && ld == o.ld && box_rows == o.box_rows;
     }
@@ -329,15 +394,16 @@ bool cached_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, i
         *map = it->second;
         return true;
     }
-    if (!make_map(map, ptr, rows, cols, ld, box_rows)) return false;
+    if (!(box_rows < 0 ? make_out_map(map, ptr, rows, cols, ld) : make_map(map, ptr, rows, cols, ld, box_rows)))
+        return false;
     if (cache.size() >= 512) cache.clear();
     cache.emplace(key, *map);
     return true;
 }
 
 template <int BN, int STAGES>
-cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, const GemmEpi& epi,
-                        int* err, cudaStream_t st) {
+cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc, int M, int N, int K,
+                        const GemmEpi& epi, int* err, cudaStream_t st) {
     const size_t smem = (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024;
     auto kern = umma_gemm_kernel<BN, STAGES>;
     static std::atomic<unsigned long long> attr_set{0};   // one bit per device
@@ -350,7 +416,7 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int
         attr_set.fetch_or(bit);
     }
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    kern<<<grid, 128, smem, st>>>(ta, tb, M, N, K, epi, err);
+    kern<<<grid, 128, smem, st>>>(ta, tb, tc, M, N, K, epi, err);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -361,12 +427,18 @@ cudaError_t umma_gemm(const void* A, int lda, const void* B, int ldb, int M, int
                       int* err, cudaStream_t st) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     const int bn = N <= 64 ? 64 : 128;
-    CUtensorMap ta, tb;
+    CUtensorMap ta, tb, tc;
     if (!cached_map(&ta, A, M, K, lda, BM) || !cached_map(&tb, B, N, K, ldb, bn)) return cudaErrorInvalidValue;
+    // FP32 outputs without a bias (the KL synthesis) leave by TMA stores when their map encodes
+    GemmEpi e2 = epi;
+    e2.tma_out = 0;
+    std::memset(&tc, 0, sizeof tc);
+    if ((epi.kind == kEpiExp || (epi.kind == kEpiStoreF32 && !epi.bias)) && cached_map(&tc, epi.out_f32, M, N, epi.ld_out, -1))
+        e2.tma_out = 1;
     // two stages (65 KB of shared memory): three CTAs per SM, so that one CTA's epilogue overlaps
     // the loads and MMAs of the others (the contractions here have short K)
-    if (bn == 64) return launch_gemm<64, 2>(ta, tb, M, N, K, epi, err, st);
-    return launch_gemm<128, 2>(ta, tb, M, N, K, epi, err, st);
+    if (bn == 64) return launch_gemm<64, 2>(ta, tb, tc, M, N, K, e2, err, st);
+    return launch_gemm<128, 2>(ta, tb, tc, M, N, K, e2, err, st);
 }
 
 }  // namespace mls2mc

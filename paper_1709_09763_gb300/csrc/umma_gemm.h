@@ -25,6 +25,7 @@ struct GemmEpi {
     int ld_act = 0;
     __nv_bfloat16* act_t = nullptr;
     int ld_act_t = 0;
+    int tma_out = 0;                // set by umma_gemm: the FP32 output leaves by TMA stores
 };
 
 // A: M x K BF16 (row stride lda elements), B: N x K BF16 (row stride ldb); lda, ldb multiples of 8,
