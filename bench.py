@@ -38,7 +38,7 @@ WORKLOAD = "mls2mc_mixed_h8_64"
 # out), measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on one launch of the same
 # kernel and scaled by the particle count (the traffic is per particle: nothing is shared between
 # blocks); None where no capture of the current build exists
-FEM64_DRAM_BYTES_PER_PARTICLE = {512: None, 1024: None, -512: (20.065792e6 + 4.740352e6) / 608}
+FEM64_DRAM_BYTES_PER_PARTICLE = {512: None, 1024: None, -512: (20.061184e6 + 4.715776e6) / 608}
 
 
 def solve_kernel_name(N, T):
