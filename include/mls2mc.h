@@ -114,7 +114,7 @@ typedef struct {
     int surrogate;             /* 0: plain pCN; 1: delayed-acceptance pCN screened by the surrogate network on
                                   the levels where an exact solve costs more than 8 surrogate passes (measured);
                                   2: screen on every level */
-    int surrogate_train_steps; /* Adam steps of the first training round of a level (<= 0: 25; later rounds 1/4) */
+    int surrogate_train_steps; /* Adam steps of the first training round of a level (<= 0: 50; later rounds 1/4) */
     int surrogate_batch;       /* training minibatch, at most the pairs held (<= 0: 8192) */
     void* stream;              /* cudaStream_t used for all work, or NULL for the default stream */
     int proposal;              /* SMC_PROP_PCN (0, the default), SMC_PROP_RWM or SMC_PROP_RWM_COV (step

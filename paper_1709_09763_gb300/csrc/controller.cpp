@@ -279,7 +279,7 @@ bool Handle::da_worth(int level) {
     return da_gate[level] > 0;
 }
 
-// training schedule: once the level has J pairs, then again after every 4 J new pairs (25 Adam
+// training schedule: once the level has J pairs, then again after every 4 J new pairs (50 Adam
 // steps the first time, a quarter of that afterwards) on minibatches of up to 8192 pairs: the
 // small GEMMs of a step are latency-bound, so few large steps train for less than many small ones
 int Handle::maybe_train(int level) {
@@ -288,7 +288,7 @@ int Handle::maybe_train(int level) {
     Mlp& M = mlps[level];
     if (M.count < smp->J) return SMC_OK;
     if (M.t > 0 && smp->pairs_new[level] < 4LL * smp->J) return SMC_OK;
-    const int base = opts.surrogate_train_steps > 0 ? opts.surrogate_train_steps : 25;
+    const int base = opts.surrogate_train_steps > 0 ? opts.surrogate_train_steps : 50;
     const int steps = M.t == 0 ? base : std::max(1, base / 4);
     const int batch = std::min(opts.surrogate_batch > 0 ? opts.surrogate_batch : 8192, M.count);
     double loss = 0.0;

@@ -326,6 +326,10 @@ int Handle::mlp_work(int B) {
     A((void**)&mwork.th, (size_t)B * K * 8);
     A((void**)&mwork.idx, (size_t)B * 4);
     A((void**)&mwork.partial, (size_t)grid_of((long long)B * dmax, 256) * 8);
+    // up to 64 split-K slices of a dmax x dmax weight gradient
+    const size_t sk = (size_t)64 * dmax * dmax;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&mwork.splitk, sk * 4);
+    if (e == cudaSuccess) mwork.splitk_floats = sk;
     if (e != cudaSuccess) {
         mwork.release();
         return fail(SMC_ENOMEM, "surrogate work buffers for batch %d: %s", B, cudaGetErrorString(e));
@@ -341,8 +345,9 @@ void MlpWork::release() {
     for (auto& p : pre) { cudaFree(p); p = nullptr; }
     for (auto& p : dZ) { cudaFree(p); p = nullptr; }
     for (auto& p : dZt) { cudaFree(p); p = nullptr; }
-    cudaFree(Z); cudaFree(tgt); cudaFree(th); cudaFree(idx); cudaFree(partial);
-    Z = tgt = nullptr; th = nullptr; idx = nullptr; partial = nullptr;
+    cudaFree(Z); cudaFree(tgt); cudaFree(th); cudaFree(idx); cudaFree(partial); cudaFree(splitk);
+    Z = tgt = nullptr; th = nullptr; idx = nullptr; partial = nullptr; splitk = nullptr;
+    splitk_floats = 0;
     cap = 0;
 }
 
@@ -414,6 +419,8 @@ int Handle::mlp_backward(int level, int B, double* loss) {
         ew.kind = kEpiStoreF32;
         ew.out_f32 = S.gW[l];
         ew.ld_out = S.d[l];
+        ew.ws = mwork.splitk;
+        ew.ws_floats = mwork.splitk_floats;
         cudaError_t e = umma_gemm(mwork.dZt[l], ldt, mwork.Xt[l], ldt, S.d[l + 1], S.d[l], B, ew, S.err, stream);
         if (e != cudaSuccess) return cuda_fail(e, "surrogate weight-gradient GEMM");
         rowsum_kernel<<<grid_of((long long)S.d[l + 1] * 32, 256), 256, 0, stream>>>(mwork.dZt[l], S.d[l + 1], B, ldt,

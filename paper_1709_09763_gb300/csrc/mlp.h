@@ -38,6 +38,8 @@ struct MlpWork {
     double* th = nullptr;
     int* idx = nullptr;
     double* partial = nullptr;
+    float* splitk = nullptr;                 // split-K partial tiles of the weight gradients
+    size_t splitk_floats = 0;
     void release();
 };
 

@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <atomic>
@@ -143,10 +144,10 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 }
 
 // epilogue of one accumulator value at (row, col), inside M x N
-__device__ __forceinline__ void epilogue(const GemmEpi& e, int row, int col, float acc) {
+__device__ __forceinline__ void epilogue(const GemmEpi& e, int row, int col, float acc, size_t zoff = 0) {
     switch (e.kind) {
         case kEpiStoreF32:
-            e.out_f32[(size_t)row * e.ld_out + col] = acc + (e.bias ? e.bias[col] : 0.0f);
+            e.out_f32[zoff + (size_t)row * e.ld_out + col] = acc + (e.bias ? e.bias[col] : 0.0f);
             break;
         case kEpiBiasGelu: {
             const float z = acc + e.bias[col];
@@ -171,7 +172,7 @@ __device__ __forceinline__ void epilogue(const GemmEpi& e, int row, int col, flo
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(128, 3)
 umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 const __grid_constant__ CUtensorMap tmC, int M, int N, int K, GemmEpi epi, int* err) {
+                 const __grid_constant__ CUtensorMap tmC, int M, int N, int K, int cps, GemmEpi epi, int* err) {
     constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
@@ -180,7 +181,12 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int nk = (K + BK - 1) / BK;
+    // split K (cps > 0): this CTA takes the K chunks [kb, kb + nk) and writes its partial product
+    // to slice blockIdx.z of the output (a workspace the caller reduces)
+    const int nk_all = (K + BK - 1) / BK;
+    const int kb = cps > 0 ? (int)blockIdx.z * cps : 0;
+    const int nk = cps > 0 ? min(cps, nk_all - kb) : nk_all;
+    const size_t zoff = (size_t)blockIdx.z * (size_t)M * (size_t)epi.ld_out;
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
 
     if (threadIdx.x == 0) {
@@ -215,8 +221,8 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             if (*(volatile int*)&abort_flag) break;
             const uint32_t a_dst = base + s * STAGE_BYTES, b_dst = a_dst + A_BYTES;
             mbar_expect_tx(smem_u32(&full_bar[s]), STAGE_BYTES);
-            tma_load_2d(a_dst, &tmA, smem_u32(&full_bar[s]), k * BK, m0);
-            tma_load_2d(b_dst, &tmB, smem_u32(&full_bar[s]), k * BK, n0);
+            tma_load_2d(a_dst, &tmA, smem_u32(&full_bar[s]), (kb + k) * BK, m0);
+            tma_load_2d(b_dst, &tmB, smem_u32(&full_bar[s]), (kb + k) * BK, n0);
         }
     } else if (threadIdx.x == 32) {
         // issuer: four K = 16 MMAs per chunk; the start address advances 32 bytes per step
@@ -293,7 +299,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 #pragma unroll 4
                 for (int rr = 0; rr < 32; ++rr) {
                     const int row = m0 + 32 * warp + rr;
-                    if (row < M && col < N) epilogue(epi, row, col, stage[rr * 33 + lane]);
+                    if (row < M && col < N) epilogue(epi, row, col, stage[rr * 33 + lane], zoff);
                 }
                 __syncwarp();
             }
@@ -321,6 +327,18 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
     }
+}
+
+// out[r][c] = sum over the splits z = 0 .. splits - 1 (in order) of ws[z][r][c], rows r < M,
+// columns c < N, row stride ld in both
+__global__ void splitk_reduce_kernel(const float* ws, int splits, int M, int N, int ld, float* out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)M * N) return;
+    const int r = (int)(t / N), c = (int)(t - (long long)r * N);
+    const size_t i = (size_t)r * ld + c, slice = (size_t)M * ld;
+    float acc = 0.0f;
+    for (int z = 0; z < splits; ++z) acc += ws[(size_t)z * slice + i];
+    out[i] = acc;
 }
 
 // ---- host side -------------------------------------------------------------------------------
@@ -403,7 +421,7 @@ bool cached_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, i
 
 template <int BN, int STAGES>
 cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc, int M, int N, int K,
-                        const GemmEpi& epi, int* err, cudaStream_t st) {
+                        int splits, int cps, const GemmEpi& epi, int* err, cudaStream_t st) {
     const size_t smem = (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024;
     auto kern = umma_gemm_kernel<BN, STAGES>;
     static std::atomic<unsigned long long> attr_set{0};   // one bit per device
@@ -415,8 +433,8 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
         if (e != cudaSuccess) return e;
         attr_set.fetch_or(bit);
     }
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    kern<<<grid, 128, smem, st>>>(ta, tb, tc, M, N, K, epi, err);
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
+    kern<<<grid, 128, smem, st>>>(ta, tb, tc, M, N, K, cps, epi, err);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -429,16 +447,41 @@ cudaError_t umma_gemm(const void* A, int lda, const void* B, int ldb, int M, int
     const int bn = N <= 64 ? 64 : 128;
     CUtensorMap ta, tb, tc;
     if (!cached_map(&ta, A, M, K, lda, BM) || !cached_map(&tb, B, N, K, ldb, bn)) return cudaErrorInvalidValue;
-    // FP32 outputs without a bias (the KL synthesis) leave by TMA stores when their map encodes
     GemmEpi e2 = epi;
     e2.tma_out = 0;
     std::memset(&tc, 0, sizeof tc);
+    // split K: a plain FP32 product with few output tiles and a long K (the surrogate's weight
+    // gradients: 256 x 256 outputs over a minibatch of thousands) runs on about a CTA per SM, each
+    // split writing its partial tile to the caller's workspace, then summed in split order
+    const int tiles = ((N + bn - 1) / bn) * ((M + BM - 1) / BM), nk = (K + BK - 1) / BK;
+    int splits = 1, cps = 0;
+    if (epi.kind == kEpiStoreF32 && !epi.bias && epi.ws && tiles < 38 && nk >= 8) {
+        const size_t slice = (size_t)M * epi.ld_out;
+        const int max_splits = (int)std::min<size_t>(epi.ws_floats / slice, 1024);
+        if (max_splits >= 2) {
+            cps = std::max(2, (nk * tiles + 151) / 152);
+            cps = std::max(cps, (nk + max_splits - 1) / max_splits);
+            splits = (nk + cps - 1) / cps;
+            if (splits < 2) splits = 1, cps = 0;
+        }
+    }
+    if (splits > 1) {
+        e2.out_f32 = epi.ws;
+        cudaError_t e = bn == 64 ? launch_gemm<64, 2>(ta, tb, tc, M, N, K, splits, cps, e2, err, st)
+                                 : launch_gemm<128, 2>(ta, tb, tc, M, N, K, splits, cps, e2, err, st);
+        if (e != cudaSuccess) return e;
+        const long long n = (long long)M * N;
+        splitk_reduce_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(epi.ws, splits, M, N, epi.ld_out, epi.out_f32);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    // FP32 outputs without a bias (the KL synthesis) leave by TMA stores when their map encodes
     if ((epi.kind == kEpiExp || (epi.kind == kEpiStoreF32 && !epi.bias)) && cached_map(&tc, epi.out_f32, M, N, epi.ld_out, -1))
         e2.tma_out = 1;
     // two stages (65 KB of shared memory): three CTAs per SM, so that one CTA's epilogue overlaps
     // the loads and MMAs of the others (the contractions here have short K)
-    if (bn == 64) return launch_gemm<64, 2>(ta, tb, tc, M, N, K, e2, err, st);
-    return launch_gemm<128, 2>(ta, tb, tc, M, N, K, e2, err, st);
+    if (bn == 64) return launch_gemm<64, 2>(ta, tb, tc, M, N, K, 1, 0, e2, err, st);
+    return launch_gemm<128, 2>(ta, tb, tc, M, N, K, 1, 0, e2, err, st);
 }
 
 }  // namespace mls2mc

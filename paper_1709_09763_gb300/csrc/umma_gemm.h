@@ -26,6 +26,8 @@ struct GemmEpi {
     __nv_bfloat16* act_t = nullptr;
     int ld_act_t = 0;
     int tma_out = 0;                // set by umma_gemm: the FP32 output leaves by TMA stores
+    float* ws = nullptr;            // kEpiStoreF32 without bias: workspace for split-K partial tiles
+    size_t ws_floats = 0;           //   (splits x M x ld_out floats at most; null: no split)
 };
 
 // A: M x K BF16 (row stride lda elements), B: N x K BF16 (row stride ldb); lda, ldb multiples of 8,

@@ -128,10 +128,14 @@ def test_batched_sampler_rejects_what_it_does_not_run():
     kw = _kwargs(sp, native.SMC_MIXED, s1.cuda_stream)
     kw["surrogate"] = 2
     h3 = _handle(kw)
-    b = native.Batch([h3])
-    with pytest.raises(native.SmcError) as e:
-        b.step()
-    assert e.value.code == native.SMC_EINVAL
-    b.close()
-    for h in (h1, h2, h3):
+    kw = _kwargs(sp, native.SMC_MIXED, s1.cuda_stream)
+    kw["proposal"] = "rwm_cov"
+    h4 = _handle(kw)
+    for h in (h3, h4):   # the screened sampler and the covariance-shaped walk run per handle only
+        b = native.Batch([h])
+        with pytest.raises(native.SmcError) as e:
+            b.step()
+        assert e.value.code == native.SMC_EINVAL
+        b.close()
+    for h in (h1, h2, h3, h4):
         h.close()

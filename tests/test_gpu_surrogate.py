@@ -82,11 +82,15 @@ def test_forward_matches_oracle():
     assert np.max(np.abs((G - Gref) / sd[:NOBS])) < 0.1 * np.max(np.abs(z))
 
 
-def test_gradients_match_oracle():
+@pytest.mark.parametrize("n", [512, 3000])
+def test_gradients_match_oracle(n):
+    """Weight gradients are products over the minibatch (K = n): split over the K chunks when the
+    output has few tiles (4 splits at 512; 24 at 3000, the last split one chunk wide and the last
+    chunk ragged), partial tiles summed in split order."""
     h = _handle()
     flat, mu, sd = _set_random(h, 5)
     rng = np.random.default_rng(2)
-    theta = rng.normal(0, 1, (512, K))
+    theta = rng.normal(0, 1, (n, K))
     G = mu[:NOBS] + sd[:NOBS] * _target_fn(theta)
     g, loss = h.surrogate_grads(0, theta, G)
     gW, gb = h.unflatten(g)
