@@ -406,8 +406,10 @@ int Handle::shape_factor() {
 }
 
 // n_mcmc pCN (or random-walk) Metropolis steps; zeta < 0: tempering target on `level`, else
-// bridging target on level, level+1
-int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, IncState* pending) {
+// bridging target on level, level+1. beta_p / zeta_p: read beta / zeta on the device (where the
+// increment search left it) instead of the host value; pending: the search state to read back
+// with the counters
+int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, IncState* pending, const double* zeta_p) {
     // networks are trained only for targets whose every level is worth screening
     if (may_screen(level, zeta)) {
         RC(maybe_train(level));
@@ -429,7 +431,7 @@ int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, Inc
         RC(smp_eval(level, S->J, S->theta_p, S->phi_cp));
         if (zeta >= 0.0) RC(smp_eval(level + 1, S->J, S->theta_p, S->phi_fp));
         PhaseTimer pt(this, kPhMove);
-        CK(pcn_accept_launch(S->J, K, S->beta, beta_p, zeta, ev, opts.seed, S->theta, S->theta_p, S->phi_c,
+        CK(pcn_accept_launch(S->J, K, S->beta, beta_p, zeta, zeta_p, ev, opts.seed, S->theta, S->theta_p, S->phi_c,
                              S->phi_cp, S->phi_f, S->phi_fp, S->n_acc, rwm ? 1 : 0, stream));
         S->mcmc_event += 1;
     }
@@ -576,12 +578,14 @@ int Handle::bridging_update(int level, double beta, double zeta0, int n_mcmc, sm
     IncState st;
     const double log_z = S->log_z, beta_s = S->beta, step0 = S->step;
     const int nm = opts.n_mcmc;
+    // the moves read zeta on the device unless they may be screened (then the host needs it)
+    const bool wait = may_screen(level, 0.0);
     S->beta = beta;
-    int rc = reweight_resample(S->a, 1.0 - zeta0, zeta0, true, st, true);
+    int rc = reweight_resample(S->a, 1.0 - zeta0, zeta0, true, st, wait);
     double rate = 0.0;
     if (rc == SMC_OK) {
         opts.n_mcmc = n_mcmc;
-        rc = mcmc(level, st.next, rate);
+        rc = wait ? mcmc(level, st.next, rate) : mcmc(level, 0.0, rate, nullptr, &st, next_param_device());
         opts.n_mcmc = nm;
     }
     S->beta = beta_s;
@@ -634,11 +638,20 @@ int Handle::lu(int head, smc_stage_info* info) {
     int nb = 0;
     IncState st;
     double rate = 0.0;
+    // the moves read zeta on the device unless they may be screened; the search state comes back
+    // with the moves' counters (one host wait per bridging step)
+    const bool wait = may_screen(l, 0.0);
     while (zeta < 1.0) {
         CK(lu_increment_launch(S->phi_c, S->phi_f, S->J, S->beta, S->a, stream));
-        RC(reweight_resample(S->a, 1.0 - zeta, zeta, true, st, true));
-        zeta = st.next;
-        RC(mcmc(l, zeta, rate));
+        RC(reweight_resample(S->a, 1.0 - zeta, zeta, true, st, wait));
+        if (wait) {
+            zeta = st.next;
+            RC(mcmc(l, zeta, rate));
+        } else {
+            RC(mcmc(l, 0.0, rate, nullptr, &st, next_param_device()));
+            zeta = st.next;
+            S->log_z += st.log_mean_w;
+        }
         record(1, zeta, st, rate, -1.0, info);
         S->path.back().n_bridge = ++nb;
         if (info) info->n_bridge = nb;

@@ -943,8 +943,9 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
     const int tid = threadIdx.x;
     Lv<Real> F = level_ptrs<Real, N, N, false, FC>(arena);
     Real* vec = arena + arena_size(N, FC);
-    Real *R = vec, *Dv = vec + NI, *XH = vec + 2 * NI, *XL = vec + 3 * NI, *RH = vec + 4 * NI, *RL = vec + 5 * NI,
-         *QV = vec + 6 * NI;
+    Real *R = vec, *Dv = vec + NI, *XH = vec + 2 * NI, *XL = vec + 3 * NI, *RH = vec + 4 * NI, *RL = vec + 5 * NI;
+    // A p is kept in the fine level's residual array (dead outside the restriction): one array
+    // fewer in the working set that must stay in L2
     Real* stage = F.e;
 
     if constexpr (FC) {   // ghost rows of the coefficient arrays, read by the boundary rows
@@ -1087,7 +1088,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
             for (int i = tid; i < NI; i += T) {
                 NODE_OF(i);
                 const Real q = stencil_apply<Real, S>(F.aE, F.aN, P, n);
-                QV[i] = q;
+                F.res[n] = q;
                 pq += P[n] * q;
             }
             block_sum<T>(pq, red_buf[parity]);
@@ -1097,7 +1098,7 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
             for (int i = tid; i < NI; i += T) {
                 NODE_OF(i);
                 Dv[i] = fma(alpha, P[n], Dv[i]);
-                const Real rn = fma(-alpha, QV[i], R[i]);
+                const Real rn = fma(-alpha, F.res[n], R[i]);
                 R[i] = rn;
                 rr += rn * rn;
                 if (((ii + jj) & 1) == 0) F.e[n] = rn * F.iD[n];   // red pre-sweep of the next cycle

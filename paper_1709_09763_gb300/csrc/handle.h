@@ -115,7 +115,8 @@ struct Handle {
     const double* next_param_device() const;
     int increment(const double* a, int n, double dmax, double base, struct IncState& st, bool wait);
     int reweight_resample(const double* a, double dmax, double base, bool carry_fine, struct IncState& st, bool wait);
-    int mcmc(int level, double zeta, double& rate, const double* beta_p = nullptr, struct IncState* pending = nullptr);
+    int mcmc(int level, double zeta, double& rate, const double* beta_p = nullptr, struct IncState* pending = nullptr,
+             const double* zeta_p = nullptr);
     int mcmc_da(int level, double zeta, double& rate);
     int maybe_train(int level);
     bool da_ready(int level, double zeta) const;

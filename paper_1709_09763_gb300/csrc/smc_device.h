@@ -68,10 +68,10 @@ cudaError_t cv_lu_launch(const double* phi_c, const double* phi_f, int n, double
 // beta_p (device, or null): read beta there instead (the tempering parameter the increment search
 // left on the device, so the host need not wait for it); rwm: random-walk proposal, whose
 // acceptance includes the prior ratio of N(0, I)
-cudaError_t pcn_accept_launch(int n, int K, double beta, const double* beta_p, double zeta, uint32_t event,
-                              uint64_t seed, double* theta, const double* theta_p, double* phi_c, const double* phi_cp,
-                              double* phi_f, const double* phi_fp, unsigned long long* n_acc, int rwm,
-                              cudaStream_t st);
+cudaError_t pcn_accept_launch(int n, int K, double beta, const double* beta_p, double zeta, const double* zeta_p,
+                              uint32_t event, uint64_t seed, double* theta, const double* theta_p, double* phi_c,
+                              const double* phi_cp, double* phi_f, const double* phi_fp, unsigned long long* n_acc,
+                              int rwm, cudaStream_t st);
 cudaError_t da_stage1_launch(int n, int K, double beta, double zeta, uint32_t event, uint64_t seed, const double* ps_c,
                              const double* ps_f, const double* psp_c, const double* psp_f, const double* theta,
                              const double* theta_p, int rwm, int* pass, int* surv_idx, int* n_surv, double* theta_s,

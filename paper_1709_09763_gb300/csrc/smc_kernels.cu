@@ -702,12 +702,13 @@ __device__ __forceinline__ bool pcn_accept_one(int j, int n, int K, double beta,
     return ok;
 }
 
-__global__ void pcn_accept_kernel(int n, int K, double beta, const double* beta_p, double zeta, uint32_t event,
-                                  uint64_t seed, double* theta, const double* theta_p, double* phi_c,
+__global__ void pcn_accept_kernel(int n, int K, double beta, const double* beta_p, double zeta, const double* zeta_p,
+                                  uint32_t event, uint64_t seed, double* theta, const double* theta_p, double* phi_c,
                                   const double* phi_cp, double* phi_f, const double* phi_fp,
                                   unsigned long long* n_acc, int rwm) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (beta_p) beta = *beta_p;
+    if (zeta_p) zeta = *zeta_p;
     const bool ok = pcn_accept_one(j, n, K, beta, zeta, event, seed, theta, theta_p, phi_c, phi_cp, phi_f, phi_fp, rwm);
     const unsigned ballot = __ballot_sync(0xffffffffu, ok);
     if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(n_acc, (unsigned long long)__popc(ballot));
@@ -1042,14 +1043,14 @@ cudaError_t cv_lu_launch(const double* phi_c, const double* phi_f, int n, double
     return cudaGetLastError();
 }
 
-cudaError_t pcn_accept_launch(int n, int K, double beta, const double* beta_p, double zeta, uint32_t event,
-                              uint64_t seed, double* theta, const double* theta_p, double* phi_c, const double* phi_cp,
-                              double* phi_f, const double* phi_fp, unsigned long long* n_acc, int rwm,
-                              cudaStream_t st) {
+cudaError_t pcn_accept_launch(int n, int K, double beta, const double* beta_p, double zeta, const double* zeta_p,
+                              uint32_t event, uint64_t seed, double* theta, const double* theta_p, double* phi_c,
+                              const double* phi_cp, double* phi_f, const double* phi_fp, unsigned long long* n_acc,
+                              int rwm, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     // 64-thread blocks: the FP64 work (log U, target potentials) spread over many SMs
-    pcn_accept_kernel<<<grid_for(n, 64), 64, 0, st>>>(n, K, beta, beta_p, zeta, event, seed, theta, theta_p, phi_c,
-                                                      phi_cp, phi_f, phi_fp, n_acc, rwm);
+    pcn_accept_kernel<<<grid_for(n, 64), 64, 0, st>>>(n, K, beta, beta_p, zeta, zeta_p, event, seed, theta, theta_p,
+                                                      phi_c, phi_cp, phi_f, phi_fp, n_acc, rwm);
     count_launches(1);
     return cudaGetLastError();
 }
