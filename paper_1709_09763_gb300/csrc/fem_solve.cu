@@ -931,7 +931,7 @@ __device__ void vcycle2(Real* garena, Real* sarena, const Real* dinv) {
 // Large levels (1/h >= 128): the same solve with the levels 1/h >= 128 in a per-block slice of
 // device memory (L2-resident for 1/128), the levels 1/h <= 64 in shared memory, and the fine-level
 // CG and refinement vectors as arrays indexed by interior node (too many nodes per thread for
-// registers). vec: 7 arrays of NI entries after the level arena: r, d, x_hi, x_lo, r_hi, r_lo, q.
+// registers). vec: 6 arrays of NI entries after the level arena: r, d, x_hi, x_lo, r_hi, r_lo.
 // FC: the flow cell (rows 0 .. N unknowns, ghost rows, the lifted Dirichlet data).
 template <typename Real, int N, int T, bool FC = false>
 __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p, Real* arena, Real* sarena,
@@ -1442,7 +1442,7 @@ cudaError_t fem_eval_compact_launch(const FemArgs& a, int T, float* ref_scratch,
 
 size_t fem_global_slice(int N, bool FC) {
     const int NI = (N - 1) * (FC ? N + 1 : N - 1);
-    const size_t floats = (size_t)arena_size(N, FC) + 7 * (size_t)NI;
+    const size_t floats = (size_t)arena_size(N, FC) + 6 * (size_t)NI;
     return (floats + 63) / 64 * 64;   // floats per block, 256-byte aligned slices
 }
 
