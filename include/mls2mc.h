@@ -81,7 +81,8 @@ extern "C" {
 typedef struct {
     int n_levels;              /* N_L >= 1 */
     const int* inv_h;          /* [n_levels] 1/h_l, coarse to fine; powers of two in [4, 32] (FP64),
-                                  [4, 256] (mixed; 128 and 256 keep their fine levels in device memory) */
+                                  [4, 256] (mixed; 1/128 keeps its fine level on chip across the two
+                                  CTAs of a thread-block cluster, 1/256 in device memory) */
     int K;                     /* KL terms N_sto: 1 <= K <= 256, or <= 512 with the FEM forward map at
                                   SMC_MIXED (Example 5.3 keeps 320); Matern: K <= 512 */
     double corr_len;           /* correlation length of the separable exponential covariance */
@@ -184,11 +185,15 @@ int smc_set_timing(smc_handle* h, int enable);
  * (shared by all handles of the same 1/h and precision). chosen [n_levels] receives the block
  * sizes, best_ms [n_levels] the time per launch (either may be NULL). smc_set_block_size forces a
  * block size for a level (T = 0 restores the default: the compact form on 1/32 and 1/64 of the
- * mixed path, else the first compiled size); T must be one of the compiled sizes. A
- * negative size -T selects the compact form with T threads per particle (mixed precision: -512 at
- * 1/h = 64, -256 at 1/h = 32): several particles per SM, the fine level in five arrays
- * and each coarse level in four, the refinement state in device memory (same results as the size
- * T, bit for bit). */
+ * mixed path, the two-CTA form on 1/128, else the first compiled size); T must be one of the
+ * compiled sizes. A negative size -T selects the compact form with T threads per particle (mixed
+ * precision: -512 at 1/h = 64, -256 at 1/h = 32): several particles per SM, the fine level in five
+ * arrays and each coarse level in four, the refinement state in device memory (same results as the
+ * size T, bit for bit). At 1/h = 128, -1024 selects the two-CTA form: one particle per cluster of two
+ * CTAs of 1024 threads on two SMs, each keeping half of the fine rows on chip with one halo row from
+ * the other through distributed shared memory, the coarse levels 1/64 .. 1/2 in both (the same
+ * algorithm as 1024, which keeps the fine level in device memory; potentials agree to rounding).
+ * Batched and flow-cell solves on 1/128 run the device-memory form. */
 int smc_autotune(smc_handle* h, int n_tune, int* chosen, float* best_ms);
 int smc_set_block_size(smc_handle* h, int level, int T);
 /* The block size the solves of `level` run with (set, tuned or the default) into *T. */

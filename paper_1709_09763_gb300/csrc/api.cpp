@@ -185,6 +185,38 @@ int Handle::eval_device(int level, int n, const double* theta, double* G, double
             if (rc != SMC_OK) return rc;
             a.kappa = synth_kappa_buf;
         }
+        if (L.N == 128 && !flow_cell && precision == SMC_MIXED) {
+            int T = tuned_block(L.N, precision);
+            if (T == 0) T = fem_default_block(L.N, precision);
+            if (T == -1024) {   // two-CTA cluster form: refinement state of its CTAs in device memory
+                const int blocks = fem_cluster_blocks();
+                if (blocks < 2) return fail(SMC_ECUDA, "no two-CTA cluster fits on this device");
+                const size_t need = (size_t)blocks * fem_cluster_ref_floats();
+                if (need > cp_cap) {
+                    cudaFree(cp_scratch);
+                    cp_scratch = nullptr;
+                    cp_cap = 0;
+                    cudaError_t ea = cudaMalloc((void**)&cp_scratch, need * sizeof(float));
+                    if (ea != cudaSuccess) return fail(SMC_ENOMEM, "cluster-form scratch: %s", cudaGetErrorString(ea));
+                    cp_cap = need;
+                }
+                if (!big_counter && cudaMalloc((void**)&big_counter, sizeof(int)) != cudaSuccess)
+                    return fail(SMC_ENOMEM, "work counter");
+                TimedLaunch t{level, nullptr, nullptr};
+                if (timing) {
+                    t.start = take_event();
+                    t.stop = take_event();
+                    cudaEventRecord(t.start, st);
+                }
+                e = fem_eval_cluster_launch(a, cp_scratch, blocks, big_counter, st);
+                if (timing) {
+                    cudaEventRecord(t.stop, st);
+                    timed.push_back(t);
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "forward-solve launch");
+                return SMC_OK;
+            }
+        }
         if (L.N >= 128) {
             // large level: hierarchy in global memory, persistent blocks
             const int blocks = fem_global_blocks(L.N);

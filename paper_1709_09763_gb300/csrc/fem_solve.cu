@@ -77,7 +77,7 @@ __host__ __device__ constexpr int coarse_offset_cp(int NL, int NC) {
 }
 __host__ __device__ constexpr int arena_size_cp(int N) { return 5 * lvl_size(N) + coarse_size_cp(N / 2); }
 
-template <typename Real, int N, int NL, bool CP = false, bool FC = false>
+template <typename Real, int N, int NL, int CP = 0, bool FC = false>
 __device__ __forceinline__ Lv<Real> level_ptrs(Real* arena) {
     if constexpr (FC) {   // ghost row -1 first: each pointer is one row stride into its array
         constexpr int z = lvl_size(NL, true);
@@ -88,6 +88,10 @@ __device__ __forceinline__ Lv<Real> level_ptrs(Real* arena) {
     if constexpr (!CP) {
         Real* b = arena + lvl_offset(N, NL);
         return Lv<Real>{b, b + z, b + 2 * z, b + 3 * z, b + 4 * z, b + 5 * z};
+    } else if constexpr (CP == 2) {   // coarse levels N/2 .. 2 alone, from the arena's start
+        static_assert(NL < N, "the two-CTA form keeps its top level apart");
+        Real* b = arena + coarse_offset_cp(N / 2, NL);
+        return Lv<Real>{b, b + z, nullptr, b + 2 * z, nullptr, b + 3 * z};
     } else if constexpr (NL == N) {
         Real* b = arena;
         return Lv<Real>{b, b + z, b + 2 * z, b + 3 * z, b + 4 * z, b + 4 * z};
@@ -264,7 +268,7 @@ __device__ __forceinline__ void restrict_gather(const Real* res, const Lv<Real>&
 
 // zero the boundary rings of e, res, rhs on every level from NL down (interior values are always
 // written before they are read; the rings must read as zero)
-template <typename Real, int N, int NL, int T, bool CP = false, bool FC = false>
+template <typename Real, int N, int NL, int T, int CP = 0, bool FC = false>
 __device__ __forceinline__ void zero_rings(Real* arena) {
     constexpr int S = fem_row_stride(NL);
     const Lv<Real> L = level_ptrs<Real, N, NL, CP, FC>(arena);
@@ -413,7 +417,7 @@ __device__ __forceinline__ void phase_sync() {
 // V(1,1) cycle on a coarse level: reads L.rhs, writes L.e. Levels with at most 4 cells per side
 // (<= 9 unknowns) run inside warp 0 only (T = 32, warp barriers); the caller's next block
 // barrier publishes the result.
-template <typename Real, int N, int NL, int T, bool WARP = false, bool CP = false, bool FC = false>
+template <typename Real, int N, int NL, int T, bool WARP = false, int CP = 0, bool FC = false>
 __device__ void vcycle_coarse(Real* arena, const Real* dinv) {
     if constexpr (NL == direct_level<Real, FC>(N)) {
         dense_solve<Real, NL, T, FC>(level_ptrs<Real, N, NL, CP, FC>(arena), dinv);
@@ -515,14 +519,14 @@ __device__ void setup_levels(Real* arena, Real* stage, bool ping) {
 
 // compact hierarchy: coefficients of coarse level NL from kappa in kin, coarser kappa into kout,
 // then recurse with the buffers swapped (no stored inverse diagonal)
-template <typename Real, int N, int NL, int T>
+template <typename Real, int N, int NL, int T, int CP = 1>
 __device__ void setup_levels_cp(Real* arena, Real* kin, Real* kout) {
-    Lv<Real> L = level_ptrs<Real, N, NL, true>(arena);
+    Lv<Real> L = level_ptrs<Real, N, NL, CP>(arena);
     build_coeffs<Real, NL, T>(L, kin);
     if constexpr (NL > 2) {
         coarsen_kappa<Real, NL / 2, T>(kin, kout);
         __syncthreads();
-        setup_levels_cp<Real, N, NL / 2, T>(arena, kout, kin);
+        setup_levels_cp<Real, N, NL / 2, T, CP>(arena, kout, kin);
     } else {
         __syncthreads();
     }
@@ -564,7 +568,7 @@ __host__ __device__ constexpr int solve_smem_reals(int N, int T) {
 // ref_ext (device memory) instead of shared memory. RHS: the load vector may come from a table
 // (a.rhs); false compiles the f = 1 path alone (the compact kernels are instantiated both ways:
 // at 64 registers a thread the table read's code costs them 20 % of their speed)
-template <typename Real, int N, int T, bool CP = false, bool RHS = true, bool FC = false>
+template <typename Real, int N, int T, int CP = 0, bool RHS = true, bool FC = false>
 __device__ __forceinline__ void solve_particle(const FemArgs& a, const int p, Real* arena, double (*red_buf)[64],
                                                Real* theta_s, Real* ref_ext = nullptr) {
     constexpr int S = Fine<Real, N>::S, NI = Fine<Real, N>::NI;
@@ -1274,6 +1278,430 @@ __global__ void __launch_bounds__(T, MINB) fem_eval_compact(FemArgs a, float* re
     }
 }
 
+// ---- two-CTA cluster form of the 1/128 solve (mixed path) ------------------------------------
+// One particle per cluster of two CTAs, one CTA per SM. CTA r keeps the fine rows 64 r + 1 ..
+// 64 r + 64 of the 1/128 level on chip (rank 1's last row, 128, is the boundary) with one halo row
+// on either side; the coarse levels 1/64 .. 1/2 are replicated, and both CTAs run the coarse
+// V-cycle on identical data. A value the partner reads (the boundary row of a sweep, the red
+// residuals of row 65, the coarse rows a CTA restricts) is also stored into the partner's shared
+// memory (distributed shared memory), and every fine-level phase ends at a cluster barrier
+// (release / acquire at cluster scope). A reduction sums the 64 warp partials of both CTAs in one
+// fixed order, so both CTAs hold bit-identical scalars and take the same branches: no barrier is
+// left waiting. Fine-level arrays (local index (j - 64 r) S + i, local rows 0 .. 65): edge
+// weights aE, aN; e, which also holds the CG direction p (p is dead while the V-cycle runs and e
+// is dead between the red post-sweep and the next pre-sweep); the red residuals in an array of
+// their own indexed by n / 2. The inverse diagonals are formed from the edge weights where a
+// sweep needs them (approximate reciprocal: they only shape the preconditioner).
+namespace cl {
+constexpr int N = 128, T = 1024, S = fem_row_stride(N), SC = fem_row_stride(N / 2);
+constexpr int FS = 66 * S;                    // floats per strip array (local rows 0 .. 65)
+constexpr int RS = padded(FS / 2);            // red-only residual array
+constexpr int NPT = 8, NPH = 4;               // fine slots per thread (4 red, 4 black)
+constexpr int OFF_AE = 0, OFF_AN = FS, OFF_E = 2 * FS, OFF_RES = 3 * FS, OFF_C = 3 * FS + RS;
+constexpr int OFF_DINV = OFF_C + coarse_size_cp(N / 2);
+constexpr int SMEM_FLOATS = OFF_DINV + dense_reals<float>(N);
+constexpr int REF_FLOATS = 4 * NPT * T;       // refinement state of one CTA (device memory)
+static_assert(fine_slots(N, T) == 2 * NPT, "two CTAs share the fine slots");
+static_assert(OFF_C % 4 == 0 && FS % 4 == 0, "16-byte aligned arrays");
+static_assert(SMEM_FLOATS * 4 <= 227 * 1024, "shared memory of one CTA");
+// packed slot: bits 0-13 local node, 14-26 coarse node under it, 27-28 (i & 1) + 2 (j & 1),
+// 29 red, 30 valid, 31 on the row the partner keeps as its halo
+__device__ __forceinline__ int sn(unsigned s) { return (int)(s & 0x3fffu); }
+__device__ __forceinline__ int sc(unsigned s) { return (int)((s >> 14) & 0x1fffu); }
+__device__ __forceinline__ int scode(unsigned s) { return (int)((s >> 27) & 3u); }
+__device__ __forceinline__ bool sv(unsigned s) { return (s >> 30) & 1u; }
+__device__ __forceinline__ bool ssend(unsigned s) { return (s >> 31) != 0u; }
+}  // namespace cl
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ int cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+// address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t peer_addr(uint32_t a, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_peer(uint32_t a, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_peer(uint32_t a, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ float2 ld_peer2(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+// all threads of both CTAs; orders shared (local and distributed) and global memory at cluster scope
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// sum over the cluster: warp sums written to [rank][warp] of both CTAs' buffers, one cluster
+// barrier, then the 64 partials summed in index order (the same value in both CTAs)
+__device__ __forceinline__ float cluster_sum(float a, float* buf, uint32_t peer_buf, int rank) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+    if ((threadIdx.x & 31) == 0) {
+        const int k = rank * 32 + (threadIdx.x >> 5);
+        buf[k] = a;
+        st_peer(peer_buf + 4u * k, a);
+    }
+    cluster_sync();
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float4 v = reinterpret_cast<const float4*>(buf)[i];
+        s += v.x;
+        s += v.y;
+        s += v.z;
+        s += v.w;
+    }
+    return s;
+}
+
+// inverse stencil diagonal at a fine node of the strip, from its four edge weights
+__device__ __forceinline__ float cl_idiag(const float* aE, const float* aN, int n) {
+    return recip_coarse(aE[n] + aE[n - 1] + aN[n] + aN[n - cl::S]);
+}
+
+// the solve of particle p by the calling cluster (all threads of both CTAs call it); sm: this
+// CTA's dynamic shared memory (cl::SMEM_FLOATS), cbuf: [2][64] reduction buffers, ref: this CTA's
+// refinement state in device memory
+template <bool RHS>
+__device__ void solve_particle_cl(const FemArgs& a, const int p, float* sm, float (*cbuf)[64], float* ref,
+                                  const int rank) {
+    using namespace cl;
+    constexpr int E = 2 * N * N, NI = (N - 1) * (N - 1);
+    const int tid = threadIdx.x, partner = rank ^ 1;
+    float* aE = sm + OFF_AE;
+    float* aN = sm + OFF_AN;
+    float* e = sm + OFF_E;   // also the CG direction p and the refinement's correction d
+    float* res = sm + OFF_RES;
+    float* coarse = sm + OFF_C;
+    float* dinv = sm + OFF_DINV;
+    // partner addresses: this CTA's row j sits at local index (j - 64 r) S + i here and at
+    // (j - 64 (1 - r)) S + i in the partner
+    const int shift = rank ? 64 * S : -64 * S;
+    const uint32_t pe = peer_addr(smem_addr(e), partner) + 4u * (uint32_t)shift;
+    const uint32_t pres = peer_addr(smem_addr(res), partner) + 4u * (uint32_t)(shift / 2);
+    const uint32_t pcb[2] = {peer_addr(smem_addr(cbuf[0]), partner), peer_addr(smem_addr(cbuf[1]), partner)};
+    const Lv<float> C1 = level_ptrs<float, N, N / 2, 2>(coarse);
+    const uint32_t pc_rhs = peer_addr(smem_addr(C1.rhs), partner), pc_e = peer_addr(smem_addr(C1.e), partner);
+
+    // 1) stencil of the strip (local rows 0 .. 65 = rows 64 r .. 64 r + 65) straight from kappa,
+    //    kappa of 1/64 staged in e, the replicated hierarchy 1/64 .. 1/2, the 1/4 inverse
+    const float* kp = a.kappa + (size_t)p * E;
+    coarsen_kappa<float, N / 2, T>(kp, e);
+    for (int n = tid; n < FS; n += T) {
+        const int lr = n / S, i = n - lr * S, j = 64 * rank + lr;
+        float ae = 0.f, an = 0.f;
+        if (i <= N && j <= N) {
+            if (i < N) {
+                if (j < N) ae += kp[2 * (j * N + i)];
+                if (j > 0) ae += kp[2 * ((j - 1) * N + i) + 1];
+            }
+            if (j < N) {
+                if (i > 0) an += kp[2 * (j * N + i - 1)];
+                if (i < N) an += kp[2 * (j * N + i) + 1];
+            }
+        }
+        aE[n] = 0.5f * ae;
+        aN[n] = 0.5f * an;
+    }
+    __syncthreads();
+    setup_levels_cp<float, N, N / 2, T, 2>(coarse, e, res);
+    for (int n = tid; n < FS + RS; n += T) e[n] = 0.f;   // e and res (contiguous): zero halos and rings
+    zero_rings<float, N, N / 2, T, 2>(coarse);
+    if (tid < 32) dense_setup<float, 4, 32>(level_ptrs<float, N, 4, 2>(coarse), dinv);
+    cluster_sync();   // also: the partner writes into this CTA's arrays only after they are zeroed
+
+    unsigned slot[NPT];
+    const int send_row = rank ? 65 : 64;
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+        const bool red = q < NPH;
+        int ii, jj;
+        const bool v = colour_node<N>(4096 * rank + tid + T * (red ? q : q - NPH), red ? 0 : 1, ii, jj);
+        if (!v) {
+            ii = 1;
+            jj = 64 * rank + 1;
+        }
+        const unsigned nl = (unsigned)((jj - 64 * rank) * S + ii);
+        const unsigned c = (unsigned)((jj >> 1) * SC + (ii >> 1));
+        const unsigned code = (unsigned)((ii & 1) + 2 * (jj & 1));
+        slot[q] = nl | (c << 14) | (code << 27) | ((red ? 1u : 0u) << 29) | ((v ? 1u : 0u) << 30) |
+                  ((v && jj == send_row) ? 1u : 0u) << 31;
+    }
+    const float h2 = 1.f / (float(N) * float(N));
+    auto XH = [&](int q) -> float& { return ref[(0 * NPT + q) * T + tid]; };
+    auto XL = [&](int q) -> float& { return ref[(1 * NPT + q) * T + tid]; };
+    auto RH = [&](int q) -> float& { return ref[(2 * NPT + q) * T + tid]; };
+    auto RL = [&](int q) -> float& { return ref[(3 * NPT + q) * T + tid]; };
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+        XH(q) = XL(q) = RL(q) = 0.f;
+        RH(q) = sv(slot[q]) ? h2 : 0.f;
+    }
+    if (RHS && a.rhs) {
+#pragma unroll 1
+        for (int q = 0; q < NPT; ++q) {
+            const bool red = q < NPH;
+            int ii, jj;
+            if (colour_node<N>(4096 * rank + tid + T * (red ? q : q - NPH), red ? 0 : 1, ii, jj)) {
+                float hi, lo;
+                load_rhs(a.rhs, jj * S + ii, hi, lo);
+                RH(q) = hi;
+                RL(q) = lo;
+            }
+        }
+    }
+    float r[NPT], d[NPT], z[NPT], pv[NPT];
+    const float bnorm2 = (RHS && a.rhs) ? float(a.bnorm2) : float(NI) * h2 * h2;
+    const float stop_outer = float(a.rtol * a.rtol) * bnorm2;
+    const float stop_last = float(0.25 * a.rtol * a.rtol) * bnorm2;
+    const float rtol_in2 = float(a.rtol_in * a.rtol_in);
+    int parity = 0, total_it = 0;
+    bool converged = false;
+    // coarse rows this CTA restricts: 1 .. 32 (rank 0; row 32 reads the red residuals of row 65
+    // from the halo) or 33 .. 63 (rank 1)
+    const int J0 = rank ? 33 : 1, NJ = rank ? 31 : 32;
+
+    for (int pass = 0; pass < a.max_outer && !converged; ++pass) {
+        float rr0 = 0.f;
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+            r[q] = RH(q);
+            d[q] = 0.f;
+            pv[q] = 0.f;
+            rr0 += r[q] * r[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NPH; ++q)   // red pre-sweep of the first cycle
+            if (sv(slot[q])) {
+                const int n = sn(slot[q]);
+                const float v = r[q] * cl_idiag(aE, aN, n);
+                e[n] = v;
+                if (ssend(slot[q])) st_peer(pe + 4u * n, v);
+            }
+        rr0 = cluster_sum(rr0, cbuf[parity], pcb[parity], rank);
+        parity ^= 1;
+        if (!(rr0 > 0.f)) break;
+        const float stop2 = fmaxf(rtol_in2 * rr0, stop_last);
+        float rz = 0.f;
+        for (int it = 0; it < a.max_inner; ++it) {
+            // black pre-sweep
+#pragma unroll
+            for (int q = NPH; q < NPT; ++q)
+                if (sv(slot[q])) {
+                    const int n = sn(slot[q]);
+                    const float v = (r[q] + offsum<float, S>(aE, aN, e, n)) * cl_idiag(aE, aN, n);
+                    e[n] = v;
+                    if (ssend(slot[q])) st_peer(pe + 4u * n, v);
+                }
+            cluster_sync();
+            // red residuals (rank 1 also sends row 65, which rank 0 restricts into coarse row 32)
+#pragma unroll
+            for (int q = 0; q < NPH; ++q)
+                if (sv(slot[q])) {
+                    const int n = sn(slot[q]);
+                    const float v = offsum<float, S>(aE, aN, e, n);
+                    res[n >> 1] = v;
+                    if (rank == 1 && ssend(slot[q])) st_peer(pres + 4u * (n >> 1), v);
+                }
+            cluster_sync();
+            // restriction of this CTA's coarse rows into both CTAs (with the coarse red pre-sweep)
+            for (int idx = tid; idx < NJ * (N / 2 - 1); idx += T) {
+                const int Jr = idx / (N / 2 - 1), J = J0 + Jr, I = idx - Jr * (N / 2 - 1) + 1;
+                const int f = (2 * J - 64 * rank) * S + 2 * I, c = J * SC + I;
+                const float v = res[f >> 1] + 0.5f * (res[(f + S + 1) >> 1] + res[(f - S - 1) >> 1]);
+                C1.rhs[c] = v;
+                st_peer(pc_rhs + 4u * c, v);
+                if (((I + J) & 1) == 0) {
+                    const float ev = v * inv_diag<float, SC>(C1, c);
+                    C1.e[c] = ev;
+                    st_peer(pc_e + 4u * c, ev);
+                }
+            }
+            cluster_sync();
+            vcycle_coarse<float, N, N / 2, T, false, 2>(coarse, dinv);
+            // black post-sweep with the prolongation folded in
+#pragma unroll
+            for (int q = NPH; q < NPT; ++q) {
+                z[q] = 0.f;
+                if (sv(slot[q])) {
+                    const int n = sn(slot[q]);
+                    const float v = (r[q] + offsum_prolong<float, S, SC>(aE, aN, e, C1.e, n, sc(slot[q]),
+                                                                          scode(slot[q]) == 1)) *
+                                    cl_idiag(aE, aN, n);
+                    z[q] = v;
+                    e[n] = v;
+                    if (ssend(slot[q])) st_peer(pe + 4u * n, v);
+                }
+            }
+            cluster_sync();
+            float rz_new = 0.f;
+#pragma unroll
+            for (int q = 0; q < NPH; ++q) {   // red post-sweep
+                z[q] = 0.f;
+                if (sv(slot[q])) {
+                    const int n = sn(slot[q]);
+                    z[q] = (r[q] + offsum<float, S>(aE, aN, e, n)) * cl_idiag(aE, aN, n);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NPT; ++q) rz_new += r[q] * z[q];
+            rz_new = cluster_sum(rz_new, cbuf[parity], pcb[parity], rank);
+            parity ^= 1;
+            const float beta = (it == 0) ? 0.f : rz_new / rz;
+            rz = rz_new;
+#pragma unroll
+            for (int q = 0; q < NPT; ++q) {
+                pv[q] = (it == 0) ? z[q] : z[q] + beta * pv[q];
+                if (sv(slot[q])) {
+                    e[sn(slot[q])] = pv[q];
+                    if (ssend(slot[q])) st_peer(pe + 4u * sn(slot[q]), pv[q]);
+                }
+            }
+            cluster_sync();
+            float qv[NPT];
+            float pq = 0.f;
+#pragma unroll
+            for (int q = 0; q < NPT; ++q) {
+                qv[q] = 0.f;
+                if (sv(slot[q])) {
+                    qv[q] = stencil_apply_at<float, S>(aE, aN, e, sn(slot[q]), pv[q]);
+                    pq += pv[q] * qv[q];
+                }
+            }
+            pq = cluster_sum(pq, cbuf[parity], pcb[parity], rank);
+            parity ^= 1;
+            const float alpha = rz / pq;
+            float rr = 0.f;
+#pragma unroll
+            for (int q = 0; q < NPT; ++q) {
+                d[q] = fmaf(alpha, pv[q], d[q]);
+                r[q] = fmaf(-alpha, qv[q], r[q]);
+                rr += r[q] * r[q];
+            }
+#pragma unroll
+            for (int q = 0; q < NPH; ++q)   // red pre-sweep of the next cycle
+                if (sv(slot[q])) {
+                    const int n = sn(slot[q]);
+                    const float v = r[q] * cl_idiag(aE, aN, n);
+                    e[n] = v;
+                    if (ssend(slot[q])) st_peer(pe + 4u * n, v);
+                }
+            rr = cluster_sum(rr, cbuf[parity], pcb[parity], rank);
+            parity ^= 1;
+            ++total_it;
+            if (!(rr > stop2)) break;
+        }
+        // refinement: x += d, r -= A d in double-float arithmetic (edge form, as in the one-CTA forms)
+#pragma unroll
+        for (int q = 0; q < NPT; ++q)
+            if (sv(slot[q])) {
+                e[sn(slot[q])] = d[q];
+                if (ssend(slot[q])) st_peer(pe + 4u * sn(slot[q]), d[q]);
+            }
+        cluster_sync();
+        float rr_out = 0.f;
+#pragma unroll
+        for (int q = 0; q < NPT; ++q)
+            if (sv(slot[q])) {
+                const int n = sn(slot[q]);
+                const float di = e[n];
+                const float w[4] = {aE[n], aE[n - 1], aN[n], aN[n - S]};
+                const float dj[4] = {e[n + 1], e[n - 1], e[n + S], e[n - S]};
+                float ah = 0.f, al = 0.f;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    float sh, sl;
+                    two_sum(di, -dj[t], sh, sl);
+                    const float ph = __fmul_rn(w[t], sh);
+                    float pl = fmaf(w[t], sh, -ph);
+                    pl = fmaf(w[t], sl, pl);
+                    df_add(ah, al, ph, pl);
+                }
+                float rh = RH(q), rl = RL(q), xh = XH(q), xl = XL(q);
+                df_add(rh, rl, -ah, -al);
+                df_add(xh, xl, d[q], 0.f);
+                RH(q) = rh;
+                RL(q) = rl;
+                XH(q) = xh;
+                XL(q) = xl;
+                rr_out += rh * rh;
+            }
+        rr_out = cluster_sum(rr_out, cbuf[parity], pcb[parity], rank);
+        parity ^= 1;
+        converged = rr_out <= stop_outer;
+    }
+
+    // ---- observations and misfit (FP64): each CTA writes its strip's solution (double-float pair
+    // as float2, boundary nodes zero) over the edge weights; warp 0 of rank 0 gathers from both
+    float2* xs = reinterpret_cast<float2*>(aE);   // FS float2 = the aE and aN arrays
+    for (int n = tid; n < FS; n += T) xs[n] = make_float2(0.f, 0.f);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NPT; ++q)
+        if (sv(slot[q])) xs[sn(slot[q])] = make_float2(XH(q), XL(q));
+    cluster_sync();
+    if (rank == 0 && tid < 32) {
+        const uint32_t pxs = peer_addr(smem_addr(xs), 1);
+        auto val = [&](int n) -> double {   // n = j S + i on the whole level
+            const int j = n / S, i = n - j * S;
+            float2 v;
+            if (j <= 64) v = xs[j * S + i];
+            else v = ld_peer2(pxs + 8u * (uint32_t)((j - 64) * S + i));
+            return (double)v.x + (double)v.y;
+        };
+        double misfit = 0.0;
+        for (int o = tid; o < a.n_obs; o += 32) {
+            const double g = a.obs_w[3 * o] * val(a.obs_idx[3 * o]) + a.obs_w[3 * o + 1] * val(a.obs_idx[3 * o + 1]) +
+                             a.obs_w[3 * o + 2] * val(a.obs_idx[3 * o + 2]);
+            if (a.G) a.G[(size_t)p * a.n_obs + o] = g;
+            const double rdf = a.y[o] - g;
+            misfit += rdf * rdf;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) misfit += __shfl_xor_sync(0xffffffffu, misfit, off);
+        if (tid == 0) {
+            a.Phi[p] = 0.5 * misfit * a.inv_sigma2;
+            if (a.iters) a.iters[p] = converged ? total_it : -(total_it + 1);
+        }
+    }
+}
+
+// persistent clusters: rank 0 takes the next particle from the counter and hands it to rank 1;
+// the cluster barrier at the end of each particle keeps either CTA from overwriting memory the
+// other still reads (halo rows, coarse rows, the solution gathered by rank 0, the ticket)
+template <bool RHS>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl::T, 1)
+    fem_eval_cluster(FemArgs a, float* ref_scratch, int* counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) float cbuf[2][64];
+    __shared__ int item_s;
+    const int rank = cluster_rank();
+    float* ref = ref_scratch + (size_t)blockIdx.x * cl::REF_FLOATS;
+    const uint32_t p_item = peer_addr(smem_addr(&item_s), rank ^ 1);
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const int item = atomicAdd(counter, 1);
+            item_s = item;
+            st_peer(p_item, item);
+        }
+        cluster_sync();
+        const int item = item_s;
+        if (item >= a.n) break;   // the same item in both CTAs
+        solve_particle_cl<RHS>(a, item, reinterpret_cast<float*>(smem_raw), cbuf, ref, rank);
+        cluster_sync();
+    }
+}
+
 // persistent form: grid-sized blocks pull (group, particle) items from a device counter; every
 // group is one problem's launch arguments at this level size (many independent inverse problems
 // in one launch)
@@ -1412,6 +1840,33 @@ int compact_resident_blocks() {
     return sms * std::max(1, per_sm);
 }
 
+// ---- two-CTA cluster form of 1/128 ----
+template <bool RHS>
+int cluster_resident_clusters() {
+    const size_t smem = sizeof(float) * (size_t)cl::SMEM_FLOATS;
+    cudaFuncSetAttribute(fem_eval_cluster<RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(cl::T, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (const void*)fem_eval_cluster<RHS>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <bool RHS>
+cudaError_t launch_cluster_t(const FemArgs& a, float* ref_scratch, int blocks, int* counter, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (size_t)cl::SMEM_FLOATS;
+    cudaError_t e = cudaFuncSetAttribute(fem_eval_cluster<RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fem_eval_cluster<RHS><<<blocks, cl::T, smem, st>>>(a, ref_scratch, counter);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int fem_compact_blocks(int N, int T) {
@@ -1427,6 +1882,28 @@ int fem_compact_blocks(int N, int T) {
     return blocks;
 }
 size_t fem_compact_ref_floats(int N, int T) { return (size_t)4 * fine_slots(N, T) * T; }
+
+int fem_cluster_blocks() {
+    // CTAs of the two-CTA form that are resident at once, queried once per device
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+    const int blocks = 2 * cluster_resident_clusters<false>();
+    if (dev >= 0 && dev < 64 && blocks > 0) cached[dev] = blocks;
+    return blocks;
+}
+size_t fem_cluster_ref_floats() { return (size_t)cl::REF_FLOATS; }
+
+cudaError_t fem_eval_cluster_launch(const FemArgs& a, float* ref_scratch, int blocks, int* counter, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    if (a.N != 128 || a.precision != SMC_MIXED || !a.kappa || a.flow_cell || blocks < 2) return cudaErrorInvalidValue;
+    const int grid = 2 * std::max(1, std::min(a.n, blocks / 2));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    return a.rhs ? launch_cluster_t<true>(a, ref_scratch, grid, counter, st)
+                 : launch_cluster_t<false>(a, ref_scratch, grid, counter, st);
+}
 
 cudaError_t fem_eval_compact_launch(const FemArgs& a, int T, float* ref_scratch, int blocks, int* counter,
                                     cudaStream_t st) {
@@ -1522,9 +1999,13 @@ bool fem_level_supported(int N, int precision) {
 }
 
 // the block size used when none was chosen: the compact form where it is compiled (it is
-// faster at J = 4000 on 1/32 and 1/64, and bit-identical to the size -T), else the first size
+// faster at J = 4000 on 1/32 and 1/64, and bit-identical to the size -T), the two-CTA form on
+// 1/128, else the first size
 int fem_default_block(int N, int precision) {
     if (precision == SMC_MIXED && (N == 32 || N == 64)) return N == 64 ? -512 : -256;
+    // 1/128: the two-CTA cluster form where a cluster fits (1.2x the device-memory form at J = 4000
+    // and 8000), else the device-memory form
+    if (precision == SMC_MIXED && N == 128) return fem_cluster_blocks() >= 2 ? -1024 : 1024;
     const std::vector<int> s = fem_block_sizes(N, precision);
     return s.empty() ? 0 : s[0];
 }
@@ -1538,7 +2019,7 @@ std::vector<int> fem_block_sizes(int N, int precision) {
             case 16: return {128, 64};
             case 32: return {256, 512, -256};   // -256: compact form, four blocks per SM
             case 64: return {512, 1024, -512};  // -512: compact form, two blocks per SM
-            case 128: return {1024};
+            case 128: return {1024, -1024};     // -1024: two-CTA cluster form (fine level on chip)
             case 256: return {1024};
         }
     } else {

@@ -94,6 +94,13 @@ int fem_compact_blocks(int N, int T);
 size_t fem_compact_ref_floats(int N, int T);
 cudaError_t fem_eval_compact_launch(const FemArgs& a, int T, float* ref_scratch, int blocks, int* counter,
                                     cudaStream_t st);
+// two-CTA cluster form of the mixed 1/128 solve (block size -1024 of fem_block_sizes): the fine
+// level split in row strips over the two CTAs of a cluster, each on its own SM;
+// fem_cluster_blocks() CTAs (0 where no cluster fits) with fem_cluster_ref_floats() floats of
+// device scratch each for the refinement state; *counter (device) is reset by the launch
+int fem_cluster_blocks();
+size_t fem_cluster_ref_floats();
+cudaError_t fem_eval_cluster_launch(const FemArgs& a, float* ref_scratch, int blocks, int* counter, cudaStream_t st);
 bool fem_level_supported(int N, int precision);
 
 }  // namespace mls2mc

@@ -173,15 +173,21 @@ def test_every_block_size_and_autotuner(prec):
         h.set_block_size(l, 0)
 
 
-@pytest.mark.parametrize("N,n", [(128, 5), (256, 2)])
-def test_large_levels_parity(N, n):
-    """1/h = 128 and 256 (hierarchy in device memory): mixed-path G within 1e-6 of the oracle."""
+@pytest.mark.parametrize("N,n,B", [(128, 5, 1024), (128, 5, -1024), (128, 1, -1024), (256, 2, 0)])
+def test_large_levels_parity(N, n, B):
+    """1/h = 128 in both forms (1024: fine level in device memory; -1024: fine level on chip across the
+    two CTAs of a cluster, also with a single particle) and 1/256: mixed-path G within 1e-6 of the
+    oracle."""
     w = wl.WORKLOADS["mls2mc_mixed_h8_64"]
     d = _data(w.name)
     obs = wl.obs_grid(7)
     theta = wl.particles(n, w.K, 300 + N)
     h = native.Handle([N], w.K, obs, d["y"], d["sigma"], corr_len=w.corr_len, precision=native.SMC_MIXED)
+    if B:
+        h.set_block_size(0, B)
+        assert h.block_size(0) == B
     G, Phi = h.eval_likelihood(0, theta)
+    h.set_block_size(0, 0)
     Gr, Phir = _oracle(N, w, theta, obs, np.array(d["y"]), d["sigma"])
     assert _rel(G, Gr).max() < 1e-6
     assert _phi_ok(Phi, Phir, Gr, d["sigma"], 1e-6)
@@ -225,6 +231,33 @@ def test_full_size_sampled_parity_large_workloads(name):
     Gr, Phir = _oracle(w.inv_h[-1], w, theta[idx], obs, np.array(d["y"]), d["sigma"])
     assert _rel(G.cpu().numpy()[idx], Gr).max() < 1e-6
     assert _phi_ok(Phi.cpu().numpy()[idx], Phir, Gr, d["sigma"], 1e-6)
+
+
+@pytest.mark.parametrize("K,J", [(32, 4000), (64, 8000)])
+def test_cluster_form_agrees_with_device_memory_form(K, J):
+    """1/128 at the surrogate workload's launch size (K = 64, J = 8000) and at J = 4000: the two-CTA
+    form (the default) and the device-memory form run the same algorithm except for the rounding of
+    the fine level's smoother diagonal, so every solve converges in both, the iteration counts
+    differ by at most one and the observations agree far inside the 1e-6 parity bar."""
+    import torch
+    obs = wl.obs_grid(7)
+    h = native.Handle([128], K, obs, np.zeros(49), 1.0, corr_len=0.1, precision=native.SMC_MIXED)
+    assert h.block_size(0) == -1024
+    theta = torch.from_numpy(wl.particles(J, K, 5151)).cuda()
+    out = {}
+    for B in (1024, -1024):
+        h.set_block_size(0, B)
+        G = torch.empty((J, 49), dtype=torch.float64, device="cuda")
+        Phi = torch.empty(J, dtype=torch.float64, device="cuda")
+        it = torch.empty(J, dtype=torch.int32, device="cuda")
+        h.eval_likelihood_device(0, J, theta.data_ptr(), G.data_ptr(), Phi.data_ptr(), it.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert int(it.min()) > 0, B
+        out[B] = (G.cpu().numpy(), it.cpu().numpy())
+    h.set_block_size(0, 0)
+    assert np.abs(out[1024][1] - out[-1024][1]).max() <= 1
+    assert _rel(out[-1024][0], out[1024][0]).max() < 1e-7
 
 
 @pytest.mark.parametrize("inv_h,T", [(64, 512), (32, 256)])

@@ -19,8 +19,8 @@ from paper_1709_09763_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 W = wl.WORKLOADS["example_5_1"]
-# compiled threads-per-particle variants (negative: compact forms); 1/128 has one form
-SIZES = {native.SMC_MIXED: {8: [64, 32], 16: [128, 64], 32: [256, 512, -256], 64: [512, 1024, -512], 128: [0]},
+# compiled threads-per-particle variants (negative: compact forms; -1024 at 1/128: the two-CTA form)
+SIZES = {native.SMC_MIXED: {8: [64, 32], 16: [128, 64], 32: [256, 512, -256], 64: [512, 1024, -512], 128: [1024, -1024]},
          native.SMC_FP64: {8: [64], 16: [128, 256], 32: [256, 512]}}
 
 
