@@ -123,34 +123,74 @@ __global__ void loss_grad_kernel(const float* Z, const float* tgt, int B, int NO
     }
 }
 
-// bias gradient: row sums of dZ^T [rows][ld] over the first B columns (one warp per row)
-__global__ void rowsum_kernel(const __nv_bfloat16* Xt, int rows, int B, int ld, float* out) {
-    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (r >= rows) return;
+// bias gradient: row sums of dZ^T [rows][ld] over the first B columns, one block of kRowsumThreads
+// per row: each thread sums eight columns per 16-byte load (ld is a multiple of 8), then a fixed
+// warp-shuffle and per-warp order (deterministic)
+constexpr int kRowsumThreads = 256;
+__global__ void __launch_bounds__(kRowsumThreads) rowsum_kernel(const __nv_bfloat16* Xt, int B, int ld, float* out) {
+    __shared__ float sh[kRowsumThreads / 32];
+    const __nv_bfloat16* x = Xt + (size_t)blockIdx.x * ld;
+    const int B8 = B & ~7;
     float s = 0.0f;
-    for (int b = lane; b < B; b += 32) s += __bfloat162float(Xt[(size_t)r * ld + b]);
+    for (int b = threadIdx.x * 8; b < B8; b += kRowsumThreads * 8) {
+        const uint4 u = *reinterpret_cast<const uint4*>(x + b);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __bfloat1622float2(h[k]);
+            s += f.x;
+            s += f.y;
+        }
+    }
+    for (int b = B8 + threadIdx.x; b < B; b += kRowsumThreads) s += __bfloat162float(x[b]);
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) out[r] = s;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kRowsumThreads / 32; ++w) t += sh[w];
+        out[blockIdx.x] = t;
+    }
 }
 
-__global__ void adam_kernel(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
-                            float eps, float c1, float c2, __nv_bfloat16* wb, __nv_bfloat16* wt, int rows, int cols,
-                            int ld_t) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = g[i];
+// the ten parameter tensors of one network (weights and biases of five layers) for one Adam launch
+struct AdamSet {
+    float* w[10];
+    const float* g[10];
+    float* m[10];
+    float* v[10];
+    __nv_bfloat16* wb[10];   // BF16 copy and its transpose [cols][ld_t] (weights only)
+    __nv_bfloat16* wt[10];
+    int cols[10];
+    int ld_t[10];
+    int start[11];           // element offsets of the tensors in the launch's index space
+};
+
+// one Adam step of every tensor of a network (Kingma & Ba 2015): element i of the launch belongs to
+// the tensor whose [start, next start) holds it; per element the arithmetic of a single-tensor step
+__global__ void adam_all_kernel(AdamSet a, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int gi_ = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi_ >= a.start[10]) return;
+    int t = 0;
+#pragma unroll
+    for (int k = 1; k < 10; ++k) t += gi_ >= a.start[k];
+    const int i = gi_ - a.start[t];
+    float* w = a.w[t];
+    float* m = a.m[t];
+    float* v = a.v[t];
+    const float gi = a.g[t][i];
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
     const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     w[i] = wi;
-    if (wb) {
+    if (a.wb[t]) {
         const __nv_bfloat16 h = __float2bfloat16_rn(wi);
-        wb[i] = h;
-        const int r = i / cols, c = i - r * cols;
-        (void)rows;
-        wt[(size_t)c * ld_t + r] = h;
+        a.wb[t][i] = h;
+        const int r = i / a.cols[t], c = i - r * a.cols[t];
+        a.wt[t][(size_t)c * a.ld_t[t] + r] = h;
     }
 }
 
@@ -423,8 +463,7 @@ int Handle::mlp_backward(int level, int B, double* loss) {
         ew.ws_floats = mwork.splitk_floats;
         cudaError_t e = umma_gemm(mwork.dZt[l], ldt, mwork.Xt[l], ldt, S.d[l + 1], S.d[l], B, ew, S.err, stream);
         if (e != cudaSuccess) return cuda_fail(e, "surrogate weight-gradient GEMM");
-        rowsum_kernel<<<grid_of((long long)S.d[l + 1] * 32, 256), 256, 0, stream>>>(mwork.dZt[l], S.d[l + 1], B, ldt,
-                                                                                    S.gb[l]);
+        rowsum_kernel<<<S.d[l + 1], kRowsumThreads, 0, stream>>>(mwork.dZt[l], B, ldt, S.gb[l]);
         count_launches(1);
         if (l > 0) {
             // input gradient through the GELU of layer l-1: dZ_{l-1} = (dZ_l W_l) * GELU'(pre_{l-1})
@@ -457,14 +496,23 @@ int Handle::mlp_adam(int level) {
     S.t += 1;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.0f - std::pow(b1, (float)S.t), c2 = 1.0f - std::pow(b2, (float)S.t);
+    AdamSet a;
+    int off = 0;
     for (int l = 0; l < 5; ++l) {
-        const int rows = S.d[l + 1], cols = S.d[l], n = rows * cols;
-        adam_kernel<<<grid_of(n, 256), 256, 0, stream>>>(S.Wm[l], S.gW[l], S.mW[l], S.vW[l], n, mlp_lr, b1, b2, eps,
-                                                        c1, c2, S.W[l], S.Wt[l], rows, cols, rows);
-        adam_kernel<<<grid_of(rows, 256), 256, 0, stream>>>(S.bm[l], S.gb[l], S.mb[l], S.vb[l], rows, mlp_lr, b1, b2,
-                                                           eps, c1, c2, nullptr, nullptr, 0, 1, 0);
-        count_launches(2);
+        const int rows = S.d[l + 1], cols = S.d[l];
+        const int tw = 2 * l, tb = 2 * l + 1;
+        a.w[tw] = S.Wm[l], a.g[tw] = S.gW[l], a.m[tw] = S.mW[l], a.v[tw] = S.vW[l];
+        a.wb[tw] = S.W[l], a.wt[tw] = S.Wt[l], a.cols[tw] = cols, a.ld_t[tw] = rows;
+        a.start[tw] = off;
+        off += rows * cols;
+        a.w[tb] = S.bm[l], a.g[tb] = S.gb[l], a.m[tb] = S.mb[l], a.v[tb] = S.vb[l];
+        a.wb[tb] = nullptr, a.wt[tb] = nullptr, a.cols[tb] = 1, a.ld_t[tb] = 0;
+        a.start[tb] = off;
+        off += rows;
     }
+    a.start[10] = off;
+    adam_all_kernel<<<grid_of(off, 256), 256, 0, stream>>>(a, mlp_lr, b1, b2, eps, c1, c2);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SMC_OK : cuda_fail(e, "surrogate Adam step");
 }

@@ -110,19 +110,6 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
     asm volatile(
@@ -304,18 +291,59 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 __syncwarp();
             }
         } else {
-            const int row = m0 + 32 * warp + lane;
+            // bias + GELU (forward) and GELU' (input gradient): 32 x 32 blocks staged through shared
+            // memory twice, so that the row-major outputs (pre-activation, activation) are written 32
+            // consecutive columns of one row per instruction and the transposed copy 32 consecutive
+            // rows of one column per instruction (a lane holding a row would write each column of the
+            // row-major outputs to 32 separate sectors)
+            float* st = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw))) + warp * (2 * 32 * 33);
+            float* st2 = st + 32 * 33;
+            const int row0 = m0 + 32 * warp;
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                float v[16];
-                tmem_ld16(t_row + (uint32_t)c0, v);
-                if (row < M) {
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                const int col = n0 + c0 + lane;
+                // the input gradient's pre-activations of this block: all 32 loads issued before the
+                // accumulator is read, one per row (32 consecutive columns per load instruction)
+                float pin[32];
+                if (epi.kind == kEpiGeluBackward) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int col = n0 + c0 + i;
-                        if (col < N) epilogue(epi, row, col, v[i]);
+                    for (int rr = 0; rr < 32; ++rr)
+                        pin[rr] = (row0 + rr < M && col < N) ? epi.pre_in[(size_t)(row0 + rr) * epi.ld_pre + col] : 0.0f;
+                }
+                float v[32];
+                tmem_ld32(t_row + (uint32_t)c0, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) st[lane * 33 + i] = v[i];
+                __syncwarp();
+                const float bcol = (epi.kind == kEpiBiasGelu && col < N) ? epi.bias[col] : 0.0f;
+#pragma unroll
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int row = row0 + rr;
+                    float out = 0.0f;
+                    if (row < M && col < N) {
+                        const float acc = st[rr * 33 + lane];
+                        __nv_bfloat16 h;
+                        if (epi.kind == kEpiBiasGelu) {
+                            const float z = acc + bcol;
+                            if (epi.pre) epi.pre[(size_t)row * epi.ld_pre + col] = z;
+                            h = __float2bfloat16_rn(gelu_f(z));
+                        } else {
+                            h = __float2bfloat16_rn(acc * gelu_grad_f(pin[rr]));
+                        }
+                        epi.act[(size_t)row * epi.ld_act + col] = h;
+                        out = __bfloat162float(h);   // exact: the transposed copy gets the same bits
+                    }
+                    st2[rr * 33 + lane] = out;
+                }
+                __syncwarp();
+                if (epi.act_t && row0 + lane < M) {
+#pragma unroll 4
+                    for (int i = 0; i < 32; ++i) {
+                        const int c = n0 + c0 + i;
+                        if (c < N) epi.act_t[(size_t)c * epi.ld_act_t + row0 + lane] = __float2bfloat16_rn(st2[lane * 33 + i]);
                     }
                 }
+                __syncwarp();
             }
         }
     } else if (lane == 0) {
@@ -337,7 +365,8 @@ __global__ void splitk_reduce_kernel(const float* ws, int splits, int M, int N, 
     const int r = (int)(t / N), c = (int)(t - (long long)r * N);
     const size_t i = (size_t)r * ld + c, slice = (size_t)M * ld;
     float acc = 0.0f;
-    for (int z = 0; z < splits; ++z) acc += ws[(size_t)z * slice + i];
+#pragma unroll 8
+    for (int z = 0; z < splits; ++z) acc += ws[(size_t)z * slice + i];   // in split order
     out[i] = acc;
 }
 
@@ -444,7 +473,11 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
 cudaError_t umma_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, const GemmEpi& epi,
                       int* err, cudaStream_t st) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-    const int bn = N <= 64 ? 64 : 128;
+    // 128-wide output tiles, or 64-wide ones where 128-wide tiles would leave SMs without one (the
+    // surrogate's 256-wide layers: 128 tiles of 128 x 128 at a minibatch of 8192 against 256 of
+    // 128 x 64, whose GELU epilogues then run on twice the warps)
+    int bn = N <= 64 ? 64 : 128;
+    if (bn == 128 && (long long)((N + 127) / 128) * ((M + BM - 1) / BM) < 152) bn = 64;
     CUtensorMap ta, tb, tc;
     if (!cached_map(&ta, A, M, K, lda, BM) || !cached_map(&tb, B, N, K, ldb, bn)) return cudaErrorInvalidValue;
     GemmEpi e2 = epi;
