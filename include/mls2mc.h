@@ -358,11 +358,14 @@ int smc_batch_run(smc_batch* b, int max_steps, int* steps);
 /* dims6 <- the six layer widths d0..d5. */
 int smc_surrogate_dims(smc_handle* h, int* dims6);
 
-/* The screening gate of surrogate = 1 on one level: *decision 0 not measured yet, 1 the level is
- * screened, -1 it is not; *solve_ms and *predict_ms the device times it compared (an exact solve
- * of J particles against a surrogate forward pass of J particles; the level is screened when the
- * solve costs more than 8 passes). Zero times when not measured or when surrogate = 2 forces the
- * screen. Any output pointer may be NULL. SMC_EINVAL for a null handle or a bad level. */
+/* The screening gate of surrogate = 1 on one level (not in the paper): *decision 0 undecided, 1 the
+ * level is screened, -1 it is not; *solve_ms and *predict_ms the device times it compared (an exact
+ * solve of J particles against a surrogate forward pass of J particles). A level whose solve costs at
+ * most 8 passes is never screened; above that, it is screened from the first update whose own
+ * n_mcmc sweeps of exact solves, with those already run on the level, cost twice its first training
+ * round (estimated as the round's Adam steps times 4 forward passes of the minibatch); until then
+ * the decision stays 0 and its training pairs are collected. Zero times when not measured or when surrogate = 2 forces the screen. Any
+ * output pointer may be NULL. SMC_EINVAL for a null handle or a bad level. */
 int smc_surrogate_gate(const smc_handle* h, int level, int* decision, double* solve_ms, double* predict_ms);
 /* Append n training pairs (theta [n][K], G [n][n_obs], host) to level's ring of recent pairs. */
 int smc_surrogate_add_pairs(smc_handle* h, int level, int n, const double* theta, const double* G);

@@ -197,11 +197,20 @@ int Handle::read_counters(unsigned long long* acc, IncState* pending) {
     return SMC_OK;
 }
 
-// Whether screening pays on a level: measured once per level (events on the handle's stream) as
-// the device time of an exact solve of J particles against a surrogate forward pass of J
-// particles; the screen is used where the solve costs more than kDaCostRatio forward passes
-// (the screen adds a forward pass, a compaction and a host read per pCN step).
+// Whether screening pays on a level (not in the paper). Measured once per level (events on the
+// handle's stream): the device time of an exact solve of J particles against a surrogate forward
+// pass of J particles; a level whose solve costs at most kDaCostRatio forward passes is never
+// screened (the screen adds a forward pass, a compaction and a host read per Markov step). A level
+// above that ratio is screened from the first update whose own Markov steps' exact solves, with
+// those already run on the level, cost kDaAmortize times the level's first training round (rent or
+// buy over the work known so far: a level the sampler passes through with little work never pays
+// for a network, one it stays on pays a bounded multiple of the best choice in hindsight). The
+// first round is estimated as its Adam steps times kDaTrainStepPasses forward passes of the
+// minibatch (one step measured 0.30 ms against about 0.075 ms for a forward pass of 8000 rows at
+// K = 64).
 constexpr double kDaCostRatio = 8.0;
+constexpr double kDaAmortize = 2.0;
+constexpr double kDaTrainStepPasses = 4.0;
 
 namespace {
 // a surrogate forward pass of J particles has the same shapes on every level (K -> 4 x 256 -> n_obs):
@@ -270,13 +279,26 @@ bool Handle::da_worth(int level) {
         da_gate[level] = 1;
         return true;
     }
-    PhaseTimer pt(this, kPhGate);
-    const float t_solve = da_solve_ms(level);
-    const float t_pred = t_solve > 0.f ? da_predict_ms(level) : -1.f;
-    da_t_solve[level] = std::max(t_solve, 0.f);
-    da_t_pred[level] = std::max(t_pred, 0.f);
-    da_gate[level] = (t_solve > 0.f && t_pred > 0.f && t_solve > kDaCostRatio * t_pred) ? 1 : -1;
-    return da_gate[level] > 0;
+    if (!(da_t_solve[level] > 0.f)) {   // the cost ratio, measured once
+        PhaseTimer pt(this, kPhGate);
+        const float t_solve = da_solve_ms(level);
+        const float t_pred = t_solve > 0.f ? da_predict_ms(level) : -1.f;
+        da_t_solve[level] = std::max(t_solve, 0.f);
+        da_t_pred[level] = std::max(t_pred, 0.f);
+        if (!(t_solve > 0.f && t_pred > 0.f && t_solve > kDaCostRatio * t_pred)) {
+            da_gate[level] = -1;
+            return false;
+        }
+    }
+    // amortization: the exact-solve time spent on the level so far and the coming update's Markov
+    // steps against the level's first training round
+    const int steps = opts.surrogate_train_steps > 0 ? opts.surrogate_train_steps : 50;
+    const int batch = opts.surrogate_batch > 0 ? opts.surrogate_batch : 8192;
+    const double t_train = steps * kDaTrainStepPasses * (double)da_t_pred[level] * batch / smp->J;
+    const double work = ((double)smp->evals[level] / smp->J + opts.n_mcmc) * da_t_solve[level];
+    if (work < kDaAmortize * t_train) return false;   // not yet: the gate stays undecided
+    da_gate[level] = 1;
+    return true;
 }
 
 // training schedule: once the level has J pairs, then again after every 4 J new pairs (50 Adam
@@ -410,12 +432,17 @@ int Handle::shape_factor() {
 // increment search left it) instead of the host value; pending: the search state to read back
 // with the counters
 int Handle::mcmc(int level, double zeta, double& rate, const double* beta_p, IncState* pending, const double* zeta_p) {
-    // networks are trained only for targets whose every level is worth screening
-    if (may_screen(level, zeta)) {
+    // The moves may be screened only where the host holds the target (the update waited for its
+    // increment); an update that reads beta or zeta on the device, with the search state still to
+    // be read back, keeps exact moves even when the screening gate opens during it (its solves can
+    // complete the gate's amortization), and the next update screens. Networks are trained only
+    // for targets whose every level is worth screening.
+    const bool host_target = !beta_p && !pending && !zeta_p;
+    if (host_target && may_screen(level, zeta)) {
         RC(maybe_train(level));
         if (zeta >= 0.0) RC(maybe_train(level + 1));
     }
-    if (da_ready(level, zeta)) return mcmc_da(level, zeta, rate);
+    if (host_target && da_ready(level, zeta)) return mcmc_da(level, zeta, rate);
     Sampler* S = smp;
     const bool rwm = opts.proposal != SMC_PROP_PCN;
     const double s = mcmc_step();
@@ -638,10 +665,11 @@ int Handle::lu(int head, smc_stage_info* info) {
     int nb = 0;
     IncState st;
     double rate = 0.0;
-    // the moves read zeta on the device unless they may be screened; the search state comes back
-    // with the moves' counters (one host wait per bridging step)
-    const bool wait = may_screen(l, 0.0);
     while (zeta < 1.0) {
+        // the moves read zeta on the device unless they may be screened; the search state comes
+        // back with the moves' counters (one host wait per bridging step). Decided per bridging
+        // step: the solves of one step can open the screening gate for the next.
+        const bool wait = may_screen(l, 0.0);
         CK(lu_increment_launch(S->phi_c, S->phi_f, S->J, S->beta, S->a, stream));
         RC(reweight_resample(S->a, 1.0 - zeta, zeta, true, st, wait));
         if (wait) {

@@ -74,23 +74,35 @@ def test_delayed_acceptance_same_posterior_fewer_solves(proposal):
 
 
 def test_cost_gate_follows_measured_costs():
-    """surrogate = 1 screens a level exactly when its measured exact solve of J particles costs more
-    than 8 surrogate passes: single-level SMC on 1/h = 64 with J = 1500 (every update an ITU on that
-    level) measures the gate once, screens its updates iff the gate says so, and reaches beta = 1."""
+    """surrogate = 1 never screens a level whose measured exact solve of J particles costs at most 8
+    surrogate passes; above that it screens from the first update whose own 5 sweeps of exact solves,
+    with those already run on the level, cost twice the first training round (50 Adam steps, each
+    estimated as 4 forward passes of its minibatch). Single-level SMC on 1/h = 64 with J = 1500 and
+    minibatches of 1500 (every update an ITU on that level): the gate's decision and the first
+    screened update follow the measured times, and the sampler reaches beta = 1."""
     K, obs, y, sigma = _problem()
-    h = native.Handle([64], K, obs, y, sigma, corr_len=0.3, J=1500, n_mcmc=5, s_pcn=0.3,
-                      precision=native.SMC_MIXED, seed=7, surrogate=1)
+    J = 1500
+    h = native.Handle([64], K, obs, y, sigma, corr_len=0.3, J=J, n_mcmc=5, s_pcn=0.3,
+                      precision=native.SMC_MIXED, seed=7, surrogate=1, surrogate_batch=J)
     h.run()
     path = h.path()
     assert all(p["kind"] == "ITU" for p in path)
     dec, t_solve, t_pred = h.surrogate_gate(0)
-    assert dec != 0 and t_solve > 0 and t_pred > 0
-    assert (dec > 0) == (t_solve > 8 * t_pred)
+    assert t_solve > 0 and t_pred > 0
+    assert (dec < 0) == (t_solve <= 8 * t_pred)
     screened = [p["da_stage1_rate"] >= 0 for p in path]
+    assert any(screened) == (dec > 0)
+    # exact-solve ms after each update, and with the next update's 5 sweeps
+    spent = [p["evals_per_level"][0] * t_solve / J for p in path]
+    threshold = 2 * 50 * 4 * t_pred
     if dec > 0:
-        assert any(screened)
-    else:
-        assert not any(screened)
+        u = screened.index(True)
+        if u >= 1:   # at the start of update u the level had spent spent[u - 1] (its updates add solves only in moves)
+            assert spent[u - 1] + 5 * t_solve >= threshold
+        if u >= 2:   # and at the start of update u - 1, spent[u - 2]
+            assert spent[u - 2] + 5 * t_solve < threshold
+    elif dec == 0:
+        assert len(path) < 2 or spent[-2] + 5 * t_solve < threshold
     assert h.state()["beta"] == 1.0
 
 
