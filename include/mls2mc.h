@@ -193,7 +193,8 @@ int smc_set_timing(smc_handle* h, int enable);
  * CTAs of 1024 threads on two SMs, each keeping half of the fine rows on chip with one halo row from
  * the other through distributed shared memory, the coarse levels 1/64 .. 1/2 in both (the same
  * algorithm as 1024, which keeps the fine level in device memory; potentials agree to rounding).
- * Batched and flow-cell solves on 1/128 run the device-memory form. */
+ * Batched solves on 1/128 run the two-CTA form where a cluster fits; flow-cell solves the
+ * device-memory form. */
 int smc_autotune(smc_handle* h, int n_tune, int* chosen, float* best_ms);
 int smc_set_block_size(smc_handle* h, int level, int T);
 /* The block size the solves of `level` run with (set, tuned or the default) into *T. */

@@ -36,9 +36,9 @@ int enqueue(Batch* b, const int* level, const int* n, const double* const* theta
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->groups.size(), st);
     for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g) {
         const auto& G = b->groups[g];
-        if (G.N >= 128)
-            e = fem_eval_global_multi_launch(G.N, G.d_args, G.d_offsets, G.d_item_group, G.total, b->big_scratch,
-                                             b->big_blocks, b->d_counters + g, st);
+        if (G.N >= 128)   // the form single solves default to (two-CTA on 1/128)
+            e = fem_eval_large_multi_launch(G.N, G.d_args, G.d_offsets, G.d_item_group, G.total, b->big_scratch,
+                                            b->d_counters + g, st);
         else
             e = fem_eval_persistent_launch(G.N, G.precision, G.T, G.d_args, G.d_offsets, G.d_item_group, G.total,
                                            b->d_counters + g, st);
@@ -137,11 +137,7 @@ int smc_batch_eval(smc_batch* bb, const int* level, const int* n, const double* 
         cudaError_t e = cudaMalloc((void**)&b->d_counters, sizeof(int) * std::max<size_t>(1, b->groups.size()));
         size_t big_need = 0;   // one scratch for all large groups: they run one after another
         for (auto& G : b->groups)
-            if (G.N >= 128) {
-                const int blocks = fem_global_blocks(G.N);
-                b->big_blocks = std::max(b->big_blocks, blocks);
-                big_need = std::max(big_need, (size_t)blocks * fem_global_slice(G.N));
-            }
+            if (G.N >= 128) big_need = std::max(big_need, fem_large_multi_scratch(G.N));
         if (e == cudaSuccess && big_need) e = cudaMalloc((void**)&b->big_scratch, big_need * sizeof(float));
         for (auto& G : b->groups) {
             if (e == cudaSuccess) e = cudaMalloc((void**)&G.d_args, sizeof(FemArgs) * G.args.size());

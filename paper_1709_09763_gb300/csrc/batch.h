@@ -27,8 +27,7 @@ struct Batch {
     };
     std::vector<Group> groups;
     int* d_counters = nullptr;
-    float* big_scratch = nullptr;    // per-block slices for the groups of large levels (1/h >= 128)
-    int big_blocks = 0;
+    float* big_scratch = nullptr;    // per-block (per-CTA) scratch of the groups of large levels (1/h >= 128)
     std::vector<long long> signature;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -48,7 +47,6 @@ struct Batch {
         d_counters = nullptr;
         cudaFree(big_scratch);
         big_scratch = nullptr;
-        big_blocks = 0;
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         exec = nullptr;

@@ -182,12 +182,8 @@ int multi_eval(Batch* b, const std::vector<EvalReq>& reqs, cudaStream_t st) {
             S->item_cap = (size_t)items;
         }
         size_t big_need = 0;
-        int big_blocks = 0;
         for (const G& g : groups)
-            if (g.N >= 128) {
-                big_blocks = std::max(big_blocks, fem_global_blocks(g.N));
-                big_need = std::max(big_need, (size_t)fem_global_blocks(g.N) * fem_global_slice(g.N));
-            }
+            if (g.N >= 128) big_need = std::max(big_need, fem_large_multi_scratch(g.N));
         if (big_need > S->big_cap) {
             cudaFree(S->big_scratch);
             S->big_scratch = nullptr;
@@ -202,10 +198,10 @@ int multi_eval(Batch* b, const std::vector<EvalReq>& reqs, cudaStream_t st) {
         cudaError_t e = cudaGetLastError();
         for (size_t gi = 0; gi < groups.size() && e == cudaSuccess; ++gi) {
             const G& g = groups[gi];
-            if (g.N >= 128)
-                e = fem_eval_global_multi_launch(g.N, S->d_args + g.first, S->d_offsets + g.first,
-                                                 S->d_item_group + g.item_base, g.total, S->big_scratch, big_blocks,
-                                                 S->d_counters + gi, st);
+            if (g.N >= 128)   // the form single solves default to (two-CTA on 1/128)
+                e = fem_eval_large_multi_launch(g.N, S->d_args + g.first, S->d_offsets + g.first,
+                                                S->d_item_group + g.item_base, g.total, S->big_scratch,
+                                                S->d_counters + gi, st);
             else
                 e = fem_eval_persistent_launch(g.N, g.precision, g.T, S->d_args + g.first, S->d_offsets + g.first,
                                                S->d_item_group + g.item_base, g.total, S->d_counters + gi, st);
@@ -258,7 +254,7 @@ int batch_step(Batch* b, smc_stage_info* infos) {
         for (Handle* h : b->h) {
             items += (size_t)h->smp->J;
             for (const Level& L : h->levels)
-                if (L.N >= 128) big = std::max(big, (size_t)fem_global_blocks(L.N) * fem_global_slice(L.N));
+                if (L.N >= 128) big = std::max(big, fem_large_multi_scratch(L.N));
             // the syntheses' buffers at their largest (J particles on the finest level): a buffer that
             // grew inside a captured update would free memory that earlier captured launches use
             if (h->precision == SMC_MIXED) {

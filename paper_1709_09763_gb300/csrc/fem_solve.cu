@@ -1702,6 +1702,38 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl::T, 1)
     }
 }
 
+// many problems at 1/128: the same persistent clusters take (problem, particle) items; the item's
+// problem is found in a per-item table and each CTA copies its launch arguments to shared memory
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl::T, 1)
+    fem_eval_cluster_multi(const FemArgs* groups, const int* offsets, const int* item_group, int total,
+                           float* ref_scratch, int* counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) float cbuf[2][64];
+    __shared__ int item_s, p_s;
+    __shared__ FemArgs args_s;
+    const int rank = cluster_rank();
+    float* ref = ref_scratch + (size_t)blockIdx.x * cl::REF_FLOATS;
+    const uint32_t p_item = peer_addr(smem_addr(&item_s), rank ^ 1);
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const int item = atomicAdd(counter, 1);
+            item_s = item;
+            st_peer(p_item, item);
+        }
+        cluster_sync();
+        const int item = item_s;
+        if (item >= total) break;   // the same item in both CTAs
+        if (threadIdx.x == 0) {
+            const int g = item_group[item];
+            args_s = groups[g];
+            p_s = item - offsets[g];
+        }
+        __syncthreads();
+        solve_particle_cl<true>(args_s, p_s, reinterpret_cast<float*>(smem_raw), cbuf, ref, rank);
+        cluster_sync();
+    }
+}
+
 // persistent form: grid-sized blocks pull (group, particle) items from a device counter; every
 // group is one problem's launch arguments at this level size (many independent inverse problems
 // in one launch)
@@ -1952,6 +1984,30 @@ cudaError_t fem_eval_global_launch(const FemArgs& a, float* scratch, int blocks,
     if (a.N == 128) return launch_global<128, 1024>(a, scratch, slice, grid, counter, st);
     if (a.N == 256) return launch_global<256, 1024>(a, scratch, slice, grid, counter, st);
     return cudaErrorInvalidValue;
+}
+
+bool fem_cluster_form(int N, int precision, bool flow_cell) {
+    return N == 128 && precision == SMC_MIXED && !flow_cell && fem_cluster_blocks() >= 2;
+}
+
+size_t fem_large_multi_scratch(int N) {
+    if (fem_cluster_form(N, SMC_MIXED, false)) return (size_t)fem_cluster_blocks() * cl::REF_FLOATS;
+    return (size_t)fem_global_blocks(N) * fem_global_slice(N);
+}
+
+cudaError_t fem_eval_large_multi_launch(int N, const FemArgs* groups, const int* offsets, const int* item_group,
+                                        int total, float* scratch, int* counter, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    if (!fem_cluster_form(N, SMC_MIXED, false))
+        return fem_eval_global_multi_launch(N, groups, offsets, item_group, total, scratch, fem_global_blocks(N),
+                                            counter, st);
+    const size_t smem = sizeof(float) * (size_t)cl::SMEM_FLOATS;
+    cudaError_t e = cudaFuncSetAttribute(fem_eval_cluster_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = 2 * std::max(1, std::min(total, fem_cluster_blocks() / 2));
+    fem_eval_cluster_multi<<<grid, cl::T, smem, st>>>(groups, offsets, item_group, total, scratch, counter);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t fem_eval_global_multi_launch(int N, const FemArgs* groups, const int* offsets, const int* item_group,

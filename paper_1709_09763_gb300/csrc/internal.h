@@ -101,6 +101,13 @@ cudaError_t fem_eval_compact_launch(const FemArgs& a, int T, float* ref_scratch,
 int fem_cluster_blocks();
 size_t fem_cluster_ref_floats();
 cudaError_t fem_eval_cluster_launch(const FemArgs& a, float* ref_scratch, int blocks, int* counter, cudaStream_t st);
+// large levels of many problems in the form single solves default to: the two-CTA form on 1/128
+// (mixed, not the flow cell) where a cluster fits, else the device-memory form; scratch floats it
+// needs (sized before any graph capture) and the launch (*counter zero before it)
+bool fem_cluster_form(int N, int precision, bool flow_cell);
+size_t fem_large_multi_scratch(int N);
+cudaError_t fem_eval_large_multi_launch(int N, const FemArgs* groups, const int* offsets, const int* item_group,
+                                        int total, float* scratch, int* counter, cudaStream_t st);
 bool fem_level_supported(int N, int precision);
 
 }  // namespace mls2mc

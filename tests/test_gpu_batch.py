@@ -1,5 +1,5 @@
-"""Many independent problems in one persistent launch per level size (1/128 and 1/256 in their
-device-memory form), captured in a CUDA graph:
+"""Many independent problems in one persistent launch per level size (1/128 in the two-CTA form,
+1/256 in the device-memory form: the forms single solves default to), captured in a CUDA graph:
 every problem's potentials equal its own single-problem evaluation bit for bit (same per-particle
 solve), in eager mode, on the first graph launch and on replays with new particle values."""
 import numpy as np
@@ -30,7 +30,6 @@ def _problems():
         obs = wl.obs_grid(7)
         y = rng.normal(0.02, 0.005, 49)
         hs.append(native.Handle(list(levels), K, obs, y, 0.002, corr_len=lc, precision=prec))
-        hs[-1].test_inv_h = list(levels)
     return hs, rng
 
 
@@ -46,16 +45,9 @@ def test_batch_matches_single_problem_evaluations():
         it = [torch.empty(n, dtype=torch.int32, device="cuda") for n in counts]
 
     def single():
-        # the batched launch runs 1/128 in its device-memory form (block size 1024); the single
-        # handle's default there is the two-CTA form, which rounds its smoother diagonal differently
         out = []
         for h, l, t in zip(hs, levels, th):
-            big = h.test_inv_h[l] == 128
-            if big:
-                h.set_block_size(l, 1024)
             _, phi = h.eval_likelihood(l, t.cpu().numpy(), want_G=False)
-            if big:
-                h.set_block_size(l, 0)
             out.append(phi)
         return out
 
