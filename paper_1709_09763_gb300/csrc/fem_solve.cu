@@ -1027,7 +1027,35 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
     Real* P = F.rhs;
 #define NODE_OF(i) const int jj = (i) / M + ROW0, ii = (i) - (jj - ROW0) * M + 1, n = jj * S + ii
     // colour sweeps run over colour_node positions (every lane busy), the vector updates over the
-    // interior index (coalesced); the red pre-sweep from zero is written where R is updated
+    // interior index (coalesced); the red pre-sweep from zero is written where R is updated.
+    // The fine level lives in device memory, so its loops are latency-bound: each takes two
+    // positions per thread at a time and reads the operands of both before it stores either
+    // result (the compiler cannot move a load above a store to an array it cannot tell apart).
+    // Within a colour sweep or a vector update no position reads what another one writes, so the
+    // results are those of the one-at-a-time loops.
+    constexpr int CPOS = colour_positions<N, FC>();
+    auto sweep2 = [&](int col, auto&& compute, auto&& commit) {
+        for (int k0 = tid; k0 < CPOS; k0 += 2 * T) {
+            int ia, ja, ib, jb;
+            const bool va = colour_node<N, FC>(k0, col, ia, ja);
+            const bool vb = colour_node<N, FC>(k0 + T, col, ib, jb);
+            Real xa = 0, xb = 0;
+            if (va) xa = compute(ia, ja);
+            if (vb) xb = compute(ib, jb);
+            if (va) commit(ia, ja, xa);
+            if (vb) commit(ib, jb, xb);
+        }
+    };
+    auto vec2 = [&](auto&& compute, auto&& commit) {
+        for (int i0 = tid; i0 < NI; i0 += 2 * T) {
+            const int i1 = i0 + T;
+            const bool vb = i1 < NI;
+            Real xa = compute(i0), xb = 0;
+            if (vb) xb = compute(i1);
+            commit(i0, xa);
+            if (vb) commit(i1, xb);
+        }
+    };
     for (int pass = 0; pass < a.max_outer && !converged; ++pass) {
         Real rr0 = 0;
         for (int i = tid; i < NI; i += T) {
@@ -1043,69 +1071,83 @@ __device__ __forceinline__ void solve_particle_mem(const FemArgs& a, const int p
         const Real stop2 = fmax(rtol_in2 * rr0, stop_last);
         Real rz = 0;
         for (int it = 0; it < a.max_inner; ++it) {
-            for (int k = tid; k < colour_positions<N, FC>(); k += T) {   // black pre-sweep
-                int ii, jj;
-                if (!colour_node<N, FC>(k, 1, ii, jj)) continue;
+            sweep2(1, [&](int ii, int jj) {   // black pre-sweep
                 const int n = jj * S + ii, i = (jj - ROW0) * M + ii - 1;
-                F.e[n] = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
-            }
+                return (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
+            }, [&](int ii, int jj, Real v) { F.e[jj * S + ii] = v; });
             __syncthreads();
-            for (int k = tid; k < colour_positions<N, FC>(); k += T) {   // red residuals
-                int ii, jj;
-                if (!colour_node<N, FC>(k, 0, ii, jj)) continue;
-                const int n = jj * S + ii;
-                F.res[n] = offsum<Real, S>(F.aE, F.aN, F.e, n);
-            }
+            sweep2(0, [&](int ii, int jj) {   // red residuals
+                return offsum<Real, S>(F.aE, F.aN, F.e, jj * S + ii);
+            }, [&](int ii, int jj, Real v) { F.res[jj * S + ii] = v; });
             __syncthreads();
             restrict_gather<Real, N / 2, T, FC>(F.res, C1);
             __syncthreads();
             vcycle2<Real, N, N / 2, T, FC>(arena, sarena, dinv);
             Real rz_new = 0;
-            for (int k = tid; k < colour_positions<N, FC>(); k += T) {   // black post-sweep with the prolongation
-                int ii, jj;
-                if (!colour_node<N, FC>(k, 1, ii, jj)) continue;
+            sweep2(1, [&](int ii, int jj) {   // black post-sweep with the prolongation
                 const int n = jj * S + ii, i = (jj - ROW0) * M + ii - 1;
                 const int c = (jj >> 1) * SC + (ii >> 1);
-                const Real z = (R[i] + offsum_prolong<Real, S, SC>(F.aE, F.aN, F.e, C1.e, n, c, (jj & 1) == 0)) * F.iD[n];
-                F.e[n] = z;
-                rz_new += R[i] * z;
-            }
+                return (R[i] + offsum_prolong<Real, S, SC>(F.aE, F.aN, F.e, C1.e, n, c, (jj & 1) == 0)) * F.iD[n];
+            }, [&](int ii, int jj, Real z) {
+                F.e[jj * S + ii] = z;
+                rz_new += R[(jj - ROW0) * M + ii - 1] * z;
+            });
             __syncthreads();
-            for (int k = tid; k < colour_positions<N, FC>(); k += T) {   // red post-sweep
-                int ii, jj;
-                if (!colour_node<N, FC>(k, 0, ii, jj)) continue;
+            sweep2(0, [&](int ii, int jj) {   // red post-sweep
                 const int n = jj * S + ii, i = (jj - ROW0) * M + ii - 1;
-                const Real z = (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
-                F.e[n] = z;
-                rz_new += R[i] * z;
-            }
+                return (R[i] + offsum<Real, S>(F.aE, F.aN, F.e, n)) * F.iD[n];
+            }, [&](int ii, int jj, Real z) {
+                F.e[jj * S + ii] = z;
+                rz_new += R[(jj - ROW0) * M + ii - 1] * z;
+            });
             block_sum<T>(rz_new, red_buf[parity]);
             parity ^= 1;
             const Real beta = (it == 0) ? Real(0) : rz_new / rz;
             rz = rz_new;
-            for (int i = tid; i < NI; i += T) {
+            vec2([&](int i) {
                 NODE_OF(i);
-                P[n] = (it == 0) ? F.e[n] : F.e[n] + beta * P[n];
-            }
+                return (it == 0) ? F.e[n] : F.e[n] + beta * P[n];
+            }, [&](int i, Real v) { NODE_OF(i); P[n] = v; });
             __syncthreads();
             Real pq = 0;
-            for (int i = tid; i < NI; i += T) {
+            vec2([&](int i) {
                 NODE_OF(i);
-                const Real q = stencil_apply<Real, S>(F.aE, F.aN, P, n);
+                return stencil_apply<Real, S>(F.aE, F.aN, P, n);
+            }, [&](int i, Real q) {
+                NODE_OF(i);
                 F.res[n] = q;
                 pq += P[n] * q;
-            }
+            });
             block_sum<T>(pq, red_buf[parity]);
             parity ^= 1;
             const Real alpha = rz / pq;
             Real rr = 0;
-            for (int i = tid; i < NI; i += T) {
-                NODE_OF(i);
-                Dv[i] = fma(alpha, P[n], Dv[i]);
-                const Real rn = fma(-alpha, F.res[n], R[i]);
-                R[i] = rn;
-                rr += rn * rn;
-                if (((ii + jj) & 1) == 0) F.e[n] = rn * F.iD[n];   // red pre-sweep of the next cycle
+            for (int i0 = tid; i0 < NI; i0 += 2 * T) {   // two positions: all loads before the stores
+                const int i1 = i0 + T;
+                const bool vb = i1 < NI;
+                const int ja = i0 / M + ROW0, ia = i0 - (ja - ROW0) * M + 1, na = ja * S + ia;
+                const int jb = vb ? i1 / M + ROW0 : ja, ib = vb ? i1 - (jb - ROW0) * M + 1 : ia, nb = jb * S + ib;
+                const bool ra = ((ia + ja) & 1) == 0, rb = vb && ((ib + jb) & 1) == 0;
+                const Real pa = P[na], da = Dv[i0], qa = F.res[na], sa = R[i0], ga = ra ? F.iD[na] : Real(0);
+                Real pb = 0, db = 0, qb = 0, sb = 0, gb = 0;
+                if (vb) {
+                    pb = P[nb];
+                    db = Dv[i1];
+                    qb = F.res[nb];
+                    sb = R[i1];
+                    gb = rb ? F.iD[nb] : Real(0);
+                }
+                const Real rna = fma(-alpha, qa, sa), rnb = fma(-alpha, qb, sb);
+                Dv[i0] = fma(alpha, pa, da);
+                R[i0] = rna;
+                rr += rna * rna;
+                if (ra) F.e[na] = rna * ga;   // red pre-sweep of the next cycle
+                if (vb) {
+                    Dv[i1] = fma(alpha, pb, db);
+                    R[i1] = rnb;
+                    rr += rnb * rnb;
+                    if (rb) F.e[nb] = rnb * gb;
+                }
             }
             block_sum<T>(rr, red_buf[parity]);
             parity ^= 1;
