@@ -33,8 +33,10 @@
 // registers (every fine node belongs to one thread for the whole solve); the
 // refinement state x, r (double-float pairs) lives in shared memory, or in a per-block
 // slice of device memory in the compact forms (two or four blocks per SM, coarse levels
-// without residual and inverse-diagonal arrays). Levels 1/128 and 1/256 keep their two
-// finest levels in device memory (fem_eval_global).
+// without residual and inverse-diagonal arrays). Level 1/128 is solved by a cluster of two CTAs
+// on two SMs, each keeping half of the fine rows on chip (fem_eval_cluster); levels 1/128 (block
+// size 1024, the flow cell) and 1/256 can keep their two finest levels in device memory
+// (fem_eval_global).
 #include <cuda_runtime.h>
 
 #include <cmath>
