@@ -222,8 +222,9 @@ int smc_sizes(const smc_handle* h, int* K, int* n_obs, int* n_levels, int* J);
  * theta[p], [n[p]][K_p]) on its level level[p], writing phi[p] [n[p]] (device) and, if iters is
  * not NULL, iters[p] [n[p]] (device, as in smc_eval_likelihood_device): the tensor-core KL
  * syntheses of all mixed-precision problems, then one persistent solve launch per level size
- * whose blocks take (problem, particle) work items from a device counter (levels 1/h >= 128 in the
- * form that keeps their fine levels in device memory). With use_graph = 1 the
+ * whose blocks take (problem, particle) work items from a device counter (1/h = 128 in the two-CTA
+ * form, whose clusters take the items, where a cluster fits; 1/h = 256 in the form that keeps its
+ * fine levels in device memory). With use_graph = 1 the
  * sequence is captured into a CUDA graph on `stream` (which must not be the default stream) the
  * first time and replayed afterwards, as long as levels, counts and pointers are unchanged. The
  * call queues work on `stream` and does not wait. Handles must be distinct FEM handles and must
